@@ -1,0 +1,170 @@
+/*
+ * adanns.h -- C ABI of the GB300 (sm_103a) AdANNS search library.
+ *
+ * AdANNS-IVF (Sec. 4.1, Algorithm 1, Table "formula" AdANNS-IVF row): queries
+ * are mapped to k-means centroids with the first d_c coordinates of a nested
+ * (Matryoshka) embedding, the n_p nearest inverted lists are scanned with the
+ * first d_s coordinates, and a fused top-k returns ids and distances.
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments are DEVICE pointers into memory the caller owns,
+ *    unless a parameter says otherwise.  Row-major, densely packed, FP32
+ *    unless stated.  Every call is asynchronous on `cuda_stream` (a
+ *    cudaStream_t; NULL = the legacy default stream) unless it says it
+ *    synchronises.  Outputs are valid once the stream reaches the call.
+ *  - Distances are squared L2.  With ADANNS_METRIC_L2_PREFIXNORM an m-prefix
+ *    used as a representation is L2-normalised at its own length,
+ *    P_m(v) = v[0:m] / ||v[0:m]||, P_m(0) = 0 (Sec. 3 "Matryoshka
+ *    Representations": the first m coordinates form an m-dim representation),
+ *    and dist_m(q, x) = ||P_m(q) - P_m(x)||^2.  ADANNS_METRIC_L2 uses raw
+ *    prefixes.
+ *  - Ties among equal distances are ordered by ascending database id (list
+ *    id for the cluster mapping).  Fewer than k candidates are padded with
+ *    id -1 and distance +inf.
+ *  - Return value: ADANNS_OK (0) or a negative ADANNS_ERR_* code; the message
+ *    is available from adanns_last_error() on the calling thread.  No entry
+ *    point aborts or traps.  Input values must be finite.
+ *  - Prefix lengths (d_c, d_s) must belong to the MR granularity set
+ *    G = {8,16,32,48,64,96,128,192,256,384,512,768,1024,2048} and not exceed
+ *    the stored dimension (the paper's nested sizes, Sec. 3 "Encoders").
+ */
+#ifndef ADANNS_H
+#define ADANNS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADANNS_OK 0
+#define ADANNS_ERR_ARG (-1)     /* invalid argument (null pointer, size out of range) */
+#define ADANNS_ERR_DIM (-2)     /* prefix length not in G, or beyond the index */
+#define ADANNS_ERR_OOM (-3)     /* device allocation failed */
+#define ADANNS_ERR_CUDA (-4)    /* a CUDA runtime call or launch failed */
+#define ADANNS_ERR_TIMEOUT (-5) /* a bounded device wait gave up */
+#define ADANNS_ERR_STATE (-6)   /* the index lacks the requested storage / OPQ data */
+
+#define ADANNS_METRIC_L2 0
+#define ADANNS_METRIC_L2_PREFIXNORM 1
+
+/* storage tiers of the database vectors (bit mask for builders) */
+#define ADANNS_STORE_F32 1
+
+typedef struct adanns_index adanns_index; /* opaque; device memory owned by the library */
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next call on the same thread. */
+const char *adanns_last_error(void);
+
+/* ABI version of this header (major * 100 + minor). */
+int adanns_version(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded, on
+ * all threads (a diagnostic counter; host-side, no device access). */
+int64_t adanns_launch_count(void);
+
+/*
+ * Stage timing (diagnostics).  adanns_profile_enable(1) starts recording a
+ * CUDA event pair, on the call's stream, around each stage of every search
+ * (0 query prep, 1 cluster mapping, 2 probe inversion, 3 list scan, 4 merge,
+ * further ids for later stages); enabling or disabling discards the records.
+ * adanns_profile_read synchronises on the recorded events and fills host
+ * arrays ms[s] (summed milliseconds) and count[s] (records) for s < nstage.
+ */
+int adanns_profile_enable(int on);
+int adanns_profile_read(double *ms, int64_t *count, int nstage);
+
+/*
+ * Build an AdANNS-IVF index (Algorithm 1 adannsConstruction; Sec. 3 "IVF":
+ * Lloyd k-means coarse quantiser and inverted lists, clustering on the d_c
+ * prefix as in Sec. 4.1).
+ *   db        N x d FP32, device, caller-owned; copied (re-laid out) into the
+ *             index, so it may be freed after the call returns.
+ *   d_c       clustering prefix (in G, <= d); nlist clusters, 1 <= nlist <= train_n.
+ *   niter     Lloyd iterations (>= 0).
+ *   train_n   training sample size, nlist <= train_n <= N.  The sample is the
+ *             first train_n entries of a splitmix64(seed) Fisher-Yates shuffle
+ *             of [0, N); the initial centroids are the sample rows at the first
+ *             nlist entries of a splitmix64(seed + 1) shuffle of [0, train_n).
+ *   metric    ADANNS_METRIC_*; storage_mask must include ADANNS_STORE_F32.
+ *   objective optional HOST pointer to niter doubles: the k-means objective
+ *             (sum of squared distances) at each iteration's assignment.
+ * Ties in the assignment go to the smallest cluster index; an empty cluster
+ * keeps its previous centroid.  Centroid sums are accumulated in FP64.
+ * Synchronises `cuda_stream` (the objective is read back every iteration).
+ * On success *out owns the index; release it with adanns_index_free.
+ */
+int adanns_build_ivf(const float *db, int64_t N, int d, int d_c, int nlist, int niter,
+                     int64_t train_n, uint64_t seed, int metric, int storage_mask,
+                     double *objective, void *cuda_stream, adanns_index **out);
+
+/*
+ * Create an index from given centroids and list assignment (import path; the
+ * same layout adanns_build_ivf produces).
+ *   db         N x d FP32 (device), centroids nlist x d_c FP32 (device),
+ *   assign     N int32 in [0, nlist) (device).
+ * Members of each list are ordered by ascending id.  Synchronises the stream.
+ */
+int adanns_index_create(const float *db, int64_t N, int d, const float *centroids, int nlist,
+                        int d_c, const int32_t *assign, int metric, int storage_mask,
+                        void *cuda_stream, adanns_index **out);
+
+/* Sizes of an index (any pointer may be NULL). Host outputs. */
+int adanns_index_info(const adanns_index *idx, int64_t *N, int *d, int *d_c, int *nlist,
+                      int *metric);
+
+/* Copy the CSR lists to device buffers: list_off int64 [nlist + 1] (member
+ * offsets), list_ids int32 [N] (database ids, ascending inside each list). */
+int adanns_index_get_lists(const adanns_index *idx, int64_t *list_off, int32_t *list_ids,
+                           void *cuda_stream);
+
+/* Copy the FP32 centroids (nlist x d_c) to a device buffer. */
+int adanns_index_get_centroids(const adanns_index *idx, float *centroids, void *cuda_stream);
+
+/* Release an index (NULL is ignored).  Waits for the device to finish using it. */
+void adanns_index_free(adanns_index *idx);
+
+/*
+ * Lloyd assignment step (Sec. 3 "IVF"): for each of n points (rows of `ld`
+ * floats, first `dim` used, prefix-normalised at dim under
+ * ADANNS_METRIC_L2_PREFIXNORM) the nearest of nc centroids (nc x dim FP32),
+ * ties to the smallest index.  out_assign int32 [n]; out_dist FP32 [n]
+ * (squared distance, may be NULL).  dim in G, 1 <= nc.
+ */
+int adanns_kmeans_assign(const float *points, int64_t n, int ld, int dim, int metric,
+                         const float *centroids, int nc, int32_t *out_assign, float *out_dist,
+                         void *cuda_stream);
+
+/*
+ * Lloyd update step (Sec. 3 "IVF"): centroid h becomes the mean of the
+ * (normalised, as above) points assigned to it, summed in FP64 and rounded
+ * to FP32; a cluster with no point keeps its value.  centroids is read and
+ * overwritten (nc x dim FP32).
+ */
+int adanns_kmeans_update(const float *points, int64_t n, int ld, int dim, int metric,
+                         const int32_t *assign, int nc, float *centroids, void *cuda_stream);
+
+/*
+ * AdANNS-IVF search (Algorithm 1 adannsInference; Table "formula"
+ * AdANNS-IVF row):
+ *   h(q): the nprobe nearest centroids to P_dc(q) by (distance, list id);
+ *   result: the k nearest members of those lists to q by dist_ds, then id.
+ *   queries  B x d FP32 (device); d_c must equal the index's d_c; d_s in G,
+ *            d_s <= d; 1 <= nprobe <= nlist; 1 <= k <= 1024.
+ *   storage  ADANNS_STORE_F32 (the exact FP32 scan).
+ *   rerank_k must be 0 for ADANNS_STORE_F32.
+ *   out_ids  int64 [B x k], out_dist FP32 [B x k] (device, caller-owned).
+ *   out_probes optional int32 [B x nprobe]: the probed lists, nearest first.
+ * Scratch memory is taken from the CUDA stream-ordered allocator and returned
+ * before the call's work completes; B is processed in slices so scratch
+ * stays bounded (about 2 GiB).
+ */
+int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                      int d_s, int nprobe, int k, int storage, int rerank_k, int64_t *out_ids,
+                      float *out_dist, int32_t *out_probes, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADANNS_H */

@@ -1,0 +1,218 @@
+"""Python binding of the AdANNS GB300 library (libadanns.so, C ABI in include/adanns.h).
+
+Argument marshalling only: tensors must already be CUDA tensors of the stated
+dtype; every step of every operation runs in the library's CUDA kernels on
+the current torch stream.  There is no CPU path: if the compiled library is
+missing, importing this module still works but every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+METRIC_L2 = 0
+METRIC_L2_PREFIXNORM = 1
+STORE_F32 = 1
+GRANULARITIES = (8, 16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 2048)
+
+ERRORS = {-1: "ARG", -2: "DIM", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "STATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadanns.so")
+_lib = None
+
+
+class AdannsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"adanns error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH} missing); run "
+                               "paper_2305_19435_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
+        L.adanns_last_error.restype = ctypes.c_char_p
+        L.adanns_version.restype = i32
+        L.adanns_launch_count.restype = i64
+        L.adanns_profile_enable.argtypes = [i32]
+        L.adanns_profile_read.argtypes = [P, P, i32]
+        L.adanns_build_ivf.argtypes = [P, i64, i32, i32, i32, i32, i64, u64, i32, i32, P, P, P]
+        L.adanns_index_create.argtypes = [P, i64, i32, P, i32, i32, P, i32, i32, P, P]
+        L.adanns_index_info.argtypes = [P, P, P, P, P, P]
+        L.adanns_index_get_lists.argtypes = [P, P, P, P]
+        L.adanns_index_get_centroids.argtypes = [P, P, P]
+        L.adanns_index_free.argtypes = [P]
+        L.adanns_index_free.restype = None
+        L.adanns_kmeans_assign.argtypes = [P, i64, i32, i32, i32, P, i32, P, P, P]
+        L.adanns_kmeans_update.argtypes = [P, i64, i32, i32, i32, P, i32, P, P]
+        L.adanns_search_ivf.argtypes = [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, P, P]
+        _lib = L
+    return _lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since load (host-side counter)."""
+    return int(lib().adanns_launch_count())
+
+
+STAGES = ("prep", "coarse", "invert", "scan", "merge")
+
+
+def profile_enable(on: bool = True):
+    """Start (or stop) recording per-stage CUDA-event timings; clears records."""
+    _check(lib().adanns_profile_enable(int(on)))
+
+
+def profile_read(nstage: int = 16) -> dict:
+    """{stage: (total ms, records)} for the recorded stages (synchronises)."""
+    ms = (ctypes.c_double * nstage)()
+    cnt = (ctypes.c_int64 * nstage)()
+    _check(lib().adanns_profile_read(ms, cnt, nstage))
+    names = list(STAGES) + [f"stage{i}" for i in range(len(STAGES), nstage)]
+    return {names[i]: (ms[i], cnt[i]) for i in range(nstage) if cnt[i]}
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise AdannsError(rc, lib().adanns_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype, name: str, ndim: int | None = None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dims")
+
+
+class Index:
+    """An index owned by the library (device memory), freed by `free()` or GC."""
+
+    def __init__(self, handle: ctypes.c_void_p, objective=None):
+        self._h = handle
+        self.objective = objective
+        N, d, dc, nl, m = (ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(),
+                           ctypes.c_int())
+        _check(lib().adanns_index_info(self._h, ctypes.byref(N), ctypes.byref(d), ctypes.byref(dc),
+                                       ctypes.byref(nl), ctypes.byref(m)))
+        self.N, self.d, self.d_c, self.nlist, self.metric = N.value, d.value, dc.value, nl.value, m.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("index already freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None and _lib is not None:
+            _lib.adanns_index_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def lists(self):
+        off = torch.empty(self.nlist + 1, dtype=torch.int64, device="cuda")
+        ids = torch.empty(self.N, dtype=torch.int32, device="cuda")
+        _check(lib().adanns_index_get_lists(self.handle, _ptr(off), _ptr(ids), _stream()))
+        return off, ids
+
+    def centroids(self):
+        c = torch.empty(self.nlist, self.d_c, dtype=torch.float32, device="cuda")
+        _check(lib().adanns_index_get_centroids(self.handle, _ptr(c), _stream()))
+        return c
+
+
+def build_ivf(db: torch.Tensor, d_c: int, nlist: int, niter: int, train_n: int, seed: int,
+              metric: int = METRIC_L2_PREFIXNORM, storage: int = STORE_F32) -> Index:
+    """AdANNS-IVF construction (k-means at d_c + CSR prefix-major lists)."""
+    _need(db, torch.float32, "db", 2)
+    obj = (ctypes.c_double * max(niter, 1))()
+    h = ctypes.c_void_p()
+    _check(lib().adanns_build_ivf(_ptr(db), db.shape[0], db.shape[1], d_c, nlist, niter, train_n,
+                                  seed, metric, storage, obj, _stream(), ctypes.byref(h)))
+    return Index(h, objective=list(obj)[:niter])
+
+
+def index_create(db: torch.Tensor, centroids: torch.Tensor, assign: torch.Tensor,
+                 metric: int = METRIC_L2_PREFIXNORM, storage: int = STORE_F32) -> Index:
+    """Index from given FP32 centroids [nlist, d_c] and list assignment int32 [N]."""
+    _need(db, torch.float32, "db", 2)
+    _need(centroids, torch.float32, "centroids", 2)
+    _need(assign, torch.int32, "assign", 1)
+    h = ctypes.c_void_p()
+    _check(lib().adanns_index_create(_ptr(db), db.shape[0], db.shape[1], _ptr(centroids),
+                                     centroids.shape[0], centroids.shape[1], _ptr(assign), metric,
+                                     storage, _stream(), ctypes.byref(h)))
+    return Index(h)
+
+
+def kmeans_assign(points: torch.Tensor, centroids: torch.Tensor, dim: int,
+                  metric: int = METRIC_L2_PREFIXNORM):
+    """Nearest centroid of each point on the `dim` prefix -> (assign int32, dist f32)."""
+    _need(points, torch.float32, "points", 2)
+    _need(centroids, torch.float32, "centroids", 2)
+    n = points.shape[0]
+    a = torch.empty(n, dtype=torch.int32, device=points.device)
+    dd = torch.empty(n, dtype=torch.float32, device=points.device)
+    _check(lib().adanns_kmeans_assign(_ptr(points), n, points.shape[1], dim, metric,
+                                      _ptr(centroids), centroids.shape[0], _ptr(a), _ptr(dd),
+                                      _stream()))
+    return a, dd
+
+
+def kmeans_update(points: torch.Tensor, assign: torch.Tensor, centroids: torch.Tensor, dim: int,
+                  metric: int = METRIC_L2_PREFIXNORM) -> torch.Tensor:
+    """One Lloyd update in place on `centroids` [nc, dim]; returns it."""
+    _need(points, torch.float32, "points", 2)
+    _need(assign, torch.int32, "assign", 1)
+    _need(centroids, torch.float32, "centroids", 2)
+    _check(lib().adanns_kmeans_update(_ptr(points), points.shape[0], points.shape[1], dim, metric,
+                                      _ptr(assign), centroids.shape[0], _ptr(centroids), _stream()))
+    return centroids
+
+
+def search_ivf(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: int, k: int,
+               storage: int = STORE_F32, rerank_k: int = 0, return_probes: bool = False,
+               out: tuple | None = None):
+    """AdANNS-IVF search -> (ids int64 [B,k], dist f32 [B,k][, probes int32 [B,nprobe]])."""
+    _need(queries, torch.float32, "queries", 2)
+    if queries.shape[1] != index.d:
+        raise ValueError(f"queries must have {index.d} columns")
+    B = queries.shape[0]
+    if out is None:
+        ids = torch.empty(B, k, dtype=torch.int64, device=queries.device)
+        dist = torch.empty(B, k, dtype=torch.float32, device=queries.device)
+    else:
+        ids, dist = out
+    probes = torch.empty(B, nprobe, dtype=torch.int32, device=queries.device) if return_probes else None
+    _check(lib().adanns_search_ivf(index.handle, _ptr(queries), B, d_c, d_s, nprobe, k, storage,
+                                   rerank_k, _ptr(ids), _ptr(dist), _ptr(probes), _stream()))
+    return (ids, dist, probes) if return_probes else (ids, dist)

@@ -1,0 +1,462 @@
+// C ABI entry points: argument checks, scratch management and the launch
+// sequence of each operation.  All arithmetic runs in the kernels.
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace adn {
+const char *last_error();
+
+namespace {
+
+cudaStream_t S(void *p) { return (cudaStream_t)p; }
+
+// splitmix64 (Steele, Lea & Flood 2014) and a partial Fisher-Yates shuffle:
+// the first `take` entries of a shuffle of [0, n), j = i + next() mod (n - i).
+uint64_t splitmix64(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+std::vector<int64_t> seeded_sample(uint64_t seed, int64_t n, int64_t take) {
+  std::vector<int64_t> a((size_t)n);
+  for (int64_t i = 0; i < n; ++i) a[(size_t)i] = i;
+  uint64_t st = seed;
+  for (int64_t i = 0; i < take; ++i) {
+    const int64_t j = i + (int64_t)(splitmix64(st) % (uint64_t)(n - i));
+    std::swap(a[(size_t)i], a[(size_t)j]);
+  }
+  a.resize((size_t)take);
+  return a;
+}
+
+template <class T>
+int dmalloc(T **p, size_t count) {
+  size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ADANNS_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  return ADANNS_OK;
+}
+
+void free_index(adanns_index *x) {
+  if (!x) return;
+  cudaFree(x->centroids);
+  cudaFree(x->cent_pm);
+  cudaFree(x->cent_off);
+  cudaFree(x->list_off);
+  cudaFree(x->list_ids);
+  cudaFree(x->xpm);
+  cudaFree(x->invn);
+  delete[] x->h_list_off;
+  delete x;
+}
+
+int check_metric(int metric) {
+  if (metric != ADANNS_METRIC_L2 && metric != ADANNS_METRIC_L2_PREFIXNORM)
+    return fail(ADANNS_ERR_ARG, "unknown metric");
+  return ADANNS_OK;
+}
+
+int check_gran(int m, int limit, const char *what) {
+  if (gran_index(m) < 0)
+    return fail(ADANNS_ERR_DIM, std::string(what) + " = " + std::to_string(m) +
+                                    " is not an MR granularity (8,16,32,48,64,96,...,2048)");
+  if (m > limit)
+    return fail(ADANNS_ERR_DIM, std::string(what) + " = " + std::to_string(m) +
+                                    " exceeds the available " + std::to_string(limit));
+  return ADANNS_OK;
+}
+
+// prefix-major copy of an nc x dim centroid table as one list of nc members
+int centroids_pm(const float *cent, int nc, int dim, float *out, cudaStream_t st) {
+  return launch_prefix_major(cent, dim, dim, pad16(dim), nullptr, nullptr, nullptr, nc, out, st);
+}
+
+int scan_grid_default() { return 0; }
+
+// top-1 sweep of `n` prepared points (rows of ldq) against a prefix-major
+// centroid table; keys[i] = (distance, centroid)
+int top1_sweep(const float *pts, int64_t n, int ldq, const float *cent_pm, const int64_t *cent_off,
+               int nc, int dim, uint64_t *keys, int *counter, cudaStream_t st) {
+  ScanArgs a{};
+  a.xpm = cent_pm;
+  a.d_pad = pad16(dim);
+  a.dims = dim;
+  a.list_off = cent_off;
+  a.list_ids = nullptr;
+  a.mscale = nullptr;
+  a.qn = pts;
+  a.ldq = ldq;
+  a.nq = (int)n;
+  a.counter = counter;
+  a.k = 1;
+  a.out_keys = keys;
+  a.grid = scan_grid_default();
+  (void)nc;
+  ADN_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+  return launch_scan_f32(a, st);
+}
+
+int make_cent_off(int64_t **off, int nc, cudaStream_t st) {
+  int rc = dmalloc(off, 2);
+  if (rc) return rc;
+  int64_t h[2] = {0, (int64_t)nc};
+  ADN_CUDA(cudaMemcpyAsync(*off, h, sizeof(h), cudaMemcpyHostToDevice, st));
+  return ADANNS_OK;
+}
+
+constexpr int64_t SWEEP_ROWS = 1 << 20;  // points per assignment slice
+
+// assign all N rows of db (first d_c coordinates, normalised per metric) to
+// the nearest of nc centroids (prefix-major table)
+int assign_all(const float *db, int64_t N, int ld, int d_c, int metric, const float *cent_pm,
+               const int64_t *cent_off, int nc, int32_t *assign, float *dist, cudaStream_t st) {
+  Scratch s(st);
+  const int dcp = pad16(d_c);
+  const int64_t rows = std::min<int64_t>(N, SWEEP_ROWS);
+  float *pn;
+  uint64_t *keys;
+  int *counter;
+  int rc;
+  if ((rc = s.get(&pn, (size_t)rows * dcp)) || (rc = s.get(&keys, (size_t)rows)) ||
+      (rc = s.get(&counter, 1)))
+    return rc;
+  for (int64_t b0 = 0; b0 < N; b0 += rows) {
+    const int64_t n = std::min(rows, N - b0);
+    if ((rc = launch_gather_normalize(db + b0 * ld, n, ld, nullptr, d_c, metric, pn, dcp, st)))
+      return rc;
+    if ((rc = top1_sweep(pn, n, dcp, cent_pm, cent_off, nc, d_c, keys, counter, st))) return rc;
+    if ((rc = launch_keys_to_result(keys, n, 1, nullptr, assign + b0, dist ? dist + b0 : nullptr,
+                                    st)))
+      return rc;
+  }
+  return ADANNS_OK;
+}
+
+int make_index(const float *db, int64_t N, int d, const float *centroids, int nlist, int d_c,
+               const int32_t *assign, int metric, int storage, cudaStream_t st,
+               adanns_index **out) {
+  adanns_index *x = new adanns_index();
+  x->N = N;
+  x->d = d;
+  x->d_pad = pad16(d);
+  x->d_c = d_c;
+  x->dc_pad = pad16(d_c);
+  x->nlist = nlist;
+  x->metric = metric;
+  x->storage = storage;
+  int rc;
+  x->ng = 0;
+  for (int g = 0; g < NGRAN; ++g)
+    if (kGran[g] <= d) x->ng = g + 1;
+  if ((rc = dmalloc(&x->centroids, (size_t)nlist * d_c)) ||
+      (rc = dmalloc(&x->cent_pm, (size_t)nlist * x->dc_pad)) ||
+      (rc = make_cent_off(&x->cent_off, nlist, st)) ||
+      (rc = dmalloc(&x->list_off, (size_t)nlist + 1)) || (rc = dmalloc(&x->list_ids, (size_t)N)) ||
+      (rc = dmalloc(&x->xpm, (size_t)N * x->d_pad)) ||
+      (rc = dmalloc(&x->invn, (size_t)std::max(x->ng, 1) * N))) {
+    free_index(x);
+    return rc;
+  }
+  auto bail = [&](int code) {
+    cudaStreamSynchronize(st);
+    free_index(x);
+    return code;
+  };
+  if (cudaMemcpyAsync(x->centroids, centroids, sizeof(float) * nlist * d_c,
+                      cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "copy centroids"));
+  if ((rc = centroids_pm(x->centroids, nlist, d_c, x->cent_pm, st))) return bail(rc);
+  if ((rc = build_csr(assign, N, nlist, x->list_off, x->list_ids, st))) return bail(rc);
+  if ((rc = launch_prefix_major(db, d, d, x->d_pad, x->list_off, x->list_ids, assign, N, x->xpm,
+                                st)))
+    return bail(rc);
+  if ((rc = launch_inv_norms(db, d, d, x->list_ids, N, metric, x->invn, x->ng, st)))
+    return bail(rc);
+  x->h_list_off = new int64_t[nlist + 1];
+  if (cudaMemcpyAsync(x->h_list_off, x->list_off, sizeof(int64_t) * (nlist + 1),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "copy list offsets"));
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "index build"));
+  int64_t mx = 0;
+  for (int l = 0; l < nlist; ++l) mx = std::max(mx, x->h_list_off[l + 1] - x->h_list_off[l]);
+  x->max_list = (int)mx;
+  *out = x;
+  return ADANNS_OK;
+}
+
+}  // namespace
+}  // namespace adn
+
+using namespace adn;
+
+extern "C" {
+
+const char *adanns_last_error(void) { return adn::last_error(); }
+
+int adanns_version(void) { return 100; }
+
+int64_t adanns_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int adanns_index_create(const float *db, int64_t N, int d, const float *centroids, int nlist,
+                        int d_c, const int32_t *assign, int metric, int storage_mask,
+                        void *cuda_stream, adanns_index **out) {
+  if (!out) return fail(ADANNS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!db || !centroids || !assign) return fail(ADANNS_ERR_ARG, "NULL input");
+  if (N < 1 || N > INT32_MAX || d < 1 || nlist < 1 || nlist > 32768)
+    return fail(ADANNS_ERR_ARG, "bad sizes");
+  int rc;
+  if ((rc = check_metric(metric)) || (rc = check_gran(d_c, d, "d_c"))) return rc;
+  if (!(storage_mask & ADANNS_STORE_F32)) return fail(ADANNS_ERR_ARG, "storage must include F32");
+  if ((rc = check_assignment(assign, N, nlist, S(cuda_stream)))) return rc;
+  return make_index(db, N, d, centroids, nlist, d_c, assign, metric, storage_mask, S(cuda_stream),
+                    out);
+}
+
+int adanns_build_ivf(const float *db, int64_t N, int d, int d_c, int nlist, int niter,
+                     int64_t train_n, uint64_t seed, int metric, int storage_mask,
+                     double *objective, void *cuda_stream, adanns_index **out) {
+  if (!out) return fail(ADANNS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!db) return fail(ADANNS_ERR_ARG, "db is NULL");
+  if (N < 1 || N > INT32_MAX || d < 1 || nlist < 1 || nlist > 32768 || niter < 0)
+    return fail(ADANNS_ERR_ARG, "bad sizes");
+  if (train_n < nlist || train_n > N) return fail(ADANNS_ERR_ARG, "need nlist <= train_n <= N");
+  int rc;
+  if ((rc = check_metric(metric)) || (rc = check_gran(d_c, d, "d_c"))) return rc;
+  if (!(storage_mask & ADANNS_STORE_F32)) return fail(ADANNS_ERR_ARG, "storage must include F32");
+  cudaStream_t st = S(cuda_stream);
+  const int dcp = pad16(d_c);
+
+  // training sample and Forgy initialisation (seeded, as the oracle defines them)
+  std::vector<int64_t> S1 = seeded_sample(seed, N, train_n);
+  std::vector<int64_t> S2 = seeded_sample(seed + 1, train_n, nlist);
+  Scratch s(st);
+  int64_t *d_s1, *d_s2, *cent_off;
+  float *tn, *cent, *cent_pm, *kd;
+  uint64_t *keys;
+  int32_t *asg, *counts, *asg_all;
+  double *sums, *obj;
+  int *counter;
+  if ((rc = s.get(&d_s1, train_n)) || (rc = s.get(&d_s2, nlist)) ||
+      (rc = s.get(&tn, (size_t)train_n * dcp)) || (rc = s.get(&cent, (size_t)nlist * d_c)) ||
+      (rc = s.get(&cent_pm, (size_t)nlist * dcp)) || (rc = s.get(&keys, train_n)) ||
+      (rc = s.get(&asg, train_n)) || (rc = s.get(&counts, nlist)) ||
+      (rc = s.get(&sums, (size_t)nlist * d_c)) || (rc = s.get(&obj, 1)) ||
+      (rc = s.get(&counter, 1)) || (rc = s.get(&cent_off, 2)) || (rc = s.get(&asg_all, N)) ||
+      (rc = s.get(&kd, 1)))
+    return rc;
+  ADN_CUDA(cudaMemcpyAsync(d_s1, S1.data(), sizeof(int64_t) * train_n, cudaMemcpyHostToDevice, st));
+  ADN_CUDA(cudaMemcpyAsync(d_s2, S2.data(), sizeof(int64_t) * nlist, cudaMemcpyHostToDevice, st));
+  const int64_t h_off[2] = {0, (int64_t)nlist};
+  ADN_CUDA(cudaMemcpyAsync(cent_off, h_off, sizeof(h_off), cudaMemcpyHostToDevice, st));
+  if ((rc = launch_gather_normalize(db, train_n, d, d_s1, d_c, metric, tn, dcp, st))) return rc;
+  if ((rc = launch_gather_normalize(tn, nlist, dcp, d_s2, d_c, ADANNS_METRIC_L2, cent, d_c, st)))
+    return rc;
+  for (int it = 0; it < niter; ++it) {
+    if ((rc = centroids_pm(cent, nlist, d_c, cent_pm, st))) return rc;
+    if ((rc = top1_sweep(tn, train_n, dcp, cent_pm, cent_off, nlist, d_c, keys, counter, st)))
+      return rc;
+    if ((rc = launch_sum_keys(keys, train_n, obj, st))) return rc;
+    if ((rc = launch_keys_to_result(keys, train_n, 1, nullptr, asg, nullptr, st))) return rc;
+    if ((rc = launch_kmeans_update(tn, train_n, dcp, d_c, asg, nlist, sums, counts, cent, st)))
+      return rc;
+    double J = 0.0;
+    ADN_CUDA(cudaMemcpyAsync(&J, obj, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ADN_CUDA(cudaStreamSynchronize(st));
+    if (objective) objective[it] = J;
+  }
+  if ((rc = centroids_pm(cent, nlist, d_c, cent_pm, st))) return rc;
+  if ((rc = assign_all(db, N, d, d_c, metric, cent_pm, cent_off, nlist, asg_all, nullptr, st)))
+    return rc;
+  return make_index(db, N, d, cent, nlist, d_c, asg_all, metric, storage_mask, st, out);
+}
+
+int adanns_index_info(const adanns_index *idx, int64_t *N, int *d, int *d_c, int *nlist,
+                      int *metric) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  if (N) *N = idx->N;
+  if (d) *d = idx->d;
+  if (d_c) *d_c = idx->d_c;
+  if (nlist) *nlist = idx->nlist;
+  if (metric) *metric = idx->metric;
+  return ADANNS_OK;
+}
+
+int adanns_index_get_lists(const adanns_index *idx, int64_t *list_off, int32_t *list_ids,
+                           void *cuda_stream) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  cudaStream_t st = S(cuda_stream);
+  if (list_off)
+    ADN_CUDA(cudaMemcpyAsync(list_off, idx->list_off, sizeof(int64_t) * (idx->nlist + 1),
+                             cudaMemcpyDeviceToDevice, st));
+  if (list_ids)
+    ADN_CUDA(cudaMemcpyAsync(list_ids, idx->list_ids, sizeof(int32_t) * idx->N,
+                             cudaMemcpyDeviceToDevice, st));
+  return ADANNS_OK;
+}
+
+int adanns_index_get_centroids(const adanns_index *idx, float *centroids, void *cuda_stream) {
+  if (!idx || !centroids) return fail(ADANNS_ERR_ARG, "NULL argument");
+  ADN_CUDA(cudaMemcpyAsync(centroids, idx->centroids, sizeof(float) * idx->nlist * idx->d_c,
+                           cudaMemcpyDeviceToDevice, S(cuda_stream)));
+  return ADANNS_OK;
+}
+
+void adanns_index_free(adanns_index *idx) {
+  if (!idx) return;
+  cudaDeviceSynchronize();
+  free_index(idx);
+}
+
+int adanns_kmeans_assign(const float *points, int64_t n, int ld, int dim, int metric,
+                         const float *centroids, int nc, int32_t *out_assign, float *out_dist,
+                         void *cuda_stream) {
+  if (!points || !centroids || !out_assign) return fail(ADANNS_ERR_ARG, "NULL argument");
+  if (n < 0 || n > INT32_MAX || nc < 1 || ld < dim) return fail(ADANNS_ERR_ARG, "bad sizes");
+  int rc;
+  if ((rc = check_metric(metric)) || (rc = check_gran(dim, ld, "dim"))) return rc;
+  if (n == 0) return ADANNS_OK;
+  cudaStream_t st = S(cuda_stream);
+  Scratch s(st);
+  float *cpm;
+  int64_t *coff;
+  if ((rc = s.get(&cpm, (size_t)nc * pad16(dim))) || (rc = s.get(&coff, 2))) return rc;
+  const int64_t h_off[2] = {0, (int64_t)nc};
+  ADN_CUDA(cudaMemcpyAsync(coff, h_off, sizeof(h_off), cudaMemcpyHostToDevice, st));
+  if ((rc = centroids_pm(centroids, nc, dim, cpm, st))) return rc;
+  return assign_all(points, n, ld, dim, metric, cpm, coff, nc, out_assign, out_dist, st);
+}
+
+int adanns_kmeans_update(const float *points, int64_t n, int ld, int dim, int metric,
+                         const int32_t *assign, int nc, float *centroids, void *cuda_stream) {
+  if (!points || !assign || !centroids) return fail(ADANNS_ERR_ARG, "NULL argument");
+  if (n < 0 || n > INT32_MAX || nc < 1 || ld < dim) return fail(ADANNS_ERR_ARG, "bad sizes");
+  int rc;
+  if ((rc = check_metric(metric)) || (rc = check_gran(dim, ld, "dim"))) return rc;
+  cudaStream_t st = S(cuda_stream);
+  Scratch s(st);
+  float *pn;
+  double *sums;
+  int32_t *counts;
+  if ((rc = s.get(&pn, (size_t)std::max<int64_t>(n, 1) * dim)) ||
+      (rc = s.get(&sums, (size_t)nc * dim)) || (rc = s.get(&counts, nc)))
+    return rc;
+  if ((rc = launch_gather_normalize(points, n, ld, nullptr, dim, metric, pn, dim, st))) return rc;
+  return launch_kmeans_update(pn, n, dim, dim, assign, nc, sums, counts, centroids, st);
+}
+
+int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                      int d_s, int nprobe, int k, int storage, int rerank_k, int64_t *out_ids,
+                      float *out_dist, int32_t *out_probes, void *cuda_stream) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  if (B < 0 || B > INT32_MAX) return fail(ADANNS_ERR_ARG, "bad batch size");
+  if (B > 0 && (!queries || !out_ids || !out_dist)) return fail(ADANNS_ERR_ARG, "NULL argument");
+  if (d_c != idx->d_c)
+    return fail(ADANNS_ERR_DIM, "d_c must equal the index's clustering prefix " +
+                                    std::to_string(idx->d_c));
+  int rc;
+  if ((rc = check_gran(d_s, idx->d, "d_s"))) return rc;
+  if (nprobe < 1 || nprobe > idx->nlist) return fail(ADANNS_ERR_ARG, "need 1 <= nprobe <= nlist");
+  if (k < 1 || k > 1024) return fail(ADANNS_ERR_ARG, "need 1 <= k <= 1024");
+  if (storage != ADANNS_STORE_F32) return fail(ADANNS_ERR_STATE, "storage tier not available");
+  if (rerank_k != 0) return fail(ADANNS_ERR_ARG, "rerank_k must be 0 for the FP32 scan");
+  if (B == 0) return ADANNS_OK;
+  cudaStream_t st = S(cuda_stream);
+  const int nlist = idx->nlist;
+  const int dcp = pad16(d_c), dsp = pad16(d_s);
+  const int qt = scan_query_tile(k);
+  // slice the batch so that the per-(query, probe) partial results stay ~2 GiB
+  const int64_t per_q = (int64_t)nprobe * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
+  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (2ll << 30) / per_q));
+  const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
+  Scratch s(st);
+  float *qc, *qs;
+  uint64_t *ckeys, *pkeys;
+  int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
+  int *ntiles, *counter;
+  if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
+      (rc = s.get(&ckeys, (size_t)Bc * nprobe)) || (rc = s.get(&pkeys, (size_t)Bc * nprobe * k)) ||
+      (rc = s.get(&lcnt, nlist)) || (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) ||
+      (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
+      (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) ||
+      (rc = s.get(&counter, 2)))
+    return rc;
+  const float *mscale = idx->metric == ADANNS_METRIC_L2_PREFIXNORM
+                            ? idx->invn + (int64_t)gran_index(d_s) * idx->N
+                            : nullptr;
+  for (int64_t b0 = 0; b0 < B; b0 += Bc) {
+    const int64_t nb = std::min(Bc, B - b0);
+    {
+      StageTimer t(ST_PREP, st);
+      if ((rc = launch_prep_queries(queries + b0 * idx->d, nb, idx->d, d_c, d_s, idx->metric, qc,
+                                    dcp, qs, dsp, st)))
+        return rc;
+    }
+    // cluster mapping: nprobe nearest centroids at d_c
+    ScanArgs c{};
+    c.xpm = idx->cent_pm;
+    c.d_pad = dcp;
+    c.dims = d_c;
+    c.list_off = idx->cent_off;
+    c.qn = qc;
+    c.ldq = dcp;
+    c.nq = (int)nb;
+    c.counter = counter;
+    c.k = nprobe;
+    c.out_keys = ckeys;
+    ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
+    {
+      StageTimer t(ST_COARSE, st);
+      if ((rc = launch_scan_f32(c, st))) return rc;
+    }
+    {
+      StageTimer t(ST_INVERT, st);
+      if ((rc = launch_invert_probes(ckeys, nb, nprobe, nlist, qt, lcnt, lbeg, lfill, tbeg, pair_q,
+                                     pair_out, tl, tb, tc, ntiles,
+                                     out_probes ? out_probes + b0 * nprobe : nullptr, st)))
+        return rc;
+    }
+    // linear scan of the probed lists at d_s
+    ScanArgs l{};
+    l.xpm = idx->xpm;
+    l.d_pad = idx->d_pad;
+    l.dims = d_s;
+    l.list_off = idx->list_off;
+    l.list_ids = idx->list_ids;
+    l.mscale = mscale;
+    l.qn = qs;
+    l.ldq = dsp;
+    l.tile_list = tl;
+    l.tile_beg = tb;
+    l.tile_cnt = tc;
+    l.ntiles_dev = ntiles;
+    l.counter = counter + 1;
+    l.pair_q = pair_q;
+    l.pair_out = pair_out;
+    l.k = k;
+    l.out_keys = pkeys;
+    {
+      StageTimer t(ST_SCAN, st);
+      if ((rc = launch_scan_f32(l, st))) return rc;
+    }
+    {
+      StageTimer t(ST_MERGE, st);
+      if ((rc = launch_merge(pkeys, nb, nprobe, k, out_ids + b0 * k, out_dist + b0 * k, st)))
+        return rc;
+    }
+  }
+  return ADANNS_OK;
+}
+
+}  // extern "C"

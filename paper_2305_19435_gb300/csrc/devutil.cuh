@@ -1,0 +1,69 @@
+// Device helpers: async copies, warp sorting of packed (distance, id) keys.
+#pragma once
+#include <stdint.h>
+
+namespace adn {
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+// Ascending sort of a[0:n) in shared memory by one warp.  Bitonic network in
+// its "flip" form over the next power of two P >= n: every compare-exchange
+// puts the smaller key at the lower index, so the missing elements [n, P)
+// behave as +inf and are simply skipped.
+__device__ __forceinline__ void warp_sort(uint64_t *a, int n) {
+  const int lane = threadIdx.x & 31;
+  int P = 1;
+  while (P < n) P <<= 1;
+  const int pairs = P >> 1;
+  for (int size = 2; size <= P; size <<= 1) {
+    const int half = size >> 1;
+    const int lh = __ffs(half) - 1;
+    for (int p = lane; p < pairs; p += 32) {
+      const int blk = p >> lh, off = p & (half - 1);
+      const int i = blk * size + off, j = blk * size + size - 1 - off;
+      if (j < n) {
+        uint64_t x = a[i], y = a[j];
+        if (y < x) { a[i] = y; a[j] = x; }
+      }
+    }
+    __syncwarp();
+    for (int stride = half >> 1; stride > 0; stride >>= 1) {
+      const int ls = __ffs(stride) - 1;
+      for (int p = lane; p < pairs; p += 32) {
+        const int i = ((p >> ls) << (ls + 1)) + (p & (stride - 1)), j = i + stride;
+        if (j < n) {
+          uint64_t x = a[i], y = a[j];
+          if (y < x) { a[i] = y; a[j] = x; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace adn

@@ -1,0 +1,164 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/adanns.h"
+
+namespace adn {
+
+constexpr uint64_t KEY_MAX = ~0ull;  // empty slot / padding key
+
+// A candidate is packed as (float bits of a non-negative distance) << 32 | id,
+// so unsigned order is (distance, id) order.
+__host__ __device__ inline uint64_t pack_key(float d, uint32_t id) {
+#ifdef __CUDA_ARCH__
+  return ((uint64_t)__float_as_uint(d) << 32) | id;
+#else
+  union { float f; uint32_t u; } c;
+  c.f = d;
+  return ((uint64_t)c.u << 32) | id;
+#endif
+}
+
+// MR granularities (Sec. 3: nested sizes 8 .. 2048)
+constexpr int NGRAN = 14;
+extern const int kGran[NGRAN];
+int gran_index(int m);  // index in kGran, or -1
+
+inline int pad16(int x) { return (x + 15) & ~15; }
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+#define ADN_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return ::adn::cuda_fail(e__, #call); \
+  } while (0)
+extern std::atomic<long long> g_launches;  // kernels launched since load
+#define ADN_LAUNCH(what)                                 \
+  do {                                                   \
+    ::adn::g_launches.fetch_add(1, std::memory_order_relaxed); \
+    cudaError_t e__ = cudaGetLastError();                \
+    if (e__ != cudaSuccess) return ::adn::cuda_fail(e__, what); \
+  } while (0)
+
+// ---------------------------------------------------------------- scratch
+// Stream-ordered scratch allocation (cudaMallocAsync on the call's stream).
+struct Scratch {
+  cudaStream_t st;
+  void *ptrs[64];
+  int n = 0;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  ~Scratch() {
+    for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], st);
+  }
+  template <class T>
+  int get(T **out, size_t count) {
+    void *p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess || n >= 64) {
+      cudaGetLastError();
+      if (p) cudaFreeAsync(p, st);
+      return fail(ADANNS_ERR_OOM, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    ptrs[n++] = p;
+    *out = (T *)p;
+    return ADANNS_OK;
+  }
+};
+
+// ---------------------------------------------------------------- scan
+// One distance-plus-top-k pass over (list, query-tile) work items.
+// Vectors are stored prefix-major: list l's block b (dims [16b, 16b+16)) is a
+// contiguous [n_l][16] slab at float offset list_off[l]*d_pad + b*16*n_l.
+struct ScanArgs {
+  const float *xpm;        // prefix-major storage
+  int d_pad;               // stored floats per vector (multiple of 16)
+  int dims;                // dimensions used (multiple of 4, <= d_pad)
+  const int64_t *list_off; // member offset of each list (nlist + 1)
+  const int32_t *list_ids; // id of each member (NULL: the member index)
+  const float *mscale;     // per-member scale in list order (NULL: 1)
+  const float *qn;         // prepared queries, rows of ldq floats (16-byte aligned)
+  int ldq;
+  // work items: either explicit tiles or a dense sweep of nq queries over list 0
+  const int32_t *tile_list, *tile_beg, *tile_cnt;
+  const int *ntiles_dev;   // device count of explicit tiles
+  int nq;                  // dense mode: number of queries
+  int *counter;            // zeroed work counter
+  const int32_t *pair_q;   // query row of each pair (NULL: pair index)
+  const int32_t *pair_out; // output row of each pair (NULL: pair index)
+  int k;
+  uint64_t *out_keys;      // [row][k] sorted keys (KEY_MAX padding)
+  int grid;                // CTAs to launch
+};
+int launch_scan_f32(const ScanArgs &a, cudaStream_t st);
+int scan_query_tile(int k);  // queries per work item for a given k
+
+// ---------------------------------------------------------------- helpers
+int launch_prep_queries(const float *q, int64_t B, int ld, int dims_a, int dims_b, int metric,
+                        float *qa, int lda, float *qb, int ldb, cudaStream_t st);
+int launch_keys_to_result(const uint64_t *keys, int64_t rows, int k, int64_t *ids, int32_t *ids32,
+                          float *dist, cudaStream_t st);
+int launch_invert_probes(const uint64_t *ckeys, int64_t B, int nprobe, int nlist, int qt,
+                         int32_t *lcnt, int32_t *lbeg, int32_t *lfill, int32_t *tbeg,
+                         int32_t *pair_q, int32_t *pair_out, int32_t *tile_list,
+                         int32_t *tile_beg, int32_t *tile_cnt, int *ntiles, int32_t *probes_out,
+                         cudaStream_t st);
+int launch_merge(const uint64_t *pkeys, int64_t B, int nprobe, int k, int64_t *out_ids,
+                 float *out_dist, cudaStream_t st);
+int num_sms();
+
+// ---------------------------------------------------------------- build
+int launch_gather_normalize(const float *x, int64_t n, int ld, const int64_t *rows, int dim,
+                            int metric, float *out, int ldo, cudaStream_t st);
+int launch_prefix_major(const float *x, int ld, int d, int d_pad, const int64_t *list_off,
+                        const int32_t *list_ids, const int32_t *assign, int64_t N, float *xpm,
+                        cudaStream_t st);
+int launch_inv_norms(const float *x, int ld, int d, const int32_t *list_ids, int64_t N,
+                     int metric, float *invn /* [ng][N] */, int ng, cudaStream_t st);
+int launch_kmeans_update(const float *t, int64_t n, int ld, int dim, const int32_t *assign,
+                         int nc, double *sums, int32_t *counts, float *cent, cudaStream_t st);
+int launch_sum_keys(const uint64_t *keys, int64_t n, double *out, cudaStream_t st);
+int check_assignment(const int32_t *a, int64_t n, int nlist, cudaStream_t st);
+int build_csr(const int32_t *assign, int64_t N, int nlist, int64_t *list_off, int32_t *list_ids,
+              cudaStream_t st);
+
+// ---------------------------------------------------------------- profiling
+enum Stage { ST_PREP = 0, ST_COARSE = 1, ST_INVERT = 2, ST_SCAN = 3, ST_MERGE = 4, ST_NSTAGE = 16 };
+// Records an event pair around its scope on `st` when profiling is enabled.
+class StageTimer {
+ public:
+  StageTimer(int stage, cudaStream_t st);
+  ~StageTimer();
+
+ private:
+  int stage_;
+  cudaStream_t st_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+}  // namespace adn
+
+// Index (opaque in the C ABI)
+struct adanns_index {
+  int64_t N = 0;
+  int d = 0, d_pad = 0, d_c = 0, dc_pad = 0, nlist = 0, metric = 0, storage = 0;
+  int max_list = 0;
+  float *centroids = nullptr;   // nlist x d_c row-major
+  float *cent_pm = nullptr;     // centroids prefix-major, one list of nlist members
+  int64_t *cent_off = nullptr;  // {0, nlist}
+  int64_t *list_off = nullptr;  // nlist + 1
+  int32_t *list_ids = nullptr;  // N
+  float *xpm = nullptr;         // prefix-major FP32 vectors
+  float *invn = nullptr;        // [ng][N] inverse prefix norms in list order
+  int ng = 0;
+  int64_t *h_list_off = nullptr;  // host copy of list offsets
+};

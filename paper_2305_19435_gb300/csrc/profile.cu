@@ -1,0 +1,88 @@
+// Optional per-stage timing with CUDA events recorded on the launching stream.
+// Off by default; when on, every profiled stage of every call records an event
+// pair around its launches, and adanns_profile_read sums the elapsed times.
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace adn {
+
+namespace {
+struct Rec {
+  int stage;
+  cudaEvent_t a, b;
+};
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+
+cudaEvent_t take_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+StageTimer::StageTimer(int stage, cudaStream_t st) : stage_(stage), st_(st) {
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_on) return;
+  a_ = take_event();
+  b_ = take_event();
+  if (a_ && b_) cudaEventRecord(a_, st_);
+}
+
+StageTimer::~StageTimer() {
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!a_ || !b_) return;
+  cudaEventRecord(b_, st_);
+  g_recs.push_back({stage_, a_, b_});
+}
+
+}  // namespace adn
+
+using namespace adn;
+
+extern "C" {
+
+int adanns_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(g_mu);
+  for (auto &r : g_recs) {
+    g_pool.push_back(r.a);
+    g_pool.push_back(r.b);
+  }
+  g_recs.clear();
+  g_on = on != 0;
+  return ADANNS_OK;
+}
+
+int adanns_profile_read(double *ms, int64_t *count, int nstage) {
+  if (!ms || !count || nstage < 1) return fail(ADANNS_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> g(g_mu);
+  for (int i = 0; i < nstage; ++i) {
+    ms[i] = 0.0;
+    count[i] = 0;
+  }
+  for (auto &r : g_recs) {
+    if (r.stage < 0 || r.stage >= nstage) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "profile event");
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "profile elapsed");
+    ms[r.stage] += t;
+    count[r.stage] += 1;
+  }
+  return ADANNS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// Exact FP32 distance scan with a fused streaming top-k.
+//
+// One kernel serves three steps of AdANNS-IVF (Algorithm 1):
+//   * cluster mapping: every query against the centroid table at d_c, keep
+//     the n_p nearest (computeDistances + sortAscending[:num_probes]);
+//   * the Lloyd assignment of the k-means builder (k = 1);
+//   * the linear scan of the probed lists at d_s, keep the k nearest
+//     (linearScan(q, candidates, d_search, k)).
+//
+// Work item = (list, up to QT queries that probe it).  The CTA streams the
+// list's members in chunks of XT through shared memory, one 16-dim prefix
+// block at a time (the prefix-major layout makes each block of a chunk one
+// contiguous 8 KB read), and forms the QT x XT tile of
+//     dist = sum_j (q_j - s_x * x_j)^2
+// in registers (difference form: no cancellation for near neighbours).
+// Distances never leave the SM: each query keeps a shared-memory candidate
+// buffer; a candidate enters only if its key beats the query's current k-th
+// key, and a warp sorts and trims the buffer when it fills.
+#include "devutil.cuh"
+#include "internal.cuh"
+
+namespace adn {
+
+namespace {
+constexpr int THREADS = 256;
+constexpr int XT = 128;      // members per chunk
+constexpr int XROW = 20;     // padded floats per 16-float smem row (conflict-free float4 reads)
+constexpr int NSTAGE = 3;    // cp.async pipeline depth over prefix blocks
+constexpr int SMEM_BUDGET = 150 * 1024;
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+struct ScanCfg {
+  int tq;    // queries per thread (QT = 16 * tq)
+  int cap;   // candidate buffer per query (0: top-1 mode)
+  size_t smem;
+};
+
+size_t base_smem(int qt) {
+  size_t s = (size_t)NSTAGE * XT * XROW * 4 + (size_t)NSTAGE * qt * XROW * 4;  // X, Q stages
+  s += XT * 4 * 2;        // ids, scales
+  s += qt * 4 * 3;        // qrow, orow, cnt
+  s = (s + 7) & ~(size_t)7;
+  s += qt * 8;            // tau
+  return s;
+}
+
+ScanCfg choose(int k) {
+  ScanCfg c;
+  if (k == 1) {
+    c.tq = 4;
+    c.cap = 0;
+    c.smem = base_smem(64);
+    return c;
+  }
+  const int kp = next_pow2(k);
+  c.tq = (kp + XT) * 64 * 8 <= SMEM_BUDGET ? 4 : 1;
+  const int qt = 16 * c.tq;
+  int cap = 2 * kp;
+  if ((size_t)cap * qt * 8 > SMEM_BUDGET) cap = kp + XT;
+  if (cap < k + XT) cap = k + XT;
+  c.cap = cap;
+  c.smem = base_smem(qt) + (size_t)qt * cap * 8;
+  return c;
+}
+}  // namespace
+
+int scan_query_tile(int k) { return 16 * choose(k).tq; }
+
+template <int TQ, bool TOP1>
+__global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) {
+  constexpr int QT = 16 * TQ;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *Xs = (float *)smem;
+  float *Qs = Xs + NSTAGE * XT * XROW;
+  int32_t *s_ids = (int32_t *)(Qs + NSTAGE * QT * XROW);
+  float *s_sc = (float *)(s_ids + XT);
+  int32_t *s_qrow = (int32_t *)(s_sc + XT);
+  int32_t *s_orow = s_qrow + QT;
+  int *s_cnt = s_orow + QT;
+  uint64_t *s_tau = (uint64_t *)(((uintptr_t)(s_cnt + QT) + 7) & ~(uintptr_t)7);
+  uint64_t *s_buf = s_tau + QT;
+  __shared__ int s_tile;
+
+  const int tid = threadIdx.x, tx = tid & 15, tq = tid >> 4;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int ntiles = a.tile_list ? *a.ntiles_dev : (a.nq + QT - 1) / QT;
+  const int nblk = (a.dims + 15) >> 4;
+
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    int list, beg, cnt;
+    if (a.tile_list) {
+      list = a.tile_list[tile];
+      beg = a.tile_beg[tile];
+      cnt = a.tile_cnt[tile];
+    } else {
+      list = 0;
+      beg = tile * QT;
+      cnt = min(QT, a.nq - beg);
+    }
+    const int64_t moff = a.list_off[list];
+    const int nl = (int)(a.list_off[list + 1] - moff);
+    const float *lbase = a.xpm + moff * (int64_t)a.d_pad;
+    if (tid < QT) {
+      const int p = beg + tid;
+      const bool v = tid < cnt;
+      s_qrow[tid] = v ? (a.pair_q ? a.pair_q[p] : p) : -1;
+      s_orow[tid] = v ? (a.pair_out ? a.pair_out[p] : p) : -1;
+      s_cnt[tid] = 0;
+      s_tau[tid] = KEY_MAX;
+    }
+    __syncthreads();
+    const int nchunk = (nl + XT - 1) / XT;
+    for (int c = 0; c < nchunk; ++c) {
+      const int m0 = c * XT;
+      const int nm = min(XT, nl - m0);
+      if (tid < XT) {
+        const int m = m0 + tid;
+        s_ids[tid] = tid < nm ? (a.list_ids ? a.list_ids[moff + m] : m) : 0;
+        s_sc[tid] = (tid < nm && a.mscale) ? a.mscale[moff + m] : 1.f;
+      }
+      __syncthreads();
+
+      auto load_stage = [&](int b, int stage) {
+        const int nd4 = min(4, (a.dims - 16 * b) >> 2);
+        const float *src = lbase + (int64_t)b * 16 * nl + (int64_t)m0 * 16;
+        float *dst = Xs + stage * XT * XROW;
+#pragma unroll
+        for (int e = tid; e < XT * 4; e += THREADS) {
+          const int m = e >> 2, part = e & 3;
+          if (m < nm && part < nd4) cp_async16(dst + m * XROW + part * 4, src + m * 16 + part * 4);
+        }
+        float *qd = Qs + stage * QT * XROW;
+        for (int e = tid; e < QT * 4; e += THREADS) {
+          const int qi = e >> 2, part = e & 3;
+          const int row = s_qrow[qi];
+          if (row >= 0 && part < nd4)
+            cp_async16(qd + qi * XROW + part * 4, a.qn + (int64_t)row * a.ldq + 16 * b + part * 4);
+        }
+      };
+
+      float sc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) sc[i] = s_sc[tx + 16 * i];
+      float acc[TQ][8];
+#pragma unroll
+      for (int j = 0; j < TQ; ++j)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[j][i] = 0.f;
+
+#pragma unroll
+      for (int s = 0; s < NSTAGE - 1; ++s) {
+        if (s < nblk) load_stage(s, s);
+        cp_async_commit();
+      }
+      for (int b = 0; b < nblk; ++b) {
+        {
+          const int bn = b + NSTAGE - 1;
+          if (bn < nblk) load_stage(bn, bn % NSTAGE);
+          cp_async_commit();
+        }
+        cp_async_wait<NSTAGE - 1>();
+        __syncthreads();
+        const float *xs = Xs + (b % NSTAGE) * XT * XROW;
+        const float *qs = Qs + (b % NSTAGE) * QT * XROW;
+        const int nd4 = min(4, (a.dims - 16 * b) >> 2);
+        auto step = [&](int s) {
+          float4 qv[TQ], xv[8];
+#pragma unroll
+          for (int j = 0; j < TQ; ++j)
+            qv[j] = *(const float4 *)(qs + (tq + 16 * j) * XROW + 4 * s);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) xv[i] = *(const float4 *)(xs + (tx + 16 * i) * XROW + 4 * s);
+#pragma unroll
+          for (int j = 0; j < TQ; ++j)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              float t;
+              t = fmaf(-sc[i], xv[i].x, qv[j].x);
+              acc[j][i] = fmaf(t, t, acc[j][i]);
+              t = fmaf(-sc[i], xv[i].y, qv[j].y);
+              acc[j][i] = fmaf(t, t, acc[j][i]);
+              t = fmaf(-sc[i], xv[i].z, qv[j].z);
+              acc[j][i] = fmaf(t, t, acc[j][i]);
+              t = fmaf(-sc[i], xv[i].w, qv[j].w);
+              acc[j][i] = fmaf(t, t, acc[j][i]);
+            }
+        };
+        if (nd4 == 4) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) step(s);
+        } else {
+          for (int s = 0; s < nd4; ++s) step(s);
+        }
+        __syncthreads();
+      }
+
+      // candidates of this chunk
+#pragma unroll
+      for (int j = 0; j < TQ; ++j) {
+        const int qi = tq + 16 * j;
+        if (qi < cnt) {
+          const uint64_t tau = s_tau[qi];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int m = tx + 16 * i;
+            if (m < nm) {
+              const uint64_t key = pack_key(acc[j][i], (uint32_t)s_ids[m]);
+              if (key < tau) {
+                if (TOP1) {
+                  atomicMin((unsigned long long *)&s_tau[qi], (unsigned long long)key);
+                } else {
+                  const int pos = atomicAdd(&s_cnt[qi], 1);
+                  s_buf[qi * cap + pos] = key;
+                }
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (!TOP1) {
+        const bool last = c == nchunk - 1;
+        for (int qi = warp; qi < cnt; qi += THREADS / 32) {
+          const int n = s_cnt[qi];
+          if (n > cap - XT || (last && n > 0)) {
+            uint64_t *buf = s_buf + qi * cap;
+            warp_sort(buf, n);
+            const int keep = min(n, a.k);
+            if (lane == 0) {
+              s_cnt[qi] = keep;
+              s_tau[qi] = keep == a.k ? buf[a.k - 1] : KEY_MAX;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // write the sorted per-(query, list) results
+    for (int qi = warp; qi < cnt; qi += THREADS / 32) {
+      uint64_t *out = a.out_keys + (int64_t)s_orow[qi] * a.k;
+      if (TOP1) {
+        if (lane == 0) out[0] = s_tau[qi];
+      } else {
+        const int n = s_cnt[qi];
+        const uint64_t *buf = s_buf + qi * cap;
+        for (int r = lane; r < a.k; r += 32) out[r] = r < n ? buf[r] : KEY_MAX;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int launch_scan_f32(const ScanArgs &a, cudaStream_t st) {
+  if (a.dims % 4 != 0 || a.dims > a.d_pad || a.d_pad % 16 != 0 || a.ldq % 4 != 0 || a.k < 1)
+    return fail(ADANNS_ERR_ARG, "scan: bad dimensions");
+  const ScanCfg c = choose(a.k);
+  void (*kern)(ScanArgs, int) = c.cap == 0 ? scan_f32_kernel<4, true>
+                                : c.tq == 4 ? scan_f32_kernel<4, false>
+                                            : scan_f32_kernel<1, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  if (e != cudaSuccess) return cuda_fail(e, "scan attribute");
+  int per_sm = 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, c.smem);
+  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  const int grid = a.grid > 0 ? a.grid : num_sms() * per_sm;
+  kern<<<grid, THREADS, c.smem, st>>>(a, c.cap);
+  ADN_LAUNCH("scan_f32_kernel");
+  return ADANNS_OK;
+}
+
+}  // namespace adn

@@ -1,0 +1,278 @@
+// Query preparation, probe inversion into (list, query-tile) work, and the
+// cross-list top-k merge of AdANNS-IVF search (Algorithm 1 adannsInference).
+#include <mutex>
+
+#include "devutil.cuh"
+#include "internal.cuh"
+
+namespace adn {
+
+const int kGran[NGRAN] = {8, 16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 2048};
+
+int gran_index(int m) {
+  for (int i = 0; i < NGRAN; ++i)
+    if (kGran[i] == m) return i;
+  return -1;
+}
+
+std::atomic<long long> g_launches{0};
+static thread_local std::string g_err;
+void set_error(const std::string &m) { g_err = m; }
+int fail(int code, const std::string &m) {
+  g_err = m;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return ADANNS_ERR_CUDA;
+}
+const char *last_error() { return g_err.c_str(); }
+
+int num_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (!sms[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = v > 0 ? v : 148;
+  }
+  return sms[dev];
+}
+
+// ---------------------------------------------------------------- queries
+// Per query (one warp): inverse prefix norms at dims_a and dims_b (FP32 sums
+// of squares, lane-strided then a shuffle tree) and the two scaled, zero
+// padded copies q * nu_a (rows of lda) and q * nu_b (rows of ldb).
+__global__ void prep_queries_kernel(const float *__restrict__ q, int64_t B, int ld, int da,
+                                    int db, int metric, float *__restrict__ qa, int lda,
+                                    float *__restrict__ qb, int ldb) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= B) return;
+  const float *src = q + row * ld;
+  float sa = 0.f, sb = 0.f;
+  const int dm = max(da, db);
+  for (int j = lane; j < dm; j += 32) {
+    const float v = src[j];
+    if (j < da) sa = fmaf(v, v, sa);
+    if (j < db) sb = fmaf(v, v, sb);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  float na = 1.f, nb = 1.f;
+  if (metric == ADANNS_METRIC_L2_PREFIXNORM) {
+    na = sa > 0.f ? 1.f / sqrtf(sa) : 0.f;
+    nb = sb > 0.f ? 1.f / sqrtf(sb) : 0.f;
+  }
+  if (qa)
+    for (int j = lane; j < lda; j += 32) qa[row * lda + j] = j < da ? src[j] * na : 0.f;
+  if (qb)
+    for (int j = lane; j < ldb; j += 32) qb[row * ldb + j] = j < db ? src[j] * nb : 0.f;
+}
+
+int launch_prep_queries(const float *q, int64_t B, int ld, int da, int db, int metric, float *qa,
+                        int lda, float *qb, int ldb, cudaStream_t st) {
+  if (B <= 0) return ADANNS_OK;
+  const int wpb = 8;
+  prep_queries_kernel<<<(unsigned)((B + wpb - 1) / wpb), wpb * 32, 0, st>>>(q, B, ld, da, db,
+                                                                           metric, qa, lda, qb, ldb);
+  ADN_LAUNCH("prep_queries_kernel");
+  return ADANNS_OK;
+}
+
+// ---------------------------------------------------------------- keys -> results
+__global__ void keys_to_result_kernel(const uint64_t *__restrict__ keys, int64_t n,
+                                      int64_t *__restrict__ ids, int32_t *__restrict__ ids32,
+                                      float *__restrict__ dist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t k = keys[i];
+  const bool pad = k == KEY_MAX;
+  if (ids) ids[i] = pad ? -1 : (int64_t)(uint32_t)(k & 0xffffffffu);
+  if (ids32) ids32[i] = pad ? -1 : (int32_t)(uint32_t)(k & 0xffffffffu);
+  if (dist) dist[i] = pad ? __int_as_float(0x7f800000) : __uint_as_float((uint32_t)(k >> 32));
+}
+
+int launch_keys_to_result(const uint64_t *keys, int64_t rows, int k, int64_t *ids, int32_t *ids32,
+                          float *dist, cudaStream_t st) {
+  const int64_t n = rows * k;
+  if (n <= 0) return ADANNS_OK;
+  keys_to_result_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, n, ids, ids32, dist);
+  ADN_LAUNCH("keys_to_result_kernel");
+  return ADANNS_OK;
+}
+
+// ---------------------------------------------------------------- probe inversion
+__global__ void probe_count_kernel(const uint64_t *__restrict__ ckeys, int64_t n,
+                                   int32_t *__restrict__ lcnt, int32_t *__restrict__ probes_out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int l = (int)(uint32_t)(ckeys[e] & 0xffffffffu);
+  atomicAdd(&lcnt[l], 1);
+  if (probes_out) probes_out[e] = l;
+}
+
+// single CTA: lbeg = exclusive scan of lcnt; per-list tile counts and their scan
+__global__ void probe_scan_kernel(const int32_t *__restrict__ lcnt, int nlist, int qt,
+                                  int32_t *__restrict__ lbeg, int32_t *__restrict__ tbeg,
+                                  int *__restrict__ ntiles) {
+  __shared__ int32_t s_a[1024], s_b[1024];
+  __shared__ int32_t carry_a, carry_b;
+  if (threadIdx.x == 0) carry_a = carry_b = 0;
+  __syncthreads();
+  for (int base = 0; base < nlist; base += 1024) {
+    const int l = base + threadIdx.x;
+    const int c = l < nlist ? lcnt[l] : 0;
+    const int t = (c + qt - 1) / qt;
+    s_a[threadIdx.x] = c;
+    s_b[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      int va = 0, vb = 0;
+      if ((int)threadIdx.x >= o) { va = s_a[threadIdx.x - o]; vb = s_b[threadIdx.x - o]; }
+      __syncthreads();
+      s_a[threadIdx.x] += va;
+      s_b[threadIdx.x] += vb;
+      __syncthreads();
+    }
+    if (l < nlist) {
+      lbeg[l] = carry_a + s_a[threadIdx.x] - c;
+      tbeg[l] = carry_b + s_b[threadIdx.x] - t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) { carry_a += s_a[1023]; carry_b += s_b[1023]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ntiles = carry_b;
+}
+
+__global__ void probe_fill_kernel(const uint64_t *__restrict__ ckeys, int64_t n, int nprobe,
+                                  const int32_t *__restrict__ lbeg, int32_t *__restrict__ lfill,
+                                  int32_t *__restrict__ pair_q, int32_t *__restrict__ pair_out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int l = (int)(uint32_t)(ckeys[e] & 0xffffffffu);
+  const int pos = lbeg[l] + atomicAdd(&lfill[l], 1);
+  pair_q[pos] = (int32_t)(e / nprobe);
+  pair_out[pos] = (int32_t)e;
+}
+
+__global__ void probe_tiles_kernel(const int32_t *__restrict__ lcnt,
+                                   const int32_t *__restrict__ lbeg,
+                                   const int32_t *__restrict__ tbeg, int nlist, int qt,
+                                   int32_t *__restrict__ tile_list, int32_t *__restrict__ tile_beg,
+                                   int32_t *__restrict__ tile_cnt) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nlist) return;
+  const int c = lcnt[l];
+  const int nt = (c + qt - 1) / qt;
+  for (int t = 0; t < nt; ++t) {
+    const int idx = tbeg[l] + t;
+    tile_list[idx] = l;
+    tile_beg[idx] = lbeg[l] + t * qt;
+    tile_cnt[idx] = min(qt, c - t * qt);
+  }
+}
+
+int launch_invert_probes(const uint64_t *ckeys, int64_t B, int nprobe, int nlist, int qt,
+                         int32_t *lcnt, int32_t *lbeg, int32_t *lfill, int32_t *tbeg,
+                         int32_t *pair_q, int32_t *pair_out, int32_t *tile_list,
+                         int32_t *tile_beg, int32_t *tile_cnt, int *ntiles, int32_t *probes_out,
+                         cudaStream_t st) {
+  const int64_t n = B * nprobe;
+  ADN_CUDA(cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * nlist, st));
+  ADN_CUDA(cudaMemsetAsync(lfill, 0, sizeof(int32_t) * nlist, st));
+  const unsigned g = (unsigned)((n + 255) / 256);
+  probe_count_kernel<<<g, 256, 0, st>>>(ckeys, n, lcnt, probes_out);
+  ADN_LAUNCH("probe_count_kernel");
+  probe_scan_kernel<<<1, 1024, 0, st>>>(lcnt, nlist, qt, lbeg, tbeg, ntiles);
+  ADN_LAUNCH("probe_scan_kernel");
+  probe_fill_kernel<<<g, 256, 0, st>>>(ckeys, n, nprobe, lbeg, lfill, pair_q, pair_out);
+  ADN_LAUNCH("probe_fill_kernel");
+  probe_tiles_kernel<<<(nlist + 255) / 256, 256, 0, st>>>(lcnt, lbeg, tbeg, nlist, qt, tile_list,
+                                                          tile_beg, tile_cnt);
+  ADN_LAUNCH("probe_tiles_kernel");
+  return ADANNS_OK;
+}
+
+// ---------------------------------------------------------------- merge
+// Per query (one warp): the nprobe sorted per-list top-k runs -> the k best.
+// tau starts at the smallest k-th key over the runs, an upper bound of the
+// final k-th key, so only keys <= tau are buffered; the buffer is sorted and
+// trimmed to k whenever it fills.
+constexpr int MERGE_WPB = 4;
+
+__global__ void merge_kernel(const uint64_t *__restrict__ pkeys, int64_t B, int nprobe, int k,
+                             int cap, int64_t *__restrict__ out_ids,
+                             float *__restrict__ out_dist) {
+  extern __shared__ uint64_t msmem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t qi = (int64_t)blockIdx.x * MERGE_WPB + warp;
+  if (qi >= B) return;
+  uint64_t *buf = msmem + (size_t)warp * cap;
+  const uint64_t *src = pkeys + qi * (int64_t)nprobe * k;
+  uint64_t tau = KEY_MAX;
+  for (int s = lane; s < nprobe; s += 32) {
+    const uint64_t v = src[(int64_t)s * k + k - 1];
+    tau = v < tau ? v : tau;
+  }
+  tau = warp_min_u64(tau);
+  int n = 0;
+  const int total = nprobe * k;
+  for (int base = 0; base < total; base += 32) {
+    const int i = base + lane;
+    const uint64_t key = i < total ? src[i] : KEY_MAX;
+    const bool take = key != KEY_MAX && key <= tau;
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (take) buf[n + __popc(m & lanemask_lt())] = key;
+    n += __popc(m);
+    if (n > cap - 32) {
+      __syncwarp();
+      warp_sort(buf, n);
+      if (n > k) n = k;
+      if (n == k) {
+        const uint64_t kth = buf[k - 1];
+        tau = kth < tau ? kth : tau;
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  warp_sort(buf, n);
+  if (n > k) n = k;
+  for (int r = lane; r < k; r += 32) {
+    const int64_t o = qi * k + r;
+    if (r < n) {
+      const uint64_t key = buf[r];
+      out_ids[o] = (int64_t)(uint32_t)(key & 0xffffffffu);
+      out_dist[o] = __uint_as_float((uint32_t)(key >> 32));
+    } else {
+      out_ids[o] = -1;
+      out_dist[o] = __int_as_float(0x7f800000);
+    }
+  }
+}
+
+int launch_merge(const uint64_t *pkeys, int64_t B, int nprobe, int k, int64_t *out_ids,
+                 float *out_dist, cudaStream_t st) {
+  if (B <= 0) return ADANNS_OK;
+  int kp = 1;
+  while (kp < k) kp <<= 1;
+  int cap = 2 * kp;
+  if (cap < kp + 32) cap = kp + 32;
+  const size_t smem = (size_t)MERGE_WPB * cap * 8;
+  cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "merge attribute");
+  merge_kernel<<<(unsigned)((B + MERGE_WPB - 1) / MERGE_WPB), MERGE_WPB * 32, smem, st>>>(
+      pkeys, B, nprobe, k, cap, out_ids, out_dist);
+  ADN_LAUNCH("merge_kernel");
+  return ADANNS_OK;
+}
+
+}  // namespace adn

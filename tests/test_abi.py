@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function include/adanns.h declares; argument checks that need no device
+memory return the documented error codes."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "adanns.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(adanns_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2305_19435_gb300 as P
+    P.build()
+    return P.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("adanns_build_ivf", "adanns_search_ivf", "adanns_index_create", "adanns_last_error"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_2305_19435_gb300 as P
+    out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_version_and_argument_errors_without_device(lib):
+    assert lib.adanns_version() == 100
+    fake = ctypes.c_void_p(16)
+    h = ctypes.c_void_p()
+    # d_c = 17 is not an MR granularity
+    rc = lib.adanns_build_ivf(fake, 100, 64, 17, 4, 2, 50, 1, 1, 1, None, None, ctypes.byref(h))
+    assert rc == -2 and b"granularity" in lib.adanns_last_error()
+    # train_n below nlist
+    rc = lib.adanns_build_ivf(fake, 100, 64, 16, 40, 2, 20, 1, 1, 1, None, None, ctypes.byref(h))
+    assert rc == -1
+    # d_c beyond d
+    rc = lib.adanns_build_ivf(fake, 100, 8, 16, 4, 2, 50, 1, 1, 1, None, None, ctypes.byref(h))
+    assert rc == -2
+    # unknown metric
+    rc = lib.adanns_build_ivf(fake, 100, 64, 16, 4, 2, 50, 1, 7, 1, None, None, ctypes.byref(h))
+    assert rc == -1
+    # NULL index
+    rc = lib.adanns_search_ivf(None, fake, 1, 16, 64, 1, 10, 1, 0, fake, fake, None, None)
+    assert rc == -1

@@ -1,0 +1,245 @@
+"""GPU-vs-oracle parity for AdANNS-IVF: index layout, k-means steps, search.
+
+Every expected value comes from the FP64 oracle on the same seeded inputs.
+Search parity runs on the oracle's own index (its FP32 centroids and list
+assignment imported through adanns_index_create), so the scan and the
+cluster mapping are compared on identical lists.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+from parity import ambiguous_probe_rows, check_topk, recall, tol
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PN, L2 = oracle.METRIC_L2_PREFIXNORM, oracle.METRIC_L2
+
+
+@pytest.fixture(scope="module")
+def A():
+    import paper_2305_19435_gb300 as P
+    P.build()
+    assert torch.cuda.is_available()
+    return P
+
+
+def cu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def import_index(A, db, oidx, metric):
+    return A.index_create(cu(db), cu(oidx["centroids"]), cu(oidx["assign"].astype(np.int32)),
+                          metric=metric)
+
+
+def search_parity(A, db, q, oidx, d_c, d_s, nprobe, k, metric, extra=24):
+    gidx = import_index(A, db, oidx, metric)
+    gi, gd, gp = A.search_ivf(gidx, cu(q), d_c, d_s, nprobe, k, return_probes=True)
+    torch.cuda.synchronize()
+    gi, gd, gp = gi.cpu().numpy(), gd.cpu().numpy(), gp.cpu().numpy()
+    o = oracle.search_ivf(db, oidx, q, d_c, d_s, nprobe, k + extra, metric=metric)
+    scale = None
+    if metric == L2:
+        scale = (q[:, :max(d_c, d_s)].astype(np.float64) ** 2).sum(1)
+    amb = ambiguous_probe_rows(o["probe_dist"], nprobe,
+                               1.0 if scale is None else scale[:, None])
+    # probe lists of unambiguous queries match exactly (as sets; order by distance)
+    for i in np.nonzero(~amb)[0]:
+        assert set(gp[i]) == set(o["probes"][i]), i
+    n, fails = check_topk(gi, gd, o["ids"], o["dist"], k, skip_rows=amb, scale=scale)
+    assert n > 0
+    assert not fails, f"{len(fails)}/{n} queries differ, e.g. {fails[:2]}"
+    gidx.free()
+    return gi, gd, o, amb
+
+
+# ---------------------------------------------------------------- index layout
+def test_index_lists_match_oracle_csr(A):
+    data = synthdata.small(5000, 1, 64, 32, 101)
+    o = oracle.build_ivf(data["db"], 16, 40, 5, 5000, seed=3)
+    g = import_index(A, data["db"], o, PN)
+    off, ids = g.lists()
+    assert np.array_equal(off.cpu().numpy(), o["list_off"])
+    assert np.array_equal(ids.cpu().numpy(), o["list_ids"])
+    assert np.array_equal(g.centroids().cpu().numpy(), o["centroids"])
+
+
+def test_empty_lists_and_tiny_lists(A):
+    data = synthdata.small(700, 30, 32, 8, 102)
+    db, q = data["db"], data["queries"]
+    o = oracle.build_ivf(db, 16, 12, 4, 700, seed=4)
+    # force two empty lists and one single-member list
+    a = o["assign"].copy()
+    a[a == 3] = 4
+    a[a == 7] = 8
+    a[5] = 7
+    o = dict(o)
+    o["assign"] = a
+    o["list_off"], o["list_ids"] = oracle.lists_from_assignment(a, 12)
+    search_parity(A, db, q, o, 16, 32, 12, 20, PN)
+    search_parity(A, db, q, o, 16, 32, 3, 7, PN)
+
+
+# ---------------------------------------------------------------- search parity
+def tiny_workload():
+    w = synthdata.WORKLOADS["tiny"]
+    return synthdata.make(w)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    data = tiny_workload()
+    o = oracle.build_ivf(data["db"], 16, 64, 20, 10_000, seed=42)
+    return data, o
+
+
+def test_tiny_config_full_parity(A, tiny):
+    """Tiny AdANNS-IVF: 10k x 64, nlist 64 at d_c=16, nprobe 4, d_s 64, k 10."""
+    data, o = tiny
+    gi, gd, orr, amb = search_parity(A, data["db"], data["queries"], o, 16, 64, 4, 10, PN)
+    assert recall(gi, orr["ids"], 10) > 0.999
+    assert amb.mean() < 0.05
+
+
+@pytest.mark.parametrize("d_s,nprobe,k", [(8, 1, 1), (16, 2, 5), (32, 4, 10), (48, 8, 33),
+                                          (64, 16, 100), (64, 64, 128), (64, 3, 300)])
+def test_tiny_sweep(A, tiny, d_s, nprobe, k):
+    data, o = tiny
+    search_parity(A, data["db"], data["queries"], o, 16, d_s, nprobe, k, PN)
+
+
+def test_full_probe_full_dim_is_exact_search(A, tiny):
+    """n_p = nlist, d_s = d: the GPU result is exact kNN (via the oracle pin)."""
+    data, o = tiny
+    search_parity(A, data["db"], data["queries"][:50], o, 16, 64, 64, 50, PN)
+
+
+def test_raw_l2_metric(A):
+    data = synthdata.small(4000, 64, 64, 16, 103)
+    o = oracle.build_ivf(data["db"], 32, 30, 6, 4000, seed=5, metric=L2)
+    search_parity(A, data["db"], data["queries"], o, 32, 64, 5, 20, L2)
+
+
+def test_duplicates_zero_vectors_and_exact_matches(A):
+    data = synthdata.small(3000, 40, 64, 16, 104)
+    db, q = data["db"].copy(), data["queries"].copy()
+    db[100:140] = db[7]            # a block of duplicates: an exact tie group
+    db[200] = 0.0                  # zero vector
+    q[0] = db[7]                   # query equal to a duplicated vector
+    q[1] = db[300] * 3.0           # same direction: distance 0 after normalisation
+    q[2] = 0.0                     # zero query
+    o = oracle.build_ivf(db, 16, 20, 5, 3000, seed=6)
+    gi, gd, orr, amb = search_parity(A, db, q, o, 16, 64, 20, 60, PN)
+    assert set(gi[0, :41].tolist()) == {7, *range(100, 140)}
+    assert gi[1, 0] == 300
+
+
+@pytest.mark.parametrize("B", [1, 17, 63, 64, 65, 129])
+def test_ragged_batches(A, tiny, B):
+    data, o = tiny
+    search_parity(A, data["db"], data["queries"][:B], o, 16, 32, 4, 10, PN)
+
+
+def test_many_tiles_wider_vectors(A):
+    """Lists long enough for many member chunks and queries for many tiles."""
+    data = synthdata.small(60_000, 600, 256, 64, 105)
+    o = oracle.build_ivf(data["db"], 32, 48, 8, 20_000, seed=7)
+    search_parity(A, data["db"], data["queries"], o, 32, 256, 6, 100, PN)
+    search_parity(A, data["db"], data["queries"][:200], o, 32, 96, 12, 10, PN)
+
+
+def test_argument_errors(A, tiny):
+    data, o = tiny
+    g = import_index(A, data["db"], o, PN)
+    qq = cu(data["queries"][:4])
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivf(g, qq, 16, 40, 4, 10)          # d_s not in G
+    assert e.value.code == -2
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivf(g, qq, 16, 128, 4, 10)         # d_s beyond d
+    assert e.value.code == -2
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivf(g, qq, 16, 64, 65, 10)         # nprobe > nlist
+    assert e.value.code == -1
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivf(g, qq, 16, 64, 4, 1025)        # k too large
+    assert e.value.code == -1
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivf(g, qq, 32, 64, 4, 10)          # d_c differs from the index
+    assert e.value.code == -2
+    ids, dist = A.search_ivf(g, cu(data["queries"][:0]), 16, 64, 4, 10)
+    assert ids.shape == (0, 10)
+    g.free()
+
+
+# ---------------------------------------------------------------- k-means steps
+def teacher_forced_case(seed=106, n=6000, d=64, d_c=32, nc=50):
+    data = synthdata.small(n, 1, d, 24, seed)
+    x = data["db"]
+    T = oracle.prefix(x, d_c)
+    init = oracle.sample(seed, n, nc)
+    C0 = T[init].astype(np.float32)
+    return x, T, C0
+
+
+def test_kmeans_assign_step_matches_oracle(A):
+    x, T, C0 = teacher_forced_case()
+    a, dist = A.kmeans_assign(cu(x), cu(C0), 32)
+    a, dist = a.cpu().numpy(), dist.cpu().numpy()
+    oa, ob, os2 = oracle.assign(T, C0.astype(np.float64))
+    tied = os2 - ob <= tol(os2)
+    assert tied.mean() < 0.01
+    assert np.array_equal(a[~tied], oa[~tied])
+    assert np.all(np.abs(dist - ob) <= tol(ob))
+
+
+def test_kmeans_update_step_matches_oracle(A):
+    x, T, C0 = teacher_forced_case(seed=107)
+    oa, _, _ = oracle.assign(T, C0.astype(np.float64))
+    want = oracle.update(T, oa, C0.astype(np.float64))
+    got = A.kmeans_update(cu(x), cu(oa.astype(np.int32)), cu(C0.copy()), 32).cpu().numpy()
+    # FP32 normalised inputs summed in FP64: within FP32 rounding of the mean,
+    # plus the normalisation rounding (2^-24 relative per coordinate)
+    assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-7)
+    # empty clusters keep their centroid
+    nc = C0.shape[0]
+    a2 = np.zeros(len(x), dtype=np.int32)
+    got2 = A.kmeans_update(cu(x), cu(a2), cu(C0.copy()), 32).cpu().numpy()
+    assert np.array_equal(got2[1:], C0[1:])
+
+
+def test_build_ivf_free_running_objective(A, tiny):
+    data, o = tiny
+    g = A.build_ivf(cu(data["db"]), 16, 64, 20, 10_000, 42)
+    Jg, Jo = np.array(g.objective), np.array(o["objectives"])
+    assert abs(Jg[0] - Jo[0]) <= 1e-5 * Jo[0]       # same sample, same init
+    assert abs(Jg[-1] - Jo[-1]) <= 1e-4 * Jo[-1]
+    assert np.all(Jg[1:] <= Jg[:-1] * (1 + 1e-6))
+    off, ids = g.lists()
+    off, ids = off.cpu().numpy(), ids.cpu().numpy()
+    assert off[-1] == 10_000 and sorted(ids.tolist()) == list(range(10_000))
+    # the GPU's final assignment is the nearest of its own centroids (oracle check)
+    C = g.centroids().cpu().numpy().astype(np.float64)
+    X = oracle.prefix(data["db"], 16)
+    oa, ob, os2 = oracle.assign(X, C)
+    lab = np.empty(10_000, dtype=np.int64)
+    for l in range(64):
+        lab[ids[off[l]:off[l + 1]]] = l
+    tied = os2 - ob <= tol(os2)
+    assert np.array_equal(lab[~tied], oa[~tied])
+    g.free()
+
+
+def test_gpu_built_index_search_recall(A, tiny):
+    """The GPU-built index, searched on the GPU, agrees with the oracle's index
+    searched by the oracle at recall@10 >= 0.95 (builds may diverge only at
+    near-ties of the Lloyd trajectory)."""
+    data, o = tiny
+    g = A.build_ivf(cu(data["db"]), 16, 64, 20, 10_000, 42)
+    gi, gd = A.search_ivf(g, cu(data["queries"]), 16, 64, 4, 10)
+    orr = oracle.search_ivf(data["db"], o, data["queries"], 16, 64, 4, 10)
+    assert recall(gi.cpu().numpy(), orr["ids"], 10) >= 0.95
+    g.free()
