@@ -35,17 +35,40 @@ def import_index(A, db, oidx, metric):
                           metric=metric)
 
 
+def full_groups(o, rerun, k):
+    """Rows whose tie group at rank k-1 runs to the end of the oracle's list are
+    searched again with every candidate returned, so that group is complete."""
+    d = o["dist"]
+    last = d[:, -1]
+    trunc = np.isfinite(last) & (last - d[:, k - 1] <= tol(last))
+    if not trunc.any():
+        return o
+    rows = np.nonzero(trunc)[0]
+    kk = int(o["ncand"][rows].max()) if "ncand" in o else 4 * d.shape[1]
+    o2 = rerun(rows, max(kk, d.shape[1]))
+    K = o2["ids"].shape[1]
+    ids = np.full((d.shape[0], K), -1, dtype=np.int64)
+    dist = np.full((d.shape[0], K), np.inf)
+    ids[:, :d.shape[1]], dist[:, :d.shape[1]] = o["ids"], d
+    ids[rows], dist[rows] = o2["ids"], o2["dist"]
+    o = dict(o)
+    o["ids"], o["dist"] = ids, dist
+    return o
+
+
 def search_parity(A, db, q, oidx, d_c, d_s, nprobe, k, metric, extra=24):
     gidx = import_index(A, db, oidx, metric)
     gi, gd, gp = A.search_ivf(gidx, cu(q), d_c, d_s, nprobe, k, return_probes=True)
     torch.cuda.synchronize()
     gi, gd, gp = gi.cpu().numpy(), gd.cpu().numpy(), gp.cpu().numpy()
-    o = oracle.search_ivf(db, oidx, q, d_c, d_s, nprobe, k + extra, metric=metric)
-    scale = None
+    o = full_groups(oracle.search_ivf(db, oidx, q, d_c, d_s, nprobe, k + extra, metric=metric),
+                    lambda rows, kk: oracle.search_ivf(db, oidx, q[rows], d_c, d_s, nprobe, kk,
+                                                       metric=metric), k)
+    scale, scale_c = None, 1.0
     if metric == L2:
-        scale = (q[:, :max(d_c, d_s)].astype(np.float64) ** 2).sum(1)
-    amb = ambiguous_probe_rows(o["probe_dist"], nprobe,
-                               1.0 if scale is None else scale[:, None])
+        scale = (q[:, :d_s].astype(np.float64) ** 2).sum(1)
+        scale_c = (q[:, :d_c].astype(np.float64) ** 2).sum(1)
+    amb = ambiguous_probe_rows(o["probe_dist"], nprobe, scale_c)
     # probe lists of unambiguous queries match exactly (as sets; order by distance)
     for i in np.nonzero(~amb)[0]:
         assert set(gp[i]) == set(o["probes"][i]), i
