@@ -164,6 +164,44 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
                       int d_s, int nprobe, int k, int storage, int rerank_k, int64_t *out_ids,
                       float *out_dist, int32_t *out_probes, void *cuda_stream);
 
+/*
+ * Size of the fixed device scratch array used by adanns_search_ivf_noalloc
+ * (64 MiB, held on every GPU that loads this library until the process exits).
+ */
+#define ADANNS_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * AdANNS-IVF search that allocates no memory (not a step of the paper, which
+ * has no counterpart; a deployment variant of adanns_search_ivf).
+ *
+ * For callers that cannot allocate device memory during a search: processes
+ * whose framework has reserved the whole device memory budget for its own
+ * pool, latency-critical loops where an allocator call that may synchronise
+ * or grow a pool is not acceptable, or hosts whose policy forbids the library
+ * from using the allocator.  It computes exactly what adanns_search_ivf
+ * computes with storage = ADANNS_STORE_F32 and rerank_k = 0, with the same
+ * arguments, layouts and error codes, but takes all scratch from one fixed
+ * file-scope device array of ADANNS_NOALLOC_SCRATCH_BYTES.  It calls no
+ * cudaMalloc, cudaFree or allocating routine.
+ *
+ * Scratch needed, each piece rounded up to 256 bytes:
+ *   B*pad16(d_c)*4 + B*pad16(d_s)*4 + B*nprobe*8 + B*nprobe*k*8
+ *   + 4*nlist*4 + 2*B*nprobe*4 + 3*T*4 + 4 + 8,  T = ceil(B*nprobe/QT) + nlist,
+ * where QT (queries per work item) is 64 for k <= 128 and 16 above.  A request
+ * that needs more returns ADANNS_ERR_ARG with the sizes in the message and
+ * launches nothing.
+ *
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call shares the one array and
+ * leaves its contents behind (work counters are cleared by each call), so
+ * calls that overlap on the GPU -- on different streams, or from several host
+ * threads -- race and corrupt each other's results: serialise them.
+ */
+int adanns_search_ivf_noalloc(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                              int d_s, int nprobe, int k, int64_t *out_ids, float *out_dist,
+                              void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
