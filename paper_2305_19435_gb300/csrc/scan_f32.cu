@@ -25,8 +25,9 @@ namespace {
 constexpr int THREADS = 256;
 constexpr int XT = 128;      // members per chunk
 constexpr int XROW = 20;     // padded floats per 16-float smem row (conflict-free float4 reads)
-constexpr int NSTAGE = 3;    // cp.async pipeline depth over prefix blocks
-constexpr int SMEM_BUDGET = 150 * 1024;
+constexpr int NSTAGE = 2;    // cp.async pipeline depth over prefix blocks
+constexpr int ROUND = 32;    // candidates appended per query between compactions
+constexpr int NWARP = THREADS / 32;
 
 int next_pow2(int x) {
   int p = 1;
@@ -40,12 +41,17 @@ struct ScanCfg {
   size_t smem;
 };
 
-size_t base_smem(int qt) {
-  size_t s = (size_t)NSTAGE * XT * XROW * 4 + (size_t)NSTAGE * qt * XROW * 4;  // X, Q stages
-  s += XT * 4 * 2;        // ids, scales
-  s += qt * 4 * 3;        // qrow, orow, cnt
+// shared memory: [X stages | merge scratch] [Q stages] ids scales qrow orow cnt nsorted tau buf
+size_t smem_bytes(int qt, int cap) {
+  size_t xs = (size_t)NSTAGE * XT * XROW * 4;
+  size_t scratch = (size_t)NWARP * cap * 8;
+  size_t s = xs > scratch ? xs : scratch;
+  s += (size_t)NSTAGE * qt * XROW * 4;
+  s += XT * 4 * 2;
+  s += qt * 4 * 4;
   s = (s + 7) & ~(size_t)7;
-  s += qt * 8;            // tau
+  s += qt * 8;
+  s += (size_t)qt * cap * 8;
   return s;
 }
 
@@ -54,18 +60,46 @@ ScanCfg choose(int k) {
   if (k == 1) {
     c.tq = 4;
     c.cap = 0;
-    c.smem = base_smem(64);
+    c.smem = smem_bytes(64, 0);
     return c;
   }
   const int kp = next_pow2(k);
-  c.tq = (kp + XT) * 64 * 8 <= SMEM_BUDGET ? 4 : 1;
-  const int qt = 16 * c.tq;
-  int cap = 2 * kp;
-  if ((size_t)cap * qt * 8 > SMEM_BUDGET) cap = kp + XT;
-  if (cap < k + XT) cap = k + XT;
-  c.cap = cap;
-  c.smem = base_smem(qt) + (size_t)qt * cap * 8;
+  c.cap = kp + ROUND;
+  c.tq = kp <= 128 ? 4 : 1;
+  c.smem = smem_bytes(16 * c.tq, c.cap);
   return c;
+}
+
+// number of keys in sorted a[0:n) that are < key
+__device__ __forceinline__ int lower_bound_u64(const uint64_t *a, int n, uint64_t key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// buf[0:na) is sorted, buf[na:n) is not: sort the new keys, merge the two runs
+// (each key's output rank = its own index + the count of smaller keys in the
+// other run; keys are unique), keep the k smallest.  One warp; returns the kept count.
+__device__ int compact_topk(uint64_t *buf, int na, int n, int k, uint64_t *scratch) {
+  const int lane = threadIdx.x & 31;
+  const int nb = n - na;
+  warp_sort(buf + na, nb);
+  const int keep = n < k ? n : k;
+  for (int i = lane; i < na && i < keep; i += 32) {
+    const int p = i + lower_bound_u64(buf + na, nb, buf[i]);
+    if (p < keep) scratch[p] = buf[i];
+  }
+  for (int j = lane; j < nb && j < keep; j += 32) {
+    const int p = j + lower_bound_u64(buf, na, buf[na + j]);
+    if (p < keep) scratch[p] = buf[na + j];
+  }
+  __syncwarp();
+  for (int i = lane; i < keep; i += 32) buf[i] = scratch[i];
+  __syncwarp();
+  return keep;
 }
 }  // namespace
 
@@ -76,13 +110,18 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
   constexpr int QT = 16 * TQ;
   extern __shared__ __align__(16) unsigned char smem[];
   float *Xs = (float *)smem;
-  float *Qs = Xs + NSTAGE * XT * XROW;
+  const size_t xbytes = (size_t)NSTAGE * XT * XROW * 4 > (size_t)NWARP * cap * 8
+                            ? (size_t)NSTAGE * XT * XROW * 4
+                            : (size_t)NWARP * cap * 8;
+  uint64_t *s_scratch = (uint64_t *)smem;  // merge scratch, reuses the X stages between chunks
+  float *Qs = (float *)(smem + xbytes);
   int32_t *s_ids = (int32_t *)(Qs + NSTAGE * QT * XROW);
   float *s_sc = (float *)(s_ids + XT);
   int32_t *s_qrow = (int32_t *)(s_sc + XT);
   int32_t *s_orow = s_qrow + QT;
   int *s_cnt = s_orow + QT;
-  uint64_t *s_tau = (uint64_t *)(((uintptr_t)(s_cnt + QT) + 7) & ~(uintptr_t)7);
+  int *s_na = s_cnt + QT;
+  uint64_t *s_tau = (uint64_t *)(((uintptr_t)(s_na + QT) + 7) & ~(uintptr_t)7);
   uint64_t *s_buf = s_tau + QT;
   __shared__ int s_tile;
 
@@ -115,6 +154,7 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
       s_qrow[tid] = v ? (a.pair_q ? a.pair_q[p] : p) : -1;
       s_orow[tid] = v ? (a.pair_out ? a.pair_out[p] : p) : -1;
       s_cnt[tid] = 0;
+      s_na[tid] = 0;
       s_tau[tid] = KEY_MAX;
     }
     __syncthreads();
@@ -203,49 +243,68 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
         __syncthreads();
       }
 
-      // candidates of this chunk
+      // candidates of this chunk, appended in rounds of ROUND per query so a
+      // buffer of k + ROUND keys suffices; compaction runs between rounds
+      if (TOP1) {
 #pragma unroll
-      for (int j = 0; j < TQ; ++j) {
-        const int qi = tq + 16 * j;
-        if (qi < cnt) {
-          const uint64_t tau = s_tau[qi];
+        for (int j = 0; j < TQ; ++j) {
+          const int qi = tq + 16 * j;
+          if (qi < cnt) {
+            const uint64_t tau = s_tau[qi];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int m = tx + 16 * i;
-            if (m < nm) {
-              const uint64_t key = pack_key(acc[j][i], (uint32_t)s_ids[m]);
-              if (key < tau) {
-                if (TOP1) {
+            for (int i = 0; i < 8; ++i) {
+              const int m = tx + 16 * i;
+              if (m < nm) {
+                const uint64_t key = pack_key(acc[j][i], (uint32_t)s_ids[m]);
+                if (key < tau)
                   atomicMin((unsigned long long *)&s_tau[qi], (unsigned long long)key);
-                } else {
-                  const int pos = atomicAdd(&s_cnt[qi], 1);
-                  s_buf[qi * cap + pos] = key;
-                }
               }
             }
           }
         }
-      }
-      __syncthreads();
-      if (!TOP1) {
-        const bool last = c == nchunk - 1;
-        for (int qi = warp; qi < cnt; qi += THREADS / 32) {
-          const int n = s_cnt[qi];
-          if (n > cap - XT || (last && n > 0)) {
-            uint64_t *buf = s_buf + qi * cap;
-            warp_sort(buf, n);
-            const int keep = min(n, a.k);
-            if (lane == 0) {
-              s_cnt[qi] = keep;
-              s_tau[qi] = keep == a.k ? buf[a.k - 1] : KEY_MAX;
+        __syncthreads();
+      } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+          for (int j = 0; j < TQ; ++j) {
+            const int qi = tq + 16 * j;
+            if (qi < cnt) {
+              const uint64_t tau = s_tau[qi];
+#pragma unroll
+              for (int ii = 0; ii < 2; ++ii) {
+                const int m = tx + 16 * (2 * r + ii);
+                if (m < nm) {
+                  const uint64_t key = pack_key(acc[j][2 * r + ii], (uint32_t)s_ids[m]);
+                  if (key < tau) {
+                    const int pos = atomicAdd(&s_cnt[qi], 1);
+                    s_buf[qi * cap + pos] = key;
+                  }
+                }
+              }
             }
           }
+          __syncthreads();
+          const bool last = c == nchunk - 1 && r == 3;
+          for (int qi = warp; qi < cnt; qi += NWARP) {
+            const int n = s_cnt[qi];
+            const int na = s_na[qi];
+            if (n > cap - ROUND || (last && n > na)) {
+              uint64_t *buf = s_buf + qi * cap;
+              const int keep = compact_topk(buf, na, n, a.k, s_scratch + (size_t)warp * cap);
+              if (lane == 0) {
+                s_cnt[qi] = keep;
+                s_na[qi] = keep;
+                s_tau[qi] = keep == a.k ? buf[a.k - 1] : KEY_MAX;
+              }
+            }
+          }
+          __syncthreads();
         }
-        __syncthreads();
       }
     }
     // write the sorted per-(query, list) results
-    for (int qi = warp; qi < cnt; qi += THREADS / 32) {
+    for (int qi = warp; qi < cnt; qi += NWARP) {
       uint64_t *out = a.out_keys + (int64_t)s_orow[qi] * a.k;
       if (TOP1) {
         if (lane == 0) out[0] = s_tau[qi];
