@@ -164,6 +164,84 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
                       int d_s, int nprobe, int k, int storage, int rerank_k, int64_t *out_ids,
                       float *out_dist, int32_t *out_probes, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * AdANNS-OPQ on the d_s prefix and the AdANNS-IVFOPQ composite
+ * (Sec. 3 "OPQ": M sub-vectors, 2^8 codewords each, m bytes per vector,
+ * search by M codebook lookups, an orthonormal rotation R learned first;
+ * Sec. 4.2: OPQ on the first d_s coordinates of the MR, sub-vectors of
+ * d_s / M dimensions; Sec. 4.3 and Table "formula" IVFOPQ row: IVF at d_c
+ * with OPQ distances inside the probed lists, read as asymmetric lookup).
+ * Layouts: R is d_s x d_s row-major with z = x R (x a row vector);
+ * codebooks are M x 256 x (d_s / M) FP32; codes are N x M bytes.
+ * The vector quantised is z = P_ds(x) R (the prefix normalised under
+ * ADANNS_METRIC_L2_PREFIXNORM, raw under ADANNS_METRIC_L2).  d_s must be in G,
+ * M must divide d_s, d_s / M <= 64.
+ * ---------------------------------------------------------------------- */
+
+/* Encode n rows (ld floats each; first d_s used): codes[i][m] = the nearest
+ * codeword of subspace m to z_i (squared L2, ties to the smallest codeword). */
+int adanns_opq_encode(const float *x, int64_t n, int ld, int d_s, int M, int metric,
+                      const float *R, const float *codebooks, uint8_t *codes, void *cuda_stream);
+
+/* One PQ Lloyd update: codeword (m, c) becomes the FP64 mean of the
+ * subspace-m slices of the rows of z (n x d_s, already rotated) whose code is
+ * c, rounded to FP32; a codeword with no member keeps its value. */
+int adanns_pq_update(const float *z, int64_t n, int d_s, int M, const uint8_t *codes,
+                     float *codebooks, void *cuda_stream);
+
+/* Orthogonal Procrustes step of OPQ: R = argmin over orthogonal R of
+ * ||Y R - Zhat||_F, i.e. the orthogonal polar factor U V^T of Y^T Zhat
+ * (Y, Zhat: n x d_s FP32), computed by a Newton-Schulz polar iteration in
+ * FP32 until ||R^T R - I||_F < 1e-6.  Synchronises the stream.  Returns
+ * ADANNS_ERR_ARG if Y^T Zhat is zero. */
+int adanns_procrustes(const float *Y, const float *Zhat, int64_t n, int d_s, float *R,
+                      void *cuda_stream);
+
+/*
+ * Train OPQ on the index's vectors and encode all of them (AdANNS-OPQ).
+ *   db          the same N x d FP32 rows the index was built from (device).
+ *   Training rows: first train_n entries of a splitmix64(seed + 2) shuffle of
+ *   [0, N); Y = P_ds of those rows; R starts at I.  Each of opq_iters outer
+ *   iterations: Z = Y R; pq_iters Lloyd steps per subspace (Forgy init from
+ *   the rows at a splitmix64(seed + 3) shuffle of [0, train_n), codeword c
+ *   taking entry c mod min(256, train_n), on the first iteration; warm start
+ *   after); encode; R = Procrustes(Y, decode(codes)).  Then final_iters Lloyd
+ *   steps on Y R, and every database vector is encoded.
+ *   trace       optional HOST array of max(3 * opq_iters, 1) doubles: the mean
+ *               squared distortion after each half-step (after the Lloyd
+ *               steps, after the rotation update, after re-assigning under the
+ *               new rotation; non-increasing up to FP32 rounding).
+ * Synchronises the stream.  Replaces any OPQ data the index held.
+ */
+int adanns_build_opq(adanns_index *idx, const float *db, int d_s, int M, int opq_iters,
+                     int pq_iters, int final_iters, int64_t train_n, uint64_t seed, double *trace,
+                     void *cuda_stream);
+
+/* Attach given OPQ data (device): R, codebooks and codes indexed by database
+ * id (N x M); the codes are re-laid out in list order.  Synchronises. */
+int adanns_index_set_opq(adanns_index *idx, int d_s, int M, const float *R,
+                         const float *codebooks, const uint8_t *codes_by_id, void *cuda_stream);
+
+/* Copy the index's OPQ data out (device buffers; any may be NULL); codes in
+ * list order (row p belongs to the id at list position p).  ADANNS_ERR_STATE
+ * if the index has no OPQ data. */
+int adanns_index_get_opq(const adanns_index *idx, float *R, float *codebooks,
+                         uint8_t *codes_list_order, void *cuda_stream);
+
+/*
+ * AdANNS-IVFOPQ search: the nprobe nearest centroids at d_c (as in
+ * adanns_search_ivf); z = P_ds(q) R, LUT[m][c] = ||z_m - C_m[c]||^2; every
+ * member of the probed lists scores sum_m LUT[m][code[m]]; the k best by
+ * (score, id) are returned.  With rerank_k > 0 (k <= rerank_k <= 2048) the
+ * rerank_k best by score are re-scored with the exact FP32 dist_ds of the
+ * stored vectors and the k best of those are returned (Sec. 4.3
+ * shortlist-rerank).  Outputs as adanns_search_ivf.  ADANNS_ERR_STATE if the
+ * index has no OPQ data.
+ */
+int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                         int nprobe, int k, int rerank_k, int64_t *out_ids, float *out_dist,
+                         int32_t *out_probes, void *cuda_stream);
+
 /*
  * Size of the fixed device scratch array used by adanns_search_ivf_noalloc
  * (64 MiB, held on every GPU that loads this library until the process exits).

@@ -59,6 +59,13 @@ def lib():
         L.adanns_kmeans_assign.argtypes = [P, i64, i32, i32, i32, P, i32, P, P, P]
         L.adanns_kmeans_update.argtypes = [P, i64, i32, i32, i32, P, i32, P, P]
         L.adanns_search_ivf.argtypes = [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, P, P]
+        L.adanns_opq_encode.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P]
+        L.adanns_pq_update.argtypes = [P, i64, i32, i32, P, P, P]
+        L.adanns_procrustes.argtypes = [P, P, i64, i32, P, P]
+        L.adanns_build_opq.argtypes = [P, P, i32, i32, i32, i32, i32, i64, u64, P, P]
+        L.adanns_index_set_opq.argtypes = [P, i32, i32, P, P, P, P]
+        L.adanns_index_get_opq.argtypes = [P, P, P, P, P]
+        L.adanns_search_ivfopq.argtypes = [P, P, i64, i32, i32, i32, i32, P, P, P, P]
         _lib = L
     return _lib
 
@@ -215,4 +222,87 @@ def search_ivf(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: 
     probes = torch.empty(B, nprobe, dtype=torch.int32, device=queries.device) if return_probes else None
     _check(lib().adanns_search_ivf(index.handle, _ptr(queries), B, d_c, d_s, nprobe, k, storage,
                                    rerank_k, _ptr(ids), _ptr(dist), _ptr(probes), _stream()))
+    return (ids, dist, probes) if return_probes else (ids, dist)
+
+
+# ---------------------------------------------------------------- OPQ / IVF-OPQ
+def opq_encode(x: torch.Tensor, d_s: int, M: int, R: torch.Tensor, codebooks: torch.Tensor,
+               metric: int = METRIC_L2_PREFIXNORM) -> torch.Tensor:
+    """codes uint8 [n, M] of z = P_ds(x) R under the given rotation / codebooks."""
+    _need(x, torch.float32, "x", 2)
+    _need(R, torch.float32, "R", 2)
+    _need(codebooks, torch.float32, "codebooks", 3)
+    codes = torch.empty(x.shape[0], M, dtype=torch.uint8, device=x.device)
+    _check(lib().adanns_opq_encode(_ptr(x), x.shape[0], x.shape[1], d_s, M, metric, _ptr(R),
+                                   _ptr(codebooks), _ptr(codes), _stream()))
+    return codes
+
+
+def pq_update(z: torch.Tensor, codes: torch.Tensor, codebooks: torch.Tensor) -> torch.Tensor:
+    """One PQ Lloyd update in place on codebooks [M, 256, d_s/M]; returns it."""
+    _need(z, torch.float32, "z", 2)
+    _need(codes, torch.uint8, "codes", 2)
+    _need(codebooks, torch.float32, "codebooks", 3)
+    _check(lib().adanns_pq_update(_ptr(z), z.shape[0], z.shape[1], codes.shape[1], _ptr(codes),
+                                  _ptr(codebooks), _stream()))
+    return codebooks
+
+
+def procrustes(Y: torch.Tensor, Zhat: torch.Tensor) -> torch.Tensor:
+    """Orthogonal R minimising ||Y R - Zhat||_F (polar factor of Y^T Zhat)."""
+    _need(Y, torch.float32, "Y", 2)
+    _need(Zhat, torch.float32, "Zhat", 2)
+    d = Y.shape[1]
+    R = torch.empty(d, d, dtype=torch.float32, device=Y.device)
+    _check(lib().adanns_procrustes(_ptr(Y), _ptr(Zhat), Y.shape[0], d, _ptr(R), _stream()))
+    return R
+
+
+def build_opq(index: Index, db: torch.Tensor, d_s: int, M: int, opq_iters: int, pq_iters: int,
+              final_iters: int, train_n: int, seed: int) -> list:
+    """Train AdANNS-OPQ on the d_s prefix and encode the index; returns the trace."""
+    _need(db, torch.float32, "db", 2)
+    tr = (ctypes.c_double * max(3 * opq_iters, 1))()
+    _check(lib().adanns_build_opq(index.handle, _ptr(db), d_s, M, opq_iters, pq_iters, final_iters,
+                                  train_n, seed, tr, _stream()))
+    index.opq = (d_s, M)
+    return list(tr)
+
+
+def set_opq(index: Index, d_s: int, M: int, R: torch.Tensor, codebooks: torch.Tensor,
+            codes_by_id: torch.Tensor):
+    """Attach OPQ data (codes indexed by database id)."""
+    _need(R, torch.float32, "R", 2)
+    _need(codebooks, torch.float32, "codebooks", 3)
+    _need(codes_by_id, torch.uint8, "codes", 2)
+    _check(lib().adanns_index_set_opq(index.handle, d_s, M, _ptr(R), _ptr(codebooks),
+                                      _ptr(codes_by_id), _stream()))
+    index.opq = (d_s, M)
+
+
+def get_opq(index: Index):
+    """(R, codebooks, codes in list order) of the index's OPQ data."""
+    d_s, M = index.opq
+    R = torch.empty(d_s, d_s, dtype=torch.float32, device="cuda")
+    C = torch.empty(M, 256, d_s // M, dtype=torch.float32, device="cuda")
+    codes = torch.empty(index.N, M, dtype=torch.uint8, device="cuda")
+    _check(lib().adanns_index_get_opq(index.handle, _ptr(R), _ptr(C), _ptr(codes), _stream()))
+    return R, C, codes
+
+
+def search_ivfopq(index: Index, queries: torch.Tensor, d_c: int, nprobe: int, k: int,
+                  rerank_k: int = 0, return_probes: bool = False, out: tuple | None = None):
+    """AdANNS-IVFOPQ search -> (ids int64 [B,k], dist f32 [B,k][, probes])."""
+    _need(queries, torch.float32, "queries", 2)
+    if queries.shape[1] != index.d:
+        raise ValueError(f"queries must have {index.d} columns")
+    B = queries.shape[0]
+    if out is None:
+        ids = torch.empty(B, k, dtype=torch.int64, device=queries.device)
+        dist = torch.empty(B, k, dtype=torch.float32, device=queries.device)
+    else:
+        ids, dist = out
+    probes = torch.empty(B, nprobe, dtype=torch.int32, device=queries.device) if return_probes else None
+    _check(lib().adanns_search_ivfopq(index.handle, _ptr(queries), B, d_c, nprobe, k, rerank_k,
+                                      _ptr(ids), _ptr(dist), _ptr(probes), _stream()))
     return (ids, dist, probes) if return_probes else (ids, dist)

@@ -54,6 +54,11 @@ void free_index(adanns_index *x) {
   cudaFree(x->list_ids);
   cudaFree(x->xpm);
   cudaFree(x->invn);
+  cudaFree(x->assign);
+  cudaFree(x->pos_of_id);
+  cudaFree(x->opq_R);
+  cudaFree(x->opq_C);
+  cudaFree(x->codes);
   delete[] x->h_list_off;
   delete x;
 }
@@ -161,7 +166,8 @@ int make_index(const float *db, int64_t N, int d, const float *centroids, int nl
       (rc = make_cent_off(&x->cent_off, nlist, st)) ||
       (rc = dmalloc(&x->list_off, (size_t)nlist + 1)) || (rc = dmalloc(&x->list_ids, (size_t)N)) ||
       (rc = dmalloc(&x->xpm, (size_t)N * x->d_pad)) ||
-      (rc = dmalloc(&x->invn, (size_t)std::max(x->ng, 1) * N))) {
+      (rc = dmalloc(&x->invn, (size_t)std::max(x->ng, 1) * N)) ||
+      (rc = dmalloc(&x->assign, (size_t)N)) || (rc = dmalloc(&x->pos_of_id, (size_t)N))) {
     free_index(x);
     return rc;
   }
@@ -180,6 +186,10 @@ int make_index(const float *db, int64_t N, int d, const float *centroids, int nl
     return bail(rc);
   if ((rc = launch_inv_norms(db, d, d, x->list_ids, N, metric, x->invn, x->ng, st)))
     return bail(rc);
+  if (cudaMemcpyAsync(x->assign, assign, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "copy assignment"));
+  if ((rc = launch_positions(x->list_ids, N, x->pos_of_id, st))) return bail(rc);
   x->h_list_off = new int64_t[nlist + 1];
   if (cudaMemcpyAsync(x->h_list_off, x->list_off, sizeof(int64_t) * (nlist + 1),
                       cudaMemcpyDeviceToHost, st) != cudaSuccess)

@@ -351,6 +351,20 @@ int launch_prefix_major(const float *x, int ld, int d, int d_pad, const int64_t 
   return ADANNS_OK;
 }
 
+// pos[list_ids[p]] = p
+__global__ void positions_kernel(const int32_t *__restrict__ list_ids, int64_t N,
+                                 int32_t *__restrict__ pos) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N) pos[list_ids[p]] = (int32_t)p;
+}
+
+int launch_positions(const int32_t *list_ids, int64_t N, int32_t *pos, cudaStream_t st) {
+  if (N <= 0) return ADANNS_OK;
+  positions_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(list_ids, N, pos);
+  ADN_LAUNCH("positions_kernel");
+  return ADANNS_OK;
+}
+
 // invn[g][p] = 1 / ||x[list_ids[p]][0:G[g]]|| (0 for a zero prefix; 1 for raw L2)
 __global__ void inv_norms_kernel(const float *__restrict__ x, int ld, int d,
                                  const int32_t *__restrict__ list_ids, int64_t N, int metric,

@@ -127,12 +127,16 @@ int launch_inv_norms(const float *x, int ld, int d, const int32_t *list_ids, int
 int launch_kmeans_update(const float *t, int64_t n, int ld, int dim, const int32_t *assign,
                          int nc, double *sums, int32_t *counts, float *cent, cudaStream_t st);
 int launch_sum_keys(const uint64_t *keys, int64_t n, double *out, cudaStream_t st);
+int launch_positions(const int32_t *list_ids, int64_t N, int32_t *pos, cudaStream_t st);
 int check_assignment(const int32_t *a, int64_t n, int nlist, cudaStream_t st);
 int build_csr(const int32_t *assign, int64_t N, int nlist, int64_t *list_off, int32_t *list_ids,
               cudaStream_t st);
 
 // ---------------------------------------------------------------- profiling
-enum Stage { ST_PREP = 0, ST_COARSE = 1, ST_INVERT = 2, ST_SCAN = 3, ST_MERGE = 4, ST_NSTAGE = 16 };
+enum Stage {
+  ST_PREP = 0, ST_COARSE = 1, ST_INVERT = 2, ST_SCAN = 3, ST_MERGE = 4, ST_LUT = 5, ST_ADC = 6,
+  ST_RERANK = 7, ST_NSTAGE = 16
+};
 // Records an event pair around its scope on `st` when profiling is enabled.
 class StageTimer {
  public:
@@ -160,5 +164,12 @@ struct adanns_index {
   float *xpm = nullptr;         // prefix-major FP32 vectors
   float *invn = nullptr;        // [ng][N] inverse prefix norms in list order
   int ng = 0;
+  int32_t *assign = nullptr;    // list of each id (N)
+  int32_t *pos_of_id = nullptr; // list-order position of each id (N)
+  // OPQ on the d_s prefix (adanns_build_opq / adanns_index_set_opq)
+  int opq_ds = 0, opq_M = 0;
+  float *opq_R = nullptr;       // d_s x d_s, z = x R
+  float *opq_C = nullptr;       // M x 256 x (d_s / M)
+  uint8_t *codes = nullptr;     // N x M, list order
   int64_t *h_list_off = nullptr;  // host copy of list offsets
 };

@@ -1,0 +1,189 @@
+"""GPU-vs-oracle parity for AdANNS-OPQ and AdANNS-IVFOPQ.
+
+Encoding, the PQ update and the Procrustes step are teacher-forced from the
+oracle's values; the search runs on the oracle's index and OPQ data imported
+to the GPU, so both sides look up the same codes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+from parity import ambiguous_probe_rows, check_topk, recall, tol
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PN = oracle.METRIC_L2_PREFIXNORM
+
+
+@pytest.fixture(scope="module")
+def A():
+    import paper_2305_19435_gb300 as P
+    P.build()
+    assert torch.cuda.is_available()
+    return P
+
+
+def cu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.fixture(scope="module")
+def case():
+    data = synthdata.small(12_000, 300, 96, 48, 301)
+    db = data["db"]
+    idx = oracle.build_ivf(db, 32, 24, 6, 12_000, seed=9)
+    out = {"data": data, "idx": idx}
+    for d_s, M in ((64, 16), (96, 32), (48, 16), (32, 4)):
+        opq = oracle.train_opq(db, d_s, M, 3, 3, 5, 4000, seed=13)
+        codes = oracle.pq_encode(db, d_s, M, opq["R"], opq["codebooks"])
+        out[(d_s, M)] = (opq, codes)
+    return out
+
+
+def gpu_index(A, case, d_s, M):
+    data, o = case["data"], case["idx"]
+    opq, codes = case[(d_s, M)]
+    g = A.index_create(cu(data["db"]), cu(o["centroids"]), cu(o["assign"].astype(np.int32)))
+    A.set_opq(g, d_s, M, cu(opq["R"]), cu(opq["codebooks"]), cu(codes))
+    return g
+
+
+@pytest.mark.parametrize("d_s,M", [(64, 16), (96, 32), (48, 16), (32, 4)])
+def test_encode_matches_oracle(A, case, d_s, M):
+    db = case["data"]["db"][:3000]
+    opq, codes = case[(d_s, M)]
+    got = A.opq_encode(cu(db), d_s, M, cu(opq["R"]), cu(opq["codebooks"])).cpu().numpy()
+    Z = oracle.prefix(db, d_s) @ opq["R"].astype(np.float64)
+    C = opq["codebooks"].astype(np.float64)
+    dsub = d_s // M
+    for m in range(M):
+        D = ((Z[:, None, m * dsub:(m + 1) * dsub] - C[m][None]) ** 2).sum(-1)
+        srt = np.sort(D, axis=1)
+        tied = srt[:, 1] - srt[:, 0] <= tol(srt[:, 1])
+        assert tied.mean() < 0.01
+        assert np.array_equal(got[~tied, m], codes[:3000][~tied, m]), m
+
+
+def test_pq_update_matches_oracle(A, case):
+    opq, codes = case[(64, 16)]
+    db = case["data"]["db"][:5000]
+    Z = (oracle.prefix(db, 64) @ opq["R"].astype(np.float64)).astype(np.float32)
+    C0 = opq["codebooks"].copy()
+    got = A.pq_update(cu(Z), cu(codes[:5000]), cu(C0.copy())).cpu().numpy()
+    for m in range(16):
+        want = oracle.update(Z[:, 4 * m:4 * m + 4].astype(np.float64), codes[:5000, m].astype(np.int32),
+                             C0[m].astype(np.float64))
+        assert np.all(np.abs(got[m] - want) <= 1e-6 * np.abs(want) + 1e-8)
+
+
+def test_procrustes_matches_oracle(A):
+    rng = np.random.default_rng(5)
+    Y = rng.standard_normal((4096, 48)) * np.linspace(1.0, 0.3, 48)
+    Q = np.linalg.qr(rng.standard_normal((48, 48)))[0]
+    Zh = Y @ Q + 0.05 * rng.standard_normal((4096, 48))
+    Y32, Z32 = Y.astype(np.float32), Zh.astype(np.float32)
+    R = A.procrustes(cu(Y32), cu(Z32)).cpu().numpy().astype(np.float64)
+    Ro = oracle.procrustes(Y32.astype(np.float64), Z32.astype(np.float64))
+    assert np.abs(R.T @ R - np.eye(48)).max() < 1e-5
+    assert np.abs(R - Ro).max() < 1e-4
+    fo = ((Y32 @ Ro - Z32) ** 2).sum()
+    fg = ((Y32 @ R - Z32) ** 2).sum()
+    assert abs(fg - fo) <= 1e-6 * fo
+
+
+@pytest.mark.parametrize("d_s,M,nprobe,k", [(64, 16, 4, 20), (96, 32, 8, 100), (48, 16, 2, 10),
+                                            (32, 4, 24, 50)])
+def test_ivfopq_search_parity(A, case, d_s, M, nprobe, k):
+    data, o = case["data"], case["idx"]
+    opq, codes = case[(d_s, M)]
+    g = gpu_index(A, case, d_s, M)
+    q = data["queries"]
+    gi, gd, gp = A.search_ivfopq(g, cu(q), 32, nprobe, k, return_probes=True)
+    gi, gd, gp = gi.cpu().numpy(), gd.cpu().numpy(), gp.cpu().numpy()
+    orr = oracle.search_ivfopq(data["db"], o, opq, codes, q, 32, nprobe, k + 40)
+    amb = ambiguous_probe_rows(orr["probe_dist"], nprobe)
+    for i in np.nonzero(~amb)[0]:
+        assert set(gp[i]) == set(orr["probes"][i])
+    n, fails = check_topk(gi, gd, orr["ids"], orr["dist"], k, skip_rows=amb)
+    assert not fails, f"{len(fails)}/{n}: {fails[:2]}"
+    g.free()
+
+
+@pytest.mark.parametrize("d_s,M,nprobe,k,kr", [(64, 16, 4, 10, 40), (96, 32, 8, 20, 80),
+                                               (32, 4, 2, 10, 2048)])
+def test_ivfopq_rerank_parity(A, case, d_s, M, nprobe, k, kr):
+    data, o = case["data"], case["idx"]
+    opq, codes = case[(d_s, M)]
+    g = gpu_index(A, case, d_s, M)
+    q = data["queries"]
+    gi, gd = A.search_ivfopq(g, cu(q), 32, nprobe, k, rerank_k=kr)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    orr = oracle.search_ivfopq(data["db"], o, opq, codes, q, 32, nprobe, k + 20, rerank_k=kr)
+    adc = oracle.search_ivfopq(data["db"], o, opq, codes, q, 32, nprobe, kr + 1)
+    # the shortlist is ambiguous when the ADC scores at ranks kr-1 and kr are
+    # nearly but not exactly equal (identical codes tie exactly on both sides
+    # and are ordered by id on both)
+    a, b = adc["dist"][:, kr - 1], adc["dist"][:, kr]
+    near = np.isfinite(b) & (b - a > 0) & (b - a <= tol(b))
+    amb = ambiguous_probe_rows(adc["probe_dist"], nprobe) | near
+    n, fails = check_topk(gi, gd, orr["ids"], orr["dist"], k, skip_rows=amb)
+    assert n > 0.8 * len(q)
+    assert not fails, f"{len(fails)}/{n}: {fails[:2]}"
+    # reranking every candidate equals the exact IVF search
+    if kr >= 2048:
+        exact = oracle.search_ivf(data["db"], o, q, 32, d_s, nprobe, k + 20)
+        n, fails = check_topk(gi, gd, exact["ids"], exact["dist"], k, skip_rows=amb)
+        assert not fails
+    g.free()
+
+
+def test_build_opq_trace_and_codes(A, case):
+    data, o = case["data"], case["idx"]
+    g = A.index_create(cu(data["db"]), cu(o["centroids"]), cu(o["assign"].astype(np.int32)))
+    tr = np.array(A.build_opq(g, cu(data["db"]), 64, 16, 3, 3, 5, 4000, 13))
+    opq, _ = case[(64, 16)]
+    to = np.array(opq["trace"])
+    assert tr.shape == to.shape
+    assert np.all(tr[1:] <= tr[:-1] * (1 + 1e-5))
+    assert abs(tr[0] - to[0]) <= 1e-4 * to[0]          # same sample, same init
+    assert abs(tr[-1] - to[-1]) <= 2e-2 * to[-1]        # free-running: close, not equal
+    R, C, codes_lo = A.get_opq(g)
+    R = R.cpu().numpy().astype(np.float64)
+    assert np.abs(R.T @ R - np.eye(64)).max() < 1e-5
+    # the stored codes are the nearest codewords under the GPU's own R, C
+    off, ids = g.lists()
+    ids = ids.cpu().numpy()
+    sub = ids[:2000]
+    Z = oracle.prefix(data["db"][sub], 64) @ R
+    Cg = C.cpu().numpy().astype(np.float64)
+    cl = codes_lo.cpu().numpy()[:2000]
+    for m in range(16):
+        D = ((Z[:, None, 4 * m:4 * m + 4] - Cg[m][None]) ** 2).sum(-1)
+        srt = np.sort(D, axis=1)
+        tied = srt[:, 1] - srt[:, 0] <= tol(srt[:, 1])
+        assert np.array_equal(cl[~tied, m], np.argmin(D, axis=1)[~tied])
+    # and the GPU-trained index searches close to the oracle-trained one
+    gi, _ = A.search_ivfopq(g, cu(data["queries"]), 32, 8, 10, rerank_k=100)
+    exact = oracle.search_ivf(data["db"], o, data["queries"], 32, 64, 8, 10)
+    assert recall(gi.cpu().numpy(), exact["ids"], 10) > 0.9
+    g.free()
+
+
+def test_opq_errors(A, case):
+    data, o = case["data"], case["idx"]
+    g = A.index_create(cu(data["db"]), cu(o["centroids"]), cu(o["assign"].astype(np.int32)))
+    q = cu(data["queries"][:4])
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivfopq(g, q, 32, 4, 10)         # no OPQ data yet
+    assert e.value.code == -6
+    opq, codes = case[(64, 16)]
+    with pytest.raises(A.AdannsError) as e:
+        A.set_opq(g, 64, 7, cu(opq["R"]), cu(opq["codebooks"]), cu(codes))   # M does not divide
+    assert e.value.code == -1
+    A.set_opq(g, 64, 16, cu(opq["R"]), cu(opq["codebooks"]), cu(codes))
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivfopq(g, q, 32, 4, 10, rerank_k=5)   # shortlist shorter than k
+    assert e.value.code == -1
+    g.free()
