@@ -48,8 +48,13 @@ extern "C" {
 #define ADANNS_METRIC_L2 0
 #define ADANNS_METRIC_L2_PREFIXNORM 1
 
-/* storage tiers of the database vectors (bit mask for builders) */
+/* storage tiers of the database vectors (bit mask for builders; one value for
+ * search).  F32 is always kept (the exact scan and the rerank read it).  BF16
+ * and FP8-E4M3 copies store x / s_x per vector with s_x = max_j |x_j| / R
+ * (R = 1 for BF16, 448 for FP8-E4M3) in the same prefix-major list layout. */
 #define ADANNS_STORE_F32 1
+#define ADANNS_STORE_BF16 2
+#define ADANNS_STORE_FP8E4M3 4
 
 typedef struct adanns_index adanns_index; /* opaque; device memory owned by the library */
 
@@ -152,8 +157,19 @@ int adanns_kmeans_update(const float *points, int64_t n, int ld, int dim, int me
  *   result: the k nearest members of those lists to q by dist_ds, then id.
  *   queries  B x d FP32 (device); d_c must equal the index's d_c; d_s in G,
  *            d_s <= d; 1 <= nprobe <= nlist; 1 <= k <= 1024.
- *   storage  ADANNS_STORE_F32 (the exact FP32 scan).
- *   rerank_k must be 0 for ADANNS_STORE_F32.
+ *   storage  ADANNS_STORE_F32: the exact FP32 scan (rerank_k must be 0).
+ *            ADANNS_STORE_BF16 / ADANNS_STORE_FP8E4M3 (tier built into the
+ *            index, metric ADANNS_METRIC_L2_PREFIXNORM, nprobe <= 128): the
+ *            probed lists are scanned on the tensor cores with FP32
+ *            accumulation, giving approximate distances
+ *            |P(q)|^2 + |P(x)|^2 - 2 s_q s_x nu_x (q_low . x_low); the
+ *            rerank_k (k <= rerank_k <= 2048) best of those are re-scored
+ *            with the exact FP32 dist_ds (Sec. 4.3 shortlist-rerank) and the
+ *            k best by (distance, id) are returned -- the returned distances
+ *            are exact; ids can differ from the FP32 scan where the exact
+ *            top-k was not in the approximate shortlist.  This variant
+ *            synchronises the stream once, at the end, to report a
+ *            tensor-core pipeline timeout as ADANNS_ERR_TIMEOUT.
  *   out_ids  int64 [B x k], out_dist FP32 [B x k] (device, caller-owned).
  *   out_probes optional int32 [B x nprobe]: the probed lists, nearest first.
  * Scratch memory is taken from the CUDA stream-ordered allocator and returned

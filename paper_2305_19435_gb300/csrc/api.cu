@@ -59,6 +59,11 @@ void free_index(adanns_index *x) {
   cudaFree(x->opq_R);
   cudaFree(x->opq_C);
   cudaFree(x->codes);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(x->lowp[i]);
+    cudaFree(x->lowp_sx[i]);
+    cudaFree(x->lowp_cx[i]);
+  }
   delete[] x->h_list_off;
   delete x;
 }
@@ -190,6 +195,8 @@ int make_index(const float *db, int64_t N, int d, const float *centroids, int nl
       cudaSuccess)
     return bail(cuda_fail(cudaGetLastError(), "copy assignment"));
   if ((rc = launch_positions(x->list_ids, N, x->pos_of_id, st))) return bail(rc);
+  if ((storage & ADANNS_STORE_BF16) && (rc = build_lowp(x, db, 0, st))) return bail(rc);
+  if ((storage & ADANNS_STORE_FP8E4M3) && (rc = build_lowp(x, db, 1, st))) return bail(rc);
   x->h_list_off = new int64_t[nlist + 1];
   if (cudaMemcpyAsync(x->h_list_off, x->list_off, sizeof(int64_t) * (nlist + 1),
                       cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -378,7 +385,19 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
   if ((rc = check_gran(d_s, idx->d, "d_s"))) return rc;
   if (nprobe < 1 || nprobe > idx->nlist) return fail(ADANNS_ERR_ARG, "need 1 <= nprobe <= nlist");
   if (k < 1 || k > 1024) return fail(ADANNS_ERR_ARG, "need 1 <= k <= 1024");
-  if (storage != ADANNS_STORE_F32) return fail(ADANNS_ERR_STATE, "storage tier not available");
+  if (storage == ADANNS_STORE_BF16 || storage == ADANNS_STORE_FP8E4M3) {
+    const int which = storage == ADANNS_STORE_BF16 ? 0 : 1;
+    if (!idx->lowp[which]) return fail(ADANNS_ERR_STATE, "the index has no such storage tier");
+    if (idx->metric != ADANNS_METRIC_L2_PREFIXNORM)
+      return fail(ADANNS_ERR_STATE, "low-precision search needs the prefix-normalised metric");
+    if (rerank_k < k || rerank_k > 2048)
+      return fail(ADANNS_ERR_ARG, "low-precision search needs k <= rerank_k <= 2048");
+    if (nprobe > 128) return fail(ADANNS_ERR_ARG, "low-precision search needs nprobe <= 128");
+    if (B == 0) return ADANNS_OK;
+    return search_mixed(idx, queries, B, d_c, d_s, nprobe, k, which, rerank_k, out_ids, out_dist,
+                        out_probes, S(cuda_stream));
+  }
+  if (storage != ADANNS_STORE_F32) return fail(ADANNS_ERR_ARG, "unknown storage tier");
   if (rerank_k != 0) return fail(ADANNS_ERR_ARG, "rerank_k must be 0 for the FP32 scan");
   if (B == 0) return ADANNS_OK;
   cudaStream_t st = S(cuda_stream);

@@ -8,6 +8,8 @@
 
 #include "../../include/adanns.h"
 
+struct adanns_index;
+
 namespace adn {
 
 constexpr uint64_t KEY_MAX = ~0ull;  // empty slot / padding key
@@ -135,7 +137,25 @@ int build_csr(const int32_t *assign, int64_t N, int nlist, int64_t *list_off, in
 // ---------------------------------------------------------------- profiling
 enum Stage {
   ST_PREP = 0, ST_COARSE = 1, ST_INVERT = 2, ST_SCAN = 3, ST_MERGE = 4, ST_LUT = 5, ST_ADC = 6,
-  ST_RERANK = 7, ST_NSTAGE = 16
+  ST_RERANK = 7, ST_MMA = 8, ST_SELECT = 9, ST_NSTAGE = 16
+};
+
+// Tensor-core list scan of the mixed-precision path (mma_scan.cu).
+struct MmaScanArgs {
+  const int32_t *tile_list, *tile_beg, *tile_cnt;
+  const int *ntiles_dev;
+  const int64_t *list_off;
+  const int32_t *pair_out;   // pair index (q * nprobe + slot) of each tile row
+  const int64_t *pbase;      // candidate segment start of each pair (multiple of 8)
+  const float *cx;           // per member (list order): s_x * nu_x(d_s), 0 for a zero prefix
+  const float *qn2;          // per query: |P_ds(q)|^2
+  const float *qsc;          // per query: operand scale s_q
+  int nprobe;
+  int nkb;                   // K-blocks of the d_s prefix
+  int d_blocks;              // storage blocks per vector
+  uint16_t *cand;            // FP16 bits of the approximate distances
+  int *err;
+  int fp8;
 };
 // Records an event pair around its scope on `st` when profiling is enabled.
 class StageTimer {
@@ -148,6 +168,11 @@ class StageTimer {
   cudaStream_t st_;
   cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
+
+int build_lowp(adanns_index *x, const float *db, int which, cudaStream_t st);
+int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
+                 int nprobe, int k, int which, int kk, int64_t *out_ids, float *out_dist,
+                 int32_t *out_probes, cudaStream_t st);
 
 }  // namespace adn
 
@@ -171,5 +196,10 @@ struct adanns_index {
   float *opq_R = nullptr;       // d_s x d_s, z = x R
   float *opq_C = nullptr;       // M x 256 x (d_s / M)
   uint8_t *codes = nullptr;     // N x M, list order
+  // low-precision tiers [0] BF16 (64-dim blocks), [1] FP8-E4M3 (128-dim blocks)
+  void *lowp[2] = {nullptr, nullptr};
+  int lowp_blocks[2] = {0, 0};
+  float *lowp_sx[2] = {nullptr, nullptr};  // per-vector scale, list order
+  float *lowp_cx[2] = {nullptr, nullptr};  // [ng][N] scale * inverse prefix norm
   int64_t *h_list_off = nullptr;  // host copy of list offsets
 };

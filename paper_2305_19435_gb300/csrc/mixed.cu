@@ -1,0 +1,428 @@
+// Mixed-precision AdANNS-IVF search: BF16 / FP8-E4M3 storage with a per-vector
+// FP32 scale, tensor-core approximate scan, per-query top-k' selection and the
+// exact FP32 rerank of the k' shortlist at d_s (Sec. 4.3 shortlist-rerank; the
+// shortlist size k' is the caller's rerank_k, 4k in the benchmark).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+
+#include "devutil.cuh"
+#include "internal.cuh"
+
+namespace adn {
+
+int launch_rerank(const int64_t *cand, int kr, int64_t B, const float *qs, int ldq, int d_s,
+                  const adanns_index *idx, const float *mscale, int k, int64_t *out_ids,
+                  float *out_dist, cudaStream_t st);
+
+// ---------------------------------------------------------------- storage
+// Member p (list order) of list l: s_x = max_j |x_j| / R (R = 448 for FP8-E4M3,
+// 1 for BF16; 1 for a zero vector); element j of block b is stored at
+// ((off_l * nblk + b * n_l + m) * epb + j % epb), value x_j / s_x rounded.
+__global__ void quantize_kernel(const float *__restrict__ x, int d, const int64_t *__restrict__ list_off,
+                                const int32_t *__restrict__ list_ids,
+                                const int32_t *__restrict__ assign, int64_t N, int fp8, int nblk,
+                                unsigned char *__restrict__ out, float *__restrict__ sx) {
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= N) return;
+  const int id = list_ids[p];
+  const int l = assign[id];
+  const int64_t off = list_off[l];
+  const int64_t nl = list_off[l + 1] - off;
+  const int64_t m = p - off;
+  const float *src = x + (int64_t)id * d;
+  float mx = 0.f;
+  for (int j = lane; j < d; j += 32) mx = fmaxf(mx, fabsf(src[j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float R = fp8 ? 448.f : 1.f;
+  const float s = mx > 0.f ? mx / R : 1.f;
+  if (lane == 0) sx[p] = s;
+  const int epb = fp8 ? 128 : 64;
+  for (int j = lane; j < nblk * epb; j += 32) {
+    const float v = j < d ? src[j] / s : 0.f;
+    const int b = j / epb, e = j - b * epb;
+    const int64_t o = ((off * nblk + b * nl + m) * epb + e);
+    if (fp8) {
+      out[o] = (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    } else {
+      ((__nv_bfloat16 *)out)[o] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// cx[g][p] = s_x[p] * invn[g][p]
+__global__ void lowp_scale_kernel(const float *__restrict__ sx, const float *__restrict__ invn,
+                                  int64_t N, int ng, float *__restrict__ cx) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * ng) return;
+  cx[e] = sx[e % N] * invn[e];
+}
+
+int build_lowp(adanns_index *x, const float *db, int which, cudaStream_t st) {
+  const int fp8 = which == 1;
+  const int epb = fp8 ? 128 : 64;
+  const int nblk = (x->d + epb - 1) / epb;
+  const size_t elems = (size_t)x->N * nblk * epb;
+  const size_t bytes = elems * (fp8 ? 1 : 2);
+  void *store = nullptr;
+  float *sx = nullptr, *cx = nullptr;
+  if (cudaMalloc(&store, bytes + 256) != cudaSuccess || cudaMalloc(&sx, sizeof(float) * x->N) != cudaSuccess ||
+      cudaMalloc(&cx, sizeof(float) * (size_t)x->N * std::max(x->ng, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(store);
+    cudaFree(sx);
+    cudaFree(cx);
+    return fail(ADANNS_ERR_OOM, "low-precision storage allocation failed");
+  }
+  quantize_kernel<<<(unsigned)((x->N + 7) / 8), 256, 0, st>>>(
+      db, x->d, x->list_off, x->list_ids, x->assign, x->N, fp8, nblk, (unsigned char *)store, sx);
+  ADN_LAUNCH("quantize_kernel");
+  const int64_t ne = x->N * (int64_t)x->ng;
+  if (ne > 0) {
+    lowp_scale_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(sx, x->invn, x->N, x->ng, cx);
+    ADN_LAUNCH("lowp_scale_kernel");
+  }
+  x->lowp[which] = store;
+  x->lowp_blocks[which] = nblk;
+  x->lowp_sx[which] = sx;
+  x->lowp_cx[which] = cx;
+  return ADANNS_OK;
+}
+
+// ---------------------------------------------------------------- queries
+// Per query (one warp): |P_ds(q)|^2, s_q = max|q| / R, and the low-precision
+// row q / s_q (nkb blocks of epb elements, zero beyond d_s).
+__global__ void prep_lowp_kernel(const float *__restrict__ qs, int ldq, int64_t B, int d_s,
+                                 int fp8, int nkb, unsigned char *__restrict__ out,
+                                 float *__restrict__ qn2, float *__restrict__ qsc) {
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= B) return;
+  const float *src = qs + q * ldq;
+  float s2 = 0.f, mx = 0.f;
+  for (int j = lane; j < d_s; j += 32) {
+    const float v = src[j];
+    s2 = fmaf(v, v, s2);
+    mx = fmaxf(mx, fabsf(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const float R = fp8 ? 448.f : 1.f;
+  const float s = mx > 0.f ? mx / R : 1.f;
+  if (lane == 0) {
+    qn2[q] = s2;
+    qsc[q] = s;
+  }
+  const int epb = fp8 ? 128 : 64;
+  const int len = nkb * epb;
+  for (int j = lane; j < len; j += 32) {
+    const float v = j < d_s ? src[j] / s : 0.f;
+    if (fp8)
+      out[q * len + j] = (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    else
+      ((__nv_bfloat16 *)out)[q * len + j] = __float2bfloat16_rn(v);
+  }
+}
+
+// Qt[t][kb][r][0:128 B] = row pair_q[tile_beg[t] + r] of the low-precision
+// queries at block kb (zero rows past the tile's count); grid (max_tiles, nkb).
+__global__ void gather_qtiles_kernel(const unsigned char *__restrict__ qlow, int nkb,
+                                     const int32_t *__restrict__ tile_beg,
+                                     const int32_t *__restrict__ tile_cnt,
+                                     const int *__restrict__ ntiles,
+                                     const int32_t *__restrict__ pair_q,
+                                     unsigned char *__restrict__ qt) {
+  const int t = blockIdx.x, kb = blockIdx.y;
+  if (t >= *ntiles) return;
+  const int beg = tile_beg[t], cnt = tile_cnt[t];
+  uint4 *dst = (uint4 *)(qt + (((int64_t)t * nkb + kb) * 128) * 128);
+  for (int e = threadIdx.x; e < 128 * 8; e += blockDim.x) {
+    const int r = e >> 3, c = e & 7;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (r < cnt) {
+      const int q = pair_q[beg + r];
+      v = ((const uint4 *)(qlow + ((int64_t)q * nkb + kb) * 128))[c];
+    }
+    dst[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------- candidate segments
+// qtot[q] = sum over slots of the list size rounded up to 8
+__global__ void cand_count_kernel(const uint64_t *__restrict__ ckeys, int64_t B, int nprobe,
+                                  const int64_t *__restrict__ list_off,
+                                  int64_t *__restrict__ qtot) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B) return;
+  int64_t t = 0;
+  for (int s = 0; s < nprobe; ++s) {
+    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
+    t += (list_off[l + 1] - list_off[l] + 7) & ~7ll;
+  }
+  qtot[q] = t;
+}
+
+// single CTA exclusive scan (int64)
+__global__ void scan64_kernel(const int64_t *__restrict__ in, int64_t n, int64_t *__restrict__ out,
+                              int64_t *__restrict__ total) {
+  __shared__ int64_t s[1024];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t x = i < n ? in[i] : 0;
+    s[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int64_t y = (int)threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (i < n) out[i] = carry + s[threadIdx.x] - x;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, int nprobe,
+                                 const int64_t *__restrict__ list_off,
+                                 const int64_t *__restrict__ qbase, int64_t *__restrict__ pbase) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B) return;
+  int64_t t = qbase[q];
+  for (int s = 0; s < nprobe; ++s) {
+    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
+    pbase[q * nprobe + s] = t;
+    t += (list_off[l + 1] - list_off[l] + 7) & ~7ll;
+  }
+}
+
+// ---------------------------------------------------------------- selection
+// Per query (one CTA): the kk smallest FP16 scores over its candidate segments
+// by a two-pass radix select on the 16-bit keys (scores are clamped >= 0, so
+// the bit patterns order like the values); ties at the threshold are taken in
+// arrival order.  Writes database ids (-1 padding).
+__global__ void __launch_bounds__(256) select_kernel(const uint16_t *__restrict__ cand,
+                                                     const uint64_t *__restrict__ ckeys,
+                                                     int nprobe, const int64_t *__restrict__ pbase,
+                                                     const int64_t *__restrict__ list_off,
+                                                     const int32_t *__restrict__ list_ids, int kk,
+                                                     int64_t *__restrict__ out) {
+  __shared__ int hist[256];
+  __shared__ int s_b1, s_below1, s_b2, s_below2, s_lt, s_eq;
+  __shared__ int s_l[128];
+  __shared__ int64_t s_off[128], s_pb[128];
+  __shared__ int s_nl[128];
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int s = tid; s < nprobe; s += 256) {
+    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
+    s_l[s] = l;
+    s_off[s] = list_off[l];
+    s_nl[s] = (int)(list_off[l + 1] - list_off[l]);
+    s_pb[s] = pbase[q * nprobe + s];
+  }
+  __syncthreads();
+  int total = 0;
+  for (int s = 0; s < nprobe; ++s) total += s_nl[s];
+  int64_t *o = out + q * kk;
+  if (total <= kk) {
+    // every candidate is kept
+    int pos = 0;
+    for (int s = 0; s < nprobe; ++s) {
+      for (int m = tid; m < s_nl[s]; m += 256) o[pos + m] = list_ids[s_off[s] + m];
+      pos += s_nl[s];
+    }
+    for (int r = total + tid; r < kk; r += 256) o[r] = -1;
+    return;
+  }
+  // pass 1: high byte
+  for (int i = tid; i < 256; i += 256) hist[i] = 0;
+  __syncthreads();
+  for (int s = 0; s < nprobe; ++s)
+    for (int m = tid; m < s_nl[s]; m += 256) atomicAdd(&hist[cand[s_pb[s] + m] >> 8], 1);
+  __syncthreads();
+  if (tid == 0) {
+    int c = 0, b = 0;
+    while (c + hist[b] < kk) c += hist[b++];
+    s_b1 = b;
+    s_below1 = c;
+  }
+  __syncthreads();
+  const int b1 = s_b1;
+  hist[tid] = 0;
+  __syncthreads();
+  for (int s = 0; s < nprobe; ++s)
+    for (int m = tid; m < s_nl[s]; m += 256) {
+      const uint16_t k = cand[s_pb[s] + m];
+      if ((k >> 8) == b1) atomicAdd(&hist[k & 255], 1);
+    }
+  __syncthreads();
+  if (tid == 0) {
+    int c = s_below1, b = 0;
+    while (c + hist[b] < kk) c += hist[b++];
+    s_b2 = b;
+    s_below2 = c;
+    s_lt = 0;
+    s_eq = 0;
+  }
+  __syncthreads();
+  const uint16_t T = (uint16_t)((b1 << 8) | s_b2);
+  const int need_eq = kk - s_below2;
+  for (int s = 0; s < nprobe; ++s)
+    for (int m = tid; m < s_nl[s]; m += 256) {
+      const uint16_t k = cand[s_pb[s] + m];
+      if (k < T) {
+        const int p = atomicAdd(&s_lt, 1);
+        o[p] = list_ids[s_off[s] + m];
+      } else if (k == T) {
+        const int p = atomicAdd(&s_eq, 1);
+        if (p < need_eq) o[s_below2 + p] = list_ids[s_off[s] + m];
+      }
+    }
+}
+
+// ---------------------------------------------------------------- tensor-core scan launcher
+int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
+                    const MmaScanArgs &a, cudaStream_t st);
+
+int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
+                 int nprobe, int k, int which, int kk, int64_t *out_ids, float *out_dist,
+                 int32_t *out_probes, cudaStream_t st) {
+  const int fp8 = which == 1;
+  const int epb = fp8 ? 128 : 64;
+  const int nkb = (d_s + epb - 1) / epb;
+  const int nlist = idx->nlist;
+  const int dcp = pad16(d_c), dsp = pad16(d_s);
+  const int qt = 128;
+  const int64_t seg_q = (int64_t)nprobe * (((int64_t)idx->max_list + 7) & ~7ll);
+  const int64_t per_q = seg_q * 2 + (int64_t)nprobe * ((int64_t)nkb * 128 * 128 / qt + 32) +
+                        (int64_t)(dcp + dsp) * 4 + (int64_t)nkb * 128 + (int64_t)kk * 8 + 64;
+  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (3ll << 30) / per_q));
+  const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
+  Scratch s(st);
+  float *qc, *qs, *qn2, *qsc;
+  uint64_t *ckeys;
+  int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
+  int *ntiles, *counter, *err;
+  int64_t *qtot, *qbase, *pbase, *cids;
+  unsigned char *qlow, *qtile;
+  uint16_t *cand;
+  int rc;
+  if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
+      (rc = s.get(&qn2, Bc)) || (rc = s.get(&qsc, Bc)) || (rc = s.get(&ckeys, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&lcnt, nlist)) || (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) ||
+      (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
+      (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) ||
+      (rc = s.get(&counter, 2)) || (rc = s.get(&err, 1)) || (rc = s.get(&qtot, Bc)) ||
+      (rc = s.get(&qbase, Bc)) || (rc = s.get(&pbase, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&cids, (size_t)Bc * kk)) || (rc = s.get(&qlow, (size_t)Bc * nkb * 128)) ||
+      (rc = s.get(&qtile, (size_t)max_tiles * nkb * 128 * 128)) ||
+      (rc = s.get(&cand, (size_t)Bc * seg_q)))
+    return rc;
+  const int gi = gran_index(d_s);
+  const float *mscale = idx->invn + (int64_t)gi * idx->N;
+  const float *cx = idx->lowp_cx[which] + (int64_t)gi * idx->N;
+  ADN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  for (int64_t b0 = 0; b0 < B; b0 += Bc) {
+    const int64_t nb = std::min(Bc, B - b0);
+    {
+      StageTimer t(ST_PREP, st);
+      if ((rc = launch_prep_queries(queries + b0 * idx->d, nb, idx->d, d_c, d_s, idx->metric, qc,
+                                    dcp, qs, dsp, st)))
+        return rc;
+      prep_lowp_kernel<<<(unsigned)((nb + 7) / 8), 256, 0, st>>>(qs, dsp, nb, d_s, fp8, nkb, qlow,
+                                                                 qn2, qsc);
+      ADN_LAUNCH("prep_lowp_kernel");
+    }
+    ScanArgs c{};
+    c.xpm = idx->cent_pm;
+    c.d_pad = dcp;
+    c.dims = d_c;
+    c.list_off = idx->cent_off;
+    c.qn = qc;
+    c.ldq = dcp;
+    c.nq = (int)nb;
+    c.counter = counter;
+    c.k = nprobe;
+    c.out_keys = ckeys;
+    ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
+    {
+      StageTimer t(ST_COARSE, st);
+      if ((rc = launch_scan_f32(c, st))) return rc;
+    }
+    {
+      StageTimer t(ST_INVERT, st);
+      if ((rc = launch_invert_probes(ckeys, nb, nprobe, nlist, qt, lcnt, lbeg, lfill, tbeg, pair_q,
+                                     pair_out, tl, tb, tc, ntiles,
+                                     out_probes ? out_probes + b0 * nprobe : nullptr, st)))
+        return rc;
+      const unsigned g = (unsigned)((nb + 255) / 256);
+      cand_count_kernel<<<g, 256, 0, st>>>(ckeys, nb, nprobe, idx->list_off, qtot);
+      ADN_LAUNCH("cand_count_kernel");
+      scan64_kernel<<<1, 1024, 0, st>>>(qtot, nb, qbase, nullptr);
+      ADN_LAUNCH("scan64_kernel");
+      cand_base_kernel<<<g, 256, 0, st>>>(ckeys, nb, nprobe, idx->list_off, qbase, pbase);
+      ADN_LAUNCH("cand_base_kernel");
+      gather_qtiles_kernel<<<dim3((unsigned)max_tiles, nkb), 256, 0, st>>>(qlow, nkb, tb, tc,
+                                                                           ntiles, pair_q, qtile);
+      ADN_LAUNCH("gather_qtiles_kernel");
+    }
+    {
+      StageTimer t(ST_MMA, st);
+      MmaScanArgs m{};
+      m.tile_list = tl;
+      m.tile_beg = tb;
+      m.tile_cnt = tc;
+      m.ntiles_dev = ntiles;
+      m.list_off = idx->list_off;
+      m.pair_out = pair_out;
+      m.pbase = pbase;
+      m.cx = cx;
+      m.qn2 = qn2;
+      m.qsc = qsc;
+      m.nprobe = nprobe;
+      m.nkb = nkb;
+      m.d_blocks = idx->lowp_blocks[which];
+      m.cand = cand;
+      m.err = err;
+      m.fp8 = fp8;
+      const int64_t xrows = idx->N * (int64_t)idx->lowp_blocks[which];
+      if ((rc = launch_mma_scan(qtile, max_tiles * nkb * 128, idx->lowp[which], xrows, m, st)))
+        return rc;
+    }
+    {
+      StageTimer t(ST_SELECT, st);
+      select_kernel<<<(unsigned)nb, 256, 0, st>>>(cand, ckeys, nprobe, pbase, idx->list_off,
+                                                  idx->list_ids, kk, cids);
+      ADN_LAUNCH("select_kernel");
+    }
+    {
+      StageTimer t(ST_RERANK, st);
+      if ((rc = launch_rerank(cids, kk, nb, qs, dsp, d_s, idx, mscale, k, out_ids + b0 * k,
+                              out_dist + b0 * k, st)))
+        return rc;
+    }
+  }
+  // surface a timed-out tensor-core pipeline as an error of this call
+  int h_err = 0;
+  ADN_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ADN_CUDA(cudaStreamSynchronize(st));
+  if (h_err) return fail(ADANNS_ERR_TIMEOUT, "tensor-core scan pipeline timed out (stage " +
+                                                 std::to_string(h_err) + ")");
+  return ADANNS_OK;
+}
+
+}  // namespace adn

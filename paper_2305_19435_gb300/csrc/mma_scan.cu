@@ -1,0 +1,407 @@
+// Mixed-precision AdANNS-IVF list scan on the 5th-generation tensor cores.
+//
+// The database is stored BF16 or FP8-E4M3 with a per-vector FP32 scale, in the
+// same prefix-major list layout as the FP32 copy but with blocks of 128 bytes
+// (64 BF16 or 128 FP8 coordinates).  For a work item (list, up to 128 queries
+// probing it) the CTA computes the 128 x n_l matrix of dot products
+//     D = Q_tile (128 x d_s) . X_list^T (d_s x n_l)
+// with tcgen05.mma (FP32 accumulation in tensor memory), 256 members at a time,
+// and turns each dot product into an approximate squared distance
+//     d ~ |q|^2 + |x|^2 - 2 s_q s_x nu_x (q . x)
+// (prefix-normalised metric), written as FP16 into the query's candidate
+// segment.  A selection kernel then keeps each query's best k' candidates and
+// the exact FP32 rerank (Sec. 4.3 shortlist-rerank) produces the result.
+//
+// Warp roles (192 threads): warp 0 issues TMA tile loads into a 4-stage
+// shared-memory ring; warp 1 owns tensor memory (512 columns: two 256-column
+// accumulators) and one elected thread issues the MMAs; warps 2-5 drain the
+// accumulators.  Every mbarrier wait is bounded: on timeout the kernel records
+// an error, stops issuing work, lets in-flight copies land and frees TMEM.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <mutex>
+
+#include "devutil.cuh"
+#include "internal.cuh"
+
+namespace adn {
+
+namespace {
+constexpr int BM = 128;          // queries per tile (TMEM lanes)
+constexpr int BN = 256;          // members per MMA tile (TMEM columns per accumulator)
+constexpr int ROWB = 128;        // bytes per K-block row (one 128-byte swizzle atom row)
+constexpr int NSTAGE = 4;
+constexpr int A_BYTES = BM * ROWB;    // 16 KB
+constexpr int B_BYTES = BN * ROWB;    // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int THREADS = 192;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait for the phase with the given parity to complete (false on timeout)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if ((i & 1023) == 1023) {
+      const uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > WAIT_LIMIT_NS) return false;
+    }
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);           // start address
+  d |= (uint64_t)0 << 16;                            // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;      // stride byte offset
+  d |= (uint64_t)1 << 46;                            // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                            // layout: SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate, bool fp8) {
+  if (fp8) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int ld_abort(const int *flag) { return *(const volatile int *)flag; }
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+}  // namespace
+
+
+
+__global__ void __launch_bounds__(THREADS, 1)
+    mma_scan_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    MmaScanArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *sA = smem;                              // NSTAGE x 16 KB
+  unsigned char *sB = smem + NSTAGE * A_BYTES;           // NSTAGE x 32 KB
+  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&tfull[s], 1);
+      mbar_init(&tempty[s], 128);
+    }
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+  const int ntiles = *a.ntiles_dev;
+  const uint32_t idesc = a.fp8 ? ((1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24))
+                               : ((1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                  ((uint32_t)(BM >> 4) << 24));
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int t = blockIdx.x; t < ntiles && !ld_abort(&abort_s); t += gridDim.x) {
+        const int list = a.tile_list[t];
+        const int64_t off = a.list_off[list];
+        const int nl = (int)(a.list_off[list + 1] - off);
+        const int nmt = (nl + BN - 1) / BN;
+        for (int mt = 0; mt < nmt && !ld_abort(&abort_s); ++mt)
+          for (int kb = 0; kb < a.nkb; ++kb) {
+            if (!mbar_wait(&empty[stage], phase ^ 1)) {
+              atomicExch(&abort_s, 1);
+              atomicExch(a.err, 1);
+              break;
+            }
+            mbar_expect_tx(&full[stage], STAGE_BYTES);
+            tma_load_2d(sA + stage * A_BYTES, &tmA, &full[stage], 0, (t * a.nkb + kb) * BM);
+            tma_load_2d(sB + stage * B_BYTES, &tmB, &full[stage], 0,
+                        (int)(off * a.d_blocks) + kb * nl + mt * BN);
+            if (++stage == NSTAGE) { stage = 0; phase ^= 1; }
+          }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t aphase = 0;
+      for (int t = blockIdx.x; t < ntiles && !ld_abort(&abort_s); t += gridDim.x) {
+        const int list = a.tile_list[t];
+        const int nl = (int)(a.list_off[list + 1] - a.list_off[list]);
+        const int nmt = (nl + BN - 1) / BN;
+        for (int mt = 0; mt < nmt && !ld_abort(&abort_s); ++mt) {
+          if (!mbar_wait(&tempty[acc], aphase ^ 1)) {
+            atomicExch(&abort_s, 1);
+            atomicExch(a.err, 2);
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
+          for (int kb = 0; kb < a.nkb; ++kb) {
+            if (!mbar_wait(&full[stage], phase)) {
+              atomicExch(&abort_s, 1);
+              atomicExch(a.err, 3);
+              break;
+            }
+            tc_fence_after();
+            const uint32_t abase = smem_u32(sA + stage * A_BYTES);
+            const uint32_t bbase = smem_u32(sB + stage * B_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              // 32 bytes of K per instruction: 16 BF16 or 32 FP8 elements
+              mma_issue(d_tmem, sw128_desc(abase + ks * 32), sw128_desc(bbase + ks * 32), idesc,
+                        (kb > 0 || ks > 0) ? 1u : 0u, a.fp8 != 0);
+            }
+            mma_commit(&empty[stage]);
+            if (++stage == NSTAGE) { stage = 0; phase ^= 1; }
+          }
+          mma_commit(&tfull[acc]);
+          if (++acc == 2) { acc = 0; aphase ^= 1; }
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, one query row per thread
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int list = a.tile_list[t];
+      const int64_t off = a.list_off[list];
+      const int nl = (int)(a.list_off[list + 1] - off);
+      const int npad = (nl + 7) & ~7;
+      const int nmt = (nl + BN - 1) / BN;
+      const int cnt = a.tile_cnt[t];
+      const bool valid = row < cnt;
+      int64_t base = 0;
+      float q2 = 0.f, qs = 0.f;
+      if (valid) {
+        const int p = a.pair_out[a.tile_beg[t] + row];
+        const int q = p / a.nprobe;
+        base = a.pbase[p];
+        q2 = a.qn2[q];
+        qs = a.qsc[q];
+      }
+      bool stop = false;
+      for (int mt = 0; mt < nmt; ++mt) {
+        if (!mbar_wait(&tfull[acc], aphase)) {
+          atomicExch(&abort_s, 1);
+          atomicExch(a.err, 4);
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(tbase + c0, r);
+          const int m0 = mt * BN + c0;
+          if (valid && m0 < npad) {
+            uint32_t packed[16];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              float dd[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int m = m0 + j + u;
+                float d = __int_as_float(0x7f800000);
+                if (m < nl) {
+                  const float c = __ldg(a.cx + off + m);
+                  d = q2 + (c > 0.f ? 1.f : 0.f) - 2.f * qs * c * __uint_as_float(r[j + u]);
+                  d = fmaxf(d, 0.f);
+                }
+                dd[u] = d;
+              }
+              const __half2 h = __floats2half2_rn(dd[0], dd[1]);
+              packed[j >> 1] = *(const uint32_t *)&h;
+            }
+            uint4 *dst = (uint4 *)(a.cand + base + m0);
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+              if (m0 + 8 * g < npad)
+                dst[g] = make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2],
+                                    packed[4 * g + 3]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[acc]);
+        if (++acc == 2) { acc = 0; aphase ^= 1; }
+      }
+      if (stop) break;
+      if (ld_abort(&abort_s)) break;
+    }
+  }
+
+  __syncthreads();
+  if (ld_abort(&abort_s)) {
+    // let any copy still in flight land before the shared memory is released
+    for (int i = 0; i < 1 << 14; ++i) __nanosleep(1000);
+  }
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2D map over rows of 128 bytes: box = 128 bytes x box_rows, 128-byte swizzle
+int make_map(CUtensorMap *m, const void *base, int64_t rows, int box_rows, bool fp8) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(ADANNS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  if (((uintptr_t)base & 15) != 0) return fail(ADANNS_ERR_ARG, "tensor base not 16-byte aligned");
+  const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[2] = {(cuuint64_t)(fp8 ? 128 : 64), (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {(cuuint32_t)(fp8 ? 128 : 64), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(ADANNS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return ADANNS_OK;
+}
+}  // namespace
+
+size_t mma_scan_smem() { return (size_t)NSTAGE * STAGE_BYTES + 1024; }
+
+int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
+                    const MmaScanArgs &a, cudaStream_t st) {
+  CUtensorMap tA, tB;
+  int rc;
+  if ((rc = make_map(&tA, qtiles, qrows, BM, a.fp8 != 0))) return rc;
+  if ((rc = make_map(&tB, xlow, xrows, BN, a.fp8 != 0))) return rc;
+  const size_t smem = mma_scan_smem();
+  ADN_CUDA(cudaFuncSetAttribute(mma_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  mma_scan_kernel<<<num_sms(), THREADS, smem, st>>>(tA, tB, a);
+  ADN_LAUNCH("mma_scan_kernel");
+  return ADANNS_OK;
+}
+
+}  // namespace adn

@@ -1,0 +1,121 @@
+"""Mixed-precision AdANNS-IVF (BF16 / FP8-E4M3 storage, tensor-core scan,
+exact FP32 rerank of the k' shortlist) against the FP64 oracle.
+
+The approximate scan only chooses the shortlist; every returned distance is
+the exact FP32 d_s distance, so each (id, distance) pair must match the
+oracle's exact distance for that id, and the ids must reach the stated
+recall@10 against the oracle's exact IVF search on the same index.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+from parity import recall, tol
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PN = oracle.METRIC_L2_PREFIXNORM
+BF16, FP8 = 2, 4
+
+
+@pytest.fixture(scope="module")
+def A():
+    import paper_2305_19435_gb300 as P
+    P.build()
+    assert torch.cuda.is_available()
+    return P
+
+
+def cu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.fixture(scope="module")
+def case(A):
+    data = synthdata.small(40_000, 700, 256, 64, 401)
+    o = oracle.build_ivf(data["db"], 32, 48, 8, 20_000, seed=21)
+    g = A.index_create(cu(data["db"]), cu(o["centroids"]), cu(o["assign"].astype(np.int32)),
+                       storage=1 | BF16 | FP8)
+    yield data, o, g
+    g.free()
+
+
+def exact_dist(db, q, ids, d_s):
+    """dist_ds of each returned id (FP64, the definition), +inf for padding."""
+    P = oracle.prefix(q[None], d_s)[0]
+    out = np.full(ids.shape, np.inf)
+    ok = ids >= 0
+    X = oracle.prefix(db[ids[ok]], d_s)
+    out[ok] = ((X - P) ** 2).sum(1)
+    return out
+
+
+def check(A, case, storage, d_s, nprobe, k, kr, min_recall, B=None):
+    data, o, g = case
+    q = data["queries"] if B is None else data["queries"][:B]
+    gi, gd = A.search_ivf(g, cu(q), 32, d_s, nprobe, k, storage=storage, rerank_k=kr)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    ref = oracle.search_ivf(data["db"], o, q, 32, d_s, nprobe, k)
+    # every returned distance is the exact distance of the returned id
+    for i in range(len(q)):
+        ex = exact_dist(data["db"], q[i], gi[i], d_s)
+        fin = np.isfinite(ex)
+        assert np.all(np.abs(gd[i][fin] - ex[fin]) <= tol(ex[fin])), i
+        assert np.all(np.diff(gd[i][fin]) >= 0)
+        assert len(set(gi[i][gi[i] >= 0].tolist())) == int((gi[i] >= 0).sum())
+    r = recall(gi, ref["ids"], min(10, k))
+    assert r >= min_recall, r
+    return r
+
+
+@pytest.mark.parametrize("storage", [BF16, FP8])
+def test_mixed_main_point(A, case, storage):
+    """d_s = 256, nprobe = 8, k = 100, shortlist 4k = 400."""
+    check(A, case, storage, 256, 8, 100, 400, 0.995 if storage == BF16 else 0.99)
+
+
+@pytest.mark.parametrize("d_s,nprobe,k,kr", [(64, 4, 10, 40), (96, 6, 10, 40), (128, 12, 50, 200),
+                                             (192, 2, 1, 4), (256, 48, 20, 80)])
+def test_mixed_bf16_sweep(A, case, d_s, nprobe, k, kr):
+    check(A, case, BF16, d_s, nprobe, k, kr, 0.98)
+
+
+@pytest.mark.parametrize("d_s", [128, 256])
+def test_mixed_fp8_sweep(A, case, d_s):
+    check(A, case, FP8, d_s, 8, 10, 40, 0.97)
+
+
+@pytest.mark.parametrize("B", [1, 3, 129])
+def test_mixed_ragged_batches(A, case, B):
+    check(A, case, BF16, 256, 8, 10, 40, 0.95, B=B)
+
+
+def test_full_shortlist_is_exact(A, case):
+    """When the shortlist holds every candidate, the result equals the exact scan."""
+    data, o, g = case
+    from parity import ambiguous_probe_rows, check_topk
+    sizes = np.diff(o["list_off"])
+    ref = oracle.search_ivf(data["db"], o, data["queries"], 32, 128, 1, 60)
+    fits = sizes[ref["probes"][:, 0]] <= 2048
+    q = data["queries"][fits][:64]
+    ref = {key: v[fits][:64] for key, v in ref.items()}
+    gi, gd = A.search_ivf(g, cu(q), 32, 128, 1, 20, storage=BF16, rerank_k=2048)
+    amb = ambiguous_probe_rows(ref["probe_dist"], 1)
+    n, fails = check_topk(gi.cpu().numpy(), gd.cpu().numpy(), ref["ids"], ref["dist"], 20,
+                          skip_rows=amb)
+    assert n > 0 and not fails, fails[:2]
+
+
+def test_mixed_errors(A, case):
+    data, o, g = case
+    q = cu(data["queries"][:4])
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivf(g, q, 32, 256, 8, 10, storage=BF16, rerank_k=5)    # shortlist < k
+    assert e.value.code == -1
+    h = A.index_create(cu(data["db"]), cu(o["centroids"]), cu(o["assign"].astype(np.int32)))
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivf(h, q, 32, 256, 8, 10, storage=BF16, rerank_k=40)    # tier not built
+    assert e.value.code == -6
+    h.free()
