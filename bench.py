@@ -55,6 +55,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle legs")
     p.add_argument("--skip-gpu-build", action="store_true",
                    help="do not time the GPU k-means build (profiling runs)")
+    p.add_argument("--mode", default="bf16", choices=["f32", "bf16", "fp8"],
+                   help="headline path: FP32 scan, or BF16 / FP8 tensor-core scan + FP32 rerank of 4k")
+    p.add_argument("--compare", nargs="*", default=["f32", "fp8"],
+                   help="other paths timed beside the headline")
     p.add_argument("--quiet", action="store_true")
     return p.parse_args()
 
@@ -136,9 +140,11 @@ def oracle_index(data, args, N):
 
 
 def workload_config(args, N, B):
+    scan = {"f32": "FP32 scan", "bf16": "BF16 tensor-core scan + FP32 rerank of 4k",
+            "fp8": "FP8-E4M3 tensor-core scan + FP32 rerank of 4k"}[args.mode]
     return {"workload": f"AdANNS-IVF {args.workload}-shaped: N={N:,} d=2048 B={B:,} "
                         f"nlist={args.nlist} d_c={args.d_c} d_s={args.d_s} nprobe={args.nprobe} "
-                        f"k={args.k} FP32 scan",
+                        f"k={args.k}, {scan}", "mode": args.mode,
             "N": N, "B": B, "d": 2048, "nlist": args.nlist, "d_c": args.d_c, "d_s": args.d_s,
             "nprobe": args.nprobe, "k": args.k, "metric": "L2 on prefix-normalised MR prefixes",
             "l2": "inputs larger than L2 (scanned lists exceed 129 MB)",
@@ -190,6 +196,29 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+MODES = {"f32": (1, 0), "bf16": (2, 4), "fp8": (4, 4)}   # storage code, rerank multiple of k
+
+
+def mode_rerank(mode, k):
+    return MODES[mode][1] * k
+
+
+def timed(P, torch, step, steps, stream):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = P.launch_count()
+    P.profile_enable(True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = (P.launch_count() - l0) // steps
+    prof = P.profile_read()
+    P.profile_enable(False)
+    return ev0.elapsed_time(ev1) / steps, launches, prof
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -209,6 +238,13 @@ def main():
         if world > 1:
             dist.barrier()
 
+    def max_over_ranks(v):
+        if world > 1:
+            t = torch.tensor([v], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            v = float(t.item())
+        return v
+
     import paper_2305_19435_gb300 as P
     if rank == 0:
         P.build()
@@ -222,18 +258,22 @@ def main():
     t0 = time.time()
     data = synthdata.make(args.workload, n=N, b=B)
     log(f"data {time.time() - t0:.1f}s")
-    # the oracle's index (rank 0 builds and caches; the others read the cache)
     if rank == 0:
         oidx = oracle_index(data, args, N)
     barrier()
     if rank != 0:
         oidx = oracle_index(data, args, N)
     log(f"oracle index ready ({oidx.get('build_s', 0):.1f}s build)")
+    modes = [args.mode] + [m for m in args.compare if m != args.mode]
+    storage = 1
+    for m in modes:
+        storage |= MODES[m][0]
     db_dev = torch.from_numpy(data["db"]).cuda()
+    tb = time.time()
     idx = P.index_create(db_dev, torch.from_numpy(oidx["centroids"]).cuda(),
-                         torch.from_numpy(oidx["assign"].astype(np.int32)).cuda())
-    # GPU build of the same configuration, timed (not part of a step)
+                         torch.from_numpy(oidx["assign"].astype(np.int32)).cuda(), storage=storage)
     torch.cuda.synchronize()
+    layout_s = time.time() - tb
     gpu_build_s = None
     if not args.skip_gpu_build:
         tb = time.time()
@@ -247,47 +287,47 @@ def main():
 
     qh = torch.from_numpy(data["queries"]).pin_memory()
     q = qh.cuda()
-    ids = torch.empty(B, args.k, dtype=torch.int64, device="cuda")
-    dd = torch.empty(B, args.k, dtype=torch.float32, device="cuda")
-
-    def step():
-        P.search_ivf(idx, q, args.d_c, args.d_s, args.nprobe, args.k, out=(ids, dd))
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
     st = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = P.launch_count()
-    P.profile_enable(True)
-    with Clocks(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        ev0.record(st)
-        for _ in range(args.steps):
+    results = {}
+    for mode in modes:
+        ids = torch.empty(B, args.k, dtype=torch.int64, device="cuda")
+        dd = torch.empty(B, args.k, dtype=torch.float32, device="cuda")
+        code, rr = MODES[mode][0], mode_rerank(mode, args.k)
+
+        def step(ids=ids, dd=dd, code=code, rr=rr):
+            P.search_ivf(idx, q, args.d_c, args.d_s, args.nprobe, args.k, storage=code,
+                         rerank_k=rr, out=(ids, dd))
+
+        for _ in range(max(3, args.warmup)):
             step()
-        ev1.record(st)
         torch.cuda.synchronize()
         barrier()
-    launches = (P.launch_count() - l0) // args.steps
-    prof = P.profile_read()
-    P.profile_enable(False)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    qps = world * B / (ms / 1000.0)
+        if mode == args.mode:
+            with Clocks(local) as clk:
+                ms, launches, prof = timed(P, torch, step, args.steps, st)
+            clocks = clk.summary()
+        else:
+            ms, launches, prof = timed(P, torch, step, args.steps, st)
+        barrier()
+        ms = max_over_ranks(ms)
+        results[mode] = {"ms": ms, "qps": world * B / (ms / 1000.0), "launches": launches,
+                         "stages_ms": {k2: v[0] / args.steps for k2, v in prof.items()},
+                         "ids": ids, "step": step}
+    main_r = results[args.mode]
 
     # end to end through the public API: pinned host queries in, results out
+    code, rr = MODES[args.mode][0], mode_rerank(args.mode, args.k)
     ih = torch.empty(B, args.k, dtype=torch.int64).pin_memory()
     dh = torch.empty(B, args.k, dtype=torch.float32).pin_memory()
+    ids_e = torch.empty(B, args.k, dtype=torch.int64, device="cuda")
+    dd_e = torch.empty(B, args.k, dtype=torch.float32, device="cuda")
 
     def e2e_step():
         qd = qh.cuda(non_blocking=True)
-        P.search_ivf(idx, qd, args.d_c, args.d_s, args.nprobe, args.k, out=(ids, dd))
-        ih.copy_(ids, non_blocking=True)
-        dh.copy_(dd, non_blocking=True)
+        P.search_ivf(idx, qd, args.d_c, args.d_s, args.nprobe, args.k, storage=code, rerank_k=rr,
+                     out=(ids_e, dd_e))
+        ih.copy_(ids_e, non_blocking=True)
+        dh.copy_(dd_e, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -299,11 +339,7 @@ def main():
         e2e_step()
     e1.record(st)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
 
     # work accounting from the probe lists of the timed batch
     _, _, probes = P.search_ivf(idx, q, args.d_c, args.d_s, args.nprobe, args.k, return_probes=True)
@@ -311,34 +347,64 @@ def main():
     sizes = np.diff(oidx["list_off"])
     pairs = int(sizes[probes].sum())
     probed = np.unique(probes)
-    uniq_bytes = int(sizes[probed].sum()) * (args.d_s * 4 + 8)
-    scan_ms = prof.get("scan", (0.0, 1))[0] / max(1, prof.get("scan", (0, 1))[1])
-    sm_count = props.multi_processor_count
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
+    sm_count = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # FP32 list scan: two FFMA per (query, member, dimension): t = q - s*x; acc += t*t
-    ffma = 2.0 * pairs * args.d_s
-    achieved_tflops = 2.0 * ffma / (scan_ms / 1e3) / 1e12
-    peak_tflops = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
-    roofline = {"kernel": "scan_f32_kernel (list scan)", "bound": "alu",
-                "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / peak_tflops, "traffic": None,
-                "peak_source": f"FP32 FFMA: {sm_count} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz",
-                "hbm_achieved_gbs": uniq_bytes / (scan_ms / 1e3) / 1e9,
-                "scan_ms": scan_ms, "pairs": pairs, "unique_list_bytes": uniq_bytes}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    ffma_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+    rooflines = {}
+    for mode, r in results.items():
+        sm = r["stages_ms"]
+        if mode == "f32":
+            t = sm.get("scan", 0.0)
+            ach = 4.0 * pairs * args.d_s / (t / 1e3) / 1e12
+            rooflines[mode] = {"kernel": "scan_f32_kernel (list scan)", "bound": "alu",
+                               "achieved": ach, "peak": ffma_peak, "unit": "TFLOP/s",
+                               "frac": ach / ffma_peak, "traffic": None, "kernel_ms": t,
+                               "peak_source": f"derived FP32 FFMA peak: {sm_count} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz"}
+        else:
+            t = sm.get("mma", 0.0)
+            epb = 64 if mode == "bf16" else 128
+            dpad = (args.d_s + epb - 1) // epb * epb
+            ach = 2.0 * pairs * dpad / (t / 1e3) / 1e12
+            peak = bf16_peak * (2.0 if mode == "fp8" else 1.0)
+            rooflines[mode] = {"kernel": "mma_scan_kernel (tensor-core list scan)", "bound": "tensor",
+                               "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                               "traffic": None, "kernel_ms": t,
+                               "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"
+                               + (" x 2 (nominal fp8/bf16 ratio)" if mode == "fp8" else "")}
+            rr_t = sm.get("rerank", 0.0)
+            rr_bytes = B * mode_rerank(mode, args.k) * args.d_s * 4
+            rooflines[mode]["rerank"] = {"kernel": "rerank_kernel", "bound": "hbm",
+                                         "achieved": rr_bytes / (rr_t / 1e3) / 1e9 if rr_t else None,
+                                         "peak": hbm_peak, "unit": "GB/s", "kernel_ms": rr_t}
+    main_roof = dict(rooflines[args.mode])
+    # the dominant kernel of the step (largest stage) carries the headline roofline
+    main_stages = main_r["stages_ms"]
+    dom = max(main_stages, key=main_stages.get) if main_stages else None
+    if args.mode != "f32" and dom == "rerank":
+        rrd = main_roof.pop("rerank")
+        main_roof = {**rrd, "frac": (rrd["achieved"] or 0) / hbm_peak, "traffic": None,
+                     "peak_source": "measured STREAM-style copy (MEASURED_PEAKS.json)",
+                     "mma": {k2: v for k2, v in rooflines[args.mode].items() if k2 != "rerank"}}
 
-    out = {"metric": "QPS at recall@10 vs oracle", "value": qps, "unit": "queries/s",
+    cfg = workload_config(args, N, B)
+    out = {"metric": "QPS at recall@10 vs oracle", "value": main_r["qps"], "unit": "queries/s",
            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
-           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic (seeded Matryoshka-like Gaussian mixture)",
-           "config": workload_config(args, N, B), "clocks": clk.summary(),
-           "gpu_launches": int(launches), "roofline": roofline,
-           "stages_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
-           "gpu_build_s": gpu_build_s,
+           "ms_per_step": main_r["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": {"f32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[args.mode],
+           "data": "synthetic (seeded Matryoshka-like Gaussian mixture)", "config": cfg,
+           "clocks": clocks, "gpu_launches": int(main_r["launches"]), "roofline": main_roof,
+           "stages_ms": main_r["stages_ms"],
+           "modes": {m: {"qps": r["qps"], "ms_per_step": r["ms"], "stages_ms": r["stages_ms"],
+                         "roofline": rooflines[m]} for m, r in results.items()},
+           "gpu_build_s": gpu_build_s, "index_layout_s": layout_s, "pairs_per_step": pairs,
+           "unique_lists_per_step": int(len(probed)),
            "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "queries/s",
                    "h2d_bytes_per_step": int(qh.numel() * 4),
                    "d2h_bytes_per_step": int(ih.numel() * 8 + dh.numel() * 4)}}
@@ -350,12 +416,14 @@ def main():
         ref = oracle.search_ivf(data["db"], oidx, data["queries"][:S], args.d_c, args.d_s,
                                 args.nprobe, args.k)
         el = time.time() - t
-        step()
-        torch.cuda.synchronize()
-        gi = ids[:S].cpu().numpy()
-        from_rec = [len(set(a[:10].tolist()) & set(b[:10].tolist())) / 10.0
-                    for a, b in zip(gi, ref["ids"])]
-        out["recall_at_10_vs_oracle"] = float(np.mean(from_rec))
+        for mode, r in results.items():
+            r["step"]()
+            torch.cuda.synchronize()
+            gi = r["ids"][:S].cpu().numpy()
+            rec = float(np.mean([len(set(a[:10].tolist()) & set(b[:10].tolist())) / 10.0
+                                 for a, b in zip(gi, ref["ids"])]))
+            out["modes"][mode]["recall_at_10_vs_oracle"] = rec
+        out["recall_at_10_vs_oracle"] = out["modes"][args.mode]["recall_at_10_vs_oracle"]
         out["recall_sample"] = S
         out["cpu_baseline"] = {"value": S / el, "unit": "queries/s", "cores": os.cpu_count(),
                                "kind": "oracle",

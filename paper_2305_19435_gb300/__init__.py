@@ -75,7 +75,9 @@ def launch_count() -> int:
     return int(lib().adanns_launch_count())
 
 
-STAGES = ("prep", "coarse", "invert", "scan", "merge")
+STAGES = ("prep", "coarse", "invert", "scan", "merge", "lut", "adc", "rerank", "mma", "select")
+STORE_BF16 = 2
+STORE_FP8 = 4
 
 
 def profile_enable(on: bool = True):
