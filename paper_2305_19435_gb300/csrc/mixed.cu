@@ -16,6 +16,9 @@ namespace adn {
 int launch_rerank(const int64_t *cand, int kr, int64_t B, const float *qs, int ldq, int d_s,
                   const adanns_index *idx, const float *mscale, int k, int64_t *out_ids,
                   float *out_dist, cudaStream_t st);
+int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs, int ldq, int d_s,
+                        const adanns_index *idx, const float *mscale, int k, int64_t *out_ids,
+                        float *out_dist, cudaStream_t st);
 
 // ---------------------------------------------------------------- storage
 // Member p (list order) of list l: s_x = max_j |x_j| / R (R = 448 for FP8-E4M3,
@@ -209,88 +212,178 @@ __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, 
 }
 
 // ---------------------------------------------------------------- selection
-// Per query (one CTA): the kk smallest FP16 scores over its candidate segments
-// by a two-pass radix select on the 16-bit keys (scores are clamped >= 0, so
-// the bit patterns order like the values); ties at the threshold are taken in
-// arrival order.  Writes database ids (-1 padding).
-__global__ void __launch_bounds__(256) select_kernel(const uint16_t *__restrict__ cand,
-                                                     const uint64_t *__restrict__ ckeys,
-                                                     int nprobe, const int64_t *__restrict__ pbase,
-                                                     const int64_t *__restrict__ list_off,
-                                                     const int32_t *__restrict__ list_ids, int kk,
-                                                     int64_t *__restrict__ out) {
-  __shared__ int hist[256];
-  __shared__ int s_b1, s_below1, s_b2, s_below2, s_lt, s_eq;
-  __shared__ int s_l[128];
-  __shared__ int64_t s_off[128], s_pb[128];
-  __shared__ int s_nl[128];
-  const int64_t q = blockIdx.x;
+// Per query (one CTA): the kk smallest 16-bit keys (fixed-point approximate
+// distances) of its candidate region [qbase, qbase + ptotal) (segments padded
+// to 8 with the largest key).
+//  1. A strided sample of up to SEL_SAMPLE keys gives a threshold T whose
+//     expected number of smaller keys is about 1.6 kk (radix select on the
+//     sample).
+//  2. One pass compacts every key < T, with its index, into a shared buffer
+//     (ballot / popc ranks, one atomic per warp step).
+//  3. If the buffer holds between kk and SEL_BUF keys, an exact two-pass
+//     radix select on the buffer fixes the cut; otherwise the exact two-pass
+//     radix select runs over the whole region.
+// Ties at the cut are taken in arrival order.  Writes database ids (-1 padding).
+constexpr int SEL_THREADS = 256;
+constexpr int SEL_WARPS = SEL_THREADS / 32;
+constexpr int SEL_SAMPLE = 2048;
+constexpr int SEL_BUF = 4096;
+
+struct SelState {
+  int hist[256];
+  int b1, below1, b2, below2, lt, lt2, eq, nb;
+};
+
+// exact kk-smallest over n keys given by key(i) (16-bit), writing id(i) for
+// the winners; h is a 256-entry shared histogram, st the shared counters.
+template <class KeyF, class IdF>
+__device__ void radix_select(int n, int kk, KeyF key, IdF id, int64_t *o, SelState &st) {
   const int tid = threadIdx.x;
-  for (int s = tid; s < nprobe; s += 256) {
-    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
-    s_l[s] = l;
-    s_off[s] = list_off[l];
-    s_nl[s] = (int)(list_off[l + 1] - list_off[l]);
-    s_pb[s] = pbase[q * nprobe + s];
-  }
+  for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
+  if (tid == 0) st.lt = st.lt2 = st.eq = 0;
   __syncthreads();
-  int total = 0;
-  for (int s = 0; s < nprobe; ++s) total += s_nl[s];
-  int64_t *o = out + q * kk;
-  if (total <= kk) {
-    // every candidate is kept
-    int pos = 0;
-    for (int s = 0; s < nprobe; ++s) {
-      for (int m = tid; m < s_nl[s]; m += 256) o[pos + m] = list_ids[s_off[s] + m];
-      pos += s_nl[s];
-    }
-    for (int r = total + tid; r < kk; r += 256) o[r] = -1;
-    return;
-  }
-  // pass 1: high byte
-  for (int i = tid; i < 256; i += 256) hist[i] = 0;
-  __syncthreads();
-  for (int s = 0; s < nprobe; ++s)
-    for (int m = tid; m < s_nl[s]; m += 256) atomicAdd(&hist[cand[s_pb[s] + m] >> 8], 1);
+  for (int i = tid; i < n; i += SEL_THREADS) atomicAdd(&st.hist[key(i) >> 8], 1);
   __syncthreads();
   if (tid == 0) {
     int c = 0, b = 0;
-    while (c + hist[b] < kk) c += hist[b++];
-    s_b1 = b;
-    s_below1 = c;
+    while (c + st.hist[b] < kk) c += st.hist[b++];
+    st.b1 = b;
+    st.below1 = c;
   }
   __syncthreads();
-  const int b1 = s_b1;
-  hist[tid] = 0;
+  const int b1 = st.b1, below1 = st.below1;
+  for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
   __syncthreads();
-  for (int s = 0; s < nprobe; ++s)
-    for (int m = tid; m < s_nl[s]; m += 256) {
-      const uint16_t k = cand[s_pb[s] + m];
-      if ((k >> 8) == b1) atomicAdd(&hist[k & 255], 1);
-    }
+  for (int i = tid; i < n; i += SEL_THREADS) {
+    const uint32_t k = key(i);
+    if ((int)(k >> 8) == b1) atomicAdd(&st.hist[k & 255u], 1);
+  }
   __syncthreads();
   if (tid == 0) {
-    int c = s_below1, b = 0;
-    while (c + hist[b] < kk) c += hist[b++];
-    s_b2 = b;
-    s_below2 = c;
-    s_lt = 0;
-    s_eq = 0;
+    int c = below1, b = 0;
+    while (c + st.hist[b] < kk) c += st.hist[b++];
+    st.b2 = b;
+    st.below2 = c;
   }
   __syncthreads();
-  const uint16_t T = (uint16_t)((b1 << 8) | s_b2);
-  const int need_eq = kk - s_below2;
-  for (int s = 0; s < nprobe; ++s)
-    for (int m = tid; m < s_nl[s]; m += 256) {
-      const uint16_t k = cand[s_pb[s] + m];
-      if (k < T) {
-        const int p = atomicAdd(&s_lt, 1);
-        o[p] = list_ids[s_off[s] + m];
-      } else if (k == T) {
-        const int p = atomicAdd(&s_eq, 1);
-        if (p < need_eq) o[s_below2 + p] = list_ids[s_off[s] + m];
+  const uint32_t T = ((uint32_t)b1 << 8) | (uint32_t)st.b2;
+  const int below2 = st.below2, need_eq = kk - below2;
+  for (int i = tid; i < n; i += SEL_THREADS) {
+    const uint32_t k = key(i);
+    if (k < T) {
+      o[atomicAdd(&st.lt, 1)] = id(i);
+    } else if (k == T) {
+      const int p = atomicAdd(&st.eq, 1);
+      if (p < need_eq) o[below2 + p] = id(i);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) select_kernel(
+    const uint16_t *__restrict__ cand, const uint64_t *__restrict__ ckeys, int nprobe,
+    const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off,
+    const int32_t *__restrict__ list_ids, int kk, int64_t *__restrict__ out) {
+  __shared__ SelState st;
+  __shared__ uint16_t samp[SEL_SAMPLE];
+  __shared__ uint32_t bkey[SEL_BUF], bidx[SEL_BUF];
+  __shared__ int s_T, s_n;
+  __shared__ int64_t s_off[128];
+  __shared__ int s_nl[128], s_pst[129];
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int s = tid; s < nprobe; s += SEL_THREADS) {
+    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
+    s_off[s] = list_off[l];
+    s_nl[s] = (int)(list_off[l + 1] - list_off[l]);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int t = 0;
+    for (int s = 0; s < nprobe; ++s) { s_pst[s] = t; t += (s_nl[s] + 7) & ~7; }
+    s_pst[nprobe] = t;
+    s_n = 0;
+  }
+  __syncthreads();
+  const int ptotal = s_pst[nprobe];
+  int total = 0;
+  for (int s = 0; s < nprobe; ++s) total += s_nl[s];
+  int64_t *o = out + q * kk;
+  auto id_at = [&](int i) -> int64_t {
+    int lo = 0, hi = nprobe - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_pst[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int m = i - s_pst[lo];
+    return m < s_nl[lo] ? (int64_t)list_ids[s_off[lo] + m] : -1;
+  };
+  if (total <= kk) {
+    for (int s = 0; s < nprobe; ++s) {
+      int pos = 0;
+      for (int s2 = 0; s2 < s; ++s2) pos += s_nl[s2];
+      for (int m = tid; m < s_nl[s]; m += SEL_THREADS) o[pos + m] = list_ids[s_off[s] + m];
+    }
+    for (int r = total + tid; r < kk; r += SEL_THREADS) o[r] = -1;
+    return;
+  }
+  const uint16_t *src = cand + qbase[q];
+  if (ptotal > 4 * SEL_SAMPLE) {
+    // 1. threshold from a strided sample
+    for (int j = tid; j < SEL_SAMPLE; j += SEL_THREADS)
+      samp[j] = src[(int)(((int64_t)j * ptotal) / SEL_SAMPLE)];
+    __syncthreads();
+    int r = (int)((1.6 * kk * SEL_SAMPLE) / ptotal) + 16;
+    if (r > SEL_SAMPLE - 1) r = SEL_SAMPLE - 1;
+    // the (r+1)-th smallest sample key: select r+1 over the sample into bidx
+    // (as scratch for ids) and take the maximum key of that set
+    {
+      int64_t *tmp = (int64_t *)bkey;  // SEL_BUF * 4 bytes >= (r+1) * 8 for r < 2048
+      radix_select(SEL_SAMPLE, r + 1, [&](int i) -> uint32_t { return samp[i]; },
+                   [&](int i) -> int64_t { return (int64_t)samp[i]; }, tmp, st);
+      __syncthreads();
+      if (tid == 0) {
+        int64_t mx = 0;
+        for (int i = 0; i <= r; ++i) mx = tmp[i] > mx ? tmp[i] : mx;
+        s_T = (int)mx + 1;
+      }
+      __syncthreads();
+    }
+    // 2. compact the keys below T
+    const uint32_t T = (uint32_t)s_T;
+    const uint4 *g = (const uint4 *)src;
+    for (int c0 = 0; c0 < (ptotal >> 3); c0 += SEL_THREADS) {
+      const int c = c0 + tid;
+      uint4 v = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+      if (c < (ptotal >> 3)) v = g[c];
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t k = (w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu;
+        const bool take = k < T;
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&s_n, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) {
+          const int p = base + __popc(m & ((1u << lane) - 1u));
+          if (p < SEL_BUF) {
+            bkey[p] = k;
+            bidx[p] = (uint32_t)(c * 8 + u);
+          }
+        }
       }
     }
+    __syncthreads();
+    const int n = s_n;
+    if (n >= kk && n <= SEL_BUF) {
+      radix_select(n, kk, [&](int i) -> uint32_t { return bkey[i]; },
+                   [&](int i) -> int64_t { return id_at((int)bidx[i]); }, o, st);
+      return;
+    }
+  }
+  // exact radix select over the whole region
+  radix_select(ptotal, kk, [&](int i) -> uint32_t { return src[i]; },
+               [&](int i) -> int64_t { return id_at(i); }, o, st);
 }
 
 // ---------------------------------------------------------------- tensor-core scan launcher
@@ -405,14 +498,14 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     }
     {
       StageTimer t(ST_SELECT, st);
-      select_kernel<<<(unsigned)nb, 256, 0, st>>>(cand, ckeys, nprobe, pbase, idx->list_off,
-                                                  idx->list_ids, kk, cids);
+      select_kernel<<<(unsigned)nb, SEL_THREADS, 0, st>>>(cand, ckeys, nprobe, qbase,
+                                                          idx->list_off, idx->list_ids, kk, cids);
       ADN_LAUNCH("select_kernel");
     }
     {
       StageTimer t(ST_RERANK, st);
-      if ((rc = launch_rerank(cids, kk, nb, qs, dsp, d_s, idx, mscale, k, out_ids + b0 * k,
-                              out_dist + b0 * k, st)))
+      if ((rc = launch_rerank_lists(cids, kk, nb, qs, dsp, d_s, idx, mscale, k, out_ids + b0 * k,
+                                    out_dist + b0 * k, st)))
         return rc;
     }
   }

@@ -8,8 +8,8 @@
 // with tcgen05.mma (FP32 accumulation in tensor memory), 256 members at a time,
 // and turns each dot product into an approximate squared distance
 //     d ~ |q|^2 + |x|^2 - 2 s_q s_x nu_x (q . x)
-// (prefix-normalised metric), written as FP16 into the query's candidate
-// segment.  A selection kernel then keeps each query's best k' candidates and
+// (prefix-normalised metric, so d lies in [0, 4]), written as a 16-bit
+// fixed-point key round(d * 2^14) into the query's candidate segment.  A selection kernel then keeps each query's best k' candidates and
 // the exact FP32 rerank (Sec. 4.3 shortlist-rerank) produces the result.
 //
 // Warp roles (192 threads): warp 0 issues TMA tile loads into a 4-stage
@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   unsigned char *sA = smem;                              // NSTAGE x 16 KB
   unsigned char *sB = smem + NSTAGE * A_BYTES;           // NSTAGE x 32 KB
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2];
+  __shared__ float s_cb[2][BN], s_ca[2][BN];  // per member of the tile: -2 s_x nu_x, |x|^2
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
 
@@ -293,6 +294,17 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         tc_fence_after();
+        // the tile's per-member terms, staged once for the four epilogue warps
+        {
+          const int et = threadIdx.x - 64;
+          for (int i = et; i < BN; i += 128) {
+            const int m = mt * BN + i;
+            const float c = m < nl ? __ldg(a.cx + off + m) : 0.f;
+            s_cb[acc][i] = -2.f * c;
+            s_ca[acc][i] = m < nl ? (c > 0.f ? 1.f : 0.f) : 3.0e38f;
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
         const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -303,20 +315,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t packed[16];
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
-              float dd[2];
+              uint32_t kk[2];
 #pragma unroll
               for (int u = 0; u < 2; ++u) {
-                const int m = m0 + j + u;
-                float d = __int_as_float(0x7f800000);
-                if (m < nl) {
-                  const float c = __ldg(a.cx + off + m);
-                  d = q2 + (c > 0.f ? 1.f : 0.f) - 2.f * qs * c * __uint_as_float(r[j + u]);
-                  d = fmaxf(d, 0.f);
-                }
-                dd[u] = d;
+                // approximate squared distance as a 16-bit fixed-point key:
+                // round(d * 2^14), d clamped to [0, 4); members past the list
+                // end get the largest key
+                const int c = c0 + j + u;
+                float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[j + u]), q2 + s_ca[acc][c]);
+                d = fminf(fmaxf(d, 0.f), 3.9999f);
+                kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
               }
-              const __half2 h = __floats2half2_rn(dd[0], dd[1]);
-              packed[j >> 1] = *(const uint32_t *)&h;
+              packed[j >> 1] = kk[0] | (kk[1] << 16);
             }
             uint4 *dst = (uint4 *)(a.cand + base + m0);
 #pragma unroll
