@@ -215,7 +215,9 @@ def timed(P, torch, step, steps, stream):
     torch.cuda.synchronize()
     launches = (P.launch_count() - l0) // steps
     prof = P.profile_read()
+    host = P.profile_read_host()
     P.profile_enable(False)
+    prof["_host_us"] = (sum(host.values()) / steps, 1)
     return ev0.elapsed_time(ev1) / steps, launches, prof
 
 

@@ -79,6 +79,8 @@ int64_t adanns_launch_count(void);
  */
 int adanns_profile_enable(int on);
 int adanns_profile_read(double *ms, int64_t *count, int nstage);
+/* Host wall time (microseconds, summed) spent issuing each stage's work. */
+int adanns_profile_read_host(double *us, int nstage);
 
 /*
  * Build an AdANNS-IVF index (Algorithm 1 adannsConstruction; Sec. 3 "IVF":

@@ -49,6 +49,7 @@ def lib():
         L.adanns_launch_count.restype = i64
         L.adanns_profile_enable.argtypes = [i32]
         L.adanns_profile_read.argtypes = [P, P, i32]
+        L.adanns_profile_read_host.argtypes = [P, i32]
         L.adanns_build_ivf.argtypes = [P, i64, i32, i32, i32, i32, i64, u64, i32, i32, P, P, P]
         L.adanns_index_create.argtypes = [P, i64, i32, P, i32, i32, P, i32, i32, P, P]
         L.adanns_index_info.argtypes = [P, P, P, P, P, P]
@@ -75,7 +76,8 @@ def launch_count() -> int:
     return int(lib().adanns_launch_count())
 
 
-STAGES = ("prep", "coarse", "invert", "scan", "merge", "lut", "adc", "rerank", "mma", "select")
+STAGES = ("prep", "coarse", "invert", "scan", "merge", "lut", "adc", "rerank", "mma", "select",
+          "rr_sort", "rr_pairs", "rr_final")
 STORE_BF16 = 2
 STORE_FP8 = 4
 
@@ -92,6 +94,14 @@ def profile_read(nstage: int = 16) -> dict:
     _check(lib().adanns_profile_read(ms, cnt, nstage))
     names = list(STAGES) + [f"stage{i}" for i in range(len(STAGES), nstage)]
     return {names[i]: (ms[i], cnt[i]) for i in range(nstage) if cnt[i]}
+
+
+def profile_read_host(nstage: int = 16) -> dict:
+    """{stage: host microseconds spent issuing it} since profiling was enabled."""
+    us = (ctypes.c_double * nstage)()
+    _check(lib().adanns_profile_read_host(us, nstage))
+    names = list(STAGES) + [f"stage{i}" for i in range(len(STAGES), nstage)]
+    return {names[i]: us[i] for i in range(nstage) if us[i]}
 
 
 def _check(rc: int):

@@ -51,7 +51,14 @@ extern std::atomic<long long> g_launches;  // kernels launched since load
   } while (0)
 
 // ---------------------------------------------------------------- scratch
-// Stream-ordered scratch allocation (cudaMallocAsync on the call's stream).
+// The library's own stream-ordered memory pool for the current device: its
+// release threshold is unlimited, so scratch freed at the end of one call is
+// reused by the next without returning memory to the driver.
+cudaMemPool_t scratch_pool();
+// Bytes of scratch one search call may hold at once (ADANNS_SCRATCH_GB, default 12).
+int64_t scratch_budget();
+
+// Stream-ordered scratch allocation from that pool on the call's stream.
 struct Scratch {
   cudaStream_t st;
   void *ptrs[64];
@@ -65,7 +72,9 @@ struct Scratch {
     void *p = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    cudaMemPool_t pool = scratch_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st)
+                         : cudaMallocAsync(&p, bytes, st);
     if (e != cudaSuccess || n >= 64) {
       cudaGetLastError();
       if (p) cudaFreeAsync(p, st);
@@ -137,7 +146,8 @@ int build_csr(const int32_t *assign, int64_t N, int nlist, int64_t *list_off, in
 // ---------------------------------------------------------------- profiling
 enum Stage {
   ST_PREP = 0, ST_COARSE = 1, ST_INVERT = 2, ST_SCAN = 3, ST_MERGE = 4, ST_LUT = 5, ST_ADC = 6,
-  ST_RERANK = 7, ST_MMA = 8, ST_SELECT = 9, ST_NSTAGE = 16
+  ST_RERANK = 7, ST_MMA = 8, ST_SELECT = 9, ST_RR_SORT = 10, ST_RR_PAIRS = 11, ST_RR_FINAL = 12,
+  ST_NSTAGE = 16
 };
 
 // Tensor-core list scan of the mixed-precision path (mma_scan.cu).
@@ -167,6 +177,7 @@ class StageTimer {
   int stage_;
   cudaStream_t st_;
   cudaEvent_t a_ = nullptr, b_ = nullptr;
+  double t0_ = 0.0;
 };
 
 int build_lowp(adanns_index *x, const float *db, int which, cudaStream_t st);

@@ -402,7 +402,8 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   const int64_t seg_q = (int64_t)nprobe * (((int64_t)idx->max_list + 7) & ~7ll);
   const int64_t per_q = seg_q * 2 + (int64_t)nprobe * ((int64_t)nkb * 128 * 128 / qt + 32) +
                         (int64_t)(dcp + dsp) * 4 + (int64_t)nkb * 128 + (int64_t)kk * 8 + 64;
-  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (3ll << 30) / per_q));
+  // slices bounded by a scratch budget (the candidate keys dominate it)
+  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
   const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
   Scratch s(st);
   float *qc, *qs, *qn2, *qsc;

@@ -1,6 +1,7 @@
 // Optional per-stage timing with CUDA events recorded on the launching stream.
 // Off by default; when on, every profiled stage of every call records an event
 // pair around its launches, and adanns_profile_read sums the elapsed times.
+#include <chrono>
 #include <mutex>
 #include <vector>
 
@@ -17,6 +18,13 @@ std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
+double g_host_us[ST_NSTAGE] = {0};
+
+double now_us() {
+  return std::chrono::duration<double, std::micro>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -36,6 +44,7 @@ cudaEvent_t take_event() {
 StageTimer::StageTimer(int stage, cudaStream_t st) : stage_(stage), st_(st) {
   std::lock_guard<std::mutex> g(g_mu);
   if (!g_on) return;
+  t0_ = now_us();
   a_ = take_event();
   b_ = take_event();
   if (a_ && b_) cudaEventRecord(a_, st_);
@@ -44,6 +53,7 @@ StageTimer::StageTimer(int stage, cudaStream_t st) : stage_(stage), st_(st) {
 StageTimer::~StageTimer() {
   std::lock_guard<std::mutex> g(g_mu);
   if (!a_ || !b_) return;
+  if (stage_ >= 0 && stage_ < ST_NSTAGE) g_host_us[stage_] += now_us() - t0_;
   cudaEventRecord(b_, st_);
   g_recs.push_back({stage_, a_, b_});
 }
@@ -61,7 +71,15 @@ int adanns_profile_enable(int on) {
     g_pool.push_back(r.b);
   }
   g_recs.clear();
+  for (int i = 0; i < ST_NSTAGE; ++i) g_host_us[i] = 0.0;
   g_on = on != 0;
+  return ADANNS_OK;
+}
+
+int adanns_profile_read_host(double *us, int nstage) {
+  if (!us || nstage < 1) return fail(ADANNS_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> g(g_mu);
+  for (int i = 0; i < nstage; ++i) us[i] = i < ST_NSTAGE ? g_host_us[i] : 0.0;
   return ADANNS_OK;
 }
 

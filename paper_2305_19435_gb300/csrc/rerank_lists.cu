@@ -156,28 +156,37 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
   if ((rc = s.get(&plist, n)) || (rc = s.get(&pmem, n)) || (rc = s.get(&byl, n)) ||
       (rc = s.get(&order, n)) || (rc = s.get(&goff, (size_t)nlist + 2)) || (rc = s.get(&keys, n)))
     return rc;
-  pair_lists_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-      cand, n, nlist, idx->assign, idx->pos_of_id, idx->list_off, plist, pmem);
-  ADN_LAUNCH("pair_lists_kernel");
-  if ((rc = build_csr(plist, n, nlist + 1, goff, byl, st))) return rc;
-  const size_t hs = ((size_t)idx->max_list + 2) * 4;
-  ADN_CUDA(cudaFuncSetAttribute(member_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)hs));
-  member_sort_kernel<<<nlist + 1, 256, hs, st>>>(goff, byl, pmem, idx->list_off, nlist, order);
-  ADN_LAUNCH("member_sort_kernel");
-  const size_t rs = (size_t)RL_WARPS * d_s * 4;
-  ADN_CUDA(cudaFuncSetAttribute(rerank_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)rs));
-  const int64_t warps = (n + 31) / 32;
-  rerank_pairs_kernel<<<(unsigned)((warps + RL_WARPS - 1) / RL_WARPS), RL_WARPS * 32, rs, st>>>(
-      order, n, plist, pmem, cand, kr, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off, mscale,
-      nlist, keys);
-  ADN_LAUNCH("rerank_pairs_kernel");
-  const size_t fs = (size_t)4 * kr * 8;
-  ADN_CUDA(cudaFuncSetAttribute(final_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fs));
-  final_topk_kernel<<<(unsigned)((B + 3) / 4), 128, fs, st>>>(keys, kr, B, k, out_ids, out_dist);
-  ADN_LAUNCH("final_topk_kernel");
+  {
+    StageTimer t(ST_RR_SORT, st);
+    pair_lists_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        cand, n, nlist, idx->assign, idx->pos_of_id, idx->list_off, plist, pmem);
+    ADN_LAUNCH("pair_lists_kernel");
+    if ((rc = build_csr(plist, n, nlist + 1, goff, byl, st))) return rc;
+    const size_t hs = ((size_t)idx->max_list + 2) * 4;
+    ADN_CUDA(cudaFuncSetAttribute(member_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)hs));
+    member_sort_kernel<<<nlist + 1, 256, hs, st>>>(goff, byl, pmem, idx->list_off, nlist, order);
+    ADN_LAUNCH("member_sort_kernel");
+  }
+  {
+    StageTimer t(ST_RR_PAIRS, st);
+    const size_t rs = (size_t)RL_WARPS * d_s * 4;
+    ADN_CUDA(cudaFuncSetAttribute(rerank_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)rs));
+    const int64_t warps = (n + 31) / 32;
+    rerank_pairs_kernel<<<(unsigned)((warps + RL_WARPS - 1) / RL_WARPS), RL_WARPS * 32, rs, st>>>(
+        order, n, plist, pmem, cand, kr, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off,
+        mscale, nlist, keys);
+    ADN_LAUNCH("rerank_pairs_kernel");
+  }
+  {
+    StageTimer t(ST_RR_FINAL, st);
+    const size_t fs = (size_t)4 * kr * 8;
+    ADN_CUDA(cudaFuncSetAttribute(final_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fs));
+    final_topk_kernel<<<(unsigned)((B + 3) / 4), 128, fs, st>>>(keys, kr, B, k, out_ids, out_dist);
+    ADN_LAUNCH("final_topk_kernel");
+  }
   return ADANNS_OK;
 }
 

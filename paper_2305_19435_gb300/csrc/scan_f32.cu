@@ -16,6 +16,10 @@
 // Distances never leave the SM: each query keeps a shared-memory candidate
 // buffer; a candidate enters only if its key beats the query's current k-th
 // key, and a warp sorts and trims the buffer when it fills.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "devutil.cuh"
 #include "internal.cuh"
 
@@ -325,11 +329,30 @@ int launch_scan_f32(const ScanArgs &a, cudaStream_t st) {
   void (*kern)(ScanArgs, int) = c.cap == 0 ? scan_f32_kernel<4, true>
                                 : c.tq == 4 ? scan_f32_kernel<4, false>
                                             : scan_f32_kernel<1, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-  if (e != cudaSuccess) return cuda_fail(e, "scan attribute");
-  int per_sm = 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, c.smem);
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  // attribute and occupancy per (kernel, shared memory size), cached per device
+  static std::mutex mu;
+  static std::map<std::tuple<int, void *, size_t>, int> occ;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_tuple(dev, (void *)kern, c.smem);
+    auto it = occ.find(key);
+    if (it != occ.end()) {
+      per_sm = it->second;
+    } else {
+      cudaError_t e =
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+      if (e != cudaSuccess) return cuda_fail(e, "scan attribute");
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, c.smem);
+      if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      occ[key] = per_sm;
+    }
+  }
   const int grid = a.grid > 0 ? a.grid : num_sms() * per_sm;
   kern<<<grid, THREADS, c.smem, st>>>(a, c.cap);
   ADN_LAUNCH("scan_f32_kernel");

@@ -1,5 +1,6 @@
 // Query preparation, probe inversion into (list, query-tile) work, and the
 // cross-list top-k merge of AdANNS-IVF search (Algorithm 1 adannsInference).
+#include <cstdlib>
 #include <mutex>
 
 #include "devutil.cuh"
@@ -27,6 +28,43 @@ int cuda_fail(cudaError_t e, const char *what) {
   return ADANNS_ERR_CUDA;
 }
 const char *last_error() { return g_err.c_str(); }
+
+cudaMemPool_t scratch_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+int64_t scratch_budget() {
+  static int64_t b = [] {
+    const char *e = getenv("ADANNS_SCRATCH_GB");
+    double gb = e ? atof(e) : 12.0;
+    if (!(gb > 0.0)) gb = 12.0;
+    return (int64_t)(gb * (double)(1ll << 30));
+  }();
+  return b;
+}
 
 int num_sms() {
   static int sms[64] = {0};
