@@ -129,6 +129,11 @@ int adanns_index_get_lists(const adanns_index *idx, int64_t *list_off, int32_t *
 /* Copy the FP32 centroids (nlist x d_c) to a device buffer. */
 int adanns_index_get_centroids(const adanns_index *idx, float *centroids, void *cuda_stream);
 
+/* Status of the index's device work: synchronises the stream, returns
+ * ADANNS_ERR_TIMEOUT if a bounded wait of a tensor-core pipeline gave up since
+ * the last check (the results of that call are then invalid), and clears it. */
+int adanns_index_status(const adanns_index *idx, void *cuda_stream);
+
 /* Release an index (NULL is ignored).  Waits for the device to finish using it. */
 void adanns_index_free(adanns_index *idx);
 
@@ -169,9 +174,8 @@ int adanns_kmeans_update(const float *points, int64_t n, int ld, int dim, int me
  *            with the exact FP32 dist_ds (Sec. 4.3 shortlist-rerank) and the
  *            k best by (distance, id) are returned -- the returned distances
  *            are exact; ids can differ from the FP32 scan where the exact
- *            top-k was not in the approximate shortlist.  This variant
- *            synchronises the stream once, at the end, to report a
- *            tensor-core pipeline timeout as ADANNS_ERR_TIMEOUT.
+ *            top-k was not in the approximate shortlist.  A tensor-core
+ *            pipeline timeout is reported by adanns_index_status.
  *   out_ids  int64 [B x k], out_dist FP32 [B x k] (device, caller-owned).
  *   out_probes optional int32 [B x nprobe]: the probed lists, nearest first.
  * Scratch memory is taken from the CUDA stream-ordered allocator and returned
@@ -259,6 +263,44 @@ int adanns_index_get_opq(const adanns_index *idx, float *R, float *codebooks,
 int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t B, int d_c,
                          int nprobe, int k, int rerank_k, int64_t *out_ids, float *out_dist,
                          int32_t *out_probes, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Autotuning of the exact FP32 list scan.  adanns_autotune_search runs the
+ * FP32 search of the given batch with each work-item shape of the list scan
+ * (64 queries per (list, query-tile) item with a 4 x 8 register tile per
+ * thread; 16 queries with 1 x 8), times each with CUDA events (1 warm-up, 3
+ * timed runs; synchronises) and records the faster for the bucket
+ * (device, k rounded up to a power of two, d_s, floor(log2(1 + B * nprobe /
+ * nlist))).  Later FP32 searches in the same bucket use it.  *chosen gets the
+ * queries per thread of the winner (4 or 1), *best_ms its time per call; both
+ * may be NULL.  out_ids / out_dist receive the batch's results.
+ * adanns_tune_save / adanns_tune_load write / merge the table as text lines
+ * "<bucket key> <queries per thread>".
+ * ---------------------------------------------------------------------- */
+int adanns_autotune_search(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                           int d_s, int nprobe, int k, int64_t *out_ids, float *out_dist,
+                           void *cuda_stream, int *chosen, float *best_ms);
+int adanns_tune_save(const char *path);
+int adanns_tune_load(const char *path);
+
+/* ------------------------------------------------------------------------
+ * Search plans (batched search replayed from a captured CUDA graph).
+ * adanns_plan_create runs adanns_search_ivf once with the given arguments on
+ * cuda_stream (validating them, setting kernel attributes, growing the
+ * scratch pool; synchronises), then captures the same call on a private
+ * stream into a CUDA graph.  The plan is bound to the given device buffers:
+ * each adanns_plan_launch re-runs the whole search (cluster mapping, probe
+ * inversion, list scan, selection, rerank, merge) on the current contents of
+ * `queries`, writing out_ids / out_dist, with one graph launch on
+ * cuda_stream.  A plan may not run concurrently with itself.  Free it with
+ * adanns_plan_free (waits for the device).
+ * ---------------------------------------------------------------------- */
+typedef struct adanns_plan adanns_plan;
+int adanns_plan_create(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
+                       int nprobe, int k, int storage, int rerank_k, int64_t *out_ids,
+                       float *out_dist, void *cuda_stream, adanns_plan **out);
+int adanns_plan_launch(adanns_plan *plan, void *cuda_stream);
+void adanns_plan_free(adanns_plan *plan);
 
 /*
  * Size of the fixed device scratch array used by adanns_search_ivf_noalloc

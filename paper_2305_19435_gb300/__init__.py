@@ -67,6 +67,14 @@ def lib():
         L.adanns_index_set_opq.argtypes = [P, i32, i32, P, P, P, P]
         L.adanns_index_get_opq.argtypes = [P, P, P, P, P]
         L.adanns_search_ivfopq.argtypes = [P, P, i64, i32, i32, i32, i32, P, P, P, P]
+        L.adanns_index_status.argtypes = [P, P]
+        L.adanns_autotune_search.argtypes = [P, P, i64, i32, i32, i32, i32, P, P, P, P, P]
+        L.adanns_tune_save.argtypes = [ctypes.c_char_p]
+        L.adanns_tune_load.argtypes = [ctypes.c_char_p]
+        L.adanns_plan_create.argtypes = [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, P, P]
+        L.adanns_plan_launch.argtypes = [P, P]
+        L.adanns_plan_free.argtypes = [P]
+        L.adanns_plan_free.restype = None
         _lib = L
     return _lib
 
@@ -162,6 +170,10 @@ class Index:
         ids = torch.empty(self.N, dtype=torch.int32, device="cuda")
         _check(lib().adanns_index_get_lists(self.handle, _ptr(off), _ptr(ids), _stream()))
         return off, ids
+
+    def status(self):
+        """Raise if a tensor-core pipeline wait timed out since the last check (synchronises)."""
+        _check(lib().adanns_index_status(self.handle, _stream()))
 
     def centroids(self):
         c = torch.empty(self.nlist, self.d_c, dtype=torch.float32, device="cuda")
@@ -318,3 +330,60 @@ def search_ivfopq(index: Index, queries: torch.Tensor, d_c: int, nprobe: int, k:
     _check(lib().adanns_search_ivfopq(index.handle, _ptr(queries), B, d_c, nprobe, k, rerank_k,
                                       _ptr(ids), _ptr(dist), _ptr(probes), _stream()))
     return (ids, dist, probes) if return_probes else (ids, dist)
+
+
+# ---------------------------------------------------------------- graph plans
+class Plan:
+    """A fixed-shape search captured into a CUDA graph; `launch()` replays it
+    on the current contents of `queries`, writing `ids` / `dist`."""
+
+    def __init__(self, index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: int,
+                 k: int, storage: int = STORE_F32, rerank_k: int = 0):
+        _need(queries, torch.float32, "queries", 2)
+        self.index, self.queries = index, queries
+        B = queries.shape[0]
+        self.ids = torch.empty(B, k, dtype=torch.int64, device=queries.device)
+        self.dist = torch.empty(B, k, dtype=torch.float32, device=queries.device)
+        h = ctypes.c_void_p()
+        _check(lib().adanns_plan_create(index.handle, _ptr(queries), B, d_c, d_s, nprobe, k,
+                                        storage, rerank_k, _ptr(self.ids), _ptr(self.dist),
+                                        _stream(), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self):
+        _check(lib().adanns_plan_launch(self._h, _stream()))
+        return self.ids, self.dist
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.adanns_plan_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- autotuner
+def autotune(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: int, k: int):
+    """Time the FP32 list-scan variants on this batch and record the faster
+    for its shape bucket; returns (queries per thread, ms per call)."""
+    _need(queries, torch.float32, "queries", 2)
+    B = queries.shape[0]
+    ids = torch.empty(B, k, dtype=torch.int64, device=queries.device)
+    dist = torch.empty(B, k, dtype=torch.float32, device=queries.device)
+    ch, ms = ctypes.c_int(), ctypes.c_float()
+    _check(lib().adanns_autotune_search(index.handle, _ptr(queries), B, d_c, d_s, nprobe, k,
+                                        _ptr(ids), _ptr(dist), _stream(), ctypes.byref(ch),
+                                        ctypes.byref(ms)))
+    return ch.value, ms.value
+
+
+def tune_save(path: str):
+    _check(lib().adanns_tune_save(path.encode()))
+
+
+def tune_load(path: str):
+    _check(lib().adanns_tune_load(path.encode()))

@@ -54,6 +54,7 @@ void free_index(adanns_index *x) {
   cudaFree(x->list_ids);
   cudaFree(x->xpm);
   cudaFree(x->invn);
+  cudaFree(x->dev_err);
   cudaFree(x->assign);
   cudaFree(x->pos_of_id);
   cudaFree(x->opq_R);
@@ -172,7 +173,8 @@ int make_index(const float *db, int64_t N, int d, const float *centroids, int nl
       (rc = dmalloc(&x->list_off, (size_t)nlist + 1)) || (rc = dmalloc(&x->list_ids, (size_t)N)) ||
       (rc = dmalloc(&x->xpm, (size_t)N * x->d_pad)) ||
       (rc = dmalloc(&x->invn, (size_t)std::max(x->ng, 1) * N)) ||
-      (rc = dmalloc(&x->assign, (size_t)N)) || (rc = dmalloc(&x->pos_of_id, (size_t)N))) {
+      (rc = dmalloc(&x->assign, (size_t)N)) || (rc = dmalloc(&x->pos_of_id, (size_t)N)) ||
+      (rc = dmalloc(&x->dev_err, 1))) {
     free_index(x);
     return rc;
   }
@@ -181,6 +183,8 @@ int make_index(const float *db, int64_t N, int d, const float *centroids, int nl
     free_index(x);
     return code;
   };
+  if (cudaMemsetAsync(x->dev_err, 0, sizeof(int), st) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "clear status"));
   if (cudaMemcpyAsync(x->centroids, centroids, sizeof(float) * nlist * d_c,
                       cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return bail(cuda_fail(cudaGetLastError(), "copy centroids"));
@@ -329,6 +333,18 @@ int adanns_index_get_centroids(const adanns_index *idx, float *centroids, void *
   return ADANNS_OK;
 }
 
+int adanns_index_status(const adanns_index *idx, void *cuda_stream) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  cudaStream_t st = S(cuda_stream);
+  int h = 0;
+  ADN_CUDA(cudaMemcpyAsync(&h, idx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ADN_CUDA(cudaMemsetAsync(idx->dev_err, 0, sizeof(int), st));
+  ADN_CUDA(cudaStreamSynchronize(st));
+  if (h) return fail(ADANNS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (stage " +
+                                             std::to_string(h) + ")");
+  return ADANNS_OK;
+}
+
 void adanns_index_free(adanns_index *idx) {
   if (!idx) return;
   cudaDeviceSynchronize();
@@ -403,7 +419,8 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
   cudaStream_t st = S(cuda_stream);
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
-  const int qt = scan_query_tile(k);
+  const int tq = tuned_scan_tq(k, d_s, (double)B * nprobe / nlist);
+  const int qt = scan_query_tile(k, tq);
   // slice the batch so that the per-(query, probe) partial results stay ~2 GiB
   const int64_t per_q = (int64_t)nprobe * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
   const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (2ll << 30) / per_q));
@@ -475,6 +492,7 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
     l.pair_out = pair_out;
     l.k = k;
     l.out_keys = pkeys;
+    l.tq = tq;
     {
       StageTimer t(ST_SCAN, st);
       if ((rc = launch_scan_f32(l, st))) return rc;

@@ -1,0 +1,137 @@
+// Autotuner for the exact FP32 list scan.
+//
+// The tunable is the work-item shape of the list scan: 64 queries per
+// (list, query-tile) item with a 4 x 8 register tile per thread, or 16
+// queries with a 1 x 8 tile.  The first amortises each list block over more
+// queries (batched regime); the second needs a quarter of the top-k buffers,
+// so more CTAs stay resident when few queries share a list (small batches,
+// serving).  adanns_autotune_search times both on the caller's real batch
+// with CUDA events and records the faster under a bucket key
+// (device, k rounded up to a power of two, d_s, log2 of queries per probed
+// list); adanns_search_ivf then uses the recorded choice for matching calls.
+#include <cmath>
+#include <cstdio>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+
+#include "internal.cuh"
+
+namespace adn {
+
+namespace {
+std::mutex g_tmu;
+std::map<std::string, int> g_table;
+thread_local int g_force_tq = 0;
+
+std::string device_tag() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string name = p.name;
+  for (auto &ch : name)
+    if (ch == ' ') ch = '_';
+  return name + "-" + std::to_string(p.multiProcessorCount);
+}
+
+std::string bucket_key(int k, int d_s, double qpl) {
+  int kp = 1;
+  while (kp < k) kp <<= 1;
+  const int qb = (int)std::floor(std::log2(qpl + 1.0));
+  return device_tag() + "|k" + std::to_string(kp) + "|ds" + std::to_string(d_s) + "|q" +
+         std::to_string(qb);
+}
+}  // namespace
+
+int tuned_scan_tq(int k, int d_s, double queries_per_list) {
+  if (g_force_tq) return g_force_tq;
+  std::lock_guard<std::mutex> g(g_tmu);
+  if (g_table.empty()) return 0;
+  auto it = g_table.find(bucket_key(k, d_s, queries_per_list));
+  return it == g_table.end() ? 0 : it->second;
+}
+
+}  // namespace adn
+
+using namespace adn;
+
+extern "C" {
+
+int adanns_autotune_search(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                           int d_s, int nprobe, int k, int64_t *out_ids, float *out_dist,
+                           void *cuda_stream, int *chosen, float *best_ms) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  if (B < 1) return fail(ADANNS_ERR_ARG, "need a non-empty batch");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0, e1;
+  ADN_CUDA(cudaEventCreate(&e0));
+  ADN_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_t = 0.f;
+  int rc = ADANNS_OK;
+  const int cands[2] = {4, 1};
+  for (int ci = 0; ci < 2 && rc == ADANNS_OK; ++ci) {
+    const int tq = cands[ci];
+    if (tq == 4 && k > 128) continue;
+    g_force_tq = tq;
+    rc = adanns_search_ivf(idx, queries, B, d_c, d_s, nprobe, k, ADANNS_STORE_F32, 0, out_ids,
+                           out_dist, nullptr, cuda_stream);
+    if (rc) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && rc == ADANNS_OK; ++r)
+      rc = adanns_search_ivf(idx, queries, B, d_c, d_s, nprobe, k, ADANNS_STORE_F32, 0, out_ids,
+                             out_dist, nullptr, cuda_stream);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.f;
+    if (best == 0 || ms < best_t) {
+      best = tq;
+      best_t = ms;
+    }
+  }
+  g_force_tq = 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> g(g_tmu);
+    g_table[bucket_key(k, d_s, (double)B * nprobe / idx->nlist)] = best;
+  }
+  if (chosen) *chosen = best;
+  if (best_ms) *best_ms = best_t;
+  return ADANNS_OK;
+}
+
+int adanns_tune_save(const char *path) {
+  if (!path) return fail(ADANNS_ERR_ARG, "path is NULL");
+  std::lock_guard<std::mutex> g(g_tmu);
+  std::ofstream f(path);
+  if (!f) return fail(ADANNS_ERR_ARG, std::string("cannot write ") + path);
+  for (auto &kv : g_table) f << kv.first << " " << kv.second << "\n";
+  return ADANNS_OK;
+}
+
+int adanns_tune_load(const char *path) {
+  if (!path) return fail(ADANNS_ERR_ARG, "path is NULL");
+  std::ifstream f(path);
+  if (!f) return fail(ADANNS_ERR_ARG, std::string("cannot read ") + path);
+  std::lock_guard<std::mutex> g(g_tmu);
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream ss(line);
+    std::string key;
+    int tq = 0;
+    if (ss >> key >> tq && (tq == 1 || tq == 4)) g_table[key] = tq;
+  }
+  return ADANNS_OK;
+}
+
+}  // extern "C"

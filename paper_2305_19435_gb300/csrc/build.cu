@@ -279,8 +279,8 @@ int build_csr(const int32_t *assign, int64_t N, int nlist, int64_t *list_off, in
   int rc;
   if ((rc = s.get(&counts, nc)) || (rc = s.get(&scanned, nc)) || (rc = s.get(&bsum, nb))) return rc;
   const size_t hs = (size_t)nlist * 4;
-  ADN_CUDA(cudaFuncSetAttribute(csr_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs));
-  ADN_CUDA(cudaFuncSetAttribute(csr_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs));
+  ADN_CUDA(ensure_smem((const void *)csr_hist_kernel, (size_t)(hs)));
+  ADN_CUDA(ensure_smem((const void *)csr_scatter_kernel, (size_t)(hs)));
   if (ntile > 0) {
     csr_hist_kernel<<<ntile, 256, hs, st>>>(assign, N, nlist, ntile, counts);
     ADN_LAUNCH("csr_hist_kernel");

@@ -109,9 +109,14 @@ struct ScanArgs {
   int k;
   uint64_t *out_keys;      // [row][k] sorted keys (KEY_MAX padding)
   int grid;                // CTAs to launch
+  int tq;                  // queries per thread (QT = 16 tq); 0 = by k
 };
 int launch_scan_f32(const ScanArgs &a, cudaStream_t st);
-int scan_query_tile(int k);  // queries per work item for a given k
+int scan_query_tile(int k, int tq = 0);  // queries per work item
+
+// Autotuned choices: queries per thread of the list scan for a shape bucket
+// (device, k, d_s, queries per probed list); 0 when not tuned.
+int tuned_scan_tq(int k, int d_s, double queries_per_list);
 
 // ---------------------------------------------------------------- helpers
 int launch_prep_queries(const float *q, int64_t B, int ld, int dims_a, int dims_b, int metric,
@@ -126,6 +131,8 @@ int launch_invert_probes(const uint64_t *ckeys, int64_t B, int nprobe, int nlist
 int launch_merge(const uint64_t *pkeys, int64_t B, int nprobe, int k, int64_t *out_ids,
                  float *out_dist, cudaStream_t st);
 int num_sms();
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (device, kernel, size)
+cudaError_t ensure_smem(const void *fn, size_t bytes);
 
 // ---------------------------------------------------------------- build
 int launch_gather_normalize(const float *x, int64_t n, int ld, const int64_t *rows, int dim,
@@ -213,4 +220,5 @@ struct adanns_index {
   float *lowp_sx[2] = {nullptr, nullptr};  // per-vector scale, list order
   float *lowp_cx[2] = {nullptr, nullptr};  // [ng][N] scale * inverse prefix norm
   int64_t *h_list_off = nullptr;  // host copy of list offsets
+  int *dev_err = nullptr;         // sticky device status word (tensor-core pipeline timeouts)
 };

@@ -409,7 +409,8 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   float *qc, *qs, *qn2, *qsc;
   uint64_t *ckeys;
   int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
-  int *ntiles, *counter, *err;
+  int *ntiles, *counter;
+  int *err = idx->dev_err;
   int64_t *qtot, *qbase, *pbase, *cids;
   unsigned char *qlow, *qtile;
   uint16_t *cand;
@@ -420,7 +421,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
       (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
       (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
       (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) ||
-      (rc = s.get(&counter, 2)) || (rc = s.get(&err, 1)) || (rc = s.get(&qtot, Bc)) ||
+      (rc = s.get(&counter, 2)) || (rc = s.get(&qtot, Bc)) ||
       (rc = s.get(&qbase, Bc)) || (rc = s.get(&pbase, (size_t)Bc * nprobe)) ||
       (rc = s.get(&cids, (size_t)Bc * kk)) || (rc = s.get(&qlow, (size_t)Bc * nkb * 128)) ||
       (rc = s.get(&qtile, (size_t)max_tiles * nkb * 128 * 128)) ||
@@ -429,7 +430,6 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   const int gi = gran_index(d_s);
   const float *mscale = idx->invn + (int64_t)gi * idx->N;
   const float *cx = idx->lowp_cx[which] + (int64_t)gi * idx->N;
-  ADN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   for (int64_t b0 = 0; b0 < B; b0 += Bc) {
     const int64_t nb = std::min(Bc, B - b0);
     {
@@ -510,12 +510,8 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
         return rc;
     }
   }
-  // surface a timed-out tensor-core pipeline as an error of this call
-  int h_err = 0;
-  ADN_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  ADN_CUDA(cudaStreamSynchronize(st));
-  if (h_err) return fail(ADANNS_ERR_TIMEOUT, "tensor-core scan pipeline timed out (stage " +
-                                                 std::to_string(h_err) + ")");
+  // a timed-out tensor-core pipeline sets the index's sticky status word,
+  // reported (and cleared) by adanns_index_status
   return ADANNS_OK;
 }
 

@@ -407,8 +407,7 @@ int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t
   if ((rc = make_map(&tA, qtiles, qrows, BM, a.fp8 != 0))) return rc;
   if ((rc = make_map(&tB, xlow, xrows, BN, a.fp8 != 0))) return rc;
   const size_t smem = mma_scan_smem();
-  ADN_CUDA(cudaFuncSetAttribute(mma_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  ADN_CUDA(ensure_smem((const void *)mma_scan_kernel, (size_t)(smem)));
   mma_scan_kernel<<<num_sms(), THREADS, smem, st>>>(tA, tB, a);
   ADN_LAUNCH("mma_scan_kernel");
   return ADANNS_OK;

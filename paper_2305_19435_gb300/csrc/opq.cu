@@ -50,8 +50,7 @@ int launch_pq_assign(const float *z, int64_t n, int ldz, int M, int dsub, const 
                      uint8_t *codes, float *mind, cudaStream_t st) {
   if (n <= 0) return ADANNS_OK;
   const size_t smem = (size_t)512 * dsub * 4;
-  ADN_CUDA(cudaFuncSetAttribute(pq_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  ADN_CUDA(ensure_smem((const void *)pq_assign_kernel, (size_t)(smem)));
   dim3 grid((unsigned)((n + 255) / 256), M);
   pq_assign_kernel<<<grid, 256, smem, st>>>(z, n, ldz, M, dsub, C, codes, mind);
   ADN_LAUNCH("pq_assign_kernel");
@@ -299,8 +298,7 @@ int launch_adc_scan(const AdcArgs &a, int qa, cudaStream_t st) {
   const size_t smem = (size_t)qa * a.M * 256 * 4 + (size_t)2 * qa * cap * 8 + (size_t)qa * 8 +
                       (size_t)qa * 16;
   if (smem > 220 * 1024) return fail(ADANNS_ERR_ARG, "ADC tile does not fit in shared memory");
-  ADN_CUDA(cudaFuncSetAttribute(adc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  ADN_CUDA(ensure_smem((const void *)adc_scan_kernel, (size_t)(smem)));
   int per_sm = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adc_scan_kernel, ADC_THREADS, smem) !=
           cudaSuccess ||
@@ -377,8 +375,7 @@ int launch_rerank(const int64_t *cand, int kr, int64_t B, const float *qs, int l
   if (B <= 0) return ADANNS_OK;
   const int cap = kr;
   const size_t smem = (size_t)RR_WARPS * ldq * 4 + (size_t)RR_WARPS * cap * 8;
-  ADN_CUDA(cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  ADN_CUDA(ensure_smem((const void *)rerank_kernel, (size_t)(smem)));
   rerank_kernel<<<(unsigned)((B + RR_WARPS - 1) / RR_WARPS), RR_WARPS * 32, smem, st>>>(
       cand, kr, B, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off, idx->assign, idx->pos_of_id,
       mscale, k, cap, out_ids, out_dist);

@@ -163,16 +163,14 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     ADN_LAUNCH("pair_lists_kernel");
     if ((rc = build_csr(plist, n, nlist + 1, goff, byl, st))) return rc;
     const size_t hs = ((size_t)idx->max_list + 2) * 4;
-    ADN_CUDA(cudaFuncSetAttribute(member_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)hs));
+    ADN_CUDA(ensure_smem((const void *)member_sort_kernel, (size_t)(hs)));
     member_sort_kernel<<<nlist + 1, 256, hs, st>>>(goff, byl, pmem, idx->list_off, nlist, order);
     ADN_LAUNCH("member_sort_kernel");
   }
   {
     StageTimer t(ST_RR_PAIRS, st);
     const size_t rs = (size_t)RL_WARPS * d_s * 4;
-    ADN_CUDA(cudaFuncSetAttribute(rerank_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)rs));
+    ADN_CUDA(ensure_smem((const void *)rerank_pairs_kernel, (size_t)(rs)));
     const int64_t warps = (n + 31) / 32;
     rerank_pairs_kernel<<<(unsigned)((warps + RL_WARPS - 1) / RL_WARPS), RL_WARPS * 32, rs, st>>>(
         order, n, plist, pmem, cand, kr, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off,
@@ -182,8 +180,7 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
   {
     StageTimer t(ST_RR_FINAL, st);
     const size_t fs = (size_t)4 * kr * 8;
-    ADN_CUDA(cudaFuncSetAttribute(final_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fs));
+    ADN_CUDA(ensure_smem((const void *)final_topk_kernel, (size_t)(fs)));
     final_topk_kernel<<<(unsigned)((B + 3) / 4), 128, fs, st>>>(keys, kr, B, k, out_ids, out_dist);
     ADN_LAUNCH("final_topk_kernel");
   }

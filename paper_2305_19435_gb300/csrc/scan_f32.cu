@@ -59,7 +59,7 @@ size_t smem_bytes(int qt, int cap) {
   return s;
 }
 
-ScanCfg choose(int k) {
+ScanCfg choose(int k, int tq) {
   ScanCfg c;
   if (k == 1) {
     c.tq = 4;
@@ -70,6 +70,7 @@ ScanCfg choose(int k) {
   const int kp = next_pow2(k);
   c.cap = kp + ROUND;
   c.tq = kp <= 128 ? 4 : 1;
+  if (tq == 1) c.tq = 1;  // a smaller query tile is valid for every k
   c.smem = smem_bytes(16 * c.tq, c.cap);
   return c;
 }
@@ -107,7 +108,7 @@ __device__ int compact_topk(uint64_t *buf, int na, int n, int k, uint64_t *scrat
 }
 }  // namespace
 
-int scan_query_tile(int k) { return 16 * choose(k).tq; }
+int scan_query_tile(int k, int tq) { return 16 * choose(k, tq).tq; }
 
 template <int TQ, bool TOP1>
 __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) {
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
 int launch_scan_f32(const ScanArgs &a, cudaStream_t st) {
   if (a.dims % 4 != 0 || a.dims > a.d_pad || a.d_pad % 16 != 0 || a.ldq % 4 != 0 || a.k < 1)
     return fail(ADANNS_ERR_ARG, "scan: bad dimensions");
-  const ScanCfg c = choose(a.k);
+  const ScanCfg c = choose(a.k, a.tq);
   void (*kern)(ScanArgs, int) = c.cap == 0 ? scan_f32_kernel<4, true>
                                 : c.tq == 4 ? scan_f32_kernel<4, false>
                                             : scan_f32_kernel<1, false>;
@@ -339,12 +340,12 @@ int launch_scan_f32(const ScanArgs &a, cudaStream_t st) {
     std::lock_guard<std::mutex> g(mu);
     auto key = std::make_tuple(dev, (void *)kern, c.smem);
     auto it = occ.find(key);
+    // the shared-memory limit is a property of the kernel: only ever raise it
+    cudaError_t e = ensure_smem((const void *)kern, c.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "scan attribute");
     if (it != occ.end()) {
       per_sm = it->second;
     } else {
-      cudaError_t e =
-          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-      if (e != cudaSuccess) return cuda_fail(e, "scan attribute");
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, c.smem);
       if (e != cudaSuccess || per_sm < 1) {
         cudaGetLastError();

@@ -1,6 +1,7 @@
 // Query preparation, probe inversion into (list, query-tile) work, and the
 // cross-list top-k merge of AdANNS-IVF search (Algorithm 1 adannsInference).
 #include <cstdlib>
+#include <map>
 #include <mutex>
 
 #include "devutil.cuh"
@@ -64,6 +65,20 @@ int64_t scratch_budget() {
     return (int64_t)(gb * (double)(1ll << 30));
   }();
   return b;
+}
+
+cudaError_t ensure_smem(const void *fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  auto key = std::make_pair(dev, fn);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[key] = bytes;
+  return e;
 }
 
 int num_sms() {
@@ -304,8 +319,7 @@ int launch_merge(const uint64_t *pkeys, int64_t B, int nprobe, int k, int64_t *o
   int cap = 2 * kp;
   if (cap < kp + 32) cap = kp + 32;
   const size_t smem = (size_t)MERGE_WPB * cap * 8;
-  cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_smem((const void *)merge_kernel, smem);
   if (e != cudaSuccess) return cuda_fail(e, "merge attribute");
   merge_kernel<<<(unsigned)((B + MERGE_WPB - 1) / MERGE_WPB), MERGE_WPB * 32, smem, st>>>(
       pkeys, B, nprobe, k, cap, out_ids, out_dist);
