@@ -134,6 +134,12 @@ int adanns_index_get_centroids(const adanns_index *idx, float *centroids, void *
  * the last check (the results of that call are then invalid), and clears it. */
 int adanns_index_status(const adanns_index *idx, void *cuda_stream);
 
+/* Upper bound of the scratch bytes adanns_search_ivf holds at once for these
+ * arguments (host-side arithmetic, no device access); -1 for bad arguments.
+ * Used for admission by device memory. */
+int64_t adanns_search_scratch_bytes(const adanns_index *idx, int64_t B, int d_c, int d_s,
+                                    int nprobe, int k, int storage, int rerank_k);
+
 /* Release an index (NULL is ignored).  Waits for the device to finish using it. */
 void adanns_index_free(adanns_index *idx);
 

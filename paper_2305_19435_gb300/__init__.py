@@ -68,6 +68,8 @@ def lib():
         L.adanns_index_get_opq.argtypes = [P, P, P, P, P]
         L.adanns_search_ivfopq.argtypes = [P, P, i64, i32, i32, i32, i32, P, P, P, P]
         L.adanns_index_status.argtypes = [P, P]
+        L.adanns_search_scratch_bytes.argtypes = [P, i64, i32, i32, i32, i32, i32, i32]
+        L.adanns_search_scratch_bytes.restype = i64
         L.adanns_autotune_search.argtypes = [P, P, i64, i32, i32, i32, i32, P, P, P, P, P]
         L.adanns_tune_save.argtypes = [ctypes.c_char_p]
         L.adanns_tune_load.argtypes = [ctypes.c_char_p]
@@ -228,6 +230,13 @@ def kmeans_update(points: torch.Tensor, assign: torch.Tensor, centroids: torch.T
     _check(lib().adanns_kmeans_update(_ptr(points), points.shape[0], points.shape[1], dim, metric,
                                       _ptr(assign), centroids.shape[0], _ptr(centroids), _stream()))
     return centroids
+
+
+def scratch_bytes(index: Index, B: int, d_c: int, d_s: int, nprobe: int, k: int,
+                  storage: int = STORE_F32, rerank_k: int = 0) -> int:
+    """Upper bound of the device scratch a search with these arguments holds."""
+    return int(lib().adanns_search_scratch_bytes(index.handle, B, d_c, d_s, nprobe, k, storage,
+                                                 rerank_k))
 
 
 def search_ivf(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: int, k: int,

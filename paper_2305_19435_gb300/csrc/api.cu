@@ -345,6 +345,25 @@ int adanns_index_status(const adanns_index *idx, void *cuda_stream) {
   return ADANNS_OK;
 }
 
+int64_t adanns_search_scratch_bytes(const adanns_index *idx, int64_t B, int d_c, int d_s,
+                                    int nprobe, int k, int storage, int rerank_k) {
+  if (!idx || B < 0 || nprobe < 1 || k < 1) return -1;
+  const int dcp = pad16(d_c), dsp = pad16(d_s);
+  if (storage == ADANNS_STORE_BF16 || storage == ADANNS_STORE_FP8E4M3) {
+    const int epb = storage == ADANNS_STORE_FP8E4M3 ? 128 : 64;
+    const int64_t nkb = (d_s + epb - 1) / epb;
+    const int64_t kk = rerank_k > k ? rerank_k : k;
+    const int64_t seg_q = (int64_t)nprobe * (((int64_t)idx->max_list + 7) & ~7ll);
+    const int64_t per_q = seg_q * 2 + (int64_t)nprobe * (nkb * 128 * 128 / 128 + 32) +
+                          (int64_t)(dcp + dsp) * 4 + nkb * 128 + kk * 8 + 64 + kk * 40;
+    const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
+    return Bc * per_q + (int64_t)idx->nlist * 64 + (64ll << 20);
+  }
+  const int64_t per_q = (int64_t)nprobe * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
+  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (2ll << 30) / per_q));
+  return Bc * per_q + (int64_t)idx->nlist * 64 + (16ll << 20);
+}
+
 void adanns_index_free(adanns_index *idx) {
   if (!idx) return;
   cudaDeviceSynchronize();

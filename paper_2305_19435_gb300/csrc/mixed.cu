@@ -229,9 +229,12 @@ constexpr int SEL_WARPS = SEL_THREADS / 32;
 constexpr int SEL_SAMPLE = 2048;
 constexpr int SEL_BUF = 4096;
 
+constexpr int SEL_TIE = 1024;
+
 struct SelState {
   int hist[256];
   int b1, below1, b2, below2, lt, lt2, eq, nb;
+  uint64_t ties[SEL_TIE];  // indices of the keys equal to the cut
 };
 
 // exact kk-smallest over n keys given by key(i) (16-bit), writing id(i) for
@@ -274,9 +277,39 @@ __device__ void radix_select(int n, int kk, KeyF key, IdF id, int64_t *o, SelSta
       o[atomicAdd(&st.lt, 1)] = id(i);
     } else if (k == T) {
       const int p = atomicAdd(&st.eq, 1);
-      if (p < need_eq) o[below2 + p] = id(i);
+      if (p < SEL_TIE) st.ties[p] = (uint64_t)i;
     }
   }
+  __syncthreads();
+  // ties at the cut: the need_eq entries with the smallest positions, so the
+  // result does not depend on thread timing
+  const int neq = st.eq;
+  if (neq <= SEL_TIE) {
+    if (threadIdx.x < 32) {
+      warp_sort(st.ties, neq);
+      for (int j = threadIdx.x; j < need_eq; j += 32) o[below2 + j] = id((int)st.ties[j]);
+    }
+  } else {
+    // many ties: an ordered pass ranks them by position (block prefix counts)
+    __shared__ int wsum[SEL_WARPS];
+    int base = 0;
+    for (int i0 = 0; i0 < n && base < need_eq; i0 += SEL_THREADS) {
+      const int i = i0 + tid;
+      const bool eq = i < n && key(i) == T;
+      const unsigned b = __ballot_sync(0xffffffffu, eq);
+      if ((tid & 31) == 0) wsum[tid >> 5] = __popc(b);
+      __syncthreads();
+      int before = base;
+      for (int w = 0; w < (tid >> 5); ++w) before += wsum[w];
+      before += __popc(b & ((1u << (tid & 31)) - 1u));
+      if (eq && before < need_eq) o[below2 + before] = id(i);
+      int tot = 0;
+      for (int w = 0; w < SEL_WARPS; ++w) tot += wsum[w];
+      __syncthreads();
+      base += tot;
+    }
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(SEL_THREADS) select_kernel(

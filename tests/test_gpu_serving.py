@@ -1,0 +1,71 @@
+"""The continuous-batching server on the GPU: requests with different budgets
+arrive while others run, are batched and overlapped, and every request's
+result equals the same request searched alone (identical ids; distances
+within the FP32 tolerance, in practice bit-identical since each query's
+arithmetic does not depend on its batch)."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+from parity import tol
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_2305_19435_gb300 as P
+    P.build()
+    data = synthdata.small(40_000, 3000, 256, 64, 601)
+    idx = {}
+    for d_c in (16, 64):
+        o = oracle.build_ivf(data["db"], d_c, 48, 6, 20_000, seed=31)
+        idx[d_c] = P.index_create(torch.from_numpy(data["db"]).cuda(),
+                                  torch.from_numpy(o["centroids"]).cuda(),
+                                  torch.from_numpy(o["assign"].astype(np.int32)).cuda(),
+                                  storage=3)
+    yield P, data, idx
+    for g in idx.values():
+        g.free()
+
+
+def test_results_same_alone_and_in_the_mix(setup):
+    P, data, idx = setup
+    from paper_2305_19435_gb300.serving import Budget, Server
+    budgets = [Budget(16, 128, 4, 10), Budget(64, 256, 8, 100, P.STORE_BF16, 400),
+               Budget(16, 64, 1, 10, P.STORE_BF16, 40), Budget(64, 192, 16, 10)]
+    rng = np.random.default_rng(7)
+    srv = Server(idx, streams=3, max_batch=1024, mem_budget=8 << 30)
+    reqs, q = [], data["queries"]
+    # a burst queued before the scheduler starts: it must be served as shared batches
+    for i in range(8):
+        b = budgets[i % 2]
+        reqs.append(srv.submit(q[100 * i:100 * i + 37], b, index_key=b.d_c))
+    srv.start()
+    for i in range(32):
+        n = int(rng.integers(1, 200))
+        lo = int(rng.integers(0, len(q) - n))
+        b = budgets[int(rng.integers(0, len(budgets)))]
+        reqs.append(srv.submit(q[lo:lo + n], b, index_key=b.d_c))
+        time.sleep(float(rng.exponential(0.002)))
+    for r in reqs:
+        assert r.wait(60)
+    srv.stop()
+    st = srv.stats()
+    assert st["requests"] == 40 and st["batches"] < 40          # some requests shared a batch
+    for r in reqs:
+        assert r.error is None, r.error
+        b = r.budget
+        ids, dist = P.search_ivf(idx[b.d_c], torch.from_numpy(np.ascontiguousarray(r.queries)).cuda(),
+                                 b.d_c, b.d_s, b.nprobe, b.k, storage=b.storage,
+                                 rerank_k=b.rerank_k)
+        ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+        assert np.array_equal(r.ids, ids), r.rid
+        fin = np.isfinite(dist)
+        assert np.all(np.abs(r.dist[fin] - dist[fin]) <= tol(dist[fin]))
+    for g in idx.values():
+        g.status()
