@@ -237,6 +237,38 @@ struct SelState {
   uint64_t ties[SEL_TIE];  // indices of the keys equal to the cut
 };
 
+// value of the kth smallest (1-based) of n 16-bit keys: two histogram passes
+template <class KeyF>
+__device__ uint32_t radix_kth(int n, int kth, KeyF key, SelState &st) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += SEL_THREADS) atomicAdd(&st.hist[key(i) >> 8], 1);
+  __syncthreads();
+  if (tid == 0) {
+    int c = 0, b = 0;
+    while (c + st.hist[b] < kth) c += st.hist[b++];
+    st.b1 = b;
+    st.below1 = c;
+  }
+  __syncthreads();
+  const int b1 = st.b1, below1 = st.below1;
+  for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += SEL_THREADS) {
+    const uint32_t k = key(i);
+    if ((int)(k >> 8) == b1) atomicAdd(&st.hist[k & 255u], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int c = below1, b = 0;
+    while (c + st.hist[b] < kth) c += st.hist[b++];
+    st.b2 = b;
+  }
+  __syncthreads();
+  return ((uint32_t)b1 << 8) | (uint32_t)st.b2;
+}
+
 // exact kk-smallest over n keys given by key(i) (16-bit), writing id(i) for
 // the winners; h is a 256-entry shared histogram, st the shared counters.
 template <class KeyF, class IdF>
@@ -367,18 +399,11 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
     __syncthreads();
     int r = (int)((1.6 * kk * SEL_SAMPLE) / ptotal) + 16;
     if (r > SEL_SAMPLE - 1) r = SEL_SAMPLE - 1;
-    // the (r+1)-th smallest sample key: select r+1 over the sample into bidx
-    // (as scratch for ids) and take the maximum key of that set
+    // threshold just above the (r+1)-th smallest sample key
     {
-      int64_t *tmp = (int64_t *)bkey;  // SEL_BUF * 4 bytes >= (r+1) * 8 for r < 2048
-      radix_select(SEL_SAMPLE, r + 1, [&](int i) -> uint32_t { return samp[i]; },
-                   [&](int i) -> int64_t { return (int64_t)samp[i]; }, tmp, st);
-      __syncthreads();
-      if (tid == 0) {
-        int64_t mx = 0;
-        for (int i = 0; i <= r; ++i) mx = tmp[i] > mx ? tmp[i] : mx;
-        s_T = (int)mx + 1;
-      }
+      const uint32_t kv = radix_kth(SEL_SAMPLE, r + 1, [&](int i) -> uint32_t { return samp[i]; },
+                                    st);
+      if (tid == 0) s_T = (int)kv + 1;
       __syncthreads();
     }
     // 2. compact the keys below T

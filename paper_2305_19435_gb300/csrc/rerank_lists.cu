@@ -56,8 +56,9 @@ __global__ void member_sort_kernel(const int64_t *__restrict__ goff, const int32
   }
 }
 
-// A warp walks 32 consecutive sorted pairs; the current member row sits in
-// the warp's shared buffer and is reloaded only when the member changes.
+// A warp walks 32 consecutive sorted pairs, two at a time (one per half-warp,
+// so two query rows are in flight); each half keeps its current member row
+// in its own shared buffer and reloads it only when its member changes.
 constexpr int RL_WARPS = 8;
 
 __global__ void __launch_bounds__(RL_WARPS * 32) rerank_pairs_kernel(
@@ -68,18 +69,20 @@ __global__ void __launch_bounds__(RL_WARPS * 32) rerank_pairs_kernel(
     uint64_t *__restrict__ keys) {
   extern __shared__ __align__(16) float rowbuf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float *row = rowbuf + (size_t)warp * d_s;
+  const int half = lane >> 4, hl = lane & 15;
+  const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
+  float *row = rowbuf + ((size_t)warp * 2 + half) * d_s;
   const int64_t w0 = ((int64_t)blockIdx.x * RL_WARPS + warp) * 32;
   if (w0 >= npairs) return;
   const int64_t w1 = min(npairs, w0 + 32);
   int cur_l = -1, cur_m = -1;
   float nu = 1.f;
   const int nseg = d_s >> 2;
-  for (int64_t i = w0; i < w1; ++i) {
+  for (int64_t i = w0 + half; i < w1; i += 2) {
     const int e = order[i];
     const int l = plist[e];
     if (l >= nlist) {
-      if (lane == 0) keys[e] = KEY_MAX;
+      if (hl == 0) keys[e] = KEY_MAX;
       continue;
     }
     const int m = pmem[e];
@@ -87,28 +90,28 @@ __global__ void __launch_bounds__(RL_WARPS * 32) rerank_pairs_kernel(
       const int64_t off = list_off[l];
       const int64_t nl = list_off[l + 1] - off;
       const float *base = xpm + off * d_pad + (int64_t)m * 16;
-      __syncwarp();
-      for (int s = lane; s < nseg; s += 32) {
+      __syncwarp(hmask);
+      for (int s = hl; s < nseg; s += 16) {
         const int b = s >> 2, part = s & 3;
         *(float4 *)(row + 4 * s) = *(const float4 *)(base + (int64_t)b * 16 * nl + part * 4);
       }
       nu = mscale ? mscale[off + m] : 1.f;
       cur_l = l;
       cur_m = m;
-      __syncwarp();
+      __syncwarp(hmask);
     }
     const int64_t q = e / kr;
     const float *qr = qs + q * ldq;
     float acc = 0.f;
-    for (int s0 = lane; s0 < nseg; s0 += 128) {
-      float4 qv[4];
+    for (int s0 = hl; s0 < nseg; s0 += 128) {
+      float4 qv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (s0 + 32 * u < nseg) qv[u] = __ldg((const float4 *)(qr + 4 * (s0 + 32 * u)));
+      for (int u = 0; u < 8; ++u)
+        if (s0 + 16 * u < nseg) qv[u] = __ldg((const float4 *)(qr + 4 * (s0 + 16 * u)));
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (s0 + 32 * u >= nseg) break;
-        const float4 xv = *(const float4 *)(row + 4 * (s0 + 32 * u));
+      for (int u = 0; u < 8; ++u) {
+        if (s0 + 16 * u >= nseg) break;
+        const float4 xv = *(const float4 *)(row + 4 * (s0 + 16 * u));
         float t;
         t = fmaf(-nu, xv.x, qv[u].x); acc = fmaf(t, t, acc);
         t = fmaf(-nu, xv.y, qv[u].y); acc = fmaf(t, t, acc);
@@ -117,8 +120,8 @@ __global__ void __launch_bounds__(RL_WARPS * 32) rerank_pairs_kernel(
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) keys[e] = pack_key(acc, (uint32_t)cand[e]);
+    for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(hmask, acc, o);
+    if (hl == 0) keys[e] = pack_key(acc, (uint32_t)cand[e]);
   }
 }
 
@@ -169,7 +172,7 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
   }
   {
     StageTimer t(ST_RR_PAIRS, st);
-    const size_t rs = (size_t)RL_WARPS * d_s * 4;
+    const size_t rs = (size_t)RL_WARPS * 2 * d_s * 4;
     ADN_CUDA(ensure_smem((const void *)rerank_pairs_kernel, (size_t)(rs)));
     const int64_t warps = (n + 31) / 32;
     rerank_pairs_kernel<<<(unsigned)((warps + RL_WARPS - 1) / RL_WARPS), RL_WARPS * 32, rs, st>>>(
