@@ -346,6 +346,48 @@ int adanns_search_ivf_noalloc(const adanns_index *idx, const float *queries, int
                               int d_s, int nprobe, int k, int64_t *out_ids, float *out_dist,
                               void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Lists partitioned over several GPUs (the IVF probe/scan is independent per
+ * inverted list, Alg. 1 and Sec. 4.2, so the lists can live on different
+ * devices; the per-device top-k of one query are then merged by distance).
+ * Each device holds an index over the rows of the lists it owns, with the
+ * full centroid table, so every device probes the same n_p lists and scans
+ * the owned ones.  These two calls are the device steps of the merge; the
+ * exchange of the per-device results between devices is the caller's.
+ * ---------------------------------------------------------------------- */
+
+#define ADANNS_MAX_SHARDS 128
+
+/*
+ * In place: ids[i] = map[ids[i]] for 0 <= ids[i] < n_map; negative ids
+ * (padding) are kept; ids >= n_map (impossible for results of a search of an
+ * index over n_map rows) become -1.
+ *   map    device, n_map int64: global id of each local row, ascending if the
+ *          merged result is to break distance ties by global id exactly as a
+ *          single-device search does
+ *   ids    device, count int64, read and written on the stream
+ * Errors: ADANNS_ERR_ARG for negative sizes or NULL pointers with count > 0.
+ * Asynchronous on cuda_stream.
+ */
+int adanns_map_ids(const int64_t *map, int64_t n_map, int64_t *ids, int64_t count,
+                   void *cuda_stream);
+
+/*
+ * Merge of G per-shard top-k results into one top-k per query, by (distance,
+ * id) ascending; fewer than k valid entries overall pad with (-1, +inf).
+ *   ids, dist  device, [G][B][k] (shard-major) int64 / float32; each row
+ *              sorted ascending by (distance, id) with padding (id < 0) at its
+ *              end, as adanns_search_ivf returns it; ids below 2^32 - 1
+ *   out_ids, out_dist  device, [B][k], written on the stream
+ * An id that appears in several shards appears that many times (shards are
+ * expected to be disjoint).
+ * Errors: ADANNS_ERR_ARG unless 1 <= G <= ADANNS_MAX_SHARDS, 1 <= k <= 1024,
+ * 0 <= B <= 2^31 - 1, and (for B > 0) no pointer is NULL.
+ * Asynchronous on cuda_stream.
+ */
+int adanns_merge_shards(const int64_t *ids, const float *dist, int G, int64_t B, int k,
+                        int64_t *out_ids, float *out_dist, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,8 @@ def lib():
         L.adanns_plan_launch.argtypes = [P, P]
         L.adanns_plan_free.argtypes = [P]
         L.adanns_plan_free.restype = None
+        L.adanns_map_ids.argtypes = [P, i64, P, i64, P]
+        L.adanns_merge_shards.argtypes = [P, P, i32, i64, i32, P, P, P]
         _lib = L
     return _lib
 
@@ -396,3 +398,29 @@ def tune_save(path: str):
 
 def tune_load(path: str):
     _check(lib().adanns_tune_load(path.encode()))
+
+
+# ---------------------------------------------------------------- lists on several GPUs
+def map_ids(ids: torch.Tensor, id_map: torch.Tensor) -> torch.Tensor:
+    """In place: local row ids of a shard index -> global ids (padding kept)."""
+    _need(ids, torch.int64, "ids")
+    _need(id_map, torch.int64, "id_map", 1)
+    _check(lib().adanns_map_ids(_ptr(id_map), id_map.numel(), _ptr(ids), ids.numel(), _stream()))
+    return ids
+
+
+def merge_shards(ids: torch.Tensor, dist: torch.Tensor, out: tuple | None = None):
+    """[G, B, k] per-shard sorted top-k -> merged (ids [B, k], dist [B, k])."""
+    _need(ids, torch.int64, "ids", 3)
+    _need(dist, torch.float32, "dist", 3)
+    if ids.shape != dist.shape:
+        raise ValueError("ids and dist must have the same shape")
+    G, B, k = ids.shape
+    if out is None:
+        oi = torch.empty(B, k, dtype=torch.int64, device=ids.device)
+        od = torch.empty(B, k, dtype=torch.float32, device=ids.device)
+    else:
+        oi, od = out
+    _check(lib().adanns_merge_shards(_ptr(ids), _ptr(dist), G, B, k, _ptr(oi), _ptr(od),
+                                     _stream()))
+    return oi, od

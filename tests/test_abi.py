@@ -60,3 +60,18 @@ def test_version_and_argument_errors_without_device(lib):
     # NULL index
     rc = lib.adanns_search_ivf(None, fake, 1, 16, 64, 1, 10, 1, 0, fake, fake, None, None)
     assert rc == -1
+    # shard merge: G, k, batch size out of range; map with negative sizes
+    rc = lib.adanns_merge_shards(fake, fake, 0, 4, 10, fake, fake, None)
+    assert rc == -1 and b"G" in lib.adanns_last_error()
+    rc = lib.adanns_merge_shards(fake, fake, 129, 4, 10, fake, fake, None)
+    assert rc == -1
+    rc = lib.adanns_merge_shards(fake, fake, 2, 4, 0, fake, fake, None)
+    assert rc == -1
+    rc = lib.adanns_merge_shards(fake, fake, 2, -1, 10, fake, fake, None)
+    assert rc == -1
+    rc = lib.adanns_merge_shards(None, fake, 2, 4, 10, fake, fake, None)
+    assert rc == -1
+    assert lib.adanns_merge_shards(None, None, 2, 0, 10, None, None, None) == 0
+    assert lib.adanns_map_ids(fake, -1, fake, 4, None) == -1
+    assert lib.adanns_map_ids(fake, 4, None, 4, None) == -1
+    assert lib.adanns_map_ids(None, 0, None, 0, None) == 0
