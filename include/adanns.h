@@ -168,8 +168,12 @@ int adanns_kmeans_update(const float *points, int64_t n, int ld, int dim, int me
  * AdANNS-IVF row):
  *   h(q): the nprobe nearest centroids to P_dc(q) by (distance, list id);
  *   result: the k nearest members of those lists to q by dist_ds, then id.
- *   queries  B x d FP32 (device); d_c must equal the index's d_c; d_s in G,
+ *   queries  B x d FP32 (device); d_c in G and <= the index's d_c; d_s in G,
  *            d_s <= d; 1 <= nprobe <= nlist; 1 <= k <= 1024.
+ *            A d_c below the built one is AdANNS-IVF-D (Table "formula"
+ *            IVF-D row; Sec. 5.1): the lists built at the larger prefix are
+ *            probed with P_dc(q) against the first d_c coordinates of each
+ *            centroid, taken as stored (not renormalised).
  *   storage  ADANNS_STORE_F32: the exact FP32 scan (rerank_k must be 0).
  *            ADANNS_STORE_BF16 / ADANNS_STORE_FP8E4M3 (tier built into the
  *            index, metric ADANNS_METRIC_L2_PREFIXNORM, nprobe <= 128): the

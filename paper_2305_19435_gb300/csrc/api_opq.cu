@@ -353,8 +353,8 @@ int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t 
   if (!idx->codes) return fail(ADANNS_ERR_STATE, "the index has no OPQ data");
   if (B < 0 || B > INT32_MAX) return fail(ADANNS_ERR_ARG, "bad batch size");
   if (B > 0 && (!queries || !out_ids || !out_dist)) return fail(ADANNS_ERR_ARG, "NULL argument");
-  if (d_c != idx->d_c)
-    return fail(ADANNS_ERR_DIM, "d_c must equal the index's clustering prefix " +
+  if (gran_index(d_c) < 0 || d_c > idx->d_c)
+    return fail(ADANNS_ERR_DIM, "d_c must be an MR granularity <= the index's clustering prefix " +
                                     std::to_string(idx->d_c));
   if (nprobe < 1 || nprobe > idx->nlist) return fail(ADANNS_ERR_ARG, "need 1 <= nprobe <= nlist");
   if (k < 1 || k > 1024) return fail(ADANNS_ERR_ARG, "need 1 <= k <= 1024");
@@ -401,7 +401,7 @@ int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t 
     }
     ScanArgs c{};
     c.xpm = idx->cent_pm;
-    c.d_pad = dcp;
+    c.d_pad = idx->dc_pad;  // stored centroid width; d_c <= built d_c (IVF-D)
     c.dims = d_c;
     c.list_off = idx->cent_off;
     c.qn = qc;

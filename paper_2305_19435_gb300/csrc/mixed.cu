@@ -501,7 +501,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     }
     ScanArgs c{};
     c.xpm = idx->cent_pm;
-    c.d_pad = dcp;
+    c.d_pad = idx->dc_pad;  // stored centroid width; d_c <= built d_c (IVF-D)
     c.dims = d_c;
     c.list_off = idx->cent_off;
     c.qn = qc;

@@ -67,8 +67,8 @@ extern "C" int adanns_search_ivf_noalloc(const adanns_index *idx, const float *q
   if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
   if (B < 0 || B > INT32_MAX) return fail(ADANNS_ERR_ARG, "bad batch size");
   if (B > 0 && (!queries || !out_ids || !out_dist)) return fail(ADANNS_ERR_ARG, "NULL argument");
-  if (d_c != idx->d_c)
-    return fail(ADANNS_ERR_DIM, "d_c must equal the index's clustering prefix " +
+  if (gran_index(d_c) < 0 || d_c > idx->d_c)
+    return fail(ADANNS_ERR_DIM, "d_c must be an MR granularity <= the index's clustering prefix " +
                                     std::to_string(idx->d_c));
   if (gran_index(d_s) < 0 || d_s > idx->d)
     return fail(ADANNS_ERR_DIM, "d_s = " + std::to_string(d_s) +
@@ -124,7 +124,7 @@ extern "C" int adanns_search_ivf_noalloc(const adanns_index *idx, const float *q
     return rc;
   ScanArgs a{};
   a.xpm = idx->cent_pm;
-  a.d_pad = dcp;
+  a.d_pad = idx->dc_pad;  // stored centroid width; d_c <= built d_c (IVF-D)
   a.dims = d_c;
   a.list_off = idx->cent_off;
   a.qn = qc;

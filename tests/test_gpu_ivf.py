@@ -191,11 +191,26 @@ def test_argument_errors(A, tiny):
         A.search_ivf(g, qq, 16, 64, 4, 1025)        # k too large
     assert e.value.code == -1
     with pytest.raises(A.AdannsError) as e:
-        A.search_ivf(g, qq, 32, 64, 4, 10)          # d_c differs from the index
+        A.search_ivf(g, qq, 32, 64, 4, 10)          # d_c above the built prefix
+    assert e.value.code == -2
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivf(g, qq, 12, 64, 4, 10)          # d_c not in G
     assert e.value.code == -2
     ids, dist = A.search_ivf(g, cu(data["queries"][:0]), 16, 64, 4, 10)
     assert ids.shape == (0, 10)
     g.free()
+
+
+# ---------------------------------------------------------------- IVF-D
+@pytest.mark.parametrize("d_hat,d_s,nprobe,metric", [(8, 64, 5, PN), (16, 128, 3, PN),
+                                                     (32, 32, 8, PN), (64, 96, 4, PN),
+                                                     (16, 96, 5, L2)])
+def test_ivf_d_probes_with_a_prefix_of_the_built_centroids(A, d_hat, d_s, nprobe, metric):
+    """AdANNS-IVF-D (Table "formula" IVF-D row): lists built at d_c = 64,
+    probed at d_hat <= 64 with the stored centroids' first d_hat coordinates."""
+    data = synthdata.small(12_000, 250, 128, 40, 131)
+    o = oracle.build_ivf(data["db"], 64, 48, 5, 12_000, seed=13, metric=metric)
+    search_parity(A, data["db"], data["queries"], o, d_hat, d_s, nprobe, 20, metric)
 
 
 # ---------------------------------------------------------------- k-means steps

@@ -52,12 +52,12 @@ def exact_dist(db, q, ids, d_s):
     return out
 
 
-def check(A, case, storage, d_s, nprobe, k, kr, min_recall, B=None):
+def check(A, case, storage, d_s, nprobe, k, kr, min_recall, B=None, d_c=32):
     data, o, g = case
     q = data["queries"] if B is None else data["queries"][:B]
-    gi, gd = A.search_ivf(g, cu(q), 32, d_s, nprobe, k, storage=storage, rerank_k=kr)
+    gi, gd = A.search_ivf(g, cu(q), d_c, d_s, nprobe, k, storage=storage, rerank_k=kr)
     gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
-    ref = oracle.search_ivf(data["db"], o, q, 32, d_s, nprobe, k)
+    ref = oracle.search_ivf(data["db"], o, q, d_c, d_s, nprobe, k)
     # every returned distance is the exact distance of the returned id
     for i in range(len(q)):
         ex = exact_dist(data["db"], q[i], gi[i], d_s)
@@ -119,3 +119,9 @@ def test_mixed_errors(A, case):
         A.search_ivf(h, q, 32, 256, 8, 10, storage=BF16, rerank_k=40)    # tier not built
     assert e.value.code == -6
     h.free()
+
+
+@pytest.mark.parametrize("storage,d_c", [(BF16, 8), (FP8, 16)])
+def test_mixed_ivf_d(A, case, storage, d_c):
+    """IVF-D on the tensor-core path: the d_c = 32 lists probed at a smaller prefix."""
+    check(A, case, storage, 128, 6, 10, 40, 0.99, d_c=d_c)

@@ -93,16 +93,18 @@ def test_procrustes_matches_oracle(A):
     assert abs(fg - fo) <= 1e-6 * fo
 
 
-@pytest.mark.parametrize("d_s,M,nprobe,k", [(64, 16, 4, 20), (96, 32, 8, 100), (48, 16, 2, 10),
-                                            (32, 4, 24, 50)])
-def test_ivfopq_search_parity(A, case, d_s, M, nprobe, k):
+@pytest.mark.parametrize("d_s,M,nprobe,k,d_c", [(64, 16, 4, 20, 32), (96, 32, 8, 100, 32),
+                                                (48, 16, 2, 10, 32), (32, 4, 24, 50, 32),
+                                                (64, 16, 4, 20, 16), (96, 32, 8, 10, 8)])
+def test_ivfopq_search_parity(A, case, d_s, M, nprobe, k, d_c):
+    """d_c below the built 32 is the IVF-D coarse step in front of the ADC scan."""
     data, o = case["data"], case["idx"]
     opq, codes = case[(d_s, M)]
     g = gpu_index(A, case, d_s, M)
     q = data["queries"]
-    gi, gd, gp = A.search_ivfopq(g, cu(q), 32, nprobe, k, return_probes=True)
+    gi, gd, gp = A.search_ivfopq(g, cu(q), d_c, nprobe, k, return_probes=True)
     gi, gd, gp = gi.cpu().numpy(), gd.cpu().numpy(), gp.cpu().numpy()
-    orr = oracle.search_ivfopq(data["db"], o, opq, codes, q, 32, nprobe, k + 40)
+    orr = oracle.search_ivfopq(data["db"], o, opq, codes, q, d_c, nprobe, k + 40)
     amb = ambiguous_probe_rows(orr["probe_dist"], nprobe)
     for i in np.nonzero(~amb)[0]:
         assert set(gp[i]) == set(orr["probes"][i])

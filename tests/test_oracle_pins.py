@@ -166,6 +166,32 @@ def test_cluster_mapping_and_single_probe():
         assert np.all(idx["assign"][got] == near[i])
 
 
+def test_ivf_d_uses_the_stored_centroid_prefix():
+    """IVF-D (Table "formula" IVF-D row) probes with P_dhat(q) against the first
+    d_hat coordinates of the centroids as stored.  Hand case, d_hat = 8 of a
+    16-dim index: P_8(q) = e0; centroid A's prefix is 0.3 e0 (distance 0.49),
+    B's is 0.8 e0 + 0.6 e1 (distance 0.40), so the single probe is B; had the
+    centroid prefix been renormalised, A (distance 0) would win."""
+    C = np.zeros((2, 16), dtype=np.float32)
+    C[0, 0], C[0, 8] = 0.3, 0.95
+    C[1, 0], C[1, 1] = 0.8, 0.6
+    db = np.zeros((2, 32), dtype=np.float32)
+    db[0, 0], db[0, 9] = 1.0, 1.0
+    db[1, 0], db[1, 1] = 1.0, 1.0
+    off, ids = oracle.lists_from_assignment(np.array([0, 1]), 2)
+    idx = {"centroids": C, "list_off": off, "list_ids": ids, "metric": PN}
+    q = np.zeros((1, 32), dtype=np.float32)
+    q[0, 0], q[0, 20] = 2.0, 5.0
+    res = oracle.search_ivf(db, idx, q, 8, 32, 1, 1)
+    assert res["probes"][0, 0] == 1 and res["ids"][0, 0] == 1
+    assert res["probe_dist"][0, 0] == pytest.approx(0.04 + 0.36, abs=1e-6)
+    assert res["probe_dist"][0, 1] == pytest.approx(0.49, abs=1e-6)
+    # d_hat = the built d_c is plain AdANNS-IVF: P_16(q) = e0 as well
+    res16 = oracle.search_ivf(db, idx, q, 16, 32, 2, 2)
+    assert res16["probe_dist"][0, 0] == pytest.approx(0.40, abs=1e-6)
+    assert res16["probe_dist"][0, 1] == pytest.approx(0.49 + 0.95 ** 2, abs=1e-6)
+
+
 def test_probes_sorted_and_padding():
     data = synthdata.small(300, 10, 16, 4, 24)
     idx = oracle.build_ivf(data["db"], 16, 30, 3, 300, seed=7)
