@@ -378,6 +378,7 @@ def main():
         results[mode] = {"ms": ms, "qps": world * B / (ms / 1000.0), "launches": launches,
                          "stages_ms": {k2: v[0] / args.steps for k2, v in prof.items()},
                          "ids": ids, "step": step}
+    idx.status()  # raises if a device-side check or a pipeline wait failed during the runs
     main_r = results[args.mode]
     # the headline step replayed from a captured CUDA graph
     code, rr = MODES[args.mode][0], mode_rerank(args.mode, args.k)

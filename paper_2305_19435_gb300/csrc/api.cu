@@ -340,8 +340,10 @@ int adanns_index_status(const adanns_index *idx, void *cuda_stream) {
   ADN_CUDA(cudaMemcpyAsync(&h, idx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   ADN_CUDA(cudaMemsetAsync(idx->dev_err, 0, sizeof(int), st));
   ADN_CUDA(cudaStreamSynchronize(st));
+  if (h & ADANNS_DEVERR_RERANK)
+    return fail(ADANNS_ERR_STATE, "rerank found a pair outside its member chunk (skipped)");
   if (h) return fail(ADANNS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (stage " +
-                                             std::to_string(h) + ")");
+                                             std::to_string(h & 0xff) + ")");
   return ADANNS_OK;
 }
 

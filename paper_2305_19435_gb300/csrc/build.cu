@@ -159,8 +159,16 @@ __global__ void csr_hist_kernel(const int32_t *__restrict__ a, int64_t N, int nl
   for (int l = threadIdx.x; l < nlist; l += blockDim.x) h[l] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * CSR_TILE;
-  for (int i = threadIdx.x; i < CSR_TILE && base + i < N; i += blockDim.x)
-    atomicAdd(&h[a[base + i]], 1);
+  // one atomic per distinct bucket in a warp (a heavily repeated bucket, e.g.
+  // a padding bucket, would otherwise serialise on one shared address)
+  const int lane = threadIdx.x & 31;
+  for (int i0 = 0; i0 < CSR_TILE; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const bool valid = base + i < N;
+    const int l = valid ? a[base + i] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, l);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[l], __popc(peers));
+  }
   __syncthreads();
   for (int l = threadIdx.x; l < nlist; l += blockDim.x)
     counts[(int64_t)l * ntile + blockIdx.x] = h[l];

@@ -14,6 +14,10 @@ namespace adn {
 
 constexpr uint64_t KEY_MAX = ~0ull;  // empty slot / padding key
 
+// bits of an index's sticky device error word (adanns_index_status); the low
+// byte is the tensor-core pipeline stage whose wait timed out
+constexpr int ADANNS_DEVERR_RERANK = 0x100;  // rerank pair outside its member chunk
+
 // A candidate is packed as (float bits of a non-negative distance) << 32 | id,
 // so unsigned order is (distance, id) order.
 __host__ __device__ inline uint64_t pack_key(float d, uint32_t id) {

@@ -7,6 +7,8 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
 
 #include "devutil.cuh"
 #include "internal.cuh"
@@ -223,7 +225,8 @@ __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, 
 //  3. If the buffer holds between kk and SEL_BUF keys, an exact two-pass
 //     radix select on the buffer fixes the cut; otherwise the exact two-pass
 //     radix select runs over the whole region.
-// Ties at the cut are taken in arrival order.  Writes database ids (-1 padding).
+// Ties at the cut are taken in candidate-position order (list rank, then member
+// position), independent of thread timing.  Writes database ids (-1 padding).
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_WARPS = SEL_THREADS / 32;
 constexpr int SEL_SAMPLE = 2048;
@@ -232,10 +235,38 @@ constexpr int SEL_BUF = 4096;
 constexpr int SEL_TIE = 1024;
 
 struct SelState {
-  int hist[256];
-  int b1, below1, b2, below2, lt, lt2, eq, nb;
-  uint64_t ties[SEL_TIE];  // indices of the keys equal to the cut
+  int hist[256], hist2[256];
+  int b1, below1, b2, below2, b1k, below1k, b2k, neq, lt, eq, overflow;
+  uint64_t ties[SEL_TIE];  // (candidate position << 32 | index) of the keys equal to the cut
 };
+
+// One full warp: the smallest bucket b of a 256-bucket histogram h with
+// base + h[0] + ... + h[b] >= target, and the count below it
+// (base + h[0] + ... + h[b-1]).  Needs target <= base + sum(h).
+__device__ __forceinline__ void warp_find_bucket(const int *h, int base, int target, int *b_out,
+                                                 int *below_out) {
+  const int lane = threadIdx.x & 31;
+  int v[8], sum = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    v[j] = h[lane * 8 + j];
+    sum += v[j];
+  }
+  int inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, base + inc >= target);
+  const int L = m ? __ffs(m) - 1 : 31;
+  if (lane == L) {
+    int c = base + inc - sum, j = 0;
+    while (j < 7 && c + v[j] < target) c += v[j++];
+    *b_out = L * 8 + j;
+    *below_out = c;
+  }
+}
 
 // value of the kth smallest (1-based) of n 16-bit keys: two histogram passes
 template <class KeyF>
@@ -245,12 +276,7 @@ __device__ uint32_t radix_kth(int n, int kth, KeyF key, SelState &st) {
   __syncthreads();
   for (int i = tid; i < n; i += SEL_THREADS) atomicAdd(&st.hist[key(i) >> 8], 1);
   __syncthreads();
-  if (tid == 0) {
-    int c = 0, b = 0;
-    while (c + st.hist[b] < kth) c += st.hist[b++];
-    st.b1 = b;
-    st.below1 = c;
-  }
+  if (tid < 32) warp_find_bucket(st.hist, 0, kth, &st.b1, &st.below1);
   __syncthreads();
   const int b1 = st.b1, below1 = st.below1;
   for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
@@ -260,66 +286,82 @@ __device__ uint32_t radix_kth(int n, int kth, KeyF key, SelState &st) {
     if ((int)(k >> 8) == b1) atomicAdd(&st.hist[k & 255u], 1);
   }
   __syncthreads();
-  if (tid == 0) {
-    int c = below1, b = 0;
-    while (c + st.hist[b] < kth) c += st.hist[b++];
-    st.b2 = b;
-  }
+  if (tid < 32) warp_find_bucket(st.hist, below1, kth, &st.b2, &st.below2);
   __syncthreads();
   return ((uint32_t)b1 << 8) | (uint32_t)st.b2;
 }
 
 // exact kk-smallest over n keys given by key(i) (16-bit), writing id(i) for
-// the winners; h is a 256-entry shared histogram, st the shared counters.
-template <class KeyF, class IdF>
-__device__ void radix_select(int n, int kk, KeyF key, IdF id, int64_t *o, SelState &st) {
+// the winners; st holds the shared histograms and counters.  Keys equal to
+// the cut are taken in order of their candidate position pos(i), so the
+// result does not depend on thread timing.  With kq > 0, winners whose key
+// exceeds the kq-th smallest key by more than prune_delta are written as -1
+// (certified pruning, see shortlist_prune_delta).  When i is not in position
+// order (ORDERED false) and more than SEL_TIE keys tie at the cut, nothing is
+// written and st.overflow is set: the caller reruns over the ordered region.
+template <bool ORDERED, class KeyF, class IdF, class PosF>
+__device__ void radix_select(int n, int kk, int kq, int prune_delta, KeyF key, IdF id, PosF pos,
+                             int64_t *o, SelState &st) {
   const int tid = threadIdx.x;
-  for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
-  if (tid == 0) st.lt = st.lt2 = st.eq = 0;
+  const int kq1 = kq > 0 ? kq : kk;  // kq <= kk <= n
+  for (int i = tid; i < 256; i += SEL_THREADS) {
+    st.hist[i] = 0;
+    st.hist2[i] = 0;
+  }
+  if (tid == 0) st.lt = st.eq = st.overflow = 0;
   __syncthreads();
   for (int i = tid; i < n; i += SEL_THREADS) atomicAdd(&st.hist[key(i) >> 8], 1);
   __syncthreads();
-  if (tid == 0) {
-    int c = 0, b = 0;
-    while (c + st.hist[b] < kk) c += st.hist[b++];
-    st.b1 = b;
-    st.below1 = c;
+  if (tid < 32) {
+    warp_find_bucket(st.hist, 0, kk, &st.b1, &st.below1);
+    warp_find_bucket(st.hist, 0, kq1, &st.b1k, &st.below1k);
   }
   __syncthreads();
-  const int b1 = st.b1, below1 = st.below1;
+  const int b1 = st.b1, below1 = st.below1, b1k = st.b1k;
   for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
   __syncthreads();
+  // second digit of the cut and, in the same pass, of the kq-th key
   for (int i = tid; i < n; i += SEL_THREADS) {
     const uint32_t k = key(i);
-    if ((int)(k >> 8) == b1) atomicAdd(&st.hist[k & 255u], 1);
+    const int hi = (int)(k >> 8);
+    if (hi == b1) atomicAdd(&st.hist[k & 255u], 1);
+    else if (hi == b1k) atomicAdd(&st.hist2[k & 255u], 1);
   }
   __syncthreads();
-  if (tid == 0) {
-    int c = below1, b = 0;
-    while (c + st.hist[b] < kk) c += st.hist[b++];
-    st.b2 = b;
-    st.below2 = c;
+  if (tid < 32) {
+    warp_find_bucket(st.hist, below1, kk, &st.b2, &st.below2);
+    int dummy;
+    warp_find_bucket(b1k == b1 ? st.hist : st.hist2, st.below1k, kq1, &st.b2k, &dummy);
+    __syncwarp();
+    if (tid == 0) st.neq = st.hist[st.b2];
   }
   __syncthreads();
   const uint32_t T = ((uint32_t)b1 << 8) | (uint32_t)st.b2;
+  const uint32_t keep_max =
+      kq > 0 ? (((uint32_t)b1k << 8) | (uint32_t)st.b2k) + (uint32_t)prune_delta : 0xFFFFFFFFu;
   const int below2 = st.below2, need_eq = kk - below2;
+  if (!ORDERED && st.neq > SEL_TIE) {  // too many ties to order here
+    if (tid == 0) st.overflow = 1;
+    __syncthreads();
+    return;
+  }
   for (int i = tid; i < n; i += SEL_THREADS) {
     const uint32_t k = key(i);
     if (k < T) {
-      o[atomicAdd(&st.lt, 1)] = id(i);
+      o[atomicAdd(&st.lt, 1)] = k <= keep_max ? id(i) : -1;
     } else if (k == T) {
       const int p = atomicAdd(&st.eq, 1);
-      if (p < SEL_TIE) st.ties[p] = (uint64_t)i;
+      if (p < SEL_TIE) st.ties[p] = ((uint64_t)(uint32_t)pos(i) << 32) | (uint32_t)i;
     }
   }
   __syncthreads();
-  // ties at the cut: the need_eq entries with the smallest positions, so the
-  // result does not depend on thread timing
+  // ties at the cut: the need_eq entries with the smallest positions
   const int neq = st.eq;
   if (neq <= SEL_TIE) {
     if (threadIdx.x < 32) {
       warp_sort(st.ties, neq);
-      for (int j = threadIdx.x; j < need_eq; j += 32) o[below2 + j] = id((int)st.ties[j]);
+      for (int j = threadIdx.x; j < need_eq; j += 32)
+        o[below2 + j] = T <= keep_max ? id((int)(uint32_t)(st.ties[j] & 0xffffffffu)) : -1;
     }
   } else {
     // many ties: an ordered pass ranks them by position (block prefix counts)
@@ -334,7 +376,7 @@ __device__ void radix_select(int n, int kk, KeyF key, IdF id, int64_t *o, SelSta
       int before = base;
       for (int w = 0; w < (tid >> 5); ++w) before += wsum[w];
       before += __popc(b & ((1u << (tid & 31)) - 1u));
-      if (eq && before < need_eq) o[below2 + before] = id(i);
+      if (eq && before < need_eq) o[below2 + before] = T <= keep_max ? id(i) : -1;
       int tot = 0;
       for (int w = 0; w < SEL_WARPS; ++w) tot += wsum[w];
       __syncthreads();
@@ -347,7 +389,8 @@ __device__ void radix_select(int n, int kk, KeyF key, IdF id, int64_t *o, SelSta
 __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
     const uint16_t *__restrict__ cand, const uint64_t *__restrict__ ckeys, int nprobe,
     const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off,
-    const int32_t *__restrict__ list_ids, int kk, int64_t *__restrict__ out) {
+    const int32_t *__restrict__ list_ids, int kk, int k, int prune_delta,
+    int64_t *__restrict__ out) {
   __shared__ SelState st;
   __shared__ uint16_t samp[SEL_SAMPLE];
   __shared__ uint32_t bkey[SEL_BUF], bidx[SEL_BUF];
@@ -434,19 +477,46 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
     __syncthreads();
     const int n = s_n;
     if (n >= kk && n <= SEL_BUF) {
-      radix_select(n, kk, [&](int i) -> uint32_t { return bkey[i]; },
-                   [&](int i) -> int64_t { return id_at((int)bidx[i]); }, o, st);
-      return;
+      radix_select<false>(n, kk, k, prune_delta, [&](int i) -> uint32_t { return bkey[i]; },
+                          [&](int i) -> int64_t { return id_at((int)bidx[i]); },
+                          [&](int i) -> int { return (int)bidx[i]; }, o, st);
+      const int ovf = st.overflow;
+      __syncthreads();  // every thread has read the flag before it is reset
+      if (!ovf) return;
     }
   }
-  // exact radix select over the whole region
-  radix_select(ptotal, kk, [&](int i) -> uint32_t { return src[i]; },
-               [&](int i) -> int64_t { return id_at(i); }, o, st);
+  // exact radix select over the whole region (index = candidate position)
+  radix_select<true>(ptotal, kk, k, prune_delta, [&](int i) -> uint32_t { return src[i]; },
+                     [&](int i) -> int64_t { return id_at(i); }, [&](int i) -> int { return i; },
+                     o, st);
 }
 
 // ---------------------------------------------------------------- tensor-core scan launcher
 int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
                     const MmaScanArgs &a, cudaStream_t st);
+
+// Certified shortlist pruning (exact: the result equals the unpruned rerank).
+// A shortlisted candidate c is dropped before the exact rerank when its key
+// exceeds the k-th smallest shortlist key by more than prune_delta, i.e. when
+// even its smallest possible exact distance is above the largest possible
+// exact distance of k other candidates.  With the BF16 tier, for unit-norm
+// prefixes,
+//   |d_exact - d_approx| <= E = 2 (2u + u^2) + e_rest,   u = 2^-8 + 2^-23,
+// from the per-coordinate relative rounding of q/s_q and x/s_x to BF16
+// (|q x - q~ x~| <= (2u + u^2) |q| |x| summed, then Cauchy-Schwarz) times the
+// factor 2 of the cross term; e_rest = 2e-3 bounds the FP32 tensor-core
+// accumulation (<= 2 d 2^-23 for d <= 2048), the norm terms and the FP32
+// rerank's own rounding.  A key is round(16384 d_approx) (+-2^-15), so c can
+// be dropped when key_c > key_k + 2 * 16384 * (2^-15 + E).  FP8-E4M3 (u =
+// 2^-4, plus subnormal steps) gives no useful bound: no pruning there, and
+// none unless ADANNS_RERANK_PRUNE is unset or non-zero.
+static int shortlist_prune_delta(int fp8) {
+  const char *env = getenv("ADANNS_RERANK_PRUNE");
+  if (fp8 || (env && env[0] == '0')) return 1 << 20;
+  const double u = std::ldexp(1.0, -8) + std::ldexp(1.0, -23);
+  const double E = 2.0 * (2.0 * u + u * u) + 2e-3;
+  return (int)std::ceil(2.0 * 16384.0 * (std::ldexp(1.0, -15) + E)) + 1;
+}
 
 int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
                  int nprobe, int k, int which, int kk, int64_t *out_ids, float *out_dist,
@@ -463,6 +533,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   // slices bounded by a scratch budget (the candidate keys dominate it)
   const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
   const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
+  const int prune_delta = shortlist_prune_delta(fp8);
   Scratch s(st);
   float *qc, *qs, *qn2, *qsc;
   uint64_t *ckeys;
@@ -558,7 +629,8 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     {
       StageTimer t(ST_SELECT, st);
       select_kernel<<<(unsigned)nb, SEL_THREADS, 0, st>>>(cand, ckeys, nprobe, qbase,
-                                                          idx->list_off, idx->list_ids, kk, cids);
+                                                          idx->list_off, idx->list_ids, kk, k,
+                                                          prune_delta, cids);
       ADN_LAUNCH("select_kernel");
     }
     {

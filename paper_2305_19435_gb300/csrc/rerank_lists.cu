@@ -33,15 +33,17 @@ __global__ void pair_lists_kernel(const int64_t *__restrict__ cand, int64_t n, i
   pmem[e] = (int32_t)(pos[id] - list_off[l]);
 }
 
-// one CTA per list group: reorder that group's pairs by member index
+// one CTA per list group: reorder that group's pairs by member index and
+// record where each member's pairs start (mstart, indexed like the lists'
+// member positions; mstart[N] = number of pairs before the padding group)
 __global__ void member_sort_kernel(const int64_t *__restrict__ goff, const int32_t *__restrict__ byl,
                                    const int32_t *__restrict__ pmem,
                                    const int64_t *__restrict__ list_off, int nlist,
-                                   int32_t *__restrict__ out) {
+                                   int32_t *__restrict__ out, int32_t *__restrict__ mstart) {
   extern __shared__ int hist[];
-  const int l = blockIdx.x;
+  const int l = blockIdx.x;  // the padding group (l = nlist) is not reranked: not sorted
   const int64_t lo = goff[l], hi = goff[l + 1];
-  const int nm = l < nlist ? (int)(list_off[l + 1] - list_off[l]) : 1;
+  const int nm = (int)(list_off[l + 1] - list_off[l]);
   for (int i = threadIdx.x; i <= nm; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&hist[pmem[byl[i]] + 1], 1);
@@ -49,6 +51,9 @@ __global__ void member_sort_kernel(const int64_t *__restrict__ goff, const int32
   if (threadIdx.x == 0)
     for (int i = 1; i <= nm; ++i) hist[i] += hist[i - 1];
   __syncthreads();
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) mstart[list_off[l] + i] = (int32_t)(lo + hist[i]);
+  if (l == 0 && threadIdx.x == 0) mstart[list_off[nlist]] = (int32_t)goff[nlist];
+  __syncthreads();  // every start is read before the scatter below advances it
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const int e = byl[i];
     const int p = atomicAdd(&hist[pmem[e]], 1);
@@ -56,72 +61,111 @@ __global__ void member_sort_kernel(const int64_t *__restrict__ goff, const int32
   }
 }
 
-// A warp walks 32 consecutive sorted pairs, two at a time (one per half-warp,
-// so two query rows are in flight); each half keeps its current member row
-// in its own shared buffer and reloads it only when its member changes.
-constexpr int RL_WARPS = 8;
+// One CTA per (list, chunk of mc members): the chunk's member rows are read
+// once, coalesced from the prefix-major storage, into shared memory (rows
+// padded by 4 floats against bank conflicts); the chunk's pairs (consecutive
+// in the sorted order) are then scored by the CTA's half-warps, each prefetching
+// its next query row into registers while it scores the current one.  Only
+// the query rows are gathered (from L2: the whole query block is small).
+constexpr int RC_THREADS = 128;
+constexpr int RC_HW = RC_THREADS / 16;  // half-warps per CTA
+constexpr int RC_META = RC_THREADS;    // pairs whose metadata are staged at once
+constexpr int RC_MAX_MC = 64;
 
-__global__ void __launch_bounds__(RL_WARPS * 32) rerank_pairs_kernel(
-    const int32_t *__restrict__ order, int64_t npairs, const int32_t *__restrict__ plist,
+inline int rerank_chunk_members(int d_s) {
+  return std::max(8, std::min(RC_MAX_MC, 32768 / (d_s * 4)));
+}
+
+__global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
+    const int32_t *__restrict__ order, const int32_t *__restrict__ mstart,
     const int32_t *__restrict__ pmem, const int64_t *__restrict__ cand, int kr,
     const float *__restrict__ qs, int ldq, int d_s, const float *__restrict__ xpm, int d_pad,
-    const int64_t *__restrict__ list_off, const float *__restrict__ mscale, int nlist,
-    uint64_t *__restrict__ keys) {
-  extern __shared__ __align__(16) float rowbuf[];
+    const int64_t *__restrict__ list_off, const float *__restrict__ mscale, int mc,
+    uint64_t *__restrict__ keys, int *__restrict__ err) {
+  extern __shared__ __align__(16) float rows[];  // [mc][d_s + 4]
+  __shared__ int s_e[RC_META], s_m[RC_META], s_q[RC_META];
+  __shared__ uint32_t s_cid[RC_META];
+  __shared__ float s_nu[RC_MAX_MC];
+  const int l = blockIdx.x;
+  const int64_t off = list_off[l];
+  const int nl = (int)(list_off[l + 1] - off);
+  const int rs = d_s + 4, nseg = d_s >> 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int half = lane >> 4, hl = lane & 15;
+  const int half = lane >> 4, hl = lane & 15, hw = warp * 2 + half;
   const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
-  float *row = rowbuf + ((size_t)warp * 2 + half) * d_s;
-  const int64_t w0 = ((int64_t)blockIdx.x * RL_WARPS + warp) * 32;
-  if (w0 >= npairs) return;
-  const int64_t w1 = min(npairs, w0 + 32);
-  int cur_l = -1, cur_m = -1;
-  float nu = 1.f;
-  const int nseg = d_s >> 2;
-  for (int64_t i = w0 + half; i < w1; i += 2) {
-    const int e = order[i];
-    const int l = plist[e];
-    if (l >= nlist) {
-      if (hl == 0) keys[e] = KEY_MAX;
-      continue;
+  for (int m0 = blockIdx.y * mc; m0 < nl; m0 += gridDim.y * mc) {
+    const int m1 = min(nl, m0 + mc), nm = m1 - m0;
+    const int p0 = mstart[off + m0], p1 = mstart[off + m1];
+    if (p0 >= p1) continue;
+    __syncthreads();  // the previous chunk's rows are no longer read
+    // member rows: block b of the chunk is nm x 16 contiguous floats
+    const int per_b = nm * 4;  // float4 per block
+    for (int t = threadIdx.x; t < per_b * ((d_s + 15) >> 4); t += RC_THREADS) {
+      const int b = t / per_b, w = t - b * per_b, mm = w >> 2, part = w & 3;
+      if (4 * b + part >= nseg) continue;  // d_s = 8: half of the last block
+      cp_async16(rows + (size_t)mm * rs + 16 * b + 4 * part,
+                 xpm + off * d_pad + (int64_t)b * 16 * nl + (int64_t)(m0 + mm) * 16 + part * 4);
     }
-    const int m = pmem[e];
-    if (l != cur_l || m != cur_m) {
-      const int64_t off = list_off[l];
-      const int64_t nl = list_off[l + 1] - off;
-      const float *base = xpm + off * d_pad + (int64_t)m * 16;
-      __syncwarp(hmask);
-      for (int s = hl; s < nseg; s += 16) {
-        const int b = s >> 2, part = s & 3;
-        *(float4 *)(row + 4 * s) = *(const float4 *)(base + (int64_t)b * 16 * nl + part * 4);
+    cp_async_commit();  // the copies land while the first metadata batch loads
+    for (int t = threadIdx.x; t < nm; t += RC_THREADS) s_nu[t] = mscale ? mscale[off + m0 + t] : 1.f;
+    for (int base = p0; base < p1; base += RC_META) {
+      const int nb = min(RC_META, p1 - base);
+      if (base != p0) __syncthreads();  // previous metadata consumed
+      if ((int)threadIdx.x < nb) {
+        const int e = order[base + threadIdx.x];
+        int mm = pmem[e] - m0;
+        if ((unsigned)mm >= (unsigned)nm) {  // inconsistent sort: report, skip the pair
+          atomicOr(err, ADANNS_DEVERR_RERANK);
+          mm = -1;
+        }
+        s_e[threadIdx.x] = e;
+        s_m[threadIdx.x] = mm;
+        s_q[threadIdx.x] = e / kr;
+        s_cid[threadIdx.x] = (uint32_t)cand[e];
       }
-      nu = mscale ? mscale[off + m] : 1.f;
-      cur_l = l;
-      cur_m = m;
-      __syncwarp(hmask);
-    }
-    const int64_t q = e / kr;
-    const float *qr = qs + q * ldq;
-    float acc = 0.f;
-    for (int s0 = hl; s0 < nseg; s0 += 128) {
-      float4 qv[8];
+      cp_async_wait<0>();
+      __syncthreads();  // rows and metadata visible
+      auto load_first = [&](int t, float4 *dst) {
+        const float *qr = qs + (int64_t)s_q[t] * ldq;
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (s0 + 16 * u < nseg) qv[u] = __ldg((const float4 *)(qr + 4 * (s0 + 16 * u)));
+        for (int u = 0; u < 8; ++u)
+          if (hl + 16 * u < nseg) dst[u] = __ldg((const float4 *)(qr + 4 * (hl + 16 * u)));
+      };
+      float4 qn[8];
+      if (hw < nb) load_first(hw, qn);
+      for (int t = hw; t < nb; t += RC_HW) {
+        float4 qv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (s0 + 16 * u >= nseg) break;
-        const float4 xv = *(const float4 *)(row + 4 * (s0 + 16 * u));
-        float t;
-        t = fmaf(-nu, xv.x, qv[u].x); acc = fmaf(t, t, acc);
-        t = fmaf(-nu, xv.y, qv[u].y); acc = fmaf(t, t, acc);
-        t = fmaf(-nu, xv.z, qv[u].z); acc = fmaf(t, t, acc);
-        t = fmaf(-nu, xv.w, qv[u].w); acc = fmaf(t, t, acc);
+        for (int u = 0; u < 8; ++u) qv[u] = qn[u];
+        if (t + RC_HW < nb) load_first(t + RC_HW, qn);
+        const int mm = s_m[t];
+        if (mm < 0) continue;  // uniform in the half-warp
+        const float *xr = rows + (size_t)mm * rs;
+        const float nu = s_nu[mm];
+        const float *qr = qs + (int64_t)s_q[t] * ldq;
+        float acc = 0.f;
+        for (int s0 = hl; s0 < nseg; s0 += 128) {
+          if (s0 != hl) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (s0 + 16 * u < nseg) qv[u] = __ldg((const float4 *)(qr + 4 * (s0 + 16 * u)));
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (s0 + 16 * u >= nseg) break;
+            const float4 xv = *(const float4 *)(xr + 4 * (s0 + 16 * u));
+            float d;
+            d = fmaf(-nu, xv.x, qv[u].x); acc = fmaf(d, d, acc);
+            d = fmaf(-nu, xv.y, qv[u].y); acc = fmaf(d, d, acc);
+            d = fmaf(-nu, xv.z, qv[u].z); acc = fmaf(d, d, acc);
+            d = fmaf(-nu, xv.w, qv[u].w); acc = fmaf(d, d, acc);
+          }
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(hmask, acc, o);
+        if (hl == 0) keys[s_e[t]] = pack_key(acc, s_cid[t]);
       }
     }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(hmask, acc, o);
-    if (hl == 0) keys[e] = pack_key(acc, (uint32_t)cand[e]);
   }
 }
 
@@ -152,12 +196,13 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
   if (n > INT32_MAX) return fail(ADANNS_ERR_ARG, "rerank slice too large");
   const int nlist = idx->nlist;
   Scratch s(st);
-  int32_t *plist, *pmem, *byl, *order;
+  int32_t *plist, *pmem, *byl, *order, *mstart;
   int64_t *goff;
   uint64_t *keys;
   int rc;
   if ((rc = s.get(&plist, n)) || (rc = s.get(&pmem, n)) || (rc = s.get(&byl, n)) ||
-      (rc = s.get(&order, n)) || (rc = s.get(&goff, (size_t)nlist + 2)) || (rc = s.get(&keys, n)))
+      (rc = s.get(&order, n)) || (rc = s.get(&goff, (size_t)nlist + 2)) || (rc = s.get(&keys, n)) ||
+      (rc = s.get(&mstart, (size_t)idx->N + 1)))
     return rc;
   {
     StageTimer t(ST_RR_SORT, st);
@@ -167,18 +212,21 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     if ((rc = build_csr(plist, n, nlist + 1, goff, byl, st))) return rc;
     const size_t hs = ((size_t)idx->max_list + 2) * 4;
     ADN_CUDA(ensure_smem((const void *)member_sort_kernel, (size_t)(hs)));
-    member_sort_kernel<<<nlist + 1, 256, hs, st>>>(goff, byl, pmem, idx->list_off, nlist, order);
+    member_sort_kernel<<<nlist, 256, hs, st>>>(goff, byl, pmem, idx->list_off, nlist, order, mstart);
     ADN_LAUNCH("member_sort_kernel");
   }
   {
     StageTimer t(ST_RR_PAIRS, st);
-    const size_t rs = (size_t)RL_WARPS * 2 * d_s * 4;
-    ADN_CUDA(ensure_smem((const void *)rerank_pairs_kernel, (size_t)(rs)));
-    const int64_t warps = (n + 31) / 32;
-    rerank_pairs_kernel<<<(unsigned)((warps + RL_WARPS - 1) / RL_WARPS), RL_WARPS * 32, rs, st>>>(
-        order, n, plist, pmem, cand, kr, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off,
-        mscale, nlist, keys);
-    ADN_LAUNCH("rerank_pairs_kernel");
+    const int mc = rerank_chunk_members(d_s);
+    const size_t rs = (size_t)mc * (d_s + 4) * 4;
+    ADN_CUDA(ensure_smem((const void *)rerank_chunks_kernel, rs));
+    // slots of padding or pruned candidates keep the empty key
+    ADN_CUDA(cudaMemsetAsync(keys, 0xFF, sizeof(uint64_t) * n, st));
+    const int chunks = std::max(1, std::min(65535, (idx->max_list + mc - 1) / mc));
+    rerank_chunks_kernel<<<dim3((unsigned)nlist, (unsigned)chunks), RC_THREADS, rs, st>>>(
+        order, mstart, pmem, cand, kr, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off, mscale,
+        mc, keys, idx->dev_err);
+    ADN_LAUNCH("rerank_chunks_kernel");
   }
   {
     StageTimer t(ST_RR_FINAL, st);

@@ -125,3 +125,56 @@ def test_mixed_errors(A, case):
 def test_mixed_ivf_d(A, case, storage, d_c):
     """IVF-D on the tensor-core path: the d_c = 32 lists probed at a smaller prefix."""
     check(A, case, storage, 128, 6, 10, 40, 0.99, d_c=d_c)
+
+
+@pytest.mark.parametrize("storage", [BF16, FP8])
+def test_shortlist_ties_are_deterministic(A, storage):
+    """Massive key ties at the shortlist cut (2,000 identical database rows,
+    queries equal to them, every other row duplicated): the shortlist takes
+    tied candidates in candidate order, so a query's result does not depend on
+    the batch it is in or on the run, and matches the oracle under the tie rule."""
+    from parity import ambiguous_probe_rows, check_topk
+    data = synthdata.small(20_000, 200, 128, 32, 409)
+    db = data["db"].copy()
+    db[1::2] = db[0::2]
+    db[5000:7000] = db[5000]
+    q = data["queries"].copy()
+    q[:8] = db[5000] * np.float32(1.5)
+    o = oracle.build_ivf(db, 32, 24, 5, 20_000, seed=23)
+    g = A.index_create(cu(db), cu(o["centroids"]), cu(o["assign"].astype(np.int32)),
+                       storage=1 | storage)
+    args = (32, 128, 4, 10)
+    full1 = A.search_ivf(g, cu(q), *args, storage=storage, rerank_k=40)[0].cpu().numpy()
+    full2 = A.search_ivf(g, cu(q), *args, storage=storage, rerank_k=40)[0].cpu().numpy()
+    part = A.search_ivf(g, cu(q[3:90]), *args, storage=storage, rerank_k=40)[0].cpu().numpy()
+    assert np.array_equal(full1, full2)
+    assert np.array_equal(part, full1[3:90])
+    gi, gd = A.search_ivf(g, cu(q[:8]), *args, storage=storage, rerank_k=40)
+    ref = oracle.search_ivf(db, o, q[:8], 32, 128, 4, 20_000)   # every candidate: whole tie group
+    amb = ambiguous_probe_rows(ref["probe_dist"], 4)
+    n, fails = check_topk(gi.cpu().numpy(), gd.cpu().numpy(), ref["ids"], ref["dist"], 10,
+                          skip_rows=amb)
+    assert not fails, fails[:2]
+    g.free()
+
+
+@pytest.mark.parametrize("d_s,nprobe,k,kr", [(256, 8, 100, 400), (128, 12, 10, 40), (64, 4, 1, 2048)])
+def test_certified_pruning_changes_nothing(A, case, d_s, nprobe, k, kr, monkeypatch):
+    """The shortlist candidates dropped before the exact rerank (BF16 error
+    bound) cannot reach the top-k: results with and without the pruning are
+    bit-identical."""
+    data, o, g = case
+    q = cu(data["queries"])
+    monkeypatch.setenv("ADANNS_RERANK_PRUNE", "0")
+    i0, d0 = A.search_ivf(g, q, 32, d_s, nprobe, k, storage=BF16, rerank_k=kr)
+    monkeypatch.setenv("ADANNS_RERANK_PRUNE", "1")
+    i1, d1 = A.search_ivf(g, q, 32, d_s, nprobe, k, storage=BF16, rerank_k=kr)
+    assert torch.equal(i0, i1)
+    assert torch.equal(d0, d1)
+
+
+def test_status_clean_after_mixed_searches(A, case):
+    """No device-side consistency check or pipeline wait fired in this module."""
+    data, o, g = case
+    A.search_ivf(g, cu(data["queries"]), 32, 256, 8, 100, storage=BF16, rerank_k=400)
+    g.status()
