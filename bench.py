@@ -220,8 +220,10 @@ def timed(P, torch, step, steps, stream):
     launches = (P.launch_count() - l0) // steps
     prof = P.profile_read()
     host = P.profile_read_host()
+    cnt = P.profile_read_counters()
     P.profile_enable(False)
     prof["_host_us"] = (sum(host.values()) / steps, 1)
+    timed.counters = {k2: v / steps for k2, v in cnt.items()}   # work counters per step
     return ev0.elapsed_time(ev1) / steps, launches, prof
 
 
@@ -377,6 +379,7 @@ def main():
         ms = max_over_ranks(ms)
         results[mode] = {"ms": ms, "qps": world * B / (ms / 1000.0), "launches": launches,
                          "stages_ms": {k2: v[0] / args.steps for k2, v in prof.items()},
+                         "counters": dict(timed.counters),
                          "ids": ids, "step": step}
     idx.status()  # raises if a device-side check or a pipeline wait failed during the runs
     main_r = results[args.mode]
@@ -452,17 +455,20 @@ def main():
                                "traffic": None, "kernel_ms": t,
                                "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"
                                + (" x 2 (nominal fp8/bf16 ratio)" if mode == "fp8" else "")}
-            # exact rerank: the k' shortlisted rows of d_s FP32 per query are the
-            # algorithmic bytes (each pair needs one candidate row)
+            # exact rerank: every database row it re-scores and every query row is
+            # needed once (N + B rows of d_s FP32 bound the unique bytes); each
+            # re-scored pair also gathers one query row (from L2)
             rr_t = sm.get("rr_pairs", sm.get("rerank", 0.0))
-            rr_bytes = B * mode_rerank(mode, args.k) * args.d_s * 4
+            rr_pairs = r["counters"].get("rerank_pairs", 0)
+            rr_bytes = (N + B) * args.d_s * 4
             rooflines[mode]["rerank"] = {
-                "kernel": "rerank_pairs_kernel (member-major exact FP32 rerank)", "bound": "hbm",
-                "achieved": rr_bytes / (rr_t / 1e3) / 1e9 if rr_t else None, "peak": hbm_peak,
-                "unit": "GB/s", "kernel_ms": rr_t,
-                "note": "algorithmic bytes = B x k' x d_s x 4 (one shortlisted row per pair); the "
-                        "member-major order serves the query rows from L2, so DRAM traffic is far "
-                        "below the algorithmic bytes"}
+                "kernel": "rerank_chunks_kernel (exact FP32 rerank of the pruned shortlist)",
+                "bound": "hbm", "achieved": rr_bytes / (rr_t / 1e3) / 1e9 if rr_t else None,
+                "peak": hbm_peak, "unit": "GB/s", "kernel_ms": rr_t,
+                "pairs": rr_pairs, "shortlist_slots": r["counters"].get("shortlist_slots", 0),
+                "gathered_query_gb": rr_pairs * args.d_s * 4 / 1e9,
+                "note": "algorithmic bytes = (N + B) x d_s x 4: each database and query row "
+                        "once; the query rows are gathered once per pair from L2"}
     main_roof = dict(rooflines[args.mode])
     # the dominant kernel of the step (largest stage) carries the headline roofline
     main_stages = main_r["stages_ms"]
@@ -483,7 +489,8 @@ def main():
            "clocks": clocks, "gpu_launches": int(main_r["launches"]), "roofline": main_roof,
            "stages_ms": main_r["stages_ms"],
            "modes": {m: {"qps": r["qps"], "ms_per_step": r["ms"], "stages_ms": r["stages_ms"],
-                         "roofline": rooflines[m]} for m, r in results.items()},
+                         "work_per_step": r["counters"], "roofline": rooflines[m]}
+                     for m, r in results.items()},
            "graph_replay": {"ms_per_step": graph_ms, "qps": world * B / (graph_ms / 1000.0)},
            "serving": serving,
            "p50_ms": (serving or {}).get(args.mode, {}).get("p50_ms"),

@@ -81,6 +81,15 @@ int adanns_profile_enable(int on);
 int adanns_profile_read(double *ms, int64_t *count, int nstage);
 /* Host wall time (microseconds, summed) spent issuing each stage's work. */
 int adanns_profile_read_host(double *us, int nstage);
+/*
+ * Work counters summed over the calls made while profiling was on (the
+ * device values are read after a device synchronisation):
+ *   values[0]  (query, candidate) pairs re-scored by the exact rerank of the
+ *              low-precision tiers, after the certified pruning
+ *   values[1]  shortlist slots (queries x rerank_k) of those calls
+ * Entries beyond the known counters are 0.
+ */
+int adanns_profile_read_counters(int64_t *values, int ncounter);
 
 /*
  * Build an AdANNS-IVF index (Algorithm 1 adannsConstruction; Sec. 3 "IVF":

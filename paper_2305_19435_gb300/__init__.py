@@ -50,6 +50,7 @@ def lib():
         L.adanns_profile_enable.argtypes = [i32]
         L.adanns_profile_read.argtypes = [P, P, i32]
         L.adanns_profile_read_host.argtypes = [P, i32]
+        L.adanns_profile_read_counters.argtypes = [P, i32]
         L.adanns_build_ivf.argtypes = [P, i64, i32, i32, i32, i32, i64, u64, i32, i32, P, P, P]
         L.adanns_index_create.argtypes = [P, i64, i32, P, i32, i32, P, i32, i32, P, P]
         L.adanns_index_info.argtypes = [P, P, P, P, P, P]
@@ -114,6 +115,16 @@ def profile_read_host(nstage: int = 16) -> dict:
     _check(lib().adanns_profile_read_host(us, nstage))
     names = list(STAGES) + [f"stage{i}" for i in range(len(STAGES), nstage)]
     return {names[i]: us[i] for i in range(nstage) if us[i]}
+
+
+COUNTERS = ("rerank_pairs", "shortlist_slots")
+
+
+def profile_read_counters() -> dict:
+    """{counter: total} of the work counters since profiling was enabled (synchronises)."""
+    v = (ctypes.c_int64 * 8)()
+    _check(lib().adanns_profile_read_counters(v, 8))
+    return {name: int(v[i]) for i, name in enumerate(COUNTERS)}
 
 
 def _check(rc: int):

@@ -179,6 +179,11 @@ struct MmaScanArgs {
   int fp8;
 };
 // Records an event pair around its scope on `st` when profiling is enabled.
+// work counters recorded while profiling is on (adanns_profile_read_counters)
+enum ProfileCounter { PC_RERANK_PAIRS = 0, PC_SHORTLIST_SLOTS = 1, PC_NCOUNTER = 8 };
+void profile_count(int counter, const int64_t *dev_value, cudaStream_t st);
+void profile_count_host(int counter, int64_t value);
+
 class StageTimer {
  public:
   StageTimer(int stage, cudaStream_t st);

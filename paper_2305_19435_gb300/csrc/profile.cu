@@ -20,6 +20,13 @@ std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 double g_host_us[ST_NSTAGE] = {0};
 
+// work counters: device values copied (stream-ordered) into device slots
+constexpr int NSLOT = 1 << 16;
+int64_t *g_slots = nullptr;
+int g_nslot = 0;
+std::vector<int> g_slot_counter;
+int64_t g_host_cnt[PC_NCOUNTER] = {0};
+
 double now_us() {
   return std::chrono::duration<double, std::micro>(
              std::chrono::steady_clock::now().time_since_epoch())
@@ -40,6 +47,29 @@ cudaEvent_t take_event() {
   return e;
 }
 }  // namespace
+
+void profile_count(int counter, const int64_t *dev_value, cudaStream_t st) {
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_on || counter < 0 || counter >= PC_NCOUNTER) return;
+  if (!g_slots && cudaMalloc(&g_slots, sizeof(int64_t) * NSLOT) != cudaSuccess) {
+    cudaGetLastError();
+    g_slots = nullptr;
+    return;
+  }
+  if (g_nslot >= NSLOT) return;
+  if (cudaMemcpyAsync(g_slots + g_nslot, dev_value, sizeof(int64_t), cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  g_slot_counter.push_back(counter);
+  ++g_nslot;
+}
+
+void profile_count_host(int counter, int64_t value) {
+  std::lock_guard<std::mutex> g(g_mu);
+  if (g_on && counter >= 0 && counter < PC_NCOUNTER) g_host_cnt[counter] += value;
+}
 
 StageTimer::StageTimer(int stage, cudaStream_t st) : stage_(stage), st_(st) {
   std::lock_guard<std::mutex> g(g_mu);
@@ -72,6 +102,9 @@ int adanns_profile_enable(int on) {
   }
   g_recs.clear();
   for (int i = 0; i < ST_NSTAGE; ++i) g_host_us[i] = 0.0;
+  for (int i = 0; i < PC_NCOUNTER; ++i) g_host_cnt[i] = 0;
+  g_nslot = 0;
+  g_slot_counter.clear();
   g_on = on != 0;
   return ADANNS_OK;
 }
@@ -99,6 +132,22 @@ int adanns_profile_read(double *ms, int64_t *count, int nstage) {
     if (e != cudaSuccess) return cuda_fail(e, "profile elapsed");
     ms[r.stage] += t;
     count[r.stage] += 1;
+  }
+  return ADANNS_OK;
+}
+
+int adanns_profile_read_counters(int64_t *values, int ncounter) {
+  if (!values || ncounter < 1) return fail(ADANNS_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> g(g_mu);
+  for (int i = 0; i < ncounter; ++i) values[i] = i < PC_NCOUNTER ? g_host_cnt[i] : 0;
+  if (g_nslot > 0) {
+    std::vector<int64_t> h(g_nslot);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h.data(), g_slots, sizeof(int64_t) * g_nslot, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "profile counters");
+    for (int i = 0; i < g_nslot; ++i)
+      if (g_slot_counter[i] < ncounter) values[g_slot_counter[i]] += h[i];
   }
   return ADANNS_OK;
 }

@@ -215,6 +215,8 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     member_sort_kernel<<<nlist, 256, hs, st>>>(goff, byl, pmem, idx->list_off, nlist, order, mstart);
     ADN_LAUNCH("member_sort_kernel");
   }
+  profile_count(PC_RERANK_PAIRS, goff + nlist, st);  // pairs left after pruning
+  profile_count_host(PC_SHORTLIST_SLOTS, n);
   {
     StageTimer t(ST_RR_PAIRS, st);
     const int mc = rerank_chunk_members(d_s);
