@@ -10,24 +10,6 @@
 
 namespace adn {
 
-__device__ __forceinline__ int kGranDev(int g) {
-  switch (g) {
-    case 0: return 8;
-    case 1: return 16;
-    case 2: return 32;
-    case 3: return 48;
-    case 4: return 64;
-    case 5: return 96;
-    case 6: return 128;
-    case 7: return 192;
-    case 8: return 256;
-    case 9: return 384;
-    case 10: return 512;
-    case 11: return 768;
-    case 12: return 1024;
-    default: return 2048;
-  }
-}
 
 // rows[r] (or r) of x, first `dim` coordinates, times 1/||x[0:dim]|| (metric
 // L2_PREFIXNORM) into out (rows of ldo, zero padded).  One warp per row.

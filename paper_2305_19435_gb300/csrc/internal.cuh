@@ -37,6 +37,27 @@ int gran_index(int m);  // index in kGran, or -1
 
 inline int pad16(int x) { return (x + 15) & ~15; }
 
+// kGran[g] on the device
+__device__ __forceinline__ int kGranDev(int g) {
+  switch (g) {
+    case 0: return 8;
+    case 1: return 16;
+    case 2: return 32;
+    case 3: return 48;
+    case 4: return 64;
+    case 5: return 96;
+    case 6: return 128;
+    case 7: return 192;
+    case 8: return 256;
+    case 9: return 384;
+    case 10: return 512;
+    case 11: return 768;
+    case 12: return 1024;
+    default: return 2048;
+  }
+}
+
+
 // ---------------------------------------------------------------- errors
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -228,6 +249,9 @@ struct adanns_index {
   int lowp_blocks[2] = {0, 0};
   float *lowp_sx[2] = {nullptr, nullptr};  // per-vector scale, list order
   float *lowp_cx[2] = {nullptr, nullptr};  // [ng][N] scale * inverse prefix norm
+  // per granularity g: max over members of nu_g(x) * |(x - s_x x~)[0:g]|, the
+  // largest relative quantisation residual of a normalised prefix (host copy)
+  float lowp_rmax[2][adn::NGRAN] = {};
   int64_t *h_list_off = nullptr;  // host copy of list offsets
   int *dev_err = nullptr;         // sticky device status word (tensor-core pipeline timeouts)
 };

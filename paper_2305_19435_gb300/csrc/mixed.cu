@@ -26,10 +26,14 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
 // Member p (list order) of list l: s_x = max_j |x_j| / R (R = 448 for FP8-E4M3,
 // 1 for BF16; 1 for a zero vector); element j of block b is stored at
 // ((off_l * nblk + b * n_l + m) * epb + j % epb), value x_j / s_x rounded.
+// It also folds, per granularity g, nu_g(p) * |(x - s_x x~)[0:g]| (the exact
+// residual of the stored values, computed with one rounding per coordinate)
+// into rmax[g] by an atomic maximum.
 __global__ void quantize_kernel(const float *__restrict__ x, int d, const int64_t *__restrict__ list_off,
                                 const int32_t *__restrict__ list_ids,
                                 const int32_t *__restrict__ assign, int64_t N, int fp8, int nblk,
-                                unsigned char *__restrict__ out, float *__restrict__ sx) {
+                                unsigned char *__restrict__ out, float *__restrict__ sx,
+                                const float *__restrict__ invn, int ng, float *__restrict__ rmax) {
   const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (p >= N) return;
@@ -47,14 +51,42 @@ __global__ void quantize_kernel(const float *__restrict__ x, int d, const int64_
   const float s = mx > 0.f ? mx / R : 1.f;
   if (lane == 0) sx[p] = s;
   const int epb = fp8 ? 128 : 64;
+  float seg[NGRAN];  // this lane's squared residuals per granularity segment
+#pragma unroll
+  for (int g = 0; g < NGRAN; ++g) seg[g] = 0.f;
+  int g = 0;
   for (int j = lane; j < nblk * epb; j += 32) {
     const float v = j < d ? src[j] / s : 0.f;
     const int b = j / epb, e = j - b * epb;
     const int64_t o = ((off * nblk + b * nl + m) * epb + e);
+    float back;
     if (fp8) {
-      out[o] = (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+      const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+      out[o] = (unsigned char)c;
+      back = __half2float(__half(__nv_cvt_fp8_to_halfraw(c, __NV_E4M3)));
     } else {
-      ((__nv_bfloat16 *)out)[o] = __float2bfloat16_rn(v);
+      const __nv_bfloat16 c = __float2bfloat16_rn(v);
+      ((__nv_bfloat16 *)out)[o] = c;
+      back = __bfloat162float(c);
+    }
+    if (j < d) {
+      while (g < NGRAN - 1 && j >= kGranDev(g)) ++g;
+      const float r = fmaf(-s, back, src[j]);
+#pragma unroll
+      for (int t = 0; t < NGRAN; ++t)
+        if (t == g) seg[t] = fmaf(r, r, seg[t]);
+    }
+  }
+  float pre = 0.f;
+#pragma unroll
+  for (int t = 0; t < NGRAN; ++t) {
+    float v = seg[t];
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+    pre += v;
+    if (lane == 0 && t < ng) {
+      const float rel = sqrtf(pre) * invn[(int64_t)t * N + p];
+      atomicMax((int *)(rmax + t), __float_as_int(rel));  // non-negative floats order as ints
     }
   }
 }
@@ -74,18 +106,30 @@ int build_lowp(adanns_index *x, const float *db, int which, cudaStream_t st) {
   const size_t elems = (size_t)x->N * nblk * epb;
   const size_t bytes = elems * (fp8 ? 1 : 2);
   void *store = nullptr;
-  float *sx = nullptr, *cx = nullptr;
+  float *sx = nullptr, *cx = nullptr, *rmax = nullptr;
   if (cudaMalloc(&store, bytes + 256) != cudaSuccess || cudaMalloc(&sx, sizeof(float) * x->N) != cudaSuccess ||
-      cudaMalloc(&cx, sizeof(float) * (size_t)x->N * std::max(x->ng, 1)) != cudaSuccess) {
+      cudaMalloc(&cx, sizeof(float) * (size_t)x->N * std::max(x->ng, 1)) != cudaSuccess ||
+      cudaMalloc(&rmax, sizeof(float) * NGRAN) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(store);
     cudaFree(sx);
     cudaFree(cx);
+    cudaFree(rmax);
     return fail(ADANNS_ERR_OOM, "low-precision storage allocation failed");
   }
+  ADN_CUDA(cudaMemsetAsync(rmax, 0, sizeof(float) * NGRAN, st));
   quantize_kernel<<<(unsigned)((x->N + 7) / 8), 256, 0, st>>>(
-      db, x->d, x->list_off, x->list_ids, x->assign, x->N, fp8, nblk, (unsigned char *)store, sx);
+      db, x->d, x->list_off, x->list_ids, x->assign, x->N, fp8, nblk, (unsigned char *)store, sx,
+      x->invn, x->ng, rmax);
   ADN_LAUNCH("quantize_kernel");
+  {
+    float h[NGRAN];
+    cudaError_t e = cudaMemcpyAsync(h, rmax, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(rmax);
+    if (e != cudaSuccess) return cuda_fail(e, "quantisation residual");
+    for (int g = 0; g < NGRAN; ++g) x->lowp_rmax[which][g] = h[g];
+  }
   const int64_t ne = x->N * (int64_t)x->ng;
   if (ne > 0) {
     lowp_scale_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(sx, x->invn, x->N, x->ng, cx);
@@ -103,7 +147,8 @@ int build_lowp(adanns_index *x, const float *db, int which, cudaStream_t st) {
 // row q / s_q (nkb blocks of epb elements, zero beyond d_s).
 __global__ void prep_lowp_kernel(const float *__restrict__ qs, int ldq, int64_t B, int d_s,
                                  int fp8, int nkb, unsigned char *__restrict__ out,
-                                 float *__restrict__ qn2, float *__restrict__ qsc) {
+                                 float *__restrict__ qn2, float *__restrict__ qsc,
+                                 float *__restrict__ qrho) {
   const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (q >= B) return;
@@ -127,13 +172,27 @@ __global__ void prep_lowp_kernel(const float *__restrict__ qs, int ldq, int64_t 
   }
   const int epb = fp8 ? 128 : 64;
   const int len = nkb * epb;
+  float r2 = 0.f;  // |P(q) - s_q q~|^2: the query's own quantisation residual
   for (int j = lane; j < len; j += 32) {
     const float v = j < d_s ? src[j] / s : 0.f;
-    if (fp8)
-      out[q * len + j] = (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
-    else
-      ((__nv_bfloat16 *)out)[q * len + j] = __float2bfloat16_rn(v);
+    float back;
+    if (fp8) {
+      const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+      out[q * len + j] = (unsigned char)c;
+      back = __half2float(__half(__nv_cvt_fp8_to_halfraw(c, __NV_E4M3)));
+    } else {
+      const __nv_bfloat16 c = __float2bfloat16_rn(v);
+      ((__nv_bfloat16 *)out)[q * len + j] = c;
+      back = __bfloat162float(c);
+    }
+    if (j < d_s) {
+      const float r = fmaf(-s, back, src[j]);
+      r2 = fmaf(r, r, r2);
+    }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  if (lane == 0) qrho[q] = sqrtf(r2);
 }
 
 // Qt[t][kb][r][0:128 B] = row pair_q[tile_beg[t] + r] of the low-precision
@@ -389,8 +448,8 @@ __device__ void radix_select(int n, int kk, int kq, int prune_delta, KeyF key, I
 __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
     const uint16_t *__restrict__ cand, const uint64_t *__restrict__ ckeys, int nprobe,
     const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off,
-    const int32_t *__restrict__ list_ids, int kk, int k, int prune_delta,
-    int64_t *__restrict__ out) {
+    const int32_t *__restrict__ list_ids, int kk, int k, const float *__restrict__ qrho,
+    float rmax, float e_rest, int prune, int64_t *__restrict__ out) {
   __shared__ SelState st;
   __shared__ uint16_t samp[SEL_SAMPLE];
   __shared__ uint32_t bkey[SEL_BUF], bidx[SEL_BUF];
@@ -399,6 +458,13 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
   __shared__ int s_nl[128], s_pst[129];
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
+  int prune_delta = 1 << 20;  // key units; larger than any key difference: no pruning
+  if (prune) {
+    const double rq = (double)qrho[q];
+    const double E = 2.0 * (rmax + rq + rmax * rq) * (1.0 + 1e-3) + e_rest;
+    prune_delta = (int)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1;
+    if (prune_delta > (1 << 20)) prune_delta = 1 << 20;
+  }
   for (int s = tid; s < nprobe; s += SEL_THREADS) {
     const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
     s_off[s] = list_off[l];
@@ -497,25 +563,29 @@ int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t
 
 // Certified shortlist pruning (exact: the result equals the unpruned rerank).
 // A shortlisted candidate c is dropped before the exact rerank when its key
-// exceeds the k-th smallest shortlist key by more than prune_delta, i.e. when
-// even its smallest possible exact distance is above the largest possible
-// exact distance of k other candidates.  With the BF16 tier, for unit-norm
-// prefixes,
-//   |d_exact - d_approx| <= E = 2 (2u + u^2) + e_rest,   u = 2^-8 + 2^-23,
-// from the per-coordinate relative rounding of q/s_q and x/s_x to BF16
-// (|q x - q~ x~| <= (2u + u^2) |q| |x| summed, then Cauchy-Schwarz) times the
-// factor 2 of the cross term; e_rest = 2e-3 bounds the FP32 tensor-core
-// accumulation (<= 2 d 2^-23 for d <= 2048), the norm terms and the FP32
-// rerank's own rounding.  A key is round(16384 d_approx) (+-2^-15), so c can
-// be dropped when key_c > key_k + 2 * 16384 * (2^-15 + E).  FP8-E4M3 (u =
-// 2^-4, plus subnormal steps) gives no useful bound: no pruning there, and
-// none unless ADANNS_RERANK_PRUNE is unset or non-zero.
-static int shortlist_prune_delta(int fp8) {
+// exceeds the k-th smallest shortlist key by more than the query's delta,
+// i.e. when even its smallest possible exact distance is above the largest
+// possible exact distance of k other candidates.  For unit-norm prefixes,
+// with r_x = x - s_x x~ and r_q = P(q) - s_q q~ the residuals of the stored
+// and the query's low-precision values,
+//   P(q).x - (s_q q~).(s_x x~) = P(q).r_x + r_q.x - r_q.r_x,
+// so by Cauchy-Schwarz |d_exact - d_approx| <= E_q with
+//   E_q = 2 (R + rho_q + R rho_q) (1 + 1e-3) + e_rest,
+// R = max over the index of nu_x |r_x[0:d_s]| (recorded when the tier is
+// built), rho_q = |r_q| (computed with the query's low-precision copy) and
+// e_rest bounding the FP32 tensor-core accumulation (2 d_pad 2^-22), the FP32
+// norm and scale terms and the FP32 rerank's own rounding (8 (d_s + 2) 2^-24),
+// plus 1e-4.  Keys are round(16384 d_approx) (+-2^-15), so c can be dropped
+// when key_c > key_k + 2 * 16384 * (2^-15 + E_q).  Set ADANNS_RERANK_PRUNE=0
+// to rerank every shortlisted candidate.
+static bool shortlist_prune_enabled() {
   const char *env = getenv("ADANNS_RERANK_PRUNE");
-  if (fp8 || (env && env[0] == '0')) return 1 << 20;
-  const double u = std::ldexp(1.0, -8) + std::ldexp(1.0, -23);
-  const double E = 2.0 * (2.0 * u + u * u) + 2e-3;
-  return (int)std::ceil(2.0 * 16384.0 * (std::ldexp(1.0, -15) + E)) + 1;
+  return !(env && env[0] == '0');
+}
+
+static float shortlist_e_rest(int d_s, int d_pad) {
+  return (float)(2.0 * d_pad * std::ldexp(1.0, -22) + 8.0 * (d_s + 2) * std::ldexp(1.0, -24) +
+                 1e-4);
 }
 
 int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
@@ -533,9 +603,11 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   // slices bounded by a scratch budget (the candidate keys dominate it)
   const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
   const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
-  const int prune_delta = shortlist_prune_delta(fp8);
+  const bool prune = shortlist_prune_enabled();
+  const float rmax = idx->lowp_rmax[which][gran_index(d_s)] * 1.001f;
+  const float e_rest = shortlist_e_rest(d_s, nkb * epb);
   Scratch s(st);
-  float *qc, *qs, *qn2, *qsc;
+  float *qc, *qs, *qn2, *qsc, *qrho;
   uint64_t *ckeys;
   int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
   int *ntiles, *counter;
@@ -545,7 +617,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   uint16_t *cand;
   int rc;
   if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
-      (rc = s.get(&qn2, Bc)) || (rc = s.get(&qsc, Bc)) || (rc = s.get(&ckeys, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&qn2, Bc)) || (rc = s.get(&qsc, Bc)) || (rc = s.get(&qrho, Bc)) || (rc = s.get(&ckeys, (size_t)Bc * nprobe)) ||
       (rc = s.get(&lcnt, nlist)) || (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) ||
       (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
       (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
@@ -567,7 +639,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
                                     dcp, qs, dsp, st)))
         return rc;
       prep_lowp_kernel<<<(unsigned)((nb + 7) / 8), 256, 0, st>>>(qs, dsp, nb, d_s, fp8, nkb, qlow,
-                                                                 qn2, qsc);
+                                                                 qn2, qsc, qrho);
       ADN_LAUNCH("prep_lowp_kernel");
     }
     ScanArgs c{};
@@ -630,7 +702,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
       StageTimer t(ST_SELECT, st);
       select_kernel<<<(unsigned)nb, SEL_THREADS, 0, st>>>(cand, ckeys, nprobe, qbase,
                                                           idx->list_off, idx->list_ids, kk, k,
-                                                          prune_delta, cids);
+                                                          qrho, rmax, e_rest, prune ? 1 : 0, cids);
       ADN_LAUNCH("select_kernel");
     }
     {

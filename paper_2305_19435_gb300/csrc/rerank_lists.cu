@@ -93,6 +93,8 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = lane >> 4, hl = lane & 15, hw = warp * 2 + half;
   const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
+  // the query block is re-read by every list: keep it in L2; member rows are read once
+  const uint64_t keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
   for (int m0 = blockIdx.y * mc; m0 < nl; m0 += gridDim.y * mc) {
     const int m1 = min(nl, m0 + mc), nm = m1 - m0;
     const int p0 = mstart[off + m0], p1 = mstart[off + m1];
@@ -103,8 +105,9 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
     for (int t = threadIdx.x; t < per_b * ((d_s + 15) >> 4); t += RC_THREADS) {
       const int b = t / per_b, w = t - b * per_b, mm = w >> 2, part = w & 3;
       if (4 * b + part >= nseg) continue;  // d_s = 8: half of the last block
-      cp_async16(rows + (size_t)mm * rs + 16 * b + 4 * part,
-                 xpm + off * d_pad + (int64_t)b * 16 * nl + (int64_t)(m0 + mm) * 16 + part * 4);
+      cp_async16_hint(rows + (size_t)mm * rs + 16 * b + 4 * part,
+                      xpm + off * d_pad + (int64_t)b * 16 * nl + (int64_t)(m0 + mm) * 16 + part * 4,
+                      stream);
     }
     cp_async_commit();  // the copies land while the first metadata batch loads
     for (int t = threadIdx.x; t < nm; t += RC_THREADS) s_nu[t] = mscale ? mscale[off + m0 + t] : 1.f;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
         const float *qr = qs + (int64_t)s_q[t] * ldq;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-          if (hl + 16 * u < nseg) dst[u] = __ldg((const float4 *)(qr + 4 * (hl + 16 * u)));
+          if (hl + 16 * u < nseg) dst[u] = ldg_f4_hint((const float4 *)(qr + 4 * (hl + 16 * u)), keep);
       };
       float4 qn[8];
       if (hw < nb) load_first(hw, qn);
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
           if (s0 != hl) {
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (s0 + 16 * u < nseg) qv[u] = __ldg((const float4 *)(qr + 4 * (s0 + 16 * u)));
+              if (s0 + 16 * u < nseg) qv[u] = ldg_f4_hint((const float4 *)(qr + 4 * (s0 + 16 * u)), keep);
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
