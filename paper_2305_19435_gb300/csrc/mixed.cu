@@ -502,9 +502,18 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
   }
   const uint16_t *src = cand + qbase[q];
   if (ptotal > 4 * SEL_SAMPLE) {
-    // 1. threshold from a strided sample
-    for (int j = tid; j < SEL_SAMPLE; j += SEL_THREADS)
-      samp[j] = src[(int)(((int64_t)j * ptotal) / SEL_SAMPLE)];
+    // 1. threshold from a sample: SEL_SAMPLE / 8 evenly spaced runs of 8 keys
+    //    (one 16-byte load each)
+    {
+      const uint4 *g = (const uint4 *)src;
+      const int nvec = ptotal >> 3;
+      for (int j = tid; j < SEL_SAMPLE / 8; j += SEL_THREADS) {
+        const uint4 v = g[(int)(((int64_t)j * nvec) / (SEL_SAMPLE / 8))];
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 8; ++u) samp[8 * j + u] = (uint16_t)((w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu);
+      }
+    }
     __syncthreads();
     int r = (int)((1.6 * kk * SEL_SAMPLE) / ptotal) + 16;
     if (r > SEL_SAMPLE - 1) r = SEL_SAMPLE - 1;
@@ -518,24 +527,33 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
     // 2. compact the keys below T
     const uint32_t T = (uint32_t)s_T;
     const uint4 *g = (const uint4 *)src;
-    for (int c0 = 0; c0 < (ptotal >> 3); c0 += SEL_THREADS) {
-      const int c = c0 + tid;
-      uint4 v = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-      if (c < (ptotal >> 3)) v = g[c];
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    const int nvec = ptotal >> 3;
+    constexpr int PF = 4;  // 16-byte loads in flight per thread
+    for (int c0 = 0; c0 < nvec; c0 += PF * SEL_THREADS) {
+      uint4 v[PF];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const uint32_t k = (w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu;
-        const bool take = k < T;
-        const unsigned m = __ballot_sync(0xffffffffu, take);
-        int base = 0;
-        if (lane == 0 && m) base = atomicAdd(&s_n, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (take) {
-          const int p = base + __popc(m & ((1u << lane) - 1u));
-          if (p < SEL_BUF) {
-            bkey[p] = k;
-            bidx[p] = (uint32_t)(c * 8 + u);
+      for (int f = 0; f < PF; ++f) {
+        const int c = c0 + f * SEL_THREADS + tid;
+        v[f] = c < nvec ? g[c] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+      }
+#pragma unroll
+      for (int f = 0; f < PF; ++f) {
+        const int c = c0 + f * SEL_THREADS + tid;
+        const uint32_t w[4] = {v[f].x, v[f].y, v[f].z, v[f].w};
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t k = (w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu;
+          const bool take = k < T;
+          const unsigned m = __ballot_sync(0xffffffffu, take);
+          int base = 0;
+          if (lane == 0 && m) base = atomicAdd(&s_n, __popc(m));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (take) {
+            const int p = base + __popc(m & ((1u << lane) - 1u));
+            if (p < SEL_BUF) {
+              bkey[p] = k;
+              bidx[p] = (uint32_t)(c * 8 + u);
+            }
           }
         }
       }

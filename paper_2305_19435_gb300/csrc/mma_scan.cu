@@ -35,7 +35,9 @@ constexpr int NSTAGE = 4;
 constexpr int A_BYTES = BM * ROWB;    // 16 KB
 constexpr int B_BYTES = BN * ROWB;    // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;                  // two per TMEM lane quadrant, half the columns each
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int THREADS = 64 + EPI_THREADS;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -141,6 +143,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// two 32-column loads in flight, one wait
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, uint32_t (&r)[32], uint32_t (&s)[32]) {
+#define ADN_LD32(R, ADDR)                                                                          \
+  asm volatile(                                                                                    \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, " \
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, " \
+      "%30, %31}, [%32];"                                                                          \
+      : "=r"(R[0]), "=r"(R[1]), "=r"(R[2]), "=r"(R[3]), "=r"(R[4]), "=r"(R[5]), "=r"(R[6]),       \
+        "=r"(R[7]), "=r"(R[8]), "=r"(R[9]), "=r"(R[10]), "=r"(R[11]), "=r"(R[12]), "=r"(R[13]),   \
+        "=r"(R[14]), "=r"(R[15]), "=r"(R[16]), "=r"(R[17]), "=r"(R[18]), "=r"(R[19]),             \
+        "=r"(R[20]), "=r"(R[21]), "=r"(R[22]), "=r"(R[23]), "=r"(R[24]), "=r"(R[25]),             \
+        "=r"(R[26]), "=r"(R[27]), "=r"(R[28]), "=r"(R[29]), "=r"(R[30]), "=r"(R[31])              \
+      : "r"(ADDR))
+  ADN_LD32(r, taddr);
+  ADN_LD32(s, taddr + 32);
+#undef ADN_LD32
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ int ld_abort(const int *flag) { return *(const volatile int *)flag; }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -160,7 +181,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *sA = smem;                              // NSTAGE x 16 KB
   unsigned char *sB = smem + NSTAGE * A_BYTES;           // NSTAGE x 32 KB
-  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2];
+  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], sfull[2];
   __shared__ float s_cb[2][BN], s_ca[2][BN];  // per member of the tile: -2 s_x nu_x, |x|^2
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
@@ -173,7 +194,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&tfull[s], 1);
-      mbar_init(&tempty[s], 128);
+      mbar_init(&tempty[s], EPI_THREADS);
+      mbar_init(&sfull[s], EPI_THREADS);
     }
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -263,8 +285,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5, one query row per thread
+    // ---------------- epilogue: warps 2..9, one query row per thread; the
+    // two warps of a TMEM lane quadrant (warp % 4) take half the columns each
     const int quarter = warp & 3;
+    const int c_lo = ((warp - 2) / 4) * (BN / 2);
     const int row = quarter * 32 + lane;
     int acc = 0;
     uint32_t aphase = 0;
@@ -294,46 +318,57 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         tc_fence_after();
-        // the tile's per-member terms, staged once for the four epilogue warps
+        // the tile's per-member terms, staged once for the epilogue warps
         {
           const int et = threadIdx.x - 64;
-          for (int i = et; i < BN; i += 128) {
+          for (int i = et; i < BN; i += EPI_THREADS) {
             const int m = mt * BN + i;
             const float c = m < nl ? __ldg(a.cx + off + m) : 0.f;
             s_cb[acc][i] = -2.f * c;
             s_ca[acc][i] = m < nl ? (c > 0.f ? 1.f : 0.f) : 3.0e38f;
           }
-          asm volatile("bar.sync 1, 128;" ::: "memory");
+          // hand-off through an mbarrier: a bounded wait, unlike bar.sync
+          mbar_arrive(&sfull[acc]);
+          if (!mbar_wait(&sfull[acc], aphase)) {
+            atomicExch(&abort_s, 1);
+            atomicExch(a.err, 5);
+            stop = true;
+            break;
+          }
         }
         const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(tbase + c0, r);
-          const int m0 = mt * BN + c0;
-          if (valid && m0 < npad) {
-            uint32_t packed[16];
+        for (int c0 = c_lo; c0 < c_lo + BN / 2; c0 += 64) {
+          uint32_t r[2][32];
+          tmem_ld32x2(tbase + c0, r[0], r[1]);
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              uint32_t kk[2];
+          for (int h = 0; h < 2; ++h) {
+            const int cb = c0 + 32 * h;
+            const int m0 = mt * BN + cb;
+            if (valid && m0 < npad) {
+              uint32_t packed[16];
 #pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                // approximate squared distance as a 16-bit fixed-point key:
-                // round(d * 2^14), d clamped to [0, 4); members past the list
-                // end get the largest key
-                const int c = c0 + j + u;
-                float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[j + u]), q2 + s_ca[acc][c]);
-                d = fminf(fmaxf(d, 0.f), 3.9999f);
-                kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
+              for (int j = 0; j < 32; j += 2) {
+                uint32_t kk[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                  // approximate squared distance as a 16-bit fixed-point key:
+                  // round(d * 2^14), d clamped to [0, 4); members past the list
+                  // end get the largest key
+                  const int c = cb + j + u;
+                  float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[h][j + u]), q2 + s_ca[acc][c]);
+                  d = fminf(fmaxf(d, 0.f), 3.9999f);
+                  kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
+                }
+                packed[j >> 1] = kk[0] | (kk[1] << 16);
               }
-              packed[j >> 1] = kk[0] | (kk[1] << 16);
-            }
-            uint4 *dst = (uint4 *)(a.cand + base + m0);
+              uint4 *dst = (uint4 *)(a.cand + base + m0);
 #pragma unroll
-            for (int g = 0; g < 4; ++g)
-              if (m0 + 8 * g < npad)
-                dst[g] = make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2],
-                                    packed[4 * g + 3]);
+              for (int g = 0; g < 4; ++g)
+                if (m0 + 8 * g < npad)
+                  dst[g] = make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2],
+                                      packed[4 * g + 3]);
+            }
           }
         }
         tc_fence_before();

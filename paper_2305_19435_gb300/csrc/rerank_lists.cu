@@ -180,11 +180,18 @@ __global__ void final_topk_kernel(const uint64_t *__restrict__ keys, int kr, int
   const int64_t q = (int64_t)blockIdx.x * 4 + warp;
   if (q >= B) return;
   uint64_t *buf = kb + (size_t)warp * kr;
-  for (int r = lane; r < kr; r += 32) buf[r] = keys[q * kr + r];
+  // keep only the re-scored slots (pruned and padding slots hold the empty key)
+  int n = 0;
+  for (int r0 = 0; r0 < kr; r0 += 32) {
+    const uint64_t key = r0 + lane < kr ? keys[q * kr + r0 + lane] : KEY_MAX;
+    const unsigned m = __ballot_sync(0xffffffffu, key != KEY_MAX);
+    if (key != KEY_MAX) buf[n + __popc(m & lanemask_lt())] = key;
+    n += __popc(m);
+  }
   __syncwarp();
-  warp_sort(buf, kr);
+  warp_sort(buf, n);
   for (int r = lane; r < k; r += 32) {
-    const uint64_t key = r < kr ? buf[r] : KEY_MAX;
+    const uint64_t key = r < n ? buf[r] : KEY_MAX;
     out_ids[q * k + r] = key == KEY_MAX ? -1 : (int64_t)(uint32_t)(key & 0xffffffffu);
     out_dist[q * k + r] = key == KEY_MAX ? __int_as_float(0x7f800000)
                                          : __uint_as_float((uint32_t)(key >> 32));

@@ -68,7 +68,11 @@ ScanCfg choose(int k, int tq) {
     return c;
   }
   const int kp = next_pow2(k);
-  c.cap = kp + ROUND;
+  // buffer slack: a query compacts only when its next round could overflow;
+  // small k (the cluster mapping) can afford room for several rounds, so the
+  // sort-and-merge runs a few times per work item instead of every round
+  const int slack = kp <= 32 ? 4 : (kp <= 64 ? 2 : 1);
+  c.cap = kp + ROUND * slack;
   c.tq = kp <= 128 ? 4 : 1;
   if (tq == 1) c.tq = 1;  // a smaller query tile is valid for every k
   c.smem = smem_bytes(16 * c.tq, c.cap);
