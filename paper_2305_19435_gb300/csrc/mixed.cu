@@ -18,6 +18,7 @@ namespace adn {
 int launch_rerank(const int64_t *cand, int kr, int64_t B, const float *qs, int ldq, int d_s,
                   const adanns_index *idx, const float *mscale, int k, int64_t *out_ids,
                   float *out_dist, cudaStream_t st);
+// cand: B x kr shortlisted candidates as (list << 32 | member position), -1 padding
 int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs, int ldq, int d_s,
                         const adanns_index *idx, const float *mscale, int k, int64_t *out_ids,
                         float *out_dist, cudaStream_t st);
@@ -285,7 +286,8 @@ __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, 
 //     radix select on the buffer fixes the cut; otherwise the exact two-pass
 //     radix select runs over the whole region.
 // Ties at the cut are taken in candidate-position order (list rank, then member
-// position), independent of thread timing.  Writes database ids (-1 padding).
+// position), independent of thread timing.  Writes (list << 32 | member
+// position) per shortlisted candidate (-1 padding).
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_WARPS = SEL_THREADS / 32;
 constexpr int SEL_SAMPLE = 2048;
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
   __shared__ uint16_t samp[SEL_SAMPLE];
   __shared__ uint32_t bkey[SEL_BUF], bidx[SEL_BUF];
   __shared__ int s_T, s_n;
-  __shared__ int64_t s_off[128];
+  __shared__ int s_lid[128];
   __shared__ int s_nl[128], s_pst[129];
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
   }
   for (int s = tid; s < nprobe; s += SEL_THREADS) {
     const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
-    s_off[s] = list_off[l];
+    s_lid[s] = l;
     s_nl[s] = (int)(list_off[l + 1] - list_off[l]);
   }
   __syncthreads();
@@ -482,6 +484,8 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
   int total = 0;
   for (int s = 0; s < nprobe; ++s) total += s_nl[s];
   int64_t *o = out + q * kk;
+  // a candidate is written as (list << 32 | member position in the list);
+  // the rerank reads the database id from the list itself
   auto id_at = [&](int i) -> int64_t {
     int lo = 0, hi = nprobe - 1;
     while (lo < hi) {
@@ -489,13 +493,14 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(
       if (s_pst[mid] <= i) lo = mid; else hi = mid - 1;
     }
     const int m = i - s_pst[lo];
-    return m < s_nl[lo] ? (int64_t)list_ids[s_off[lo] + m] : -1;
+    return m < s_nl[lo] ? (((int64_t)s_lid[lo] << 32) | (int64_t)m) : -1;
   };
   if (total <= kk) {
     for (int s = 0; s < nprobe; ++s) {
       int pos = 0;
       for (int s2 = 0; s2 < s; ++s2) pos += s_nl[s2];
-      for (int m = tid; m < s_nl[s]; m += SEL_THREADS) o[pos + m] = list_ids[s_off[s] + m];
+      for (int m = tid; m < s_nl[s]; m += SEL_THREADS)
+        o[pos + m] = ((int64_t)s_lid[s] << 32) | (int64_t)m;
     }
     for (int r = total + tid; r < kk; r += SEL_THREADS) o[r] = -1;
     return;

@@ -14,23 +14,15 @@
 
 namespace adn {
 
-// pair e = (query e / kr, rank e % kr): its list (nlist for padding) and member index
+// pair e = (query e / kr, rank e % kr), given as (list << 32 | member
+// position): its list (nlist for padding) and member index
 __global__ void pair_lists_kernel(const int64_t *__restrict__ cand, int64_t n, int nlist,
-                                  const int32_t *__restrict__ assign,
-                                  const int32_t *__restrict__ pos,
-                                  const int64_t *__restrict__ list_off, int32_t *__restrict__ plist,
-                                  int32_t *__restrict__ pmem) {
+                                  int32_t *__restrict__ plist, int32_t *__restrict__ pmem) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const int64_t id = cand[e];
-  if (id < 0) {
-    plist[e] = nlist;
-    pmem[e] = 0;
-    return;
-  }
-  const int l = assign[id];
-  plist[e] = l;
-  pmem[e] = (int32_t)(pos[id] - list_off[l]);
+  const int64_t v = cand[e];
+  plist[e] = v < 0 ? nlist : (int32_t)(v >> 32);
+  pmem[e] = v < 0 ? 0 : (int32_t)(v & 0xffffffffll);
 }
 
 // one CTA per list group: reorder that group's pairs by member index and
@@ -78,14 +70,14 @@ inline int rerank_chunk_members(int d_s) {
 
 __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
     const int32_t *__restrict__ order, const int32_t *__restrict__ mstart,
-    const int32_t *__restrict__ pmem, const int64_t *__restrict__ cand, int kr,
+    const int32_t *__restrict__ pmem, const int32_t *__restrict__ list_ids, int kr,
     const float *__restrict__ qs, int ldq, int d_s, const float *__restrict__ xpm, int d_pad,
     const int64_t *__restrict__ list_off, const float *__restrict__ mscale, int mc,
     uint64_t *__restrict__ keys, int *__restrict__ err) {
   extern __shared__ __align__(16) float rows[];  // [mc][d_s + 4]
   __shared__ int s_e[RC_META], s_m[RC_META], s_q[RC_META];
-  __shared__ uint32_t s_cid[RC_META];
   __shared__ float s_nu[RC_MAX_MC];
+  __shared__ uint32_t s_id[RC_MAX_MC];
   const int l = blockIdx.x;
   const int64_t off = list_off[l];
   const int nl = (int)(list_off[l + 1] - off);
@@ -110,7 +102,10 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
                       stream);
     }
     cp_async_commit();  // the copies land while the first metadata batch loads
-    for (int t = threadIdx.x; t < nm; t += RC_THREADS) s_nu[t] = mscale ? mscale[off + m0 + t] : 1.f;
+    for (int t = threadIdx.x; t < nm; t += RC_THREADS) {
+      s_nu[t] = mscale ? mscale[off + m0 + t] : 1.f;
+      s_id[t] = (uint32_t)list_ids[off + m0 + t];
+    }
     for (int base = p0; base < p1; base += RC_META) {
       const int nb = min(RC_META, p1 - base);
       if (base != p0) __syncthreads();  // previous metadata consumed
@@ -124,7 +119,6 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
         s_e[threadIdx.x] = e;
         s_m[threadIdx.x] = mm;
         s_q[threadIdx.x] = e / kr;
-        s_cid[threadIdx.x] = (uint32_t)cand[e];
       }
       cp_async_wait<0>();
       __syncthreads();  // rows and metadata visible
@@ -166,7 +160,7 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
         }
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(hmask, acc, o);
-        if (hl == 0) keys[s_e[t]] = pack_key(acc, s_cid[t]);
+        if (hl == 0) keys[s_e[t]] = pack_key(acc, s_id[mm]);
       }
     }
   }
@@ -216,8 +210,7 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     return rc;
   {
     StageTimer t(ST_RR_SORT, st);
-    pair_lists_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-        cand, n, nlist, idx->assign, idx->pos_of_id, idx->list_off, plist, pmem);
+    pair_lists_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, n, nlist, plist, pmem);
     ADN_LAUNCH("pair_lists_kernel");
     if ((rc = build_csr(plist, n, nlist + 1, goff, byl, st))) return rc;
     const size_t hs = ((size_t)idx->max_list + 2) * 4;
@@ -236,8 +229,8 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     ADN_CUDA(cudaMemsetAsync(keys, 0xFF, sizeof(uint64_t) * n, st));
     const int chunks = std::max(1, std::min(65535, (idx->max_list + mc - 1) / mc));
     rerank_chunks_kernel<<<dim3((unsigned)nlist, (unsigned)chunks), RC_THREADS, rs, st>>>(
-        order, mstart, pmem, cand, kr, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off, mscale,
-        mc, keys, idx->dev_err);
+        order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off,
+        mscale, mc, keys, idx->dev_err);
     ADN_LAUNCH("rerank_chunks_kernel");
   }
   {
