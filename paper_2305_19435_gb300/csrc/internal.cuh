@@ -195,16 +195,17 @@ struct MmaScanArgs {
   int nprobe;
   int nkb;                   // K-blocks of the d_s prefix
   int d_blocks;              // storage blocks per vector
-  uint16_t *cand;            // FP16 bits of the approximate distances
+  uint16_t *cand;            // 16-bit fixed-point approximate distance keys
   int *err;
+  int *tile_counter;         // zeroed before the launch: next tile to take
   int fp8;
 };
-// Records an event pair around its scope on `st` when profiling is enabled.
 // work counters recorded while profiling is on (adanns_profile_read_counters)
 enum ProfileCounter { PC_RERANK_PAIRS = 0, PC_SHORTLIST_SLOTS = 1, PC_NCOUNTER = 8 };
 void profile_count(int counter, const int64_t *dev_value, cudaStream_t st);
 void profile_count_host(int counter, int64_t value);
 
+// Records an event pair around its scope on `st` when profiling is enabled.
 class StageTimer {
  public:
   StageTimer(int stage, cudaStream_t st);

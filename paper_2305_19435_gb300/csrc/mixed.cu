@@ -716,6 +716,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
       m.d_blocks = idx->lowp_blocks[which];
       m.cand = cand;
       m.err = err;
+      m.tile_counter = counter + 1;  // zeroed with the cluster-mapping counter
       m.fp8 = fp8;
       const int64_t xrows = idx->N * (int64_t)idx->lowp_blocks[which];
       if ((rc = launch_mma_scan(qtile, max_tiles * nkb * 128, idx->lowp[which], xrows, m, st)))

@@ -38,6 +38,7 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 8;                  // two per TMEM lane quadrant, half the columns each
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int THREADS = 64 + EPI_THREADS;
+constexpr int TQD = 4;  // tile queue depth
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -182,6 +183,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   unsigned char *sA = smem;                              // NSTAGE x 16 KB
   unsigned char *sB = smem + NSTAGE * A_BYTES;           // NSTAGE x 32 KB
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], sfull[2];
+  // tile queue: the producer takes tiles from a global counter (dynamic load
+  // balance) and hands their ids to the MMA issuer and the epilogue in order
+  __shared__ uint64_t qfull[TQD], qempty[TQD];
+  __shared__ int qids[TQD];
   __shared__ float s_cb[2][BN], s_ca[2][BN];  // per member of the tile: -2 s_x nu_x, |x|^2
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
@@ -196,6 +201,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&tfull[s], 1);
       mbar_init(&tempty[s], EPI_THREADS);
       mbar_init(&sfull[s], EPI_THREADS);
+    }
+    for (int s = 0; s < TQD; ++s) {
+      mbar_init(&qfull[s], 1);
+      mbar_init(&qempty[s], 1 + EPI_THREADS);
     }
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -222,7 +231,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
       int stage = 0;
       uint32_t phase = 0;
-      for (int t = blockIdx.x; t < ntiles && !ld_abort(&abort_s); t += gridDim.x) {
+      int qs = 0;
+      uint32_t qph = 0;
+      for (;;) {
+        int t = atomicAdd(a.tile_counter, 1);
+        if (t >= ntiles || ld_abort(&abort_s)) t = -1;
+        if (!mbar_wait(&qempty[qs], qph ^ 1)) {
+          atomicExch(&abort_s, 1);
+          atomicExch(a.err, 6);
+          break;
+        }
+        qids[qs] = t;
+        mbar_arrive(&qfull[qs]);
+        if (++qs == TQD) { qs = 0; qph ^= 1; }
+        if (t < 0) break;
         const int list = a.tile_list[t];
         const int64_t off = a.list_off[list];
         const int nl = (int)(a.list_off[list + 1] - off);
@@ -249,7 +271,18 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0;
       int acc = 0;
       uint32_t aphase = 0;
-      for (int t = blockIdx.x; t < ntiles && !ld_abort(&abort_s); t += gridDim.x) {
+      int qs = 0;
+      uint32_t qph = 0;
+      while (!ld_abort(&abort_s)) {
+        if (!mbar_wait(&qfull[qs], qph)) {
+          atomicExch(&abort_s, 1);
+          atomicExch(a.err, 7);
+          break;
+        }
+        const int t = qids[qs];
+        mbar_arrive(&qempty[qs]);
+        if (++qs == TQD) { qs = 0; qph ^= 1; }
+        if (t < 0) break;
         const int list = a.tile_list[t];
         const int nl = (int)(a.list_off[list + 1] - a.list_off[list]);
         const int nmt = (nl + BN - 1) / BN;
@@ -292,7 +325,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int row = quarter * 32 + lane;
     int acc = 0;
     uint32_t aphase = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int qs = 0;
+    uint32_t qph = 0;
+    for (;;) {
+      if (!mbar_wait(&qfull[qs], qph)) {
+        atomicExch(&abort_s, 1);
+        atomicExch(a.err, 8);
+        break;
+      }
+      const int t = qids[qs];
+      mbar_arrive(&qempty[qs]);
+      if (++qs == TQD) { qs = 0; qph ^= 1; }
+      if (t < 0) break;
       const int list = a.tile_list[t];
       const int64_t off = a.list_off[list];
       const int nl = (int)(a.list_off[list + 1] - off);
