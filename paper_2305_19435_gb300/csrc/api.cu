@@ -485,7 +485,9 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
     ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
     {
       StageTimer t(ST_COARSE, st);
-      if ((rc = launch_scan_f32(c, st))) return rc;
+      rc = launch_coarse(idx->centroids, idx->d_c, nlist, d_c, qc, dcp, nb, nprobe, ckeys, st);
+      if (rc == 1) rc = launch_scan_f32(c, st);
+      if (rc) return rc;
     }
     {
       StageTimer t(ST_INVERT, st);

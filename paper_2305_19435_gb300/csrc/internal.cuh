@@ -205,6 +205,13 @@ enum ProfileCounter { PC_RERANK_PAIRS = 0, PC_SHORTLIST_SLOTS = 1, PC_NCOUNTER =
 void profile_count(int counter, const int64_t *dev_value, cudaStream_t st);
 void profile_count_host(int counter, int64_t value);
 
+// Cluster mapping for d_c <= 64 and n_p <= 64: out[q][0:k] = the k smallest
+// (distance, list) keys of the query rows qc [B][ldq] against the row-major
+// centroids (first d_c of ldc columns).  Returns 1, launching nothing, for
+// other shapes (the caller then uses the general scan kernel).
+int launch_coarse(const float *cent, int ldc, int nlist, int d_c, const float *qc, int ldq,
+                  int64_t B, int k, uint64_t *out, cudaStream_t st);
+
 // Records an event pair around its scope on `st` when profiling is enabled.
 class StageTimer {
  public:

@@ -291,9 +291,9 @@ __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, 
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_WARPS = SEL_THREADS / 32;
 constexpr int SEL_SAMPLE = 2048;
-constexpr int SEL_BUF = 4096;
+constexpr int SEL_BUF = 2048;
 
-constexpr int SEL_TIE = 1024;
+constexpr int SEL_TIE = 512;
 
 struct SelState {
   int hist[256], hist2[256];
@@ -447,7 +447,7 @@ __device__ void radix_select(int n, int kk, int kq, int prune_delta, KeyF key, I
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(SEL_THREADS) select_kernel(
+__global__ void __launch_bounds__(SEL_THREADS, 6) select_kernel(
     const uint16_t *__restrict__ cand, const uint64_t *__restrict__ ckeys, int nprobe,
     const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off,
     const int32_t *__restrict__ list_ids, int kk, int k, const float *__restrict__ qrho,
@@ -679,7 +679,9 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
     {
       StageTimer t(ST_COARSE, st);
-      if ((rc = launch_scan_f32(c, st))) return rc;
+      rc = launch_coarse(idx->centroids, idx->d_c, nlist, d_c, qc, dcp, nb, nprobe, ckeys, st);
+      if (rc == 1) rc = launch_scan_f32(c, st);
+      if (rc) return rc;
     }
     {
       StageTimer t(ST_INVERT, st);

@@ -133,7 +133,9 @@ extern "C" int adanns_search_ivf_noalloc(const adanns_index *idx, const float *q
   a.counter = counter;
   a.k = nprobe;
   a.out_keys = ckeys;
-  if ((rc = launch_scan_f32(a, st))) return rc;
+  rc = launch_coarse(idx->centroids, idx->d_c, nlist, d_c, qc, dcp, B, nprobe, ckeys, st);
+  if (rc == 1) rc = launch_scan_f32(a, st);
+  if (rc) return rc;
   if ((rc = launch_invert_probes(ckeys, B, nprobe, nlist, qt, lcnt, lbeg, lfill, tbeg, pair_q,
                                  pair_out, tl, tb, tc, ntiles, nullptr, st)))
     return rc;
