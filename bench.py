@@ -282,6 +282,41 @@ def serving_phase(P, torch, data, db_dev, args, B):
             **out}
 
 
+def scan_hbm_phase(P, torch, idx, q, oidx, args, hbm_peak, modes):
+    """The list scans where they are memory-bound: a serving-sized batch
+    (2,048 queries) with one probe, so almost every probed list is read for a
+    single query.  Achieved bandwidth = unique bytes of the probed lists at d_s
+    (stored values + per-member ids or scales) / the scan kernel's time."""
+    Bq, nprobe, k = 2048, 1, 10
+    qq = q[:Bq]
+    _, _, probes = P.search_ivf(idx, qq, args.d_c, args.d_s, nprobe, k, return_probes=True)
+    probed = np.unique(probes.cpu().numpy())
+    sizes = np.diff(oidx["list_off"])[probed].astype(np.int64)
+    out = {"workload": f"{Bq} queries, nprobe={nprobe}, k={k}, {len(probed)} distinct lists "
+                       f"({int(sizes.sum()):,} members)"}
+    for d_s in (512, 2048):
+        for mode in modes:
+            code, mult = MODES[mode]
+            rr = mult * k
+            epb = {"f32": 16, "bf16": 64, "fp8": 128}[mode]
+            e = {"f32": 4, "bf16": 2, "fp8": 1}[mode]
+            dpad = (d_s + epb - 1) // epb * epb if mode != "f32" else d_s
+            per_member = dpad * e + (8 if mode == "f32" else 4)
+            step = lambda: P.search_ivf(idx, qq, args.d_c, d_s, nprobe, k, storage=code,
+                                        rerank_k=rr)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            ms, _, prof = timed(P, torch, step, 10, torch.cuda.current_stream())
+            stage = "scan" if mode == "f32" else "mma"
+            t = prof.get(stage, (0.0, 1))[0] / 10
+            gbs = int(sizes.sum()) * per_member / (t / 1e3) / 1e9 if t else None
+            out[f"{mode}_ds{d_s}"] = {"kernel": "scan_f32_kernel" if mode == "f32" else "mma_scan_kernel",
+                                      "kernel_ms": t, "step_ms": ms, "achieved_gbs": gbs,
+                                      "frac_of_hbm": gbs / hbm_peak if gbs else None}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -469,6 +504,7 @@ def main():
                 "gathered_query_gb": rr_pairs * args.d_s * 4 / 1e9,
                 "note": "algorithmic bytes = (N + B) x d_s x 4: each database and query row "
                         "once; the query rows are gathered once per pair from L2"}
+    scan_hbm = scan_hbm_phase(P, torch, idx, q, oidx, args, hbm_peak, list(results))
     main_roof = dict(rooflines[args.mode])
     # the dominant kernel of the step (largest stage) carries the headline roofline
     main_stages = main_r["stages_ms"]
@@ -493,6 +529,7 @@ def main():
                      for m, r in results.items()},
            "graph_replay": {"ms_per_step": graph_ms, "qps": world * B / (graph_ms / 1000.0)},
            "serving": serving,
+           "scan_hbm_regime": scan_hbm,
            "p50_ms": (serving or {}).get(args.mode, {}).get("p50_ms"),
            "p99_ms": (serving or {}).get(args.mode, {}).get("p99_ms"),
            "gpu_build_s": gpu_build_s, "index_layout_s": layout_s, "pairs_per_step": pairs,

@@ -219,6 +219,26 @@ int make_index(const float *db, int64_t N, int d, const float *centroids, int nl
 
 using namespace adn;
 
+// Work shape of the FP32 list scan for a batch: queries per thread (tq), the
+// query tile (qt) and member ranges per tile (nsplit).
+static void fp32_scan_shape(const adanns_index *idx, int64_t B, int d_s, int nprobe, int k, int *tq,
+                            int *qt, int *nsplit) {
+  const double qpl = (double)B * nprobe / idx->nlist;  // queries per probed list
+  int t = tuned_scan_tq(k, d_s, qpl);
+  if (t == 0 && qpl < 16) t = 1;  // untuned: few queries share a list, small tile
+  *tq = t;
+  *qt = scan_query_tile(k, t);
+  // few work items (a small batch over few lists): split each list into
+  // member ranges so every SM has work; each range leaves its own top-k run
+  *nsplit = 1;
+  const int64_t tiles_est = qpl < *qt ? std::min<int64_t>(idx->nlist, B * nprobe)
+                                      : (int64_t)(B * nprobe + *qt - 1) / *qt;
+  const int64_t target = (int64_t)num_sms() * 8;
+  if (tiles_est > 0 && tiles_est < target)
+    *nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((target + tiles_est - 1) / tiles_est,
+                                                          (idx->max_list + 255) / 256));
+}
+
 extern "C" {
 
 const char *adanns_last_error(void) { return adn::last_error(); }
@@ -361,7 +381,10 @@ int64_t adanns_search_scratch_bytes(const adanns_index *idx, int64_t B, int d_c,
     const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
     return Bc * per_q + (int64_t)idx->nlist * 64 + (64ll << 20);
   }
-  const int64_t per_q = (int64_t)nprobe * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
+  int tq, qt, nsplit;
+  fp32_scan_shape(idx, B, d_s, nprobe, k, &tq, &qt, &nsplit);
+  const int64_t per_q =
+      (int64_t)nprobe * nsplit * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
   const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (2ll << 30) / per_q));
   return Bc * per_q + (int64_t)idx->nlist * 64 + (16ll << 20);
 }
@@ -440,10 +463,11 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
   cudaStream_t st = S(cuda_stream);
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
-  const int tq = tuned_scan_tq(k, d_s, (double)B * nprobe / nlist);
-  const int qt = scan_query_tile(k, tq);
+  int tq, qt, nsplit;
+  fp32_scan_shape(idx, B, d_s, nprobe, k, &tq, &qt, &nsplit);
   // slice the batch so that the per-(query, probe) partial results stay ~2 GiB
-  const int64_t per_q = (int64_t)nprobe * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
+  const int64_t per_q =
+      (int64_t)nprobe * nsplit * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
   const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (2ll << 30) / per_q));
   const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
   Scratch s(st);
@@ -452,7 +476,7 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
   int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
   int *ntiles, *counter;
   if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
-      (rc = s.get(&ckeys, (size_t)Bc * nprobe)) || (rc = s.get(&pkeys, (size_t)Bc * nprobe * k)) ||
+      (rc = s.get(&ckeys, (size_t)Bc * nprobe)) || (rc = s.get(&pkeys, (size_t)Bc * nprobe * nsplit * k)) ||
       (rc = s.get(&lcnt, nlist)) || (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) ||
       (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
       (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
@@ -516,13 +540,15 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
     l.k = k;
     l.out_keys = pkeys;
     l.tq = tq;
+    l.nsplit = nsplit;
     {
       StageTimer t(ST_SCAN, st);
       if ((rc = launch_scan_f32(l, st))) return rc;
     }
     {
       StageTimer t(ST_MERGE, st);
-      if ((rc = launch_merge(pkeys, nb, nprobe, k, out_ids + b0 * k, out_dist + b0 * k, st)))
+      if ((rc = launch_merge(pkeys, nb, nprobe * nsplit, k, out_ids + b0 * k, out_dist + b0 * k,
+                             st)))
         return rc;
     }
   }

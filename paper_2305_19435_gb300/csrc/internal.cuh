@@ -135,6 +135,9 @@ struct ScanArgs {
   uint64_t *out_keys;      // [row][k] sorted keys (KEY_MAX padding)
   int grid;                // CTAs to launch
   int tq;                  // queries per thread (QT = 16 tq); 0 = by k
+  int nsplit;              // explicit tiles: member ranges per tile (0 or 1: whole list);
+                           // item t = (tile t / nsplit, range t % nsplit), output row
+                           // pair_out * nsplit + range
 };
 int launch_scan_f32(const ScanArgs &a, cudaStream_t st);
 int scan_query_tile(int k, int tq = 0);  // queries per work item

@@ -19,6 +19,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "devutil.cuh"
 #include "internal.cuh"
@@ -29,7 +30,10 @@ namespace {
 constexpr int THREADS = 256;
 constexpr int XT = 128;      // members per chunk
 constexpr int XROW = 20;     // padded floats per 16-float smem row (conflict-free float4 reads)
-constexpr int NSTAGE = 2;    // cp.async pipeline depth over prefix blocks
+// cp.async pipeline depth over prefix blocks: 2 for the 64-query tile (the
+// batched regime, compute-bound), 4 for the 16-query tile (few queries per
+// list: memory-bound, so more blocks in flight)
+constexpr int nstage_for(int tq) { return tq == 1 ? 4 : 2; }
 constexpr int ROUND = 32;    // candidates appended per query between compactions
 constexpr int NWARP = THREADS / 32;
 
@@ -47,6 +51,7 @@ struct ScanCfg {
 
 // shared memory: [X stages | merge scratch] [Q stages] ids scales qrow orow cnt nsorted tau buf
 size_t smem_bytes(int qt, int cap) {
+  const int NSTAGE = nstage_for(qt / 16);
   size_t xs = (size_t)NSTAGE * XT * XROW * 4;
   size_t scratch = (size_t)NWARP * cap * 8;
   size_t s = xs > scratch ? xs : scratch;
@@ -117,6 +122,7 @@ int scan_query_tile(int k, int tq) { return 16 * choose(k, tq).tq; }
 template <int TQ, bool TOP1>
 __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) {
   constexpr int QT = 16 * TQ;
+  constexpr int NSTAGE = nstage_for(TQ);
   extern __shared__ __align__(16) unsigned char smem[];
   float *Xs = (float *)smem;
   const size_t xbytes = (size_t)NSTAGE * XT * XROW * 4 > (size_t)NWARP * cap * 8
@@ -136,14 +142,16 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
 
   const int tid = threadIdx.x, tx = tid & 15, tq = tid >> 4;
   const int warp = tid >> 5, lane = tid & 31;
-  const int ntiles = a.tile_list ? *a.ntiles_dev : (a.nq + QT - 1) / QT;
+  const int nsplit = (a.tile_list && a.nsplit > 1) ? a.nsplit : 1;
+  const int ntiles = a.tile_list ? *a.ntiles_dev * nsplit : (a.nq + QT - 1) / QT;
   const int nblk = (a.dims + 15) >> 4;
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(a.counter, 1);
     __syncthreads();
-    const int tile = s_tile;
-    if (tile >= ntiles) break;
+    const int item = s_tile;
+    if (item >= ntiles) break;
+    const int tile = item / nsplit, range = item - tile * nsplit;
     int list, beg, cnt;
     if (a.tile_list) {
       list = a.tile_list[tile];
@@ -167,8 +175,12 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
       s_tau[tid] = KEY_MAX;
     }
     __syncthreads();
-    const int nchunk = (nl + XT - 1) / XT;
-    for (int c = 0; c < nchunk; ++c) {
+    // this item's member chunks: range `range` of nsplit equal chunk ranges
+    const int nchunk_all = (nl + XT - 1) / XT;
+    const int cper = (nchunk_all + nsplit - 1) / nsplit;
+    const int c_begin = min(nchunk_all, range * cper);
+    const int nchunk = min(nchunk_all, c_begin + cper);
+    for (int c = c_begin; c < nchunk; ++c) {
       const int m0 = c * XT;
       const int nm = min(XT, nl - m0);
       if (tid < XT) {
@@ -221,7 +233,9 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
         const float *xs = Xs + (b % NSTAGE) * XT * XROW;
         const float *qs = Qs + (b % NSTAGE) * QT * XROW;
         const int nd4 = min(4, (a.dims - 16 * b) >> 2);
-        auto step = [&](int s) {
+        // FULL: every query slot of the tile is used (the batched regime);
+        // otherwise slots past the tile's count are skipped
+        auto step = [&](int s, auto full) {
           float4 qv[TQ], xv[8];
 #pragma unroll
           for (int j = 0; j < TQ; ++j)
@@ -229,7 +243,8 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
 #pragma unroll
           for (int i = 0; i < 8; ++i) xv[i] = *(const float4 *)(xs + (tx + 16 * i) * XROW + 4 * s);
 #pragma unroll
-          for (int j = 0; j < TQ; ++j)
+          for (int j = 0; j < TQ; ++j) {
+            if (!decltype(full)::value && tq + 16 * j >= cnt) continue;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               float t;
@@ -242,12 +257,18 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
               t = fmaf(-sc[i], xv[i].w, qv[j].w);
               acc[j][i] = fmaf(t, t, acc[j][i]);
             }
+          }
         };
-        if (nd4 == 4) {
+        if (cnt >= QT && nd4 == 4) {
 #pragma unroll
-          for (int s = 0; s < 4; ++s) step(s);
+          for (int s = 0; s < 4; ++s) step(s, std::true_type{});
+        } else if (cnt >= QT) {
+          for (int s = 0; s < nd4; ++s) step(s, std::true_type{});
+        } else if (nd4 == 4) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) step(s, std::false_type{});
         } else {
-          for (int s = 0; s < nd4; ++s) step(s);
+          for (int s = 0; s < nd4; ++s) step(s, std::false_type{});
         }
         __syncthreads();
       }
@@ -314,7 +335,7 @@ __global__ void __launch_bounds__(THREADS) scan_f32_kernel(ScanArgs a, int cap) 
     }
     // write the sorted per-(query, list) results
     for (int qi = warp; qi < cnt; qi += NWARP) {
-      uint64_t *out = a.out_keys + (int64_t)s_orow[qi] * a.k;
+      uint64_t *out = a.out_keys + ((int64_t)s_orow[qi] * nsplit + range) * a.k;
       if (TOP1) {
         if (lane == 0) out[0] = s_tau[qi];
       } else {
