@@ -64,6 +64,14 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=20000.0,
                    help="mean offered load of the serving runs, queries/s")
     p.add_argument("--quiet", action="store_true")
+    p.add_argument("--accuracy-sweep", action="store_true",
+                   help="recall and distance error of every tier vs the FP64 oracle per "
+                        "(d_c, d_s, nprobe) on a query sample, instead of the timed run")
+    p.add_argument("--sweep-queries", type=int, default=500)
+    p.add_argument("--ivfopq", action="store_true",
+                   help="IVF-OPQ on the NQ-shaped workload (build, QPS per (d_s, M, nprobe), "
+                        "recall@10 against exact search on a query sample) instead of the timed run")
+    p.add_argument("--gt-queries", type=int, default=100)
     return p.parse_args()
 
 
@@ -317,10 +325,152 @@ def scan_hbm_phase(P, torch, idx, q, oidx, args, hbm_peak, modes):
     return out
 
 
+def accuracy_sweep(args):
+    """Recall@10 / recall@100 and relative distance error of the FP32, BF16 and
+    FP8 paths against the FP64 oracle, for every (d_c, d_s, nprobe) of the
+    ImageNet-shaped grid, on the first `sweep_queries` queries."""
+    import torch
+    import oracle
+    import paper_2305_19435_gb300 as P
+    P.build()
+    w = synthdata.WORKLOADS[args.workload]
+    N = args.n or w.N
+    data = synthdata.make(args.workload, n=N, b=max(args.sweep_queries, 8))
+    qs = data["queries"][:args.sweep_queries]
+    db_dev = torch.from_numpy(data["db"]).cuda()
+    q_dev = torch.from_numpy(qs).cuda()
+    k = args.k
+    rows = []
+    for d_c in (16, 32, 64):
+        a2 = argparse.Namespace(**{**vars(args), "d_c": d_c})
+        oidx = oracle_index(data, a2, N)
+        idx = P.index_create(db_dev, torch.from_numpy(oidx["centroids"]).cuda(),
+                             torch.from_numpy(oidx["assign"].astype(np.int32)).cuda(),
+                             storage=1 | P.STORE_BF16 | P.STORE_FP8)
+        for d_s in (64, 128, 256, 512, 1024, 2048):
+            for nprobe in (1, 4, 16, 32):
+                ref = oracle.search_ivf(data["db"], oidx, qs, d_c, d_s, nprobe, k)
+                row = {"d_c": d_c, "d_s": d_s, "nprobe": nprobe}
+                for mode, (code, mult) in MODES.items():
+                    gi, gd = P.search_ivf(idx, q_dev, d_c, d_s, nprobe, k, storage=code,
+                                          rerank_k=mult * k)
+                    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+                    r10 = float(np.mean([len(set(a[:10]) & set(b[:10])) / 10.0
+                                         for a, b in zip(gi, ref["ids"])]))
+                    r100 = float(np.mean([len(set(a) & set(b)) / float(k)
+                                          for a, b in zip(gi, ref["ids"])]))
+                    errs = []
+                    for a, da, b, db_ in zip(gi, gd, ref["ids"], ref["dist"]):
+                        m = dict(zip(b.tolist(), db_.tolist()))
+                        for i, d in zip(a.tolist(), da.tolist()):
+                            if i in m and m[i] > 0:
+                                errs.append(abs(d - m[i]) / m[i])
+                    errs = np.array(errs) if errs else np.zeros(1)
+                    row[mode] = {"recall10": r10, "recall100": r100,
+                                 "max_rel_err": float(errs.max()), "mean_rel_err": float(errs.mean())}
+                rows.append(row)
+                log(json.dumps(row))
+        idx.free()
+    print(json.dumps({"accuracy_sweep": rows, "queries": len(qs), "k": k,
+                      "rerank_k": {m: MODES[m][1] * k for m in MODES},
+                      "workload": f"{args.workload}-shaped, N={N:,}"}))
+
+
+def exact_topk_prefixnorm(db, q, d_s, k, chunk=1 << 20):
+    """Exact k nearest by squared L2 on normalised d_s prefixes (numpy, FP32
+    matrix products over database chunks): the ground truth for recall."""
+    Q = q[:, :d_s].astype(np.float32)
+    qn = np.linalg.norm(Q, axis=1, keepdims=True)
+    Q = np.where(qn > 0, Q / np.maximum(qn, 1e-30), 0).astype(np.float32)
+    q2 = (Q * Q).sum(1, keepdims=True)
+    best_d = np.full((len(Q), k), np.inf, dtype=np.float32)
+    best_i = np.full((len(Q), k), -1, dtype=np.int64)
+    for c0 in range(0, db.shape[0], chunk):
+        X = db[c0:c0 + chunk, :d_s]
+        xn = np.linalg.norm(X, axis=1)
+        X = np.where(xn[:, None] > 0, X / np.maximum(xn, 1e-30)[:, None], 0).astype(np.float32)
+        x2 = (xn > 0).astype(np.float32)[None, :]
+        d = q2 + x2 - 2.0 * (Q @ X.T)
+        ids = np.arange(c0, c0 + X.shape[0])[None, :].repeat(len(Q), 0)
+        cd = np.concatenate([best_d, d], 1)
+        ci = np.concatenate([best_i, ids], 1)
+        o = np.argpartition(cd, k - 1, axis=1)[:, :k]
+        best_d = np.take_along_axis(cd, o, 1)
+        best_i = np.take_along_axis(ci, o, 1)
+    return best_i
+
+
+def ivfopq_bench(args):
+    """AdANNS-IVF-OPQ on the NQ-shaped workload: coarse k-means at d_c = 64
+    over 4,096 lists, OPQ codes of the d_s prefix, ADC scan of the probed lists
+    (optionally an exact FP32 rerank of the top 4k)."""
+    import torch
+    import paper_2305_19435_gb300 as P
+    P.build()
+    w = synthdata.WORKLOADS["nq"]
+    N = args.n or w.N
+    B = args.b or w.B
+    t0 = time.time()
+    data = synthdata.make("nq", n=N, b=B)
+    log(f"data {time.time() - t0:.1f}s")
+    db_dev = torch.from_numpy(data["db"]).cuda()
+    q = torch.from_numpy(data["queries"]).cuda()
+    nlist = 4096 if N >= 4096 * 64 else max(64, N // 512)
+    torch.cuda.synchronize()
+    tb = time.time()
+    g = P.build_ivf(db_dev, 64, nlist, args.niter, min(N, 256 * nlist), args.seed)
+    torch.cuda.synchronize()
+    ivf_build_s = time.time() - tb
+    log(f"ivf build {ivf_build_s:.1f}s")
+    S = min(args.gt_queries, B)
+    st = torch.cuda.current_stream()
+    rows = []
+    for d_s, M in ((192, 16), (384, 32), (768, 64)):
+        tb = time.time()
+        P.build_opq(g, db_dev, d_s, M, 10, 4, 20, min(N, 65536), args.seed + 7)
+        torch.cuda.synchronize()
+        opq_build_s = time.time() - tb
+        gt = exact_topk_prefixnorm(data["db"], data["queries"][:S], d_s, 10)
+        for nprobe in (8, 32, 128):
+            for rr in (0, 4 * args.k):
+                ids = torch.empty(B, args.k, dtype=torch.int64, device="cuda")
+                dd = torch.empty(B, args.k, dtype=torch.float32, device="cuda")
+
+                def step(nprobe=nprobe, rr=rr, ids=ids, dd=dd):
+                    P.search_ivfopq(g, q, 64, nprobe, args.k, rerank_k=rr, out=(ids, dd))
+
+                for _ in range(3):
+                    step()
+                torch.cuda.synchronize()
+                ms, launches, prof = timed(P, torch, step, args.steps, st)
+                gi = ids[:S].cpu().numpy()
+                rec = float(np.mean([len(set(a[:10].tolist()) & set(b.tolist())) / 10.0
+                                     for a, b in zip(gi, gt)]))
+                row = {"d_s": d_s, "M": M, "nprobe": nprobe, "rerank_k": rr,
+                       "qps": B / (ms / 1e3), "ms_per_step": ms,
+                       "stages_ms": {k2: v[0] / args.steps for k2, v in prof.items()},
+                       "recall10_vs_exact": rec, "opq_build_s": opq_build_s,
+                       "gpu_launches": launches}
+                rows.append(row)
+                log(json.dumps(row))
+    g.free()
+    print(json.dumps({"ivfopq": rows, "workload": f"NQ-shaped IVF-OPQ: N={N:,} d=768 B={B:,} "
+                                                 f"nlist={nlist} d_c=64 k={args.k}",
+                      "ivf_build_s": ivf_build_s, "recall_sample": S,
+                      "recall_reference": "exact top-10 by L2 on normalised d_s prefixes "
+                                          "(numpy over the whole database)"}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.accuracy_sweep:
+        accuracy_sweep(args)
+        return
+    if args.ivfopq:
+        ivfopq_bench(args)
         return
     import torch
     import torch.distributed as dist
