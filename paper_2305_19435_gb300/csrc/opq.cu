@@ -160,6 +160,7 @@ struct AdcArgs {
 
 constexpr int ADC_THREADS = 256;
 constexpr int ADC_NW = ADC_THREADS / 32;
+constexpr int ADC_MAXM = 64;  // code bytes held in registers by the fast path
 
 // Work item = (list, up to QA queries that probe it).  The queries' LUTs sit in
 // shared memory; each thread takes one member per chunk of 256, reads its M
@@ -210,26 +211,51 @@ __global__ void __launch_bounds__(ADC_THREADS) adc_scan_kernel(AdcArgs a, int qa
       if (mem < nl) {
         const uint32_t id = (uint32_t)a.list_ids[off + mem];
         const uint8_t *cp = a.codes + (off + mem) * (int64_t)M;
-        for (int qa = 0; qa < cnt; ++qa) {
-          const float *L = s_lut + (size_t)qa * lut_sz;
-          float d = 0.f;
-          if ((M & 3) == 0) {
-            const uint32_t *cw = (const uint32_t *)cp;
-            for (int w = 0; w < (M >> 2); ++w) {
-              const uint32_t word = cw[w];
-              const float *Lw = L + w * 4 * 256;
-              d += Lw[word & 0xff];
-              d += Lw[256 + ((word >> 8) & 0xff)];
-              d += Lw[512 + ((word >> 16) & 0xff)];
-              d += Lw[768 + (word >> 24)];
-            }
-          } else {
-            for (int m = 0; m < M; ++m) d += L[m * 256 + cp[m]];
-          }
+        auto offer = [&](int qa, float d) {
           const uint64_t key = pack_key(d, id);
           if (key < s_tau[qa]) {
             const int pos = atomicAdd(&s_cnt[qa], 1);
             s_buf[(size_t)qa * cap + pos] = key;
+          }
+        };
+        if ((M & 3) == 0 && M <= ADC_MAXM) {
+          // the member's code words stay in registers; four queries at a time,
+          // each with four partial sums (one per byte of a word), so sixteen
+          // independent lookup chains are in flight
+          uint32_t cw[ADC_MAXM / 4];
+#pragma unroll
+          for (int w = 0; w < ADC_MAXM / 4; ++w)
+            if (w < (M >> 2)) cw[w] = ((const uint32_t *)cp)[w];
+          for (int qa0 = 0; qa0 < cnt; qa0 += 4) {
+            float sum[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) sum[j][b] = 0.f;
+#pragma unroll
+            for (int w = 0; w < ADC_MAXM / 4; ++w) {
+              if (w >= (M >> 2)) break;
+              const uint32_t word = cw[w];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                if (qa0 + j >= cnt) break;
+                const float *Lw = s_lut + (size_t)(qa0 + j) * lut_sz + w * 4 * 256;
+                sum[j][0] += Lw[word & 0xff];
+                sum[j][1] += Lw[256 + ((word >> 8) & 0xff)];
+                sum[j][2] += Lw[512 + ((word >> 16) & 0xff)];
+                sum[j][3] += Lw[768 + (word >> 24)];
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (qa0 + j < cnt) offer(qa0 + j, (sum[j][0] + sum[j][1]) + (sum[j][2] + sum[j][3]));
+          }
+        } else {
+          for (int qa = 0; qa < cnt; ++qa) {
+            const float *L = s_lut + (size_t)qa * lut_sz;
+            float d = 0.f;
+            for (int m = 0; m < M; ++m) d += L[m * 256 + cp[m]];
+            offer(qa, d);
           }
         }
       }
