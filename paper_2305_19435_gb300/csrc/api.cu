@@ -48,6 +48,9 @@ int dmalloc(T **p, size_t count) {
 void free_index(adanns_index *x) {
   if (!x) return;
   cudaFree(x->centroids);
+  cudaFree(x->cent_low);
+  cudaFree(x->cent_sc);
+  cudaFree(x->cent_n2);
   cudaFree(x->cent_pm);
   cudaFree(x->cent_off);
   cudaFree(x->list_off);
@@ -189,6 +192,7 @@ int make_index(const float *db, int64_t N, int d, const float *centroids, int nl
                       cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return bail(cuda_fail(cudaGetLastError(), "copy centroids"));
   if ((rc = centroids_pm(x->centroids, nlist, d_c, x->cent_pm, st))) return bail(rc);
+  if ((rc = build_centroid_lowp(x, st))) return bail(rc);
   if ((rc = build_csr(assign, N, nlist, x->list_off, x->list_ids, st))) return bail(rc);
   if ((rc = launch_prefix_major(db, d, d, x->d_pad, x->list_off, x->list_ids, assign, N, x->xpm,
                                 st)))
@@ -509,9 +513,7 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
     ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
     {
       StageTimer t(ST_COARSE, st);
-      rc = launch_coarse(idx->centroids, idx->d_c, nlist, d_c, qc, dcp, nb, nprobe, ckeys, st);
-      if (rc == 1) rc = launch_scan_f32(c, st);
-      if (rc) return rc;
+      if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, c, st))) return rc;
     }
     {
       StageTimer t(ST_INVERT, st);

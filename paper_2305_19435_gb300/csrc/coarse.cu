@@ -14,6 +14,12 @@
 // current n_p-th key; a few survivors are inserted one by one (a shift by one
 // lane), many are sorted in registers and merged with a bitonic half-cleaner.
 // No shared-memory buffer and no block barrier inside a chunk.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+
 #include "devutil.cuh"
 #include "internal.cuh"
 
@@ -195,6 +201,306 @@ int launch_coarse(const float *cent, int ldc, int nlist, int d_c, const float *q
   }
   ADN_LAUNCH("coarse_topk_kernel");
   return ADANNS_OK;
+}
+
+}  // namespace adn
+
+// ---------------------------------------------------------------- tensor-core cluster mapping
+// The BF16 products only shortlist: with r_c = c - s_c c~ and r_q = P(q) - s_q q~
+// the residuals of the stored low-precision values,
+//   P(q).c - (s_q q~).(s_c c~) = P(q).r_c + r_q.c - r_q.r_c,
+// so, by Cauchy-Schwarz with |P(q)| <= 1, the approximate distance is within
+//   E_q = 2 (R + rho_q |c|max + R rho_q) (1 + 1e-3) + e_rest
+// of the exact one (R = max |r_c[0:d_c]|, rho_q = |r_q|; e_rest bounds the FP32
+// tensor-core accumulation 2 d_pad 2^-22, the FP32 norm terms 8 (d_c + 2) 2^-24,
+// plus 1e-4).  Keys are round(16384 d~) (+-2^-15): every centroid whose key is
+// within 2 * 16384 * (2^-15 + E_q) of the k-th smallest key is scored exactly,
+// and nothing beyond can be among the k nearest.
+namespace adn {
+namespace {
+
+constexpr int CT_BM = 128;  // queries per tensor-core tile
+
+// one warp per centroid: BF16 blocks, scale, squared prefix norms, residuals
+__global__ void centroid_lowp_kernel(const float *__restrict__ cent, int d_c, int nlist, int nblk,
+                                     int ng, __nv_bfloat16 *__restrict__ out,
+                                     float *__restrict__ sc, float *__restrict__ n2,
+                                     float *__restrict__ rmax, float *__restrict__ maxnorm) {
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= nlist) return;
+  const float *src = cent + (int64_t)c * d_c;
+  float mx = 0.f;
+  for (int j = lane; j < d_c; j += 32) mx = fmaxf(mx, fabsf(src[j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float s = mx > 0.f ? mx : 1.f;
+  if (lane == 0) sc[c] = s;
+  float rseg[NGRAN], xseg[NGRAN];
+#pragma unroll
+  for (int g = 0; g < NGRAN; ++g) rseg[g] = xseg[g] = 0.f;
+  int g = 0;
+  for (int j = lane; j < nblk * 64; j += 32) {
+    const float v = j < d_c ? src[j] / s : 0.f;
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    out[((int64_t)(j >> 6) * nlist + c) * 64 + (j & 63)] = b;
+    if (j < d_c) {
+      while (g < NGRAN - 1 && j >= kGranDev(g)) ++g;
+      const float r = fmaf(-s, __bfloat162float(b), src[j]);
+#pragma unroll
+      for (int t = 0; t < NGRAN; ++t)
+        if (t == g) {
+          rseg[t] = fmaf(r, r, rseg[t]);
+          xseg[t] = fmaf(src[j], src[j], xseg[t]);
+        }
+    }
+  }
+  float rpre = 0.f, xpre = 0.f;
+#pragma unroll
+  for (int t = 0; t < NGRAN; ++t) {
+    float rv = rseg[t], xv = xseg[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rv += __shfl_xor_sync(0xffffffffu, rv, o);
+      xv += __shfl_xor_sync(0xffffffffu, xv, o);
+    }
+    rpre += rv;
+    xpre += xv;
+    if (lane == 0 && t < ng) {
+      n2[(int64_t)t * nlist + c] = xpre;
+      atomicMax((int *)(rmax + t), __float_as_int(sqrtf(rpre)));  // non-negative floats order as ints
+    }
+  }
+  if (lane == 0) atomicMax((int *)maxnorm, __float_as_int(sqrtf(xpre)));
+}
+
+// query rows P_dc(q) (FP32, zero beyond d_c) -> BF16 tensor-core tiles
+// [tile][kb][128 rows][64], the squared norm, the scale and the residual norm
+__global__ void coarse_prep_kernel(const float *__restrict__ qc, int ldq, int64_t B, int d_c,
+                                   int nkb, int64_t rows, __nv_bfloat16 *__restrict__ tiles,
+                                   float *__restrict__ qn2, float *__restrict__ qsc,
+                                   float *__restrict__ qrho) {
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= rows) return;
+  const int64_t t = q / CT_BM, r = q - t * CT_BM;
+  const bool valid = q < B;
+  const float *src = qc + q * ldq;
+  float s2 = 0.f, mx = 0.f;
+  if (valid)
+    for (int j = lane; j < d_c; j += 32) {
+      const float v = src[j];
+      s2 = fmaf(v, v, s2);
+      mx = fmaxf(mx, fabsf(v));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const float s = mx > 0.f ? mx : 1.f;
+  float r2 = 0.f;
+  for (int j = lane; j < nkb * 64; j += 32) {
+    const float v = (valid && j < d_c) ? src[j] / s : 0.f;
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    tiles[((t * nkb + (j >> 6)) * CT_BM + r) * 64 + (j & 63)] = b;
+    if (valid && j < d_c) {
+      const float e = fmaf(-s, __bfloat162float(b), src[j]);
+      r2 = fmaf(e, e, r2);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  if (valid && lane == 0) {
+    qn2[q] = s2;
+    qsc[q] = s;
+    qrho[q] = sqrtf(r2);
+  }
+}
+
+// the tensor-core scan's work description: every tile is (centroid list,
+// 128 consecutive queries); pair p = query p, its key segment at p * npad
+__global__ void coarse_tiles_kernel(int64_t B, int ntiles, int64_t npad, int32_t *__restrict__ tl,
+                                    int32_t *__restrict__ tb, int32_t *__restrict__ tc,
+                                    int32_t *__restrict__ pair_out, int64_t *__restrict__ pbase,
+                                    int *__restrict__ ntiles_dev, int *__restrict__ counter) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ntiles) {
+    tl[i] = 0;
+    tb[i] = (int32_t)(i * CT_BM);
+    tc[i] = (int32_t)min((int64_t)CT_BM, B - i * CT_BM);
+  }
+  if (i < B) {
+    pair_out[i] = (int32_t)i;
+    pbase[i] = i * npad;
+  }
+  if (i == 0) {
+    *ntiles_dev = ntiles;
+    *counter = 0;
+  }
+}
+
+// one warp per query: the k smallest keys give the threshold, every centroid
+// under it is scored exactly (same arithmetic as the FP32 kernels), and the k
+// nearest by (distance, list id) are written
+__global__ void __launch_bounds__(256) coarse_pick_kernel(
+    const uint16_t *__restrict__ keys, int64_t npad, int nlist, const float *__restrict__ qc,
+    int ldq, int d_c, const float *__restrict__ cent, int ldc, const float *__restrict__ qrho,
+    float rmax, float cmax, float e_rest, int64_t B, int k, uint64_t *__restrict__ out) {
+  __shared__ float s_q[8][CM_MAXD];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * 8 + warp;
+  if (q >= B) return;
+  for (int j = lane; j < d_c; j += 32) s_q[warp][j] = qc[q * ldq + j];
+  __syncwarp();
+  const uint16_t *kq = keys + q * npad;
+  uint64_t lst = KEY_MAX;
+  for (int c0 = 0; c0 < nlist; c0 += 32) {
+    const int c = c0 + lane;
+    topk_insert(lst, c < nlist ? (((uint64_t)kq[c] << 32) | (uint32_t)c) : KEY_MAX, k);
+  }
+  const uint32_t kth = (uint32_t)(__shfl_sync(0xffffffffu, lst, k - 1) >> 32);
+  const double rq = (double)qrho[q];
+  const double E = 2.0 * (rmax + rq * cmax + rmax * rq) * (1.0 + 1e-3) + e_rest;
+  const uint32_t thr = kth + (uint32_t)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1u;
+  uint64_t best = KEY_MAX;
+  for (int c0 = 0; c0 < nlist; c0 += 32) {
+    const int c = c0 + lane;
+    uint64_t key = KEY_MAX;
+    if (c < nlist && kq[c] <= thr) {
+      const float *x = cent + (int64_t)c * ldc;
+      float acc = 0.f;
+      for (int t = 0; t < d_c; ++t) {
+        const float d = fmaf(-1.f, x[t], s_q[warp][t]);
+        acc = fmaf(d, d, acc);
+      }
+      key = pack_key(acc, (uint32_t)c);
+    }
+    topk_insert(best, key, k);
+  }
+  if (lane < k) out[q * k + lane] = best;
+}
+
+}  // namespace
+
+int build_centroid_lowp(adanns_index *x, cudaStream_t st) {
+  if (x->metric != ADANNS_METRIC_L2_PREFIXNORM || x->nlist < 256) return ADANNS_OK;
+  const int nblk = (x->d_c + 63) / 64;
+  int ng = 0;
+  for (int g = 0; g < NGRAN; ++g)
+    if (kGran[g] <= x->d_c) ng = g + 1;
+  void *lowp = nullptr;
+  float *sc = nullptr, *n2 = nullptr, *tmp = nullptr;
+  if (cudaMalloc(&lowp, (size_t)nblk * x->nlist * 64 * 2) != cudaSuccess ||
+      cudaMalloc(&sc, sizeof(float) * x->nlist) != cudaSuccess ||
+      cudaMalloc(&n2, sizeof(float) * x->nlist * std::max(ng, 1)) != cudaSuccess ||
+      cudaMalloc(&tmp, sizeof(float) * (NGRAN + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(lowp);
+    cudaFree(sc);
+    cudaFree(n2);
+    cudaFree(tmp);
+    return fail(ADANNS_ERR_OOM, "centroid low-precision copy allocation failed");
+  }
+  ADN_CUDA(cudaMemsetAsync(tmp, 0, sizeof(float) * (NGRAN + 1), st));
+  centroid_lowp_kernel<<<(unsigned)((x->nlist + 7) / 8), 256, 0, st>>>(
+      x->centroids, x->d_c, x->nlist, nblk, ng, (__nv_bfloat16 *)lowp, sc, n2, tmp, tmp + NGRAN);
+  ADN_LAUNCH("centroid_lowp_kernel");
+  float h[NGRAN + 1];
+  cudaError_t e = cudaMemcpyAsync(h, tmp, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(tmp);
+  if (e != cudaSuccess) {
+    cudaFree(lowp);
+    cudaFree(sc);
+    cudaFree(n2);
+    return cuda_fail(e, "centroid low-precision copy");
+  }
+  x->cent_low = lowp;
+  x->cent_low_blocks = nblk;
+  x->cent_sc = sc;
+  x->cent_n2 = n2;
+  for (int g = 0; g < NGRAN; ++g) x->cent_rmax[g] = h[g];
+  x->cent_maxnorm = h[NGRAN];
+  return ADANNS_OK;
+}
+
+int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
+                    const MmaScanArgs &a, cudaStream_t st);
+
+int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
+                     uint64_t *out, cudaStream_t st) {
+  const char *env = getenv("ADANNS_COARSE_TC");
+  // small tables stay on the FP32 kernels (they are cheap there, and the
+  // tensor-core tile reads 256 centroid rows at a time)
+  if ((env && env[0] == '0') || !idx->cent_low || k > CM_MAXK || d_c > CM_MAXD ||
+      k > idx->nlist || idx->nlist < 256)
+    return 1;
+  if (B == 0) return ADANNS_OK;
+  const int gi = gran_index(d_c);
+  if (gi < 0) return 1;
+  const int nlist = idx->nlist, nkb = (d_c + 63) / 64;
+  const int ntiles = (int)((B + CT_BM - 1) / CT_BM);
+  const int64_t rows = (int64_t)ntiles * CT_BM;
+  const int64_t npad = (nlist + 7) & ~7;
+  Scratch s(st);
+  __nv_bfloat16 *tiles;
+  float *qn2, *qsc, *qrho;
+  uint16_t *keys;
+  int32_t *tl, *tb, *tc, *pair_out;
+  int64_t *pbase;
+  int *ntiles_dev, *counter;
+  int rc;
+  if ((rc = s.get(&tiles, (size_t)rows * nkb * 64)) || (rc = s.get(&qn2, B)) ||
+      (rc = s.get(&qsc, B)) || (rc = s.get(&qrho, B)) || (rc = s.get(&keys, (size_t)B * npad)) ||
+      (rc = s.get(&tl, ntiles)) || (rc = s.get(&tb, ntiles)) || (rc = s.get(&tc, ntiles)) ||
+      (rc = s.get(&pair_out, B)) || (rc = s.get(&pbase, B)) || (rc = s.get(&ntiles_dev, 1)) ||
+      (rc = s.get(&counter, 1)))
+    return rc;
+  const int64_t nfill = std::max<int64_t>(B, ntiles);
+  coarse_tiles_kernel<<<(unsigned)((nfill + 255) / 256), 256, 0, st>>>(
+      B, ntiles, npad, tl, tb, tc, pair_out, pbase, ntiles_dev, counter);
+  ADN_LAUNCH("coarse_tiles_kernel");
+  coarse_prep_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(qc, ldq, B, d_c, nkb, rows, tiles,
+                                                                 qn2, qsc, qrho);
+  ADN_LAUNCH("coarse_prep_kernel");
+  MmaScanArgs m{};
+  m.tile_list = tl;
+  m.tile_beg = tb;
+  m.tile_cnt = tc;
+  m.ntiles_dev = ntiles_dev;
+  m.list_off = idx->cent_off;
+  m.pair_out = pair_out;
+  m.pbase = pbase;
+  m.cx = idx->cent_sc;
+  m.x2 = idx->cent_n2 + (int64_t)gi * nlist;
+  m.qn2 = qn2;
+  m.qsc = qsc;
+  m.nprobe = 1;
+  m.nkb = nkb;
+  m.d_blocks = idx->cent_low_blocks;
+  m.cand = keys;
+  m.err = idx->dev_err;
+  m.tile_counter = counter;
+  m.fp8 = 0;
+  if ((rc = launch_mma_scan(tiles, rows * nkb, idx->cent_low,
+                            (int64_t)nlist * idx->cent_low_blocks, m, st)))
+    return rc;
+  const float e_rest = (float)(2.0 * nkb * 64 * std::ldexp(1.0, -22) +
+                               8.0 * (d_c + 2) * std::ldexp(1.0, -24) + 1e-4);
+  coarse_pick_kernel<<<(unsigned)((B + 7) / 8), 256, 0, st>>>(
+      keys, npad, nlist, qc, ldq, d_c, idx->centroids, idx->d_c, qrho,
+      idx->cent_rmax[gi] * 1.001f, idx->cent_maxnorm * 1.001f, e_rest, B, k, out);
+  ADN_LAUNCH("coarse_pick_kernel");
+  return ADANNS_OK;
+}
+
+int run_coarse(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
+               uint64_t *out, const ScanArgs &c, cudaStream_t st) {
+  int rc = launch_coarse_tc(idx, qc, ldq, B, d_c, k, out, st);
+  if (rc == 1) rc = launch_coarse(idx->centroids, idx->d_c, idx->nlist, d_c, qc, ldq, B, k, out, st);
+  if (rc == 1) rc = launch_scan_f32(c, st);
+  return rc;
 }
 
 }  // namespace adn

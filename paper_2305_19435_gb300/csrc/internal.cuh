@@ -199,6 +199,8 @@ struct MmaScanArgs {
   int nkb;                   // K-blocks of the d_s prefix
   int d_blocks;              // storage blocks per vector
   uint16_t *cand;            // 16-bit fixed-point approximate distance keys
+  const float *x2;           // per member: squared norm of the used prefix (NULL: 1, or 0 for
+                             // a zero prefix, as for normalised prefixes)
   int *err;
   int *tile_counter;         // zeroed before the launch: next tile to take
   int fp8;
@@ -214,6 +216,17 @@ void profile_count_host(int counter, int64_t value);
 // other shapes (the caller then uses the general scan kernel).
 int launch_coarse(const float *cent, int ldc, int nlist, int d_c, const float *qc, int ldq,
                   int64_t B, int k, uint64_t *out, cudaStream_t st);
+// Cluster mapping on the tensor cores with the same result: BF16 products of
+// the query and centroid prefixes shortlist every centroid that can be among
+// the k nearest (a bound on the quantisation error), which are then scored
+// exactly in FP32 as above.  Returns 1, launching nothing, when the index has
+// no BF16 centroid copy, has fewer than 256 lists, or k > 32.
+int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
+                     uint64_t *out, cudaStream_t st);
+// Both, in order of preference, then the general scan kernel with `c`.
+int run_coarse(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
+               uint64_t *out, const ScanArgs &c, cudaStream_t st);
+int build_centroid_lowp(adanns_index *x, cudaStream_t st);
 
 // Records an event pair around its scope on `st` when profiling is enabled.
 class StageTimer {
@@ -241,6 +254,17 @@ struct adanns_index {
   int d = 0, d_pad = 0, d_c = 0, dc_pad = 0, nlist = 0, metric = 0, storage = 0;
   int max_list = 0;
   float *centroids = nullptr;   // nlist x d_c row-major
+  // BF16 copy of the centroids for the tensor-core cluster mapping (metric
+  // L2_PREFIXNORM): blocks of 64 coordinates [block][centroid][64], the
+  // per-centroid scale, squared prefix norms [granularity][nlist], and per
+  // granularity the largest absolute quantisation residual |(c - s c~)[0:g]|
+  // and the largest centroid norm (host copies)
+  void *cent_low = nullptr;
+  int cent_low_blocks = 0;
+  float *cent_sc = nullptr;
+  float *cent_n2 = nullptr;
+  float cent_rmax[adn::NGRAN] = {};
+  float cent_maxnorm = 0.f;
   float *cent_pm = nullptr;     // centroids prefix-major, one list of nlist members
   int64_t *cent_off = nullptr;  // {0, nlist}
   int64_t *list_off = nullptr;  // nlist + 1

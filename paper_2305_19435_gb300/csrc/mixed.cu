@@ -679,9 +679,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
     {
       StageTimer t(ST_COARSE, st);
-      rc = launch_coarse(idx->centroids, idx->d_c, nlist, d_c, qc, dcp, nb, nprobe, ckeys, st);
-      if (rc == 1) rc = launch_scan_f32(c, st);
-      if (rc) return rc;
+      if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, c, st))) return rc;
     }
     {
       StageTimer t(ST_INVERT, st);

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int m = mt * BN + i;
             const float c = m < nl ? __ldg(a.cx + off + m) : 0.f;
             s_cb[acc][i] = -2.f * c;
-            s_ca[acc][i] = m < nl ? (c > 0.f ? 1.f : 0.f) : 3.0e38f;
+            s_ca[acc][i] = m < nl ? (a.x2 ? __ldg(a.x2 + off + m) : (c > 0.f ? 1.f : 0.f)) : 3.0e38f;
           }
           // hand-off through an mbarrier: a bounded wait, unlike bar.sync
           mbar_arrive(&sfull[acc]);

@@ -281,3 +281,31 @@ def test_gpu_built_index_search_recall(A, tiny):
     orr = oracle.search_ivf(data["db"], o, data["queries"], 16, 64, 4, 10)
     assert recall(gi.cpu().numpy(), orr["ids"], 10) >= 0.95
     g.free()
+
+
+# ---------------------------------------------------------------- tensor-core cluster mapping
+@pytest.fixture(scope="module")
+def wide(A):
+    """An index with enough lists (320) for the tensor-core cluster mapping."""
+    data = synthdata.small(60_000, 500, 128, 96, 151)
+    o = oracle.build_ivf(data["db"], 64, 320, 4, 30_000, seed=17)
+    return data, o
+
+
+@pytest.mark.parametrize("d_c,nprobe", [(64, 1), (64, 16), (32, 32), (16, 8)])
+def test_tensor_core_cluster_mapping_is_exact(A, wide, d_c, nprobe, monkeypatch):
+    """BF16 tensor-core shortlist + exact FP32 re-score of every centroid within
+    the quantisation bound: the same probes and results as the FP32 cluster
+    mapping (d_c < 64 is IVF-D on the d_c = 64 index), and oracle parity."""
+    data, o = wide
+    g = import_index(A, data["db"], o, PN)
+    q = cu(data["queries"])
+    monkeypatch.setenv("ADANNS_COARSE_TC", "0")
+    i0, d0, p0 = A.search_ivf(g, q, d_c, 128, nprobe, 20, return_probes=True)
+    monkeypatch.setenv("ADANNS_COARSE_TC", "1")
+    i1, d1, p1 = A.search_ivf(g, q, d_c, 128, nprobe, 20, return_probes=True)
+    assert torch.equal(p0, p1)
+    assert torch.equal(i0, i1) and torch.equal(d0, d1)
+    g.status()
+    g.free()
+    search_parity(A, data["db"], data["queries"], o, d_c, 128, nprobe, 20, PN)
