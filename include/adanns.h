@@ -277,7 +277,11 @@ int adanns_index_get_opq(const adanns_index *idx, float *R, float *codebooks,
  * rerank_k best by score are re-scored with the exact FP32 dist_ds of the
  * stored vectors and the k best of those are returned (Sec. 4.3
  * shortlist-rerank).  Outputs as adanns_search_ivf.  ADANNS_ERR_STATE if the
- * index has no OPQ data.
+ * index has no OPQ data.  With nprobe <= 256 the scores are written to stream
+ * scratch (4 bytes per member of the probed lists; the batch is sliced so
+ * that this stays within the scratch budget) and the best are selected
+ * afterwards; ADANNS_ADC_SELECT=0, or nprobe > 256, keeps a running top-k per
+ * (query, list) instead.  Both give the same result.
  */
 int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t B, int d_c,
                          int nprobe, int k, int rerank_k, int64_t *out_ids, float *out_dist,

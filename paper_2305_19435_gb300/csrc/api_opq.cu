@@ -36,6 +36,27 @@ namespace {
 
 cudaStream_t S(void *p) { return (cudaStream_t)p; }
 
+// The ADC stage writes every probed member's distance and selects the top k'
+// per query afterwards (adc_dist_kernel + select32_kernel) when n_p <= 256;
+// ADANNS_ADC_SELECT=0 keeps a running top-k' per (query, list) instead
+// (adc_scan_kernel + merge).
+bool adc_select_enabled(int nprobe) {
+  const char *env = getenv("ADANNS_ADC_SELECT");
+  return nprobe <= 256 && !(env && env[0] == '0');
+}
+
+// the largest candidate segment one query can have: the n_p longest lists,
+// each padded to 8 members
+int64_t max_probe_members(const adanns_index *idx, int nprobe) {
+  std::vector<int64_t> len((size_t)idx->nlist);
+  for (int l = 0; l < idx->nlist; ++l)
+    len[(size_t)l] = (idx->h_list_off[l + 1] - idx->h_list_off[l] + 7) & ~7ll;
+  std::partial_sort(len.begin(), len.begin() + nprobe, len.end(), std::greater<int64_t>());
+  int64_t t = 0;
+  for (int s = 0; s < nprobe; ++s) t += len[(size_t)s];
+  return t;
+}
+
 uint64_t splitmix64(uint64_t &s) {
   uint64_t z = (s += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -154,6 +175,111 @@ int encode_lists(adanns_index *x, const float *db, cudaStream_t st) {
       return rc;
     if ((rc = launch_pq_assign(z, n, d_s, M, d_s / M, x->opq_C, x->codes + p0 * M, nullptr, st)))
       return rc;
+  }
+  return ADANNS_OK;
+}
+
+// AdANNS-IVFOPQ search with the distance-then-select ADC stage (Sec. 4.3):
+// per chunk of queries, prep -> cluster mapping -> (list, query tile) work
+// items -> LUTs -> every probed member's ADC distance into the query's
+// candidate segment -> the k' smallest (distance, id) per query -> the k best
+// (no rerank) or the exact FP32 rerank of the k'.
+int search_ivfopq_select(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                         int nprobe, int k, int kr, bool rerank, int64_t *out_ids, float *out_dist,
+                         int32_t *out_probes, cudaStream_t st) {
+  const int d_s = idx->opq_ds, M = idx->opq_M, dsub = d_s / M;
+  const int nlist = idx->nlist;
+  const int dcp = pad16(d_c), dsp = pad16(d_s);
+  const int qa = adc_dist_query_tile(M);
+  const int64_t seg_q = max_probe_members(idx, nprobe);
+  const int64_t per_q = seg_q * 4 + (int64_t)(dcp + dsp + d_s) * 4 + (int64_t)M * 1024 +
+                        (int64_t)kr * 16 + (int64_t)nprobe * 40 + 16;
+  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
+  const int64_t max_tiles = (Bc * nprobe + qa - 1) / qa + nlist;
+  Scratch s(st);
+  float *qc, *qs, *z, *lut;
+  uint64_t *ckeys, *keys;
+  uint32_t *cand;
+  int64_t *qtot, *qbase, *pbase, *cids;
+  int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
+  int *ntiles, *counter;
+  int rc;
+  if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
+      (rc = s.get(&z, (size_t)Bc * d_s)) || (rc = s.get(&lut, (size_t)Bc * M * 256)) ||
+      (rc = s.get(&ckeys, (size_t)Bc * nprobe)) || (rc = s.get(&cand, (size_t)(Bc * seg_q))) ||
+      (rc = s.get(&keys, (size_t)Bc * kr)) || (rc = s.get(&cids, (size_t)Bc * kr)) ||
+      (rc = s.get(&qtot, (size_t)Bc)) || (rc = s.get(&qbase, (size_t)Bc)) ||
+      (rc = s.get(&pbase, (size_t)Bc * nprobe)) || (rc = s.get(&lcnt, nlist)) ||
+      (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) || (rc = s.get(&tbeg, nlist)) ||
+      (rc = s.get(&pair_q, (size_t)Bc * nprobe)) || (rc = s.get(&pair_out, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&tl, max_tiles)) || (rc = s.get(&tb, max_tiles)) ||
+      (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) || (rc = s.get(&counter, 2)))
+    return rc;
+  const float *mscale = idx->metric == ADANNS_METRIC_L2_PREFIXNORM
+                            ? idx->invn + (int64_t)gran_index(d_s) * idx->N
+                            : nullptr;
+  for (int64_t b0 = 0; b0 < B; b0 += Bc) {
+    const int64_t nb = std::min(Bc, B - b0);
+    {
+      StageTimer t(ST_PREP, st);
+      if ((rc = launch_prep_queries(queries + b0 * idx->d, nb, idx->d, d_c, d_s, idx->metric, qc,
+                                    dcp, qs, dsp, st)))
+        return rc;
+    }
+    ScanArgs c{};
+    c.xpm = idx->cent_pm;
+    c.d_pad = idx->dc_pad;  // stored centroid width; d_c <= built d_c (IVF-D)
+    c.dims = d_c;
+    c.list_off = idx->cent_off;
+    c.qn = qc;
+    c.ldq = dcp;
+    c.nq = (int)nb;
+    c.counter = counter;
+    c.k = nprobe;
+    c.out_keys = ckeys;
+    ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
+    {
+      StageTimer t(ST_COARSE, st);
+      if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, c, st))) return rc;
+    }
+    {
+      StageTimer t(ST_INVERT, st);
+      if ((rc = launch_invert_probes(ckeys, nb, nprobe, nlist, qa, lcnt, lbeg, lfill, tbeg, pair_q,
+                                     pair_out, tl, tb, tc, ntiles,
+                                     out_probes ? out_probes + b0 * nprobe : nullptr, st)))
+        return rc;
+      if ((rc = launch_cand_segments(ckeys, nb, nprobe, idx->list_off, qtot, qbase, pbase, st)))
+        return rc;
+    }
+    {
+      StageTimer t(ST_LUT, st);
+      if ((rc = launch_gemm_f32(false, (int)nb, d_s, d_s, 1.f, qs, dsp, idx->opq_R, d_s, 0.f, z,
+                                d_s, st)))
+        return rc;
+      if ((rc = launch_pq_lut(z, nb, d_s, M, dsub, idx->opq_C, lut, st))) return rc;
+    }
+    {
+      StageTimer t(ST_ADC, st);
+      if ((rc = launch_adc_dist(idx->codes, idx->list_off, M, lut, tl, tb, tc, ntiles, counter + 1,
+                                pair_q, pair_out, pbase, cand, qa, st)))
+        return rc;
+    }
+    {
+      StageTimer t(ST_MERGE, st);
+      if ((rc = launch_select32(cand, ckeys, nprobe, qbase, idx->list_off, idx->list_ids, nb, kr,
+                                keys, st)))
+        return rc;
+      if (!rerank &&
+          (rc = launch_final_topk(keys, kr, nb, k, out_ids + b0 * k, out_dist + b0 * k, st)))
+        return rc;
+    }
+    if (rerank) {
+      StageTimer t(ST_RERANK, st);
+      if ((rc = launch_keys_to_ids(keys, nb * kr, cids, st))) return rc;
+      if ((rc = launch_rerank(cids, kr, nb, qs, dsp, d_s, idx, mscale, k, out_ids + b0 * k,
+                              out_dist + b0 * k, st)))
+        return rc;
+    }
   }
   return ADANNS_OK;
 }
@@ -366,6 +492,9 @@ int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t 
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
   const int kr = rerank_k > 0 ? rerank_k : k;
+  if (adc_select_enabled(nprobe))
+    return search_ivfopq_select(idx, queries, B, d_c, nprobe, k, kr, rerank_k > 0, out_ids,
+                                out_dist, out_probes, st);
   const int qa = adc_query_tile(M, kr);
   const int64_t per_q = (int64_t)nprobe * kr * 8 + (int64_t)(dcp + dsp + d_s) * 4 +
                         (int64_t)M * 1024 + (int64_t)kr * 12 + nprobe * 24;

@@ -47,6 +47,34 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// One full warp: the smallest bucket b of a 256-bucket histogram h with
+// base + h[0] + ... + h[b] >= target, and the count below it
+// (base + h[0] + ... + h[b-1]).  Needs target <= base + sum(h).
+__device__ __forceinline__ void warp_find_bucket(const int *h, int base, int target, int *b_out,
+                                                 int *below_out) {
+  const int lane = threadIdx.x & 31;
+  int v[8], sum = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    v[j] = h[lane * 8 + j];
+    sum += v[j];
+  }
+  int inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, base + inc >= target);
+  const int L = m ? __ffs(m) - 1 : 31;
+  if (lane == L) {
+    int c = base + inc - sum, j = 0;
+    while (j < 7 && c + v[j] < target) c += v[j++];
+    *b_out = L * 8 + j;
+    *below_out = c;
+  }
+}
+
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -227,6 +227,26 @@ int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t 
 int run_coarse(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
                uint64_t *out, const ScanArgs &c, cudaStream_t st);
 int build_centroid_lowp(adanns_index *x, cudaStream_t st);
+// Candidate segments of a batch: per query, the probed lists' sizes rounded
+// up to 8, laid end to end (qtot: per-query total, qbase: its start, pbase:
+// start of each (query, probe) segment).
+int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int64_t *list_off,
+                         int64_t *qtot, int64_t *qbase, int64_t *pbase, cudaStream_t st);
+// Per query, the kk smallest 32-bit keys (order-preserving: non-negative
+// FP32 distance bits) of its candidate segments, written as
+// (key << 32 | database id), KEY_MAX padding; ties at the cut go to the
+// smallest candidate positions.  nprobe <= 256.
+int launch_keys_to_ids(const uint64_t *keys, int64_t n, int64_t *ids, cudaStream_t st);
+int launch_final_topk(const uint64_t *keys, int kr, int64_t B, int k, int64_t *out_ids,
+                      float *out_dist, cudaStream_t st);
+int adc_dist_query_tile(int M);
+int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const float *lut,
+                    const int32_t *tl, const int32_t *tb, const int32_t *tc, const int *ntiles,
+                    int *counter, const int32_t *pair_q, const int32_t *pair_out,
+                    const int64_t *pbase, uint32_t *cand, int qa, cudaStream_t st);
+int launch_select32(const uint32_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
+                    const int64_t *list_off, const int32_t *list_ids, int64_t B, int kk,
+                    uint64_t *out, cudaStream_t st);
 
 // Records an event pair around its scope on `st` when profiling is enabled.
 class StageTimer {

@@ -273,6 +273,20 @@ __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, 
   }
 }
 
+// per-query candidate segments: qtot, qbase (exclusive scan) and pbase
+int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int64_t *list_off,
+                         int64_t *qtot, int64_t *qbase, int64_t *pbase, cudaStream_t st) {
+  if (B <= 0) return ADANNS_OK;
+  const unsigned g = (unsigned)((B + 255) / 256);
+  cand_count_kernel<<<g, 256, 0, st>>>(ckeys, B, nprobe, list_off, qtot);
+  ADN_LAUNCH("cand_count_kernel");
+  scan64_kernel<<<1, 1024, 0, st>>>(qtot, B, qbase, nullptr);
+  ADN_LAUNCH("scan64_kernel");
+  cand_base_kernel<<<g, 256, 0, st>>>(ckeys, B, nprobe, list_off, qbase, pbase);
+  ADN_LAUNCH("cand_base_kernel");
+  return ADANNS_OK;
+}
+
 // ---------------------------------------------------------------- selection
 // Per query (one CTA): the kk smallest 16-bit keys (fixed-point approximate
 // distances) of its candidate region [qbase, qbase + ptotal) (segments padded
@@ -300,34 +314,6 @@ struct SelState {
   int b1, below1, b2, below2, b1k, below1k, b2k, neq, lt, eq, overflow;
   uint64_t ties[SEL_TIE];  // (candidate position << 32 | index) of the keys equal to the cut
 };
-
-// One full warp: the smallest bucket b of a 256-bucket histogram h with
-// base + h[0] + ... + h[b] >= target, and the count below it
-// (base + h[0] + ... + h[b-1]).  Needs target <= base + sum(h).
-__device__ __forceinline__ void warp_find_bucket(const int *h, int base, int target, int *b_out,
-                                                 int *below_out) {
-  const int lane = threadIdx.x & 31;
-  int v[8], sum = 0;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    v[j] = h[lane * 8 + j];
-    sum += v[j];
-  }
-  int inc = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  const unsigned m = __ballot_sync(0xffffffffu, base + inc >= target);
-  const int L = m ? __ffs(m) - 1 : 31;
-  if (lane == L) {
-    int c = base + inc - sum, j = 0;
-    while (j < 7 && c + v[j] < target) c += v[j++];
-    *b_out = L * 8 + j;
-    *below_out = c;
-  }
-}
 
 // value of the kth smallest (1-based) of n 16-bit keys: two histogram passes
 template <class KeyF>

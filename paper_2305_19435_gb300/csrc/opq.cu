@@ -582,4 +582,146 @@ int launch_identity(float *R, int d, cudaStream_t st) {
   return ADANNS_OK;
 }
 
+
+// ---------------------------------------------------------------- ADC distances
+// Distances first, selection after (adanns_search_ivfopq for nprobe <= 256):
+// a work item = (list, up to QA queries probing it) computes the exact FP32
+// ADC distance of every member for each query (the same four partial sums
+// per code word as adc_scan_kernel) and writes its bits into the pair's
+// candidate segment (the segment's padding to 8 gets 0xFFFFFFFF).  No
+// per-query state is kept, so QA is bounded by the lookup tables alone.
+struct AdcDistArgs {
+  const uint8_t *codes;     // [N][M] in list order
+  const int64_t *list_off;
+  int M;
+  const float *lut;         // [B][M][256]
+  const int32_t *tile_list, *tile_beg, *tile_cnt;
+  const int *ntiles_dev;
+  int *counter;
+  const int32_t *pair_q, *pair_out;
+  const int64_t *pbase;     // candidate segment start of each pair
+  uint32_t *cand;           // FP32 distance bits
+};
+
+constexpr int AD_THREADS = 256;
+constexpr int AD_MAXQA = 16;
+
+__global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int M = a.M;
+  const int lut_sz = M * 256;
+  float *s_lut = (float *)smem;
+  __shared__ int s_qrow[AD_MAXQA];
+  __shared__ int64_t s_pb[AD_MAXQA];
+  __shared__ int s_tile;
+  const int tid = threadIdx.x;
+  const int ntiles = *a.ntiles_dev;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    const int list = a.tile_list[tile], beg = a.tile_beg[tile], cnt = a.tile_cnt[tile];
+    if (tid < cnt) {
+      s_qrow[tid] = a.pair_q[beg + tid];
+      s_pb[tid] = a.pbase[a.pair_out[beg + tid]];
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt * (lut_sz / 4); e += AD_THREADS) {
+      const int qa = e / (lut_sz / 4), r = e - qa * (lut_sz / 4);
+      ((float4 *)s_lut)[(size_t)qa * (lut_sz / 4) + r] =
+          ((const float4 *)(a.lut + (int64_t)s_qrow[qa] * lut_sz))[r];
+    }
+    __syncthreads();
+    const int64_t off = a.list_off[list];
+    const int nl = (int)(a.list_off[list + 1] - off);
+    const int npad = (nl + 7) & ~7;
+    for (int m0 = 0; m0 < npad; m0 += AD_THREADS) {
+      const int mem = m0 + tid;
+      if (mem < nl) {
+        const uint8_t *cp = a.codes + (off + mem) * (int64_t)M;
+        if ((M & 3) == 0 && M <= ADC_MAXM) {
+          uint32_t cw[ADC_MAXM / 4];
+#pragma unroll
+          for (int w = 0; w < ADC_MAXM / 4; ++w)
+            if (w < (M >> 2)) cw[w] = ((const uint32_t *)cp)[w];
+          for (int qa0 = 0; qa0 < cnt; qa0 += 4) {
+            float sum[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) sum[j][b] = 0.f;
+#pragma unroll
+            for (int w = 0; w < ADC_MAXM / 4; ++w) {
+              if (w >= (M >> 2)) break;
+              const uint32_t word = cw[w];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                if (qa0 + j >= cnt) break;
+                const float *Lw = s_lut + (size_t)(qa0 + j) * lut_sz + w * 4 * 256;
+                sum[j][0] += Lw[word & 0xff];
+                sum[j][1] += Lw[256 + ((word >> 8) & 0xff)];
+                sum[j][2] += Lw[512 + ((word >> 16) & 0xff)];
+                sum[j][3] += Lw[768 + (word >> 24)];
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (qa0 + j < cnt)
+                a.cand[s_pb[qa0 + j] + mem] =
+                    __float_as_uint((sum[j][0] + sum[j][1]) + (sum[j][2] + sum[j][3]));
+          }
+        } else {
+          for (int qa = 0; qa < cnt; ++qa) {
+            const float *L = s_lut + (size_t)qa * lut_sz;
+            float d = 0.f;
+            for (int m = 0; m < M; ++m) d += L[m * 256 + cp[m]];
+            a.cand[s_pb[qa] + mem] = __float_as_uint(d);
+          }
+        }
+      } else if (mem < npad) {
+        for (int qa = 0; qa < cnt; ++qa) a.cand[s_pb[qa] + mem] = 0xFFFFFFFFu;
+      }
+    }
+    __syncthreads();  // the next tile's tables overwrite these
+  }
+}
+
+// queries per ADC distance work item: as many tables as fit in ~200 KB
+int adc_dist_query_tile(int M) {
+  return std::max(1, std::min(AD_MAXQA, (200 * 1024) / (M * 256 * 4)));
+}
+
+int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const float *lut,
+                    const int32_t *tl, const int32_t *tb, const int32_t *tc, const int *ntiles,
+                    int *counter, const int32_t *pair_q, const int32_t *pair_out,
+                    const int64_t *pbase, uint32_t *cand, int qa, cudaStream_t st) {
+  AdcDistArgs a{};
+  a.codes = codes;
+  a.list_off = list_off;
+  a.M = M;
+  a.lut = lut;
+  a.tile_list = tl;
+  a.tile_beg = tb;
+  a.tile_cnt = tc;
+  a.ntiles_dev = ntiles;
+  a.counter = counter;
+  a.pair_q = pair_q;
+  a.pair_out = pair_out;
+  a.pbase = pbase;
+  a.cand = cand;
+  const size_t smem = (size_t)qa * M * 256 * 4;
+  ADN_CUDA(ensure_smem((const void *)adc_dist_kernel, smem));
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adc_dist_kernel, AD_THREADS, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  adc_dist_kernel<<<num_sms() * per_sm, AD_THREADS, smem, st>>>(a);
+  ADN_LAUNCH("adc_dist_kernel");
+  return ADANNS_OK;
+}
+
 }  // namespace adn

@@ -192,6 +192,17 @@ __global__ void final_topk_kernel(const uint64_t *__restrict__ keys, int kr, int
   }
 }
 
+// per query: the k best of kr packed keys, as (ids, distances)
+int launch_final_topk(const uint64_t *keys, int kr, int64_t B, int k, int64_t *out_ids,
+                      float *out_dist, cudaStream_t st) {
+  if (B <= 0) return ADANNS_OK;
+  const size_t fs = (size_t)4 * kr * 8;
+  ADN_CUDA(ensure_smem((const void *)final_topk_kernel, fs));
+  final_topk_kernel<<<(unsigned)((B + 3) / 4), 128, fs, st>>>(keys, kr, B, k, out_ids, out_dist);
+  ADN_LAUNCH("final_topk_kernel");
+  return ADANNS_OK;
+}
+
 int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs, int ldq, int d_s,
                         const adanns_index *idx, const float *mscale, int k, int64_t *out_ids,
                         float *out_dist, cudaStream_t st) {

@@ -189,3 +189,80 @@ def test_opq_errors(A, case):
         A.search_ivfopq(g, q, 32, 4, 10, rerank_k=5)   # shortlist shorter than k
     assert e.value.code == -1
     g.free()
+
+
+def _search_both(A, g, q, d_c, nprobe, k, kr=0):
+    """The same IVF-OPQ search through the distance-then-select ADC stage and
+    through the running per-(query, list) top-k ADC stage."""
+    import os
+    a = [t.cpu().numpy() for t in A.search_ivfopq(g, q, d_c, nprobe, k, rerank_k=kr)]
+    os.environ["ADANNS_ADC_SELECT"] = "0"
+    try:
+        b = [t.cpu().numpy() for t in A.search_ivfopq(g, q, d_c, nprobe, k, rerank_k=kr)]
+    finally:
+        del os.environ["ADANNS_ADC_SELECT"]
+    return a, b
+
+
+@pytest.mark.parametrize("d_s,M,nprobe,k,kr", [(64, 16, 24, 10, 0), (64, 16, 24, 100, 0),
+                                               (96, 32, 20, 10, 400), (32, 4, 24, 50, 2000),
+                                               (48, 16, 3, 20, 0), (64, 16, 1, 10, 700)])
+def test_adc_select_equals_running_topk(A, case, d_s, M, nprobe, k, kr):
+    """Both ADC stages score members with the same FP32 arithmetic and keep
+    the best by (score, id), so ids and distances agree bit for bit: sampled
+    threshold + buffer select (24 lists of ~500), the whole-region select
+    (few lists), and k' at or above the probed members."""
+    g = gpu_index(A, case, d_s, M)
+    (ai, ad), (bi, bd) = _search_both(A, g, cu(case["data"]["queries"]), 32, nprobe, k, kr)
+    assert np.array_equal(ai, bi)
+    assert np.array_equal(ad.view(np.uint32), bd.view(np.uint32))
+    g.free()
+
+
+@pytest.fixture(scope="module")
+def dup_case():
+    """1,200 copies of one vector (identical codes, so exactly equal ADC
+    scores) in a 12k database; queries are that vector plus small noise."""
+    data = synthdata.small(12_000, 40, 96, 48, 303)
+    db = data["db"].copy()
+    rng = np.random.default_rng(5)
+    dup = np.sort(rng.choice(12_000, 1_200, replace=False))
+    db[dup] = db[dup[0]]
+    q = (db[dup[0]][None, :] + 1e-3 * rng.standard_normal((40, 96))).astype(np.float32)
+    idx = oracle.build_ivf(db, 32, 24, 6, 12_000, seed=9)
+    opq = oracle.train_opq(db, 64, 16, 3, 3, 5, 4000, seed=13)
+    codes = oracle.pq_encode(db, 64, 16, opq["R"], opq["codebooks"])
+    return {"db": db, "q": q, "dup": dup, "idx": idx, "opq": opq, "codes": codes}
+
+
+@pytest.mark.parametrize("nprobe,k,kr", [(24, 100, 0), (24, 10, 1000), (2, 300, 0),
+                                         (24, 1000, 0)])
+def test_adc_select_tie_rule(A, dup_case, nprobe, k, kr):
+    """The cut falls inside a group of >512 exactly equal scores (the second,
+    id-keyed radix select, in the shared buffer and over the whole region):
+    the group's smallest ids are kept, as the oracle's (score, id) order
+    does."""
+    c = dup_case
+    g = A.index_create(cu(c["db"]), cu(c["idx"]["centroids"]),
+                       cu(c["idx"]["assign"].astype(np.int32)))
+    A.set_opq(g, 64, 16, cu(c["opq"]["R"]), cu(c["opq"]["codebooks"]), cu(c["codes"]))
+    q = cu(c["q"])
+    kk = kr or k
+    (ai, ad), (bi, bd) = _search_both(A, g, q, 32, nprobe, k, kr)
+    assert np.array_equal(ai, bi)
+    assert np.array_equal(ad.view(np.uint32), bd.view(np.uint32))
+    orr = oracle.search_ivfopq(c["db"], c["idx"], c["opq"], c["codes"], c["q"], 32, nprobe,
+                               kk + 20)
+    dupset = set(c["dup"].tolist())
+    for i in range(len(c["q"])):
+        if kr == 0:
+            # the duplicates returned are the smallest ids of the group
+            got = sorted(x for x in ai[i].tolist() if x in dupset)
+            assert got == sorted(c["dup"].tolist())[:len(got)]
+            want = [x for x in orr["ids"][i, :k].tolist() if x in dupset]
+            assert len(got) == len(want)
+    if kr == 0:
+        amb = ambiguous_probe_rows(orr["probe_dist"], nprobe)
+        n, fails = check_topk(ai, ad, orr["ids"], orr["dist"], k, skip_rows=amb)
+        assert not fails, f"{len(fails)}/{n}: {fails[:2]}"
+    g.free()
