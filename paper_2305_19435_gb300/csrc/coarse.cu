@@ -381,6 +381,84 @@ __global__ void __launch_bounds__(256) coarse_pick_kernel(
   if (lane < k) out[q * k + lane] = best;
 }
 
+// One CTA per query, for 32 < k <= 1,024 over at most CPB_MAXLIST centroids:
+// the k-th smallest 16-bit key (two-digit radix select on the query's key
+// row staged in shared memory) gives the same threshold as above; every
+// centroid under it gets its exact FP32 distance, the rest +inf bits; a
+// four-digit radix select on those bits with ties to the lowest list id picks
+// the k nearest, which one warp sorts by (distance, list id).
+constexpr int CPB_THREADS = 256;
+constexpr int CPB_MAXK = 1024;
+constexpr int CPB_MAXLIST = 16384;
+
+__global__ void __launch_bounds__(CPB_THREADS) coarse_pick_block_kernel(
+    const uint16_t *__restrict__ keys, int64_t npad, int nlist, const float *__restrict__ qc,
+    int ldq, int d_c, const float *__restrict__ cent, int ldc, const float *__restrict__ qrho,
+    float rmax, float cmax, float e_rest, int k, uint64_t *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *cd = (uint32_t *)smem;          // [nlist] exact distance bits
+  uint16_t *k16 = (uint16_t *)(cd + nlist);  // [nlist] tensor-core keys
+  __shared__ float s_q[CM_MAXD];
+  __shared__ int hist[256], sh[2], wsum[CPB_THREADS / 32];
+  __shared__ int s_lt;
+  __shared__ uint64_t s_out[CPB_MAXK];
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int j = tid; j < d_c; j += CPB_THREADS) s_q[j] = qc[q * ldq + j];
+  const uint16_t *kq = keys + q * npad;
+  for (int c = tid; c < nlist; c += CPB_THREADS) k16[c] = kq[c];
+  if (tid == 0) s_lt = 0;
+  __syncthreads();
+  int below, neq;
+  const uint32_t kth = block_radix_kth<CPB_THREADS, 2>(
+      nlist, k, [&](int i) -> uint32_t { return k16[i]; }, hist, sh, &below, &neq);
+  const double rq = (double)qrho[q];
+  const double E = 2.0 * (rmax + rq * cmax + rmax * rq) * (1.0 + 1e-3) + e_rest;
+  const uint32_t thr = kth + (uint32_t)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1u;
+  for (int c = tid; c < nlist; c += CPB_THREADS) {
+    uint32_t v = 0xFFFFFFFFu;
+    if (k16[c] <= thr) {
+      const float *x = cent + (int64_t)c * ldc;
+      float acc = 0.f;
+      for (int t = 0; t < d_c; ++t) {
+        const float d = fmaf(-1.f, x[t], s_q[t]);
+        acc = fmaf(d, d, acc);
+      }
+      v = __float_as_uint(acc);
+    }
+    cd[c] = v;
+  }
+  __syncthreads();
+  const uint32_t T = block_radix_kth<CPB_THREADS, 4>(
+      nlist, k, [&](int i) -> uint32_t { return cd[i]; }, hist, sh, &below, &neq);
+  for (int c = tid; c < nlist; c += CPB_THREADS)
+    if (cd[c] < T) s_out[atomicAdd(&s_lt, 1)] = ((uint64_t)cd[c] << 32) | (uint32_t)c;
+  // the k - below lowest list ids among the centroids at distance T
+  const int need = k - below;
+  int base = 0;
+  for (int c0 = 0; c0 < nlist && base < need; c0 += CPB_THREADS) {
+    const int c = c0 + tid;
+    const bool eq = c < nlist && cd[c] == T;
+    const unsigned b = __ballot_sync(0xffffffffu, eq);
+    if (lane == 0) wsum[warp] = __popc(b);
+    __syncthreads();
+    int before = base, tot = 0;
+    for (int w = 0; w < CPB_THREADS / 32; ++w) {
+      if (w < warp) before += wsum[w];
+      tot += wsum[w];
+    }
+    before += __popc(b & lanemask_lt());
+    if (eq && before < need) s_out[below + before] = ((uint64_t)T << 32) | (uint32_t)c;
+    __syncthreads();
+    base += tot;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    warp_sort(s_out, k);
+    for (int r = lane; r < k; r += 32) out[q * k + r] = s_out[r];
+  }
+}
+
 }  // namespace
 
 int build_centroid_lowp(adanns_index *x, cudaStream_t st) {
@@ -433,8 +511,8 @@ int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t 
   const char *env = getenv("ADANNS_COARSE_TC");
   // small tables stay on the FP32 kernels (they are cheap there, and the
   // tensor-core tile reads 256 centroid rows at a time)
-  if ((env && env[0] == '0') || !idx->cent_low || k > CM_MAXK || d_c > CM_MAXD ||
-      k > idx->nlist || idx->nlist < 256)
+  if ((env && env[0] == '0') || !idx->cent_low || d_c > CM_MAXD || k > idx->nlist ||
+      idx->nlist < 256 || k > CPB_MAXK || (k > CM_MAXK && idx->nlist > CPB_MAXLIST))
     return 1;
   if (B == 0) return ADANNS_OK;
   const int gi = gran_index(d_c);
@@ -488,10 +566,19 @@ int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t 
     return rc;
   const float e_rest = (float)(2.0 * nkb * 64 * std::ldexp(1.0, -22) +
                                8.0 * (d_c + 2) * std::ldexp(1.0, -24) + 1e-4);
-  coarse_pick_kernel<<<(unsigned)((B + 7) / 8), 256, 0, st>>>(
-      keys, npad, nlist, qc, ldq, d_c, idx->centroids, idx->d_c, qrho,
-      idx->cent_rmax[gi] * 1.001f, idx->cent_maxnorm * 1.001f, e_rest, B, k, out);
-  ADN_LAUNCH("coarse_pick_kernel");
+  if (k <= CM_MAXK) {
+    coarse_pick_kernel<<<(unsigned)((B + 7) / 8), 256, 0, st>>>(
+        keys, npad, nlist, qc, ldq, d_c, idx->centroids, idx->d_c, qrho,
+        idx->cent_rmax[gi] * 1.001f, idx->cent_maxnorm * 1.001f, e_rest, B, k, out);
+    ADN_LAUNCH("coarse_pick_kernel");
+  } else {
+    const size_t sm = (size_t)nlist * 6;
+    ADN_CUDA(ensure_smem((const void *)coarse_pick_block_kernel, sm));
+    coarse_pick_block_kernel<<<(unsigned)B, CPB_THREADS, sm, st>>>(
+        keys, npad, nlist, qc, ldq, d_c, idx->centroids, idx->d_c, qrho,
+        idx->cent_rmax[gi] * 1.001f, idx->cent_maxnorm * 1.001f, e_rest, k, out);
+    ADN_LAUNCH("coarse_pick_block_kernel");
+  }
   return ADANNS_OK;
 }
 

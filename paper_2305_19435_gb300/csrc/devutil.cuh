@@ -75,6 +75,40 @@ __device__ __forceinline__ void warp_find_bucket(const int *h, int base, int tar
   }
 }
 
+// Block-wide radix select over n keys key(i) of NPASS * 8 bits: the kth
+// smallest (1-based, 1 <= kth <= n) by NPASS passes of 8-bit digits, most
+// significant first, over the 256-int shared histogram hist.  *below = keys
+// smaller than the result, *neq = keys equal to it.  All NT threads of the
+// block call it; sh is 2 shared ints; it ends with the block synchronised.
+template <int NT, int NPASS, class KeyF>
+__device__ uint32_t block_radix_kth(int n, int kth, KeyF key, int *hist, int *sh, int *below_out,
+                                    int *neq_out) {
+  const int tid = threadIdx.x;
+  uint32_t prefix = 0, mask = 0;
+  int below = 0, neq = 0;
+  for (int pass = 0; pass < NPASS; ++pass) {
+    const int shift = 8 * (NPASS - 1 - pass);
+    for (int i = tid; i < 256; i += NT) hist[i] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += NT) {
+      const uint32_t k = key(i);
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    if (tid < 32) warp_find_bucket(hist, below, kth, sh, sh + 1);
+    __syncthreads();
+    const int digit = sh[0];
+    prefix |= (uint32_t)digit << shift;
+    mask |= 255u << shift;
+    below = sh[1];
+    if (pass == NPASS - 1) neq = hist[digit];
+    __syncthreads();  // hist and sh are rewritten by the next pass or the caller
+  }
+  *below_out = below;
+  *neq_out = neq;
+  return prefix;
+}
+
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

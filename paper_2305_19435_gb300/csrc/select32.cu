@@ -2,8 +2,9 @@
 // candidate segments (the ADC distances of the probed lists, one FP32
 // distance per member, whose bits order like the distances).  One CTA per
 // query:
-//  1. a sample of 2,048 keys (512 evenly spaced 16-byte runs) gives a
-//     threshold T with about 1.6 kk smaller keys (radix select on the sample);
+//  1. a sample of up to 8,192 keys (2,048 evenly spaced 16-byte runs) gives a
+//     threshold T with about (kk + 4,096) / 2 smaller keys (radix select on
+//     the sample);
 //  2. one pass compacts every key < T, with its position, into a shared buffer;
 //  3. if the buffer holds between kk and S32_BUF keys, an exact radix select
 //     (four 8-bit digits) on the buffer fixes the cut, otherwise the same
@@ -17,44 +18,21 @@ namespace adn {
 namespace {
 
 constexpr int S32_THREADS = 256;
-constexpr int S32_SAMPLE = 2048;
-constexpr int S32_BUF = 2048;
+constexpr int S32_SAMPLE = 8192;  // keys sampled (2,048 runs of 4)
+constexpr int S32_BUF = 4096;     // keys compacted below the threshold (same shared space)
 constexpr int S32_TIE = 512;
 constexpr int S32_MAXP = 256;  // probed lists per query
 
 struct S32State {
   int hist[256];
-  int digit, below, neq, lt, eq;
+  int sh[2], lt, eq;
   uint64_t ties[S32_TIE];  // (id << 32 | index) of the keys equal to the cut
 };
 
-// the kth smallest (1-based) of n keys; st.below = keys below it, st.neq = keys equal
+// the kth smallest (1-based) of n keys; below = keys below it, neq = keys equal
 template <class KeyF>
-__device__ uint32_t radix_kth32(int n, int kth, KeyF key, S32State &st) {
-  const int tid = threadIdx.x;
-  uint32_t prefix = 0, mask = 0;
-  int below = 0;
-  for (int pass = 0; pass < 4; ++pass) {
-    const int shift = 24 - 8 * pass;
-    for (int i = tid; i < 256; i += S32_THREADS) st.hist[i] = 0;
-    __syncthreads();
-    for (int i = tid; i < n; i += S32_THREADS) {
-      const uint32_t k = key(i);
-      if ((k & mask) == prefix) atomicAdd(&st.hist[(k >> shift) & 255u], 1);
-    }
-    __syncthreads();
-    if (tid < 32) {
-      warp_find_bucket(st.hist, below, kth, &st.digit, &st.below);
-      __syncwarp();
-      if (tid == 0 && pass == 3) st.neq = st.hist[st.digit];
-    }
-    __syncthreads();
-    prefix |= (uint32_t)st.digit << shift;
-    mask |= 255u << shift;
-    below = st.below;
-    __syncthreads();  // st.digit / st.below are rewritten by the next pass
-  }
-  return prefix;
+__device__ uint32_t radix_kth32(int n, int kth, KeyF key, S32State &st, int &below, int &neq) {
+  return block_radix_kth<S32_THREADS, 4>(n, kth, key, st.hist, st.sh, &below, &neq);
 }
 
 // the kk smallest of n keys in (key, id) order: key(i), database id id(i)
@@ -65,8 +43,9 @@ __device__ uint32_t radix_kth32(int n, int kth, KeyF key, S32State &st) {
 template <class KeyF, class IdF, class ValF>
 __device__ void select_into(int n, int kk, KeyF key, IdF id, ValF val, uint64_t *o, S32State &st) {
   const int tid = threadIdx.x;
-  const uint32_t T = radix_kth32(n, kk, key, st);
-  const int below = st.below, need_eq = kk - below, neq = st.neq;
+  int below, neq;
+  const uint32_t T = radix_kth32(n, kk, key, st, below, neq);
+  const int need_eq = kk - below;
   if (tid == 0) st.lt = st.eq = 0;
   __syncthreads();
   for (int i = tid; i < n; i += S32_THREADS) {
@@ -85,8 +64,10 @@ __device__ void select_into(int n, int kk, KeyF key, IdF id, ValF val, uint64_t 
       for (int j = tid; j < need_eq; j += 32) o[below + j] = val((int)(uint32_t)st.ties[j]);
     }
   } else {
+    int b2, n2;
     const uint32_t idT = radix_kth32(
-        n, need_eq, [&](int i) -> uint32_t { return key(i) == T ? id(i) : 0xFFFFFFFFu; }, st);
+        n, need_eq, [&](int i) -> uint32_t { return key(i) == T ? id(i) : 0xFFFFFFFFu; }, st, b2,
+        n2);
     if (tid == 0) st.eq = 0;
     __syncthreads();
     for (int i = tid; i < n; i += S32_THREADS)
@@ -103,8 +84,9 @@ __global__ void __launch_bounds__(S32_THREADS) select32_kernel(
     const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off,
     const int32_t *__restrict__ list_ids, int kk, uint64_t *__restrict__ out) {
   __shared__ S32State st;
-  __shared__ uint32_t samp[S32_SAMPLE];
-  __shared__ uint32_t bkey[S32_BUF], bidx[S32_BUF];
+  // the sample, then (once the threshold is known) the compacted keys and positions
+  __shared__ __align__(16) uint32_t space[S32_SAMPLE];
+  uint32_t *samp = space, *bkey = space, *bidx = space + S32_BUF;
   __shared__ int s_n;
   __shared__ int64_t s_off[S32_MAXP];
   __shared__ int s_nl[S32_MAXP], s_pst[S32_MAXP + 1];
@@ -149,21 +131,26 @@ __global__ void __launch_bounds__(S32_THREADS) select32_kernel(
     for (int r = total + tid; r < kk; r += S32_THREADS) o[r] = KEY_MAX;
     return;
   }
-  if (ptotal > 4 * S32_SAMPLE) {
-    // 1. threshold from a sample of S32_SAMPLE / 4 evenly spaced 16-byte runs
+  if (ptotal > 2 * S32_BUF) {
+    // 1. threshold from a sample of up to S32_SAMPLE / 4 evenly spaced 16-byte
+    //    runs, aimed at (kk + S32_BUF) / 2 keys below it
     const uint4 *g = (const uint4 *)src;
     const int nvec = ptotal >> 2;
-    for (int j = tid; j < S32_SAMPLE / 4; j += S32_THREADS) {
-      const uint4 v = g[(int)(((int64_t)j * nvec) / (S32_SAMPLE / 4))];
+    const int nrun = min(S32_SAMPLE / 4, nvec), ns = 4 * nrun;
+    for (int j = tid; j < nrun; j += S32_THREADS) {
+      const uint4 v = g[(int)(((int64_t)j * nvec) / nrun)];
       samp[4 * j] = v.x;
       samp[4 * j + 1] = v.y;
       samp[4 * j + 2] = v.z;
       samp[4 * j + 3] = v.w;
     }
     __syncthreads();
-    int r = (int)((1.6 * kk * S32_SAMPLE) / ptotal) + 16;
-    if (r > S32_SAMPLE - 1) r = S32_SAMPLE - 1;
-    const uint32_t kv = radix_kth32(S32_SAMPLE, r + 1, [&](int i) -> uint32_t { return samp[i]; }, st);
+    int r = (int)((0.5 * (kk + S32_BUF) * ns) / ptotal);
+    r = max(0, min(r, ns - 1));
+    int b2, n2;
+    const uint32_t kv =
+        radix_kth32(ns, r + 1, [&](int i) -> uint32_t { return samp[i]; }, st, b2, n2);
+    __syncthreads();  // the sample's space is reused by the compaction
     if (kv != 0xFFFFFFFFu) {
       const uint32_t T = kv + 1;  // keys strictly below T survive
       // 2. compact the keys below T

@@ -292,11 +292,13 @@ def wide(A):
     return data, o
 
 
-@pytest.mark.parametrize("d_c,nprobe", [(64, 1), (64, 16), (32, 32), (16, 8)])
+@pytest.mark.parametrize("d_c,nprobe", [(64, 1), (64, 16), (32, 32), (16, 8), (64, 33),
+                                         (64, 100), (32, 300), (16, 64)])
 def test_tensor_core_cluster_mapping_is_exact(A, wide, d_c, nprobe, monkeypatch):
     """BF16 tensor-core shortlist + exact FP32 re-score of every centroid within
     the quantisation bound: the same probes and results as the FP32 cluster
-    mapping (d_c < 64 is IVF-D on the d_c = 64 index), and oracle parity."""
+    mapping (d_c < 64 is IVF-D on the d_c = 64 index), and oracle parity.
+    n_p <= 32 picks with one warp per query, larger n_p with one CTA."""
     data, o = wide
     g = import_index(A, data["db"], o, PN)
     q = cu(data["queries"])
