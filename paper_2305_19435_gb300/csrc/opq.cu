@@ -606,11 +606,32 @@ struct AdcDistArgs {
 constexpr int AD_THREADS = 256;
 constexpr int AD_MAXQA = 16;
 
+template <int G> struct LutVec;
+template <> struct LutVec<4> { using T = float4; };
+template <> struct LutVec<2> { using T = float2; };
+template <> struct LutVec<1> { using T = float; };
+__device__ __forceinline__ float lane_of(const float4 &v, int j) {
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ float lane_of(const float2 &v, int j) { return j == 0 ? v.x : v.y; }
+__device__ __forceinline__ float lane_of(const float &v, int) { return v; }
+
+// Work item = (list, up to qa queries).  The tile's tables are staged
+// query-interleaved in groups of G queries, [group][m][code][G], so one
+// shared-memory load of G floats serves G queries' lookups of one code byte.
+// One thread per member: its code words stay in registers; per query four
+// partial sums (byte b of each word into sum[b]), combined as
+// (s0 + s1) + (s2 + s3), the same arithmetic as the running top-k scan.
+// Every probed member's distance bits go to the query's candidate segment,
+// padding slots [n_l, pad8(n_l)) get 0xFFFFFFFF.
+template <int G>
 __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
+  using V = typename LutVec<G>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   const int M = a.M;
   const int lut_sz = M * 256;
   float *s_lut = (float *)smem;
+  const V *s_lv = (const V *)smem;
   __shared__ int s_qrow[AD_MAXQA];
   __shared__ int64_t s_pb[AD_MAXQA];
   __shared__ int s_tile;
@@ -622,15 +643,16 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
     const int tile = s_tile;
     if (tile >= ntiles) break;
     const int list = a.tile_list[tile], beg = a.tile_beg[tile], cnt = a.tile_cnt[tile];
+    const int ng = (cnt + G - 1) / G;
     if (tid < cnt) {
       s_qrow[tid] = a.pair_q[beg + tid];
       s_pb[tid] = a.pbase[a.pair_out[beg + tid]];
     }
     __syncthreads();
-    for (int e = tid; e < cnt * (lut_sz / 4); e += AD_THREADS) {
-      const int qa = e / (lut_sz / 4), r = e - qa * (lut_sz / 4);
-      ((float4 *)s_lut)[(size_t)qa * (lut_sz / 4) + r] =
-          ((const float4 *)(a.lut + (int64_t)s_qrow[qa] * lut_sz))[r];
+    for (int e = tid; e < ng * G * lut_sz; e += AD_THREADS) {
+      const int qa = e / lut_sz, r = e - qa * lut_sz;
+      s_lut[((qa / G) * lut_sz + r) * G + (qa % G)] =
+          qa < cnt ? a.lut[(int64_t)s_qrow[qa] * lut_sz + r] : 0.f;
     }
     __syncthreads();
     const int64_t off = a.list_off[list];
@@ -645,37 +667,39 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
 #pragma unroll
           for (int w = 0; w < ADC_MAXM / 4; ++w)
             if (w < (M >> 2)) cw[w] = ((const uint32_t *)cp)[w];
-          for (int qa0 = 0; qa0 < cnt; qa0 += 4) {
-            float sum[4][4];
+          for (int g = 0; g < ng; ++g) {
+            const V *Lg = s_lv + (size_t)g * lut_sz;
+            float sum[G][4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < G; ++j)
 #pragma unroll
               for (int b = 0; b < 4; ++b) sum[j][b] = 0.f;
 #pragma unroll
             for (int w = 0; w < ADC_MAXM / 4; ++w) {
               if (w >= (M >> 2)) break;
               const uint32_t word = cw[w];
+              const V *Lw = Lg + w * 4 * 256;
+              const V v0 = Lw[word & 0xff], v1 = Lw[256 + ((word >> 8) & 0xff)],
+                      v2 = Lw[512 + ((word >> 16) & 0xff)], v3 = Lw[768 + (word >> 24)];
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                if (qa0 + j >= cnt) break;
-                const float *Lw = s_lut + (size_t)(qa0 + j) * lut_sz + w * 4 * 256;
-                sum[j][0] += Lw[word & 0xff];
-                sum[j][1] += Lw[256 + ((word >> 8) & 0xff)];
-                sum[j][2] += Lw[512 + ((word >> 16) & 0xff)];
-                sum[j][3] += Lw[768 + (word >> 24)];
+              for (int j = 0; j < G; ++j) {
+                sum[j][0] += lane_of(v0, j);
+                sum[j][1] += lane_of(v1, j);
+                sum[j][2] += lane_of(v2, j);
+                sum[j][3] += lane_of(v3, j);
               }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (qa0 + j < cnt)
-                a.cand[s_pb[qa0 + j] + mem] =
+            for (int j = 0; j < G; ++j)
+              if (g * G + j < cnt)
+                a.cand[s_pb[g * G + j] + mem] =
                     __float_as_uint((sum[j][0] + sum[j][1]) + (sum[j][2] + sum[j][3]));
           }
         } else {
           for (int qa = 0; qa < cnt; ++qa) {
-            const float *L = s_lut + (size_t)qa * lut_sz;
+            const float *L = s_lut + (size_t)(qa / G) * lut_sz * G + (qa % G);
             float d = 0.f;
-            for (int m = 0; m < M; ++m) d += L[m * 256 + cp[m]];
+            for (int m = 0; m < M; ++m) d += L[(m * 256 + cp[m]) * G];
             a.cand[s_pb[qa] + mem] = __float_as_uint(d);
           }
         }
@@ -687,9 +711,17 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
   }
 }
 
-// queries per ADC distance work item: as many tables as fit in ~200 KB
+// queries interleaved per table entry: 4 when a group of 4 tables fits in
+// ~200 KB of shared memory, else 2, else 1
+int adc_dist_group(int M) {
+  const int t = M * 256 * 4;
+  return 4 * t <= 200 * 1024 ? 4 : 2 * t <= 200 * 1024 ? 2 : 1;
+}
+
+// queries per ADC distance work item: whole groups of tables within ~200 KB
 int adc_dist_query_tile(int M) {
-  return std::max(1, std::min(AD_MAXQA, (200 * 1024) / (M * 256 * 4)));
+  const int G = adc_dist_group(M), t = M * 256 * 4;
+  return std::max(1, std::min(AD_MAXQA, (200 * 1024) / (G * t) * G));
 }
 
 int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const float *lut,
@@ -710,16 +742,21 @@ int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const 
   a.pair_out = pair_out;
   a.pbase = pbase;
   a.cand = cand;
-  const size_t smem = (size_t)qa * M * 256 * 4;
-  ADN_CUDA(ensure_smem((const void *)adc_dist_kernel, smem));
+  const int G = adc_dist_group(M);
+  const size_t smem = (size_t)((qa + G - 1) / G) * G * M * 256 * 4;
+  const void *fn = G == 4 ? (const void *)adc_dist_kernel<4>
+                   : G == 2 ? (const void *)adc_dist_kernel<2>
+                            : (const void *)adc_dist_kernel<1>;
+  ADN_CUDA(ensure_smem(fn, smem));
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adc_dist_kernel, AD_THREADS, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, AD_THREADS, smem) !=
           cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
-  adc_dist_kernel<<<num_sms() * per_sm, AD_THREADS, smem, st>>>(a);
+  void *args[] = {&a};
+  ADN_CUDA(cudaLaunchKernel(fn, dim3(num_sms() * per_sm), dim3(AD_THREADS), args, smem, st));
   ADN_LAUNCH("adc_dist_kernel");
   return ADANNS_OK;
 }
