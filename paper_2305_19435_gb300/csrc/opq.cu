@@ -649,10 +649,21 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
       s_pb[tid] = a.pbase[a.pair_out[beg + tid]];
     }
     __syncthreads();
-    for (int e = tid; e < ng * G * lut_sz; e += AD_THREADS) {
-      const int qa = e / lut_sz, r = e - qa * lut_sz;
-      s_lut[((qa / G) * lut_sz + r) * G + (qa % G)] =
-          qa < cnt ? a.lut[(int64_t)s_qrow[qa] * lut_sz + r] : 0.f;
+    for (int g = 0; g < ng; ++g) {
+      const float *src[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        src[j] = g * G + j < cnt ? a.lut + (int64_t)s_qrow[g * G + j] * lut_sz : nullptr;
+      V *dst = (V *)s_lut + (size_t)g * lut_sz;
+      for (int r = tid; r < lut_sz; r += AD_THREADS) {
+        union {
+          V v;
+          float f[G];
+        } u;
+#pragma unroll
+        for (int j = 0; j < G; ++j) u.f[j] = src[j] ? src[j][r] : 0.f;
+        dst[r] = u.v;
+      }
     }
     __syncthreads();
     const int64_t off = a.list_off[list];

@@ -21,6 +21,7 @@ constexpr int S32_THREADS = 256;
 constexpr int S32_SAMPLE = 8192;  // keys sampled (2,048 runs of 4)
 constexpr int S32_BUF = 4096;     // keys compacted below the threshold (same shared space)
 constexpr int S32_TIE = 512;
+constexpr int S32_UNROLL = 4;     // 16-byte loads in flight per thread in the compaction
 constexpr int S32_MAXP = 256;  // probed lists per query
 
 struct S32State {
@@ -153,24 +154,35 @@ __global__ void __launch_bounds__(S32_THREADS) select32_kernel(
     __syncthreads();  // the sample's space is reused by the compaction
     if (kv != 0xFFFFFFFFu) {
       const uint32_t T = kv + 1;  // keys strictly below T survive
-      // 2. compact the keys below T
-      for (int c0 = 0; c0 < nvec; c0 += S32_THREADS) {
-        const int c = c0 + tid;
-        uint4 v = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-        if (c < nvec) v = g[c];
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      // 2. compact the keys below T: S32_UNROLL 16-byte loads in flight per
+      //    thread; a warp votes once per load and skips the word-by-word
+      //    ranking when none of its 128 keys survives (the common case)
+      for (int c0 = 0; c0 < nvec; c0 += S32_THREADS * S32_UNROLL) {
+        uint4 v[S32_UNROLL];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool take = w[u] < T;
-          const unsigned m = __ballot_sync(0xffffffffu, take);
-          int base = 0;
-          if (lane == 0 && m) base = atomicAdd(&s_n, __popc(m));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if (take) {
-            const int p = base + __popc(m & lanemask_lt());
-            if (p < S32_BUF) {
-              bkey[p] = w[u];
-              bidx[p] = (uint32_t)(4 * c + u);
+        for (int u = 0; u < S32_UNROLL; ++u) {
+          const int c = c0 + u * S32_THREADS + tid;
+          v[u] = c < nvec ? g[c] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        }
+#pragma unroll
+        for (int u = 0; u < S32_UNROLL; ++u) {
+          const int c = c0 + u * S32_THREADS + tid;
+          const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+          const uint32_t lo = min(min(w[0], w[1]), min(w[2], w[3]));
+          if (!__any_sync(0xffffffffu, lo < T)) continue;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const bool take = w[e] < T;
+            const unsigned m = __ballot_sync(0xffffffffu, take);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&s_n, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) {
+              const int p = base + __popc(m & lanemask_lt());
+              if (p < S32_BUF) {
+                bkey[p] = w[e];
+                bidx[p] = (uint32_t)(4 * c + e);
+              }
             }
           }
         }
