@@ -236,6 +236,9 @@ int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int
 // FP32 distance bits) of its candidate segments, written as
 // (key << 32 | database id), KEY_MAX padding; ties at the cut go to the
 // smallest candidate positions.  nprobe <= 256.
+int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
+                    const int64_t *list_off, int kk, int k, const float *qrho, float rmax,
+                    float e_rest, int prune, int64_t B, int64_t *out, cudaStream_t st);
 int launch_keys_to_ids(const uint64_t *keys, int64_t n, int64_t *ids, cudaStream_t st);
 int launch_final_topk(const uint64_t *keys, int kr, int64_t B, int k, int64_t *out_ids,
                       float *out_dist, cudaStream_t st);

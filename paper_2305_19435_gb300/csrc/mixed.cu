@@ -287,285 +287,6 @@ int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int
   return ADANNS_OK;
 }
 
-// ---------------------------------------------------------------- selection
-// Per query (one CTA): the kk smallest 16-bit keys (fixed-point approximate
-// distances) of its candidate region [qbase, qbase + ptotal) (segments padded
-// to 8 with the largest key).
-//  1. A strided sample of up to SEL_SAMPLE keys gives a threshold T whose
-//     expected number of smaller keys is about 1.6 kk (radix select on the
-//     sample).
-//  2. One pass compacts every key < T, with its index, into a shared buffer
-//     (ballot / popc ranks, one atomic per warp step).
-//  3. If the buffer holds between kk and SEL_BUF keys, an exact two-pass
-//     radix select on the buffer fixes the cut; otherwise the exact two-pass
-//     radix select runs over the whole region.
-// Ties at the cut are taken in candidate-position order (list rank, then member
-// position), independent of thread timing.  Writes (list << 32 | member
-// position) per shortlisted candidate (-1 padding).
-constexpr int SEL_THREADS = 256;
-constexpr int SEL_WARPS = SEL_THREADS / 32;
-constexpr int SEL_SAMPLE = 2048;
-constexpr int SEL_BUF = 2048;
-
-constexpr int SEL_TIE = 512;
-
-struct SelState {
-  int hist[256], hist2[256];
-  int b1, below1, b2, below2, b1k, below1k, b2k, neq, lt, eq, overflow;
-  uint64_t ties[SEL_TIE];  // (candidate position << 32 | index) of the keys equal to the cut
-};
-
-// value of the kth smallest (1-based) of n 16-bit keys: two histogram passes
-template <class KeyF>
-__device__ uint32_t radix_kth(int n, int kth, KeyF key, SelState &st) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
-  __syncthreads();
-  for (int i = tid; i < n; i += SEL_THREADS) atomicAdd(&st.hist[key(i) >> 8], 1);
-  __syncthreads();
-  if (tid < 32) warp_find_bucket(st.hist, 0, kth, &st.b1, &st.below1);
-  __syncthreads();
-  const int b1 = st.b1, below1 = st.below1;
-  for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
-  __syncthreads();
-  for (int i = tid; i < n; i += SEL_THREADS) {
-    const uint32_t k = key(i);
-    if ((int)(k >> 8) == b1) atomicAdd(&st.hist[k & 255u], 1);
-  }
-  __syncthreads();
-  if (tid < 32) warp_find_bucket(st.hist, below1, kth, &st.b2, &st.below2);
-  __syncthreads();
-  return ((uint32_t)b1 << 8) | (uint32_t)st.b2;
-}
-
-// exact kk-smallest over n keys given by key(i) (16-bit), writing id(i) for
-// the winners; st holds the shared histograms and counters.  Keys equal to
-// the cut are taken in order of their candidate position pos(i), so the
-// result does not depend on thread timing.  With kq > 0, winners whose key
-// exceeds the kq-th smallest key by more than prune_delta are written as -1
-// (certified pruning, see shortlist_prune_delta).  When i is not in position
-// order (ORDERED false) and more than SEL_TIE keys tie at the cut, nothing is
-// written and st.overflow is set: the caller reruns over the ordered region.
-template <bool ORDERED, class KeyF, class IdF, class PosF>
-__device__ void radix_select(int n, int kk, int kq, int prune_delta, KeyF key, IdF id, PosF pos,
-                             int64_t *o, SelState &st) {
-  const int tid = threadIdx.x;
-  const int kq1 = kq > 0 ? kq : kk;  // kq <= kk <= n
-  for (int i = tid; i < 256; i += SEL_THREADS) {
-    st.hist[i] = 0;
-    st.hist2[i] = 0;
-  }
-  if (tid == 0) st.lt = st.eq = st.overflow = 0;
-  __syncthreads();
-  for (int i = tid; i < n; i += SEL_THREADS) atomicAdd(&st.hist[key(i) >> 8], 1);
-  __syncthreads();
-  if (tid < 32) {
-    warp_find_bucket(st.hist, 0, kk, &st.b1, &st.below1);
-    warp_find_bucket(st.hist, 0, kq1, &st.b1k, &st.below1k);
-  }
-  __syncthreads();
-  const int b1 = st.b1, below1 = st.below1, b1k = st.b1k;
-  for (int i = tid; i < 256; i += SEL_THREADS) st.hist[i] = 0;
-  __syncthreads();
-  // second digit of the cut and, in the same pass, of the kq-th key
-  for (int i = tid; i < n; i += SEL_THREADS) {
-    const uint32_t k = key(i);
-    const int hi = (int)(k >> 8);
-    if (hi == b1) atomicAdd(&st.hist[k & 255u], 1);
-    else if (hi == b1k) atomicAdd(&st.hist2[k & 255u], 1);
-  }
-  __syncthreads();
-  if (tid < 32) {
-    warp_find_bucket(st.hist, below1, kk, &st.b2, &st.below2);
-    int dummy;
-    warp_find_bucket(b1k == b1 ? st.hist : st.hist2, st.below1k, kq1, &st.b2k, &dummy);
-    __syncwarp();
-    if (tid == 0) st.neq = st.hist[st.b2];
-  }
-  __syncthreads();
-  const uint32_t T = ((uint32_t)b1 << 8) | (uint32_t)st.b2;
-  const uint32_t keep_max =
-      kq > 0 ? (((uint32_t)b1k << 8) | (uint32_t)st.b2k) + (uint32_t)prune_delta : 0xFFFFFFFFu;
-  const int below2 = st.below2, need_eq = kk - below2;
-  if (!ORDERED && st.neq > SEL_TIE) {  // too many ties to order here
-    if (tid == 0) st.overflow = 1;
-    __syncthreads();
-    return;
-  }
-  for (int i = tid; i < n; i += SEL_THREADS) {
-    const uint32_t k = key(i);
-    if (k < T) {
-      o[atomicAdd(&st.lt, 1)] = k <= keep_max ? id(i) : -1;
-    } else if (k == T) {
-      const int p = atomicAdd(&st.eq, 1);
-      if (p < SEL_TIE) st.ties[p] = ((uint64_t)(uint32_t)pos(i) << 32) | (uint32_t)i;
-    }
-  }
-  __syncthreads();
-  // ties at the cut: the need_eq entries with the smallest positions
-  const int neq = st.eq;
-  if (neq <= SEL_TIE) {
-    if (threadIdx.x < 32) {
-      warp_sort(st.ties, neq);
-      for (int j = threadIdx.x; j < need_eq; j += 32)
-        o[below2 + j] = T <= keep_max ? id((int)(uint32_t)(st.ties[j] & 0xffffffffu)) : -1;
-    }
-  } else {
-    // many ties: an ordered pass ranks them by position (block prefix counts)
-    __shared__ int wsum[SEL_WARPS];
-    int base = 0;
-    for (int i0 = 0; i0 < n && base < need_eq; i0 += SEL_THREADS) {
-      const int i = i0 + tid;
-      const bool eq = i < n && key(i) == T;
-      const unsigned b = __ballot_sync(0xffffffffu, eq);
-      if ((tid & 31) == 0) wsum[tid >> 5] = __popc(b);
-      __syncthreads();
-      int before = base;
-      for (int w = 0; w < (tid >> 5); ++w) before += wsum[w];
-      before += __popc(b & ((1u << (tid & 31)) - 1u));
-      if (eq && before < need_eq) o[below2 + before] = T <= keep_max ? id(i) : -1;
-      int tot = 0;
-      for (int w = 0; w < SEL_WARPS; ++w) tot += wsum[w];
-      __syncthreads();
-      base += tot;
-    }
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(SEL_THREADS, 6) select_kernel(
-    const uint16_t *__restrict__ cand, const uint64_t *__restrict__ ckeys, int nprobe,
-    const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off,
-    const int32_t *__restrict__ list_ids, int kk, int k, const float *__restrict__ qrho,
-    float rmax, float e_rest, int prune, int64_t *__restrict__ out) {
-  __shared__ SelState st;
-  __shared__ uint16_t samp[SEL_SAMPLE];
-  __shared__ uint32_t bkey[SEL_BUF], bidx[SEL_BUF];
-  __shared__ int s_T, s_n;
-  __shared__ int s_lid[128];
-  __shared__ int s_nl[128], s_pst[129];
-  const int64_t q = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31;
-  int prune_delta = 1 << 20;  // key units; larger than any key difference: no pruning
-  if (prune) {
-    const double rq = (double)qrho[q];
-    const double E = 2.0 * (rmax + rq + rmax * rq) * (1.0 + 1e-3) + e_rest;
-    prune_delta = (int)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1;
-    if (prune_delta > (1 << 20)) prune_delta = 1 << 20;
-  }
-  for (int s = tid; s < nprobe; s += SEL_THREADS) {
-    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
-    s_lid[s] = l;
-    s_nl[s] = (int)(list_off[l + 1] - list_off[l]);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int t = 0;
-    for (int s = 0; s < nprobe; ++s) { s_pst[s] = t; t += (s_nl[s] + 7) & ~7; }
-    s_pst[nprobe] = t;
-    s_n = 0;
-  }
-  __syncthreads();
-  const int ptotal = s_pst[nprobe];
-  int total = 0;
-  for (int s = 0; s < nprobe; ++s) total += s_nl[s];
-  int64_t *o = out + q * kk;
-  // a candidate is written as (list << 32 | member position in the list);
-  // the rerank reads the database id from the list itself
-  auto id_at = [&](int i) -> int64_t {
-    int lo = 0, hi = nprobe - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_pst[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    const int m = i - s_pst[lo];
-    return m < s_nl[lo] ? (((int64_t)s_lid[lo] << 32) | (int64_t)m) : -1;
-  };
-  if (total <= kk) {
-    for (int s = 0; s < nprobe; ++s) {
-      int pos = 0;
-      for (int s2 = 0; s2 < s; ++s2) pos += s_nl[s2];
-      for (int m = tid; m < s_nl[s]; m += SEL_THREADS)
-        o[pos + m] = ((int64_t)s_lid[s] << 32) | (int64_t)m;
-    }
-    for (int r = total + tid; r < kk; r += SEL_THREADS) o[r] = -1;
-    return;
-  }
-  const uint16_t *src = cand + qbase[q];
-  if (ptotal > 4 * SEL_SAMPLE) {
-    // 1. threshold from a sample: SEL_SAMPLE / 8 evenly spaced runs of 8 keys
-    //    (one 16-byte load each)
-    {
-      const uint4 *g = (const uint4 *)src;
-      const int nvec = ptotal >> 3;
-      for (int j = tid; j < SEL_SAMPLE / 8; j += SEL_THREADS) {
-        const uint4 v = g[(int)(((int64_t)j * nvec) / (SEL_SAMPLE / 8))];
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int u = 0; u < 8; ++u) samp[8 * j + u] = (uint16_t)((w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu);
-      }
-    }
-    __syncthreads();
-    int r = (int)((1.6 * kk * SEL_SAMPLE) / ptotal) + 16;
-    if (r > SEL_SAMPLE - 1) r = SEL_SAMPLE - 1;
-    // threshold just above the (r+1)-th smallest sample key
-    {
-      const uint32_t kv = radix_kth(SEL_SAMPLE, r + 1, [&](int i) -> uint32_t { return samp[i]; },
-                                    st);
-      if (tid == 0) s_T = (int)kv + 1;
-      __syncthreads();
-    }
-    // 2. compact the keys below T
-    const uint32_t T = (uint32_t)s_T;
-    const uint4 *g = (const uint4 *)src;
-    const int nvec = ptotal >> 3;
-    constexpr int PF = 4;  // 16-byte loads in flight per thread
-    for (int c0 = 0; c0 < nvec; c0 += PF * SEL_THREADS) {
-      uint4 v[PF];
-#pragma unroll
-      for (int f = 0; f < PF; ++f) {
-        const int c = c0 + f * SEL_THREADS + tid;
-        v[f] = c < nvec ? g[c] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-      }
-#pragma unroll
-      for (int f = 0; f < PF; ++f) {
-        const int c = c0 + f * SEL_THREADS + tid;
-        const uint32_t w[4] = {v[f].x, v[f].y, v[f].z, v[f].w};
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const uint32_t k = (w[u >> 1] >> ((u & 1) * 16)) & 0xFFFFu;
-          const bool take = k < T;
-          const unsigned m = __ballot_sync(0xffffffffu, take);
-          int base = 0;
-          if (lane == 0 && m) base = atomicAdd(&s_n, __popc(m));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if (take) {
-            const int p = base + __popc(m & ((1u << lane) - 1u));
-            if (p < SEL_BUF) {
-              bkey[p] = k;
-              bidx[p] = (uint32_t)(c * 8 + u);
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-    const int n = s_n;
-    if (n >= kk && n <= SEL_BUF) {
-      radix_select<false>(n, kk, k, prune_delta, [&](int i) -> uint32_t { return bkey[i]; },
-                          [&](int i) -> int64_t { return id_at((int)bidx[i]); },
-                          [&](int i) -> int { return (int)bidx[i]; }, o, st);
-      const int ovf = st.overflow;
-      __syncthreads();  // every thread has read the flag before it is reset
-      if (!ovf) return;
-    }
-  }
-  // exact radix select over the whole region (index = candidate position)
-  radix_select<true>(ptotal, kk, k, prune_delta, [&](int i) -> uint32_t { return src[i]; },
-                     [&](int i) -> int64_t { return id_at(i); }, [&](int i) -> int { return i; },
-                     o, st);
-}
-
 // ---------------------------------------------------------------- tensor-core scan launcher
 int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
                     const MmaScanArgs &a, cudaStream_t st);
@@ -710,10 +431,9 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     }
     {
       StageTimer t(ST_SELECT, st);
-      select_kernel<<<(unsigned)nb, SEL_THREADS, 0, st>>>(cand, ckeys, nprobe, qbase,
-                                                          idx->list_off, idx->list_ids, kk, k,
-                                                          qrho, rmax, e_rest, prune ? 1 : 0, cids);
-      ADN_LAUNCH("select_kernel");
+      if ((rc = launch_select16(cand, ckeys, nprobe, qbase, idx->list_off, kk, k, qrho, rmax,
+                                e_rest, prune ? 1 : 0, nb, cids, st)))
+        return rc;
     }
     {
       StageTimer t(ST_RERANK, st);

@@ -1,0 +1,280 @@
+// Per-query shortlist of the mixed-precision search (Sec. 4.3 shortlist): the
+// kk smallest 16-bit keys (fixed-point approximate distances) of the query's
+// candidate region [qbase, qbase + ptotal) (probed lists in rank order, each
+// padded to 8 with the largest key).  One warp per query, four per CTA, no
+// block barriers, so many queries' memory latencies overlap on an SM:
+//  1. a sample of up to 2,048 keys (256 evenly spaced 16-byte runs) gives a
+//     threshold T aimed at (kk + SW_BUF) / 2 smaller keys (radix select on
+//     the sample);
+//  2. one pass over the region (eight 16-byte loads in flight per lane)
+//     compacts every key < T, with its position, into a per-warp buffer;
+//  3. if the buffer holds between kk and SW_BUF keys, an exact two-digit
+//     radix select on it fixes the cut; otherwise the same select runs over
+//     the whole region in position order.
+// Keys equal to the cut are taken in candidate-position order (list rank,
+// then member position), independent of thread timing.  With certified
+// pruning, winners whose key exceeds the k-th smallest key by more than the
+// query's delta are written as -1 (the bound is derived beside
+// shortlist_prune_enabled).  A winner is written as (list << 32 | member
+// position); padding slots as -1.
+#include "devutil.cuh"
+#include "internal.cuh"
+
+namespace adn {
+namespace {
+
+constexpr int SW_WARPS = 4;
+constexpr int SW_SAMPLE = 2048;
+constexpr int SW_BUF = 1024;
+constexpr int SW_TIE = 256;
+constexpr int SW_MAXP = 128;
+constexpr int SW_PF = 8;
+
+struct SwState {
+  int hist[256];
+  int digit, below, n, cnt, ecnt;
+  int lid[SW_MAXP], nl[SW_MAXP], pst[SW_MAXP + 1];
+  union {
+    uint16_t samp[SW_SAMPLE];
+    uint64_t ties[SW_TIE];  // (candidate position << 32 | index) of the keys at the cut
+  } u;
+  uint16_t bkey[SW_BUF];
+  uint32_t bidx[SW_BUF];
+};
+
+// the kth smallest (1-based, kth <= n) of n 16-bit keys, by one warp
+template <class KeyF>
+__device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, SwState &s, int &below, int &neq) {
+  const int lane = threadIdx.x & 31;
+  uint32_t prefix = 0;
+  int bl = 0;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int shift = pass == 0 ? 8 : 0;
+    for (int i = lane; i < 256; i += 32) s.hist[i] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const uint32_t k = key(i);
+      if (pass == 0 || (k >> 8) == (prefix >> 8)) atomicAdd(&s.hist[(k >> shift) & 255u], 1);
+    }
+    __syncwarp();
+    warp_find_bucket(s.hist, bl, kth, &s.digit, &s.below);
+    __syncwarp();
+    prefix |= (uint32_t)s.digit << shift;
+    bl = s.below;
+    if (pass == 1) neq = s.hist[s.digit];
+    __syncwarp();
+  }
+  below = bl;
+  return prefix;
+}
+
+// The kk smallest of n keys into o[0, kk) (any order): key(i), database
+// entry id(i), candidate position pos(i).  kq > 0: winners above the kq-th
+// smallest key + prune_delta become -1.  When the keys are not in position
+// order (ORDERED false) and more than SW_TIE tie at the cut, nothing is
+// written and false is returned.
+template <bool ORDERED, class KeyF, class IdF, class PosF>
+__device__ __forceinline__ bool warp_select16(int n, int kk, int kq, int prune_delta, KeyF key, IdF id, PosF pos,
+                              int64_t *o, SwState &s) {
+  const int lane = threadIdx.x & 31;
+  int below, neq;
+  const uint32_t T = warp_kth16(n, kk, key, s, below, neq);
+  if (!ORDERED && neq > SW_TIE) return false;
+  uint32_t keep_max = 0xFFFFFFFFu;
+  if (kq > 0) {
+    int b2, n2;
+    keep_max = warp_kth16(n, kq, key, s, b2, n2) + (uint32_t)prune_delta;
+  }
+  if (lane == 0) s.cnt = s.ecnt = 0;
+  __syncwarp();
+  const int need_eq = kk - below;
+  const bool few_ties = neq <= SW_TIE;
+  for (int i = lane; i < n; i += 32) {
+    const uint32_t k = key(i);
+    if (k < T) {
+      o[atomicAdd(&s.cnt, 1)] = k <= keep_max ? id(i) : -1;
+    } else if (k == T && few_ties) {
+      const int p = atomicAdd(&s.ecnt, 1);
+      if (p < SW_TIE) s.u.ties[p] = ((uint64_t)(uint32_t)pos(i) << 32) | (uint32_t)i;
+    }
+  }
+  __syncwarp();
+  if (few_ties) {
+    warp_sort(s.u.ties, neq);
+    for (int j = lane; j < need_eq; j += 32)
+      o[below + j] = T <= keep_max ? id((int)(uint32_t)(s.u.ties[j] & 0xffffffffu)) : -1;
+  } else {
+    // many ties, keys in position order: rank them with warp prefix counts
+    int base = 0;
+    for (int i0 = 0; i0 < n && base < need_eq; i0 += 32) {
+      const int i = i0 + lane;
+      const bool eq = i < n && key(i) == T;
+      const unsigned b = __ballot_sync(0xffffffffu, eq);
+      const int before = base + __popc(b & lanemask_lt());
+      if (eq && before < need_eq) o[below + before] = T <= keep_max ? id(i) : -1;
+      base += __popc(b);
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+__global__ void __launch_bounds__(SW_WARPS * 32) select16_kernel(
+    const uint16_t *__restrict__ cand, const uint64_t *__restrict__ ckeys, int nprobe,
+    const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off, int kk, int k,
+    const float *__restrict__ qrho, float rmax, float e_rest, int prune, int64_t B,
+    int64_t *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  SwState &s = ((SwState *)smem)[warp];
+  const int64_t q = (int64_t)blockIdx.x * SW_WARPS + warp;
+  if (q >= B) return;
+  int prune_delta = 0;
+  if (prune) {
+    const double rq = (double)qrho[q];
+    const double E = 2.0 * (rmax + rq + rmax * rq) * (1.0 + 1e-3) + e_rest;
+    prune_delta = (int)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1;
+    if (prune_delta > (1 << 20)) prune_delta = 1 << 20;
+  }
+  // probed lists: ids, sizes, padded starts (warp scan over 4 entries per lane)
+  int ln[4], pl[4], tot = 0, ptot = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int sl = lane * 4 + j;
+    ln[j] = 0;
+    if (sl < nprobe) {
+      const int l = (int)(uint32_t)(ckeys[q * nprobe + sl] & 0xffffffffu);
+      s.lid[sl] = l;
+      ln[j] = (int)(list_off[l + 1] - list_off[l]);
+      s.nl[sl] = ln[j];
+    }
+    pl[j] = (ln[j] + 7) & ~7;
+    tot += ln[j];
+    ptot += pl[j];
+  }
+  int inc = ptot;
+#pragma unroll
+  for (int o2 = 1; o2 < 32; o2 <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o2);
+    if (lane >= o2) inc += y;
+  }
+  {
+    int run = inc - ptot;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int sl = lane * 4 + j;
+      if (sl <= nprobe) s.pst[sl] = run;
+      run += pl[j];
+    }
+  }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o2);
+  const int ptotal = __shfl_sync(0xffffffffu, inc, 31);
+  const int total = tot;
+  __syncwarp();
+  int64_t *o = out + q * kk;
+  auto id_at = [&](int i) -> int64_t {
+    int lo = 0, hi = nprobe - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s.pst[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int m = i - s.pst[lo];
+    return m < s.nl[lo] ? (((int64_t)s.lid[lo] << 32) | (int64_t)m) : -1;
+  };
+  if (total <= kk) {
+    int p0 = 0;
+    for (int sl = 0; sl < nprobe; ++sl) {
+      const int nl = s.nl[sl];
+      for (int m = lane; m < nl; m += 32) o[p0 + m] = ((int64_t)s.lid[sl] << 32) | (int64_t)m;
+      p0 += nl;
+    }
+    for (int r = total + lane; r < kk; r += 32) o[r] = -1;
+    return;
+  }
+  const int kq = prune ? k : 0;
+  const uint16_t *src = cand + qbase[q];
+  if (ptotal > 2 * SW_BUF) {
+    // 1. threshold from a sample of evenly spaced runs of 8 keys
+    const uint4 *g = (const uint4 *)src;
+    const int nvec = ptotal >> 3;
+    const int nrun = min(SW_SAMPLE / 8, nvec), ns = 8 * nrun;
+    for (int j = lane; j < nrun; j += 32) {
+      const uint4 v = g[(int)(((int64_t)j * nvec) / nrun)];
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) s.u.samp[8 * j + e] = (uint16_t)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu);
+    }
+    __syncwarp();
+    int r = (int)((0.5 * (kk + SW_BUF) * ns) / ptotal);
+    r = max(0, min(r, ns - 1));
+    int b_, n_;
+    const uint32_t kv =
+        warp_kth16(ns, r + 1, [&](int i) -> uint32_t { return s.u.samp[i]; }, s, b_, n_);
+    if (kv < 0xFFFFu) {
+      const uint32_t T = kv + 1;  // keys strictly below T survive
+      if (lane == 0) s.n = 0;
+      __syncwarp();
+      // 2. compaction
+      for (int c0 = 0; c0 < nvec; c0 += 32 * SW_PF) {
+        uint4 v[SW_PF];
+#pragma unroll
+        for (int f = 0; f < SW_PF; ++f) {
+          const int c = c0 + f * 32 + lane;
+          v[f] = c < nvec ? g[c] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        }
+#pragma unroll
+        for (int f = 0; f < SW_PF; ++f) {
+          const int c = c0 + f * 32 + lane;
+          const uint32_t w[4] = {v[f].x, v[f].y, v[f].z, v[f].w};
+          unsigned m = 0;
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            m |= (((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu) < T ? 1u : 0u) << e;
+          if (m) {
+            int p = atomicAdd(&s.n, __popc(m));
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if ((m >> e) & 1u) {
+                if (p < SW_BUF) {
+                  s.bkey[p] = (uint16_t)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu);
+                  s.bidx[p] = (uint32_t)(c * 8 + e);
+                }
+                ++p;
+              }
+          }
+        }
+      }
+      __syncwarp();
+      const int n = s.n;
+      // 3. exact select on the buffer
+      if (n >= kk && n <= SW_BUF &&
+          warp_select16<false>(n, kk, kq, prune_delta,
+                               [&](int i) -> uint32_t { return s.bkey[i]; },
+                               [&](int i) -> int64_t { return id_at((int)s.bidx[i]); },
+                               [&](int i) -> int { return (int)s.bidx[i]; }, o, s))
+        return;
+    }
+  }
+  // exact select over the whole region (index = candidate position)
+  warp_select16<true>(ptotal, kk, kq, prune_delta, [&](int i) -> uint32_t { return src[i]; }, id_at,
+                      [&](int i) -> int { return i; }, o, s);
+}
+
+}  // namespace
+
+int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
+                    const int64_t *list_off, int kk, int k, const float *qrho, float rmax,
+                    float e_rest, int prune, int64_t B, int64_t *out, cudaStream_t st) {
+  if (nprobe > SW_MAXP) return fail(ADANNS_ERR_ARG, "select16: nprobe above 128");
+  if (B <= 0) return ADANNS_OK;
+  const size_t sm = sizeof(SwState) * SW_WARPS;
+  ADN_CUDA(ensure_smem((const void *)select16_kernel, sm));
+  select16_kernel<<<(unsigned)((B + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, sm, st>>>(
+      cand, ckeys, nprobe, qbase, list_off, kk, k, qrho, rmax, e_rest, prune, B, out);
+  ADN_LAUNCH("select16_kernel");
+  return ADANNS_OK;
+}
+
+}  // namespace adn
