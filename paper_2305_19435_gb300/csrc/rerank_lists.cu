@@ -68,6 +68,9 @@ inline int rerank_chunk_members(int d_s) {
   return std::max(8, std::min(RC_MAX_MC, 32768 / (d_s * 4)));
 }
 
+// FULL: d_s is a multiple of 512 (every half-warp lane holds 8 whole float4
+// of each 512-coordinate segment), so no coordinate bound is checked.
+template <bool FULL>
 __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
     const int32_t *__restrict__ order, const int32_t *__restrict__ mstart,
     const int32_t *__restrict__ pmem, const int32_t *__restrict__ list_ids, int kr,
@@ -122,21 +125,18 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
       }
       cp_async_wait<0>();
       __syncthreads();  // rows and metadata visible
-      auto load_first = [&](int t, float4 *dst) {
+      // query row of pair t, first 512 coordinates, into registers
+      auto load_first = [&](int t, float4(&dst)[8]) {
         const float *qr = qs + (int64_t)s_q[t] * ldq;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-          if (hl + 16 * u < nseg) dst[u] = ldg_f4_hint((const float4 *)(qr + 4 * (hl + 16 * u)), keep);
+          if (FULL || hl + 16 * u < nseg)
+            dst[u] = ldg_f4_hint((const float4 *)(qr + 4 * (hl + 16 * u)), keep);
       };
-      float4 qn[8];
-      if (hw < nb) load_first(hw, qn);
-      for (int t = hw; t < nb; t += RC_HW) {
-        float4 qv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) qv[u] = qn[u];
-        if (t + RC_HW < nb) load_first(t + RC_HW, qn);
+      // exact difference-form distance of pair t (first 512 coordinates in qv)
+      auto score = [&](int t, float4(&qv)[8]) {
         const int mm = s_m[t];
-        if (mm < 0) continue;  // uniform in the half-warp
+        if (mm < 0) return;  // uniform in the half-warp
         const float *xr = rows + (size_t)mm * rs;
         const float nu = s_nu[mm];
         const float *qr = qs + (int64_t)s_q[t] * ldq;
@@ -145,11 +145,12 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
           if (s0 != hl) {
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (s0 + 16 * u < nseg) qv[u] = ldg_f4_hint((const float4 *)(qr + 4 * (s0 + 16 * u)), keep);
+              if (FULL || s0 + 16 * u < nseg)
+                qv[u] = ldg_f4_hint((const float4 *)(qr + 4 * (s0 + 16 * u)), keep);
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            if (s0 + 16 * u >= nseg) break;
+            if (!FULL && s0 + 16 * u >= nseg) break;
             const float4 xv = *(const float4 *)(xr + 4 * (s0 + 16 * u));
             float d;
             d = fmaf(-nu, xv.x, qv[u].x); acc = fmaf(d, d, acc);
@@ -161,6 +162,21 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(hmask, acc, o);
         if (hl == 0) keys[s_e[t]] = pack_key(acc, s_id[mm]);
+      };
+      // the half-warp's pairs t = hw, hw + RC_HW, ...: the next pair's query
+      // row loads into the other register buffer while this one is scored
+      float4 qa[8], qb[8];
+      int t = hw;
+      if (t < nb) load_first(t, qa);
+      while (t < nb) {
+        const int t2 = t + RC_HW;
+        if (t2 < nb) load_first(t2, qb);
+        score(t, qa);
+        if (t2 >= nb) break;
+        const int t3 = t2 + RC_HW;
+        if (t3 < nb) load_first(t3, qa);
+        score(t2, qb);
+        t = t3;
       }
     }
   }
@@ -235,13 +251,22 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     StageTimer t(ST_RR_PAIRS, st);
     const int mc = rerank_chunk_members(d_s);
     const size_t rs = (size_t)mc * (d_s + 4) * 4;
-    ADN_CUDA(ensure_smem((const void *)rerank_chunks_kernel, rs));
+    const bool full = d_s % 512 == 0;
+    const void *fn = full ? (const void *)rerank_chunks_kernel<true>
+                          : (const void *)rerank_chunks_kernel<false>;
+    ADN_CUDA(ensure_smem(fn, rs));
     // slots of padding or pruned candidates keep the empty key
     ADN_CUDA(cudaMemsetAsync(keys, 0xFF, sizeof(uint64_t) * n, st));
     const int chunks = std::max(1, std::min(65535, (idx->max_list + mc - 1) / mc));
-    rerank_chunks_kernel<<<dim3((unsigned)nlist, (unsigned)chunks), RC_THREADS, rs, st>>>(
-        order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad, idx->list_off,
-        mscale, mc, keys, idx->dev_err);
+    const dim3 grid((unsigned)nlist, (unsigned)chunks);
+    if (full)
+      rerank_chunks_kernel<true><<<grid, RC_THREADS, rs, st>>>(
+          order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad,
+          idx->list_off, mscale, mc, keys, idx->dev_err);
+    else
+      rerank_chunks_kernel<false><<<grid, RC_THREADS, rs, st>>>(
+          order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad,
+          idx->list_off, mscale, mc, keys, idx->dev_err);
     ADN_LAUNCH("rerank_chunks_kernel");
   }
   {
