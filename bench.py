@@ -628,6 +628,18 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     ffma_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+    # DRAM bytes (read + write) per launch from one ncu capture of the default
+    # ImageNet-shaped bf16 step (profiles/mixed_bf16_imagenet_dram.md); reported
+    # only for that workload, and to be removed whenever the kernel changes
+    traffic_table = {("bf16", "mma"): 2.512444416e9 + 2.356903936e9,
+                     ("bf16", "rerank"): 6.539436288e9 + 0.149764864e9}
+    default_wl = (args.workload == "imagenet" and N == w.N and B == w.B and args.d_c == 32
+                  and args.d_s == 512 and args.nprobe == 16 and args.k == 100
+                  and args.nlist == 1024)
+
+    def traffic(mode, kern):
+        return traffic_table.get((mode, kern)) if default_wl else None
+
     rooflines = {}
     for mode, r in results.items():
         sm = r["stages_ms"]
@@ -646,7 +658,7 @@ def main():
             peak = bf16_peak * (2.0 if mode == "fp8" else 1.0)
             rooflines[mode] = {"kernel": "mma_scan_kernel (tensor-core list scan)", "bound": "tensor",
                                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                               "traffic": None, "kernel_ms": t,
+                               "traffic": traffic(mode, "mma"), "kernel_ms": t,
                                "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"
                                + (" x 2 (nominal fp8/bf16 ratio)" if mode == "fp8" else "")}
             # exact rerank: every database row it re-scores and every query row is
@@ -659,6 +671,7 @@ def main():
                 "kernel": "rerank_chunks_kernel (exact FP32 rerank of the pruned shortlist)",
                 "bound": "hbm", "achieved": rr_bytes / (rr_t / 1e3) / 1e9 if rr_t else None,
                 "peak": hbm_peak, "unit": "GB/s", "kernel_ms": rr_t,
+                "traffic": traffic(mode, "rerank"),
                 "pairs": rr_pairs, "shortlist_slots": r["counters"].get("shortlist_slots", 0),
                 "gathered_query_gb": rr_pairs * args.d_s * 4 / 1e9,
                 "note": "algorithmic bytes = (N + B) x d_s x 4: each database and query row "
@@ -671,7 +684,7 @@ def main():
     dom = max(kern_stages, key=kern_stages.get) if kern_stages else None
     if args.mode != "f32" and dom == "rr_pairs":
         rrd = main_roof.pop("rerank")
-        main_roof = {**rrd, "frac": (rrd["achieved"] or 0) / hbm_peak, "traffic": None,
+        main_roof = {**rrd, "frac": (rrd["achieved"] or 0) / hbm_peak,
                      "peak_source": "measured STREAM-style copy (MEASURED_PEAKS.json)",
                      "mma": {k2: v for k2, v in rooflines[args.mode].items() if k2 != "rerank"}}
 
