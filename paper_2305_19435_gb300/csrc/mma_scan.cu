@@ -12,10 +12,10 @@
 // fixed-point key round(d * 2^14) into the query's candidate segment.  A selection kernel then keeps each query's best k' candidates and
 // the exact FP32 rerank (Sec. 4.3 shortlist-rerank) produces the result.
 //
-// Warp roles (192 threads): warp 0 issues TMA tile loads into a 4-stage
+// Warp roles (576 threads): warp 0 issues TMA tile loads into a 4-stage
 // shared-memory ring; warp 1 owns tensor memory (512 columns: two 256-column
-// accumulators) and one elected thread issues the MMAs; warps 2-5 drain the
-// accumulators.  Every mbarrier wait is bounded: on timeout the kernel records
+// accumulators) and one elected thread issues the MMAs; warps 2-17 drain the
+// accumulators (four warps per TMEM lane quadrant, 64 columns each).  Every mbarrier wait is bounded: on timeout the kernel records
 // an error, stops issuing work, lets in-flight copies land and frees TMEM.
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -35,8 +35,9 @@ constexpr int NSTAGE = 4;
 constexpr int A_BYTES = BM * ROWB;    // 16 KB
 constexpr int B_BYTES = BN * ROWB;    // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_WARPS = 8;                  // two per TMEM lane quadrant, half the columns each
+constexpr int EPI_WARPS = 16;                 // four per TMEM lane quadrant
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int EPI_SPAN = BN / (EPI_WARPS / 4);  // accumulator columns per epilogue warp
 constexpr int THREADS = 64 + EPI_THREADS;
 constexpr int TQD = 4;  // tile queue depth
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait
@@ -141,25 +142,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// two 32-column loads in flight, one wait
-__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, uint32_t (&r)[32], uint32_t (&s)[32]) {
-#define ADN_LD32(R, ADDR)                                                                          \
-  asm volatile(                                                                                    \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, " \
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, " \
-      "%30, %31}, [%32];"                                                                          \
-      : "=r"(R[0]), "=r"(R[1]), "=r"(R[2]), "=r"(R[3]), "=r"(R[4]), "=r"(R[5]), "=r"(R[6]),       \
-        "=r"(R[7]), "=r"(R[8]), "=r"(R[9]), "=r"(R[10]), "=r"(R[11]), "=r"(R[12]), "=r"(R[13]),   \
-        "=r"(R[14]), "=r"(R[15]), "=r"(R[16]), "=r"(R[17]), "=r"(R[18]), "=r"(R[19]),             \
-        "=r"(R[20]), "=r"(R[21]), "=r"(R[22]), "=r"(R[23]), "=r"(R[24]), "=r"(R[25]),             \
-        "=r"(R[26]), "=r"(R[27]), "=r"(R[28]), "=r"(R[29]), "=r"(R[30]), "=r"(R[31])              \
-      : "r"(ADDR))
-  ADN_LD32(r, taddr);
-  ADN_LD32(s, taddr + 32);
-#undef ADN_LD32
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -318,10 +300,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..9, one query row per thread; the
-    // two warps of a TMEM lane quadrant (warp % 4) take half the columns each
+    // ---------------- epilogue: warps 2..17, one query row per thread; the
+    // four warps of a TMEM lane quadrant (warp % 4) take a quarter of the
+    // columns each
     const int quarter = warp & 3;
-    const int c_lo = ((warp - 2) / 4) * (BN / 2);
+    const int c_lo = ((warp - 2) / 4) * EPI_SPAN;
+    const int et = threadIdx.x - 64;
     const int row = quarter * 32 + lane;
     int acc = 0;
     uint32_t aphase = 0;
@@ -354,6 +338,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         qs = a.qsc[q];
       }
       bool stop = false;
+      // per-member terms of member tile mt (thread et < BN holds member et of
+      // the tile), loaded one tile ahead so the loads overlap the drain
+      auto load_terms = [&](int mt) -> float2 {
+        float2 v = make_float2(0.f, 0.f);
+        if (et < BN) {
+          const int m = mt * BN + et;
+          const float c = m < nl ? __ldg(a.cx + off + m) : 0.f;
+          v.x = -2.f * c;
+          v.y = m < nl ? (a.x2 ? __ldg(a.x2 + off + m) : (c > 0.f ? 1.f : 0.f)) : 3.0e38f;
+        }
+        return v;
+      };
+      float2 terms = load_terms(0);
       for (int mt = 0; mt < nmt; ++mt) {
         if (!mbar_wait(&tfull[acc], aphase)) {
           atomicExch(&abort_s, 1);
@@ -364,12 +361,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc_fence_after();
         // the tile's per-member terms, staged once for the epilogue warps
         {
-          const int et = threadIdx.x - 64;
-          for (int i = et; i < BN; i += EPI_THREADS) {
-            const int m = mt * BN + i;
-            const float c = m < nl ? __ldg(a.cx + off + m) : 0.f;
-            s_cb[acc][i] = -2.f * c;
-            s_ca[acc][i] = m < nl ? (a.x2 ? __ldg(a.x2 + off + m) : (c > 0.f ? 1.f : 0.f)) : 3.0e38f;
+          if (et < BN) {
+            s_cb[acc][et] = terms.x;
+            s_ca[acc][et] = terms.y;
           }
           // hand-off through an mbarrier: a bounded wait, unlike bar.sync
           mbar_arrive(&sfull[acc]);
@@ -380,13 +374,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
         }
+        if (mt + 1 < nmt) terms = load_terms(mt + 1);
         const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
-        for (int c0 = c_lo; c0 < c_lo + BN / 2; c0 += 64) {
-          uint32_t r[2][32];
-          tmem_ld32x2(tbase + c0, r[0], r[1]);
+        for (int c0 = c_lo; c0 < c_lo + EPI_SPAN; c0 += 32) {
+          uint32_t r[1][32];
+          tmem_ld32(tbase + c0, r[0]);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < 1; ++h) {
             const int cb = c0 + 32 * h;
             const int m0 = mt * BN + cb;
             if (valid && m0 < npad) {
