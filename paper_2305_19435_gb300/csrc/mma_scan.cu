@@ -12,7 +12,7 @@
 // fixed-point key round(d * 2^14) into the query's candidate segment.  A selection kernel then keeps each query's best k' candidates and
 // the exact FP32 rerank (Sec. 4.3 shortlist-rerank) produces the result.
 //
-// Warp roles (576 threads): warp 0 issues TMA tile loads into a 4-stage
+// Warp roles (576 threads): warp 0 issues TMA tile loads into a 3-stage
 // shared-memory ring; warp 1 owns tensor memory (512 columns: two 256-column
 // accumulators) and one elected thread issues the MMAs; warps 2-17 drain the
 // accumulators (four warps per TMEM lane quadrant, 64 columns each).  Every mbarrier wait is bounded: on timeout the kernel records
@@ -31,13 +31,15 @@ namespace {
 constexpr int BM = 128;          // queries per tile (TMEM lanes)
 constexpr int BN = 256;          // members per MMA tile (TMEM columns per accumulator)
 constexpr int ROWB = 128;        // bytes per K-block row (one 128-byte swizzle atom row)
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 3;
 constexpr int A_BYTES = BM * ROWB;    // 16 KB
 constexpr int B_BYTES = BN * ROWB;    // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 16;                 // four per TMEM lane quadrant
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int EPI_SPAN = BN / (EPI_WARPS / 4);  // accumulator columns per epilogue warp
+constexpr int STG_BYTES = 32 * EPI_SPAN * 2;    // a warp's 32 rows of 16-bit keys
+static_assert(EPI_SPAN == 64, "the key staging holds 8 16-byte chunks per row");
 constexpr int THREADS = 64 + EPI_THREADS;
 constexpr int TQD = 4;  // tile queue depth
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *sA = smem;                              // NSTAGE x 16 KB
   unsigned char *sB = smem + NSTAGE * A_BYTES;           // NSTAGE x 32 KB
+  unsigned char *sStage = smem + NSTAGE * STAGE_BYTES;   // EPI_WARPS x 4 KB key staging
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], sfull[2];
   // tile queue: the producer takes tiles from a global counter (dynamic load
   // balance) and hands their ids to the MMA issuer and the epilogue in order
@@ -376,40 +379,51 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (mt + 1 < nmt) terms = load_terms(mt + 1);
         const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+        // this warp's 32 rows x 64 columns of keys are staged row-major in
+        // shared memory (16-byte chunks XOR-swizzled by row: conflict-free
+        // both ways), then stored as whole 128-byte row segments
+        uint4 *stg = (uint4 *)(sStage + (size_t)(warp - 2) * STG_BYTES);
 #pragma unroll 1
-        for (int c0 = c_lo; c0 < c_lo + EPI_SPAN; c0 += 32) {
-          uint32_t r[1][32];
-          tmem_ld32(tbase + c0, r[0]);
+        for (int c0 = 0; c0 < EPI_SPAN; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(tbase + c_lo + c0, r);
+          uint32_t packed[16];
 #pragma unroll
-          for (int h = 0; h < 1; ++h) {
-            const int cb = c0 + 32 * h;
-            const int m0 = mt * BN + cb;
-            if (valid && m0 < npad) {
-              uint32_t packed[16];
+          for (int j = 0; j < 32; j += 2) {
+            uint32_t kk[2];
 #pragma unroll
-              for (int j = 0; j < 32; j += 2) {
-                uint32_t kk[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                  // approximate squared distance as a 16-bit fixed-point key:
-                  // round(d * 2^14), d clamped to [0, 4); members past the list
-                  // end get the largest key
-                  const int c = cb + j + u;
-                  float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[h][j + u]), q2 + s_ca[acc][c]);
-                  d = fminf(fmaxf(d, 0.f), 3.9999f);
-                  kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
-                }
-                packed[j >> 1] = kk[0] | (kk[1] << 16);
-              }
-              uint4 *dst = (uint4 *)(a.cand + base + m0);
-#pragma unroll
-              for (int g = 0; g < 4; ++g)
-                if (m0 + 8 * g < npad)
-                  dst[g] = make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2],
-                                      packed[4 * g + 3]);
+            for (int u = 0; u < 2; ++u) {
+              // approximate squared distance as a 16-bit fixed-point key:
+              // round(d * 2^14), d clamped to [0, 4); members past the list
+              // end get the largest key
+              const int c = c_lo + c0 + j + u;
+              float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[j + u]), q2 + s_ca[acc][c]);
+              d = fminf(fmaxf(d, 0.f), 3.9999f);
+              kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
             }
+            packed[j >> 1] = kk[0] | (kk[1] << 16);
+          }
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int ch = (c0 >> 3) + g;
+            stg[lane * 8 + (ch ^ (lane & 7))] =
+                make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2], packed[4 * g + 3]);
           }
         }
+        __syncwarp();
+        {
+          // 8 lanes per row: one instruction stores 4 rows x 128 bytes
+          const int m0 = mt * BN + c_lo, ch = lane & 7;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int rr = i * 4 + (lane >> 3);
+            const long long b = __shfl_sync(0xffffffffu, (long long)base, rr);
+            const int ok = __shfl_sync(0xffffffffu, valid ? 1 : 0, rr);
+            const uint4 v = stg[rr * 8 + (ch ^ (rr & 7))];
+            if (ok && m0 + 8 * ch < npad) *(uint4 *)(a.cand + b + m0 + 8 * ch) = v;
+          }
+        }
+        __syncwarp();  // the staging buffer is rewritten for the next tile
         tc_fence_before();
         mbar_arrive(&tempty[acc]);
         if (++acc == 2) { acc = 0; aphase ^= 1; }
@@ -472,7 +486,7 @@ int make_map(CUtensorMap *m, const void *base, int64_t rows, int box_rows, bool 
 }
 }  // namespace
 
-size_t mma_scan_smem() { return (size_t)NSTAGE * STAGE_BYTES + 1024; }
+size_t mma_scan_smem() { return (size_t)NSTAGE * STAGE_BYTES + (size_t)EPI_WARPS * STG_BYTES + 1024; }
 
 int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
                     const MmaScanArgs &a, cudaStream_t st) {
