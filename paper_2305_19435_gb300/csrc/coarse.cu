@@ -353,30 +353,48 @@ __global__ void __launch_bounds__(256) coarse_pick_kernel(
   if (q >= B) return;
   for (int j = lane; j < d_c; j += 32) s_q[warp][j] = qc[q * ldq + j];
   __syncwarp();
-  const uint16_t *kq = keys + q * npad;
+  // the key row, 8 keys per 16-byte load (npad is a multiple of 8)
+  const uint4 *kv = (const uint4 *)(keys + q * npad);
+  const int nv = (int)(npad >> 3);
+  auto key_of = [](const uint4 &u, int e) -> uint32_t {
+    const uint32_t w = e < 2 ? u.x : e < 4 ? u.y : e < 6 ? u.z : u.w;
+    return (w >> ((e & 1) * 16)) & 0xFFFFu;
+  };
+  const uint4 none = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
   uint64_t lst = KEY_MAX;
-  for (int c0 = 0; c0 < nlist; c0 += 32) {
-    const int c = c0 + lane;
-    topk_insert(lst, c < nlist ? (((uint64_t)kq[c] << 32) | (uint32_t)c) : KEY_MAX, k);
+  for (int v0 = 0; v0 < nv; v0 += 32) {
+    const int vi = v0 + lane;
+    const uint4 u = vi < nv ? __ldg(kv + vi) : none;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c = vi * 8 + e;
+      topk_insert(lst, c < nlist ? (((uint64_t)key_of(u, e) << 32) | (uint32_t)c) : KEY_MAX, k);
+    }
   }
   const uint32_t kth = (uint32_t)(__shfl_sync(0xffffffffu, lst, k - 1) >> 32);
   const double rq = (double)qrho[q];
   const double E = 2.0 * (rmax + rq * cmax + rmax * rq) * (1.0 + 1e-3) + e_rest;
   const uint32_t thr = kth + (uint32_t)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1u;
   uint64_t best = KEY_MAX;
-  for (int c0 = 0; c0 < nlist; c0 += 32) {
-    const int c = c0 + lane;
-    uint64_t key = KEY_MAX;
-    if (c < nlist && kq[c] <= thr) {
-      const float *x = cent + (int64_t)c * ldc;
-      float acc = 0.f;
-      for (int t = 0; t < d_c; ++t) {
-        const float d = fmaf(-1.f, x[t], s_q[warp][t]);
-        acc = fmaf(d, d, acc);
+  for (int v0 = 0; v0 < nv; v0 += 32) {
+    const int vi = v0 + lane;
+    const uint4 u = vi < nv ? __ldg(kv + vi) : none;
+#pragma unroll 1
+    for (int e = 0; e < 8; ++e) {
+      const int c = vi * 8 + e;
+      uint64_t key = KEY_MAX;
+      if (c < nlist && key_of(u, e) <= thr) {
+        const float *x = cent + (int64_t)c * ldc;
+        float acc = 0.f;
+#pragma unroll 8
+        for (int t = 0; t < d_c; ++t) {
+          const float d = fmaf(-1.f, __ldg(x + t), s_q[warp][t]);
+          acc = fmaf(d, d, acc);
+        }
+        key = pack_key(acc, (uint32_t)c);
       }
-      key = pack_key(acc, (uint32_t)c);
+      topk_insert(best, key, k);
     }
-    topk_insert(best, key, k);
   }
   if (lane < k) out[q * k + lane] = best;
 }

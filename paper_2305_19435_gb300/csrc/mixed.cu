@@ -234,30 +234,50 @@ __global__ void cand_count_kernel(const uint64_t *__restrict__ ckeys, int64_t B,
   qtot[q] = t;
 }
 
-// single CTA exclusive scan (int64)
-__global__ void scan64_kernel(const int64_t *__restrict__ in, int64_t n, int64_t *__restrict__ out,
-                              int64_t *__restrict__ total) {
-  __shared__ int64_t s[1024];
-  __shared__ int64_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < n; base += 1024) {
-    const int64_t i = base + threadIdx.x;
-    const int64_t x = i < n ? in[i] : 0;
-    s[threadIdx.x] = x;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const int64_t y = (int)threadIdx.x >= o ? s[threadIdx.x - o] : 0;
-      __syncthreads();
-      s[threadIdx.x] += y;
-      __syncthreads();
+// single CTA exclusive scan (int64): rounds of 1024 threads x 8 consecutive
+// values (serial per thread, shuffle scan per warp, one scan of the warp sums)
+__global__ void __launch_bounds__(1024) scan64_kernel(const int64_t *__restrict__ in, int64_t n,
+                                                      int64_t *__restrict__ out,
+                                                      int64_t *__restrict__ total) {
+  __shared__ int64_t wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int64_t carry = 0;
+  for (int64_t base = 0; base < n; base += 8192) {
+    const int64_t i0 = base + (int64_t)tid * 8;
+    int64_t v[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      v[j] = i0 + j < n ? in[i0 + j] : 0;
+      sum += v[j];
     }
-    if (i < n) out[i] = carry + s[threadIdx.x] - x;
+    int64_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
     __syncthreads();
-    if (threadIdx.x == 1023) carry += s[1023];
+    if (warp == 0) {
+      int64_t w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
     __syncthreads();
+    int64_t ex = carry + (warp > 0 ? wsum[warp - 1] : 0) + inc - sum;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (i0 + j < n) out[i0 + j] = ex;
+      ex += v[j];
+    }
+    carry += wsum[31];
+    __syncthreads();  // wsum is rewritten by the next round
   }
-  if (threadIdx.x == 0 && total) *total = carry;
+  if (tid == 0 && total) *total = carry;
 }
 
 __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, int nprobe,

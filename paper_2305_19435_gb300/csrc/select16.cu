@@ -200,8 +200,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32) select16_kernel(
     const uint4 *g = (const uint4 *)src;
     const int nvec = ptotal >> 3;
     const int nrun = min(SW_SAMPLE / 8, nvec), ns = 8 * nrun;
+    const uint64_t step = ((uint64_t)nvec << 20) / (uint64_t)nrun;  // 2^-20 units
     for (int j = lane; j < nrun; j += 32) {
-      const uint4 v = g[(int)(((int64_t)j * nvec) / nrun)];
+      const uint4 v = g[(int)(((uint64_t)j * step) >> 20)];
       const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int e = 0; e < 8; ++e) s.u.samp[8 * j + e] = (uint16_t)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu);

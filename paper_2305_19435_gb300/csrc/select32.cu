@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(S32_THREADS) select32_kernel(
     const uint4 *g = (const uint4 *)src;
     const int nvec = ptotal >> 2;
     const int nrun = min(S32_SAMPLE / 4, nvec), ns = 4 * nrun;
+    const uint64_t step = ((uint64_t)nvec << 20) / (uint64_t)nrun;  // 2^-20 units
     for (int j = tid; j < nrun; j += S32_THREADS) {
-      const uint4 v = g[(int)(((int64_t)j * nvec) / nrun)];
+      const uint4 v = g[(int)(((uint64_t)j * step) >> 20)];
       samp[4 * j] = v.x;
       samp[4 * j + 1] = v.y;
       samp[4 * j + 2] = v.z;
