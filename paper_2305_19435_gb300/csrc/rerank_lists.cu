@@ -192,11 +192,19 @@ __global__ void final_topk_kernel(const uint64_t *__restrict__ keys, int kr, int
   uint64_t *buf = kb + (size_t)warp * kr;
   // keep only the re-scored slots (pruned and padding slots hold the empty key)
   int n = 0;
-  for (int r0 = 0; r0 < kr; r0 += 32) {
-    const uint64_t key = r0 + lane < kr ? keys[q * kr + r0 + lane] : KEY_MAX;
-    const unsigned m = __ballot_sync(0xffffffffu, key != KEY_MAX);
-    if (key != KEY_MAX) buf[n + __popc(m & lanemask_lt())] = key;
-    n += __popc(m);
+  for (int r0 = 0; r0 < kr; r0 += 128) {
+    uint64_t key[4];  // four loads in flight before the first ballot
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + 32 * u + lane;
+      key[u] = r < kr ? __ldg(keys + q * kr + r) : KEY_MAX;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, key[u] != KEY_MAX);
+      if (key[u] != KEY_MAX) buf[n + __popc(m & lanemask_lt())] = key[u];
+      n += __popc(m);
+    }
   }
   __syncwarp();
   warp_sort(buf, n);
