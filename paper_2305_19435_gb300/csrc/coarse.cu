@@ -340,60 +340,66 @@ __global__ void coarse_tiles_kernel(int64_t B, int ntiles, int64_t npad, int32_t
   }
 }
 
-// one warp per query: the k smallest keys give the threshold, every centroid
-// under it is scored exactly (same arithmetic as the FP32 kernels), and the k
-// nearest by (distance, list id) are written
-__global__ void __launch_bounds__(256) coarse_pick_kernel(
+// One warp per query (k <= 32): the k-th smallest key (two-digit warp radix
+// select over the key row) gives the threshold; the centroids under it (at
+// most CP_CAND, collected in list order) are scored exactly, one per lane,
+// with the same arithmetic as the FP32 kernels, and the k nearest by
+// (distance, list id) are written.  More candidates than CP_CAND (a loose
+// bound) take a second pass that scores them while streaming the row.
+constexpr int CP_WARPS = 8;
+constexpr int CP_CAND = 64;
+
+__global__ void __launch_bounds__(CP_WARPS * 32) coarse_pick_kernel(
     const uint16_t *__restrict__ keys, int64_t npad, int nlist, const float *__restrict__ qc,
     int ldq, int d_c, const float *__restrict__ cent, int ldc, const float *__restrict__ qrho,
     float rmax, float cmax, float e_rest, int64_t B, int k, uint64_t *__restrict__ out) {
-  __shared__ float s_q[8][CM_MAXD];
+  __shared__ float s_q[CP_WARPS][CM_MAXD];
+  __shared__ int s_hist[CP_WARPS][256];
+  __shared__ int s_sh[CP_WARPS][2];
+  __shared__ int s_cand[CP_WARPS][CP_CAND];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t q = (int64_t)blockIdx.x * 8 + warp;
+  const int64_t q = (int64_t)blockIdx.x * CP_WARPS + warp;
   if (q >= B) return;
   for (int j = lane; j < d_c; j += 32) s_q[warp][j] = qc[q * ldq + j];
-  __syncwarp();
-  // the key row, 8 keys per 16-byte load (npad is a multiple of 8)
-  const uint4 *kv = (const uint4 *)(keys + q * npad);
-  const int nv = (int)(npad >> 3);
-  auto key_of = [](const uint4 &u, int e) -> uint32_t {
-    const uint32_t w = e < 2 ? u.x : e < 4 ? u.y : e < 6 ? u.z : u.w;
-    return (w >> ((e & 1) * 16)) & 0xFFFFu;
-  };
-  const uint4 none = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-  uint64_t lst = KEY_MAX;
-  for (int v0 = 0; v0 < nv; v0 += 32) {
-    const int vi = v0 + lane;
-    const uint4 u = vi < nv ? __ldg(kv + vi) : none;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int c = vi * 8 + e;
-      topk_insert(lst, c < nlist ? (((uint64_t)key_of(u, e) << 32) | (uint32_t)c) : KEY_MAX, k);
-    }
-  }
-  const uint32_t kth = (uint32_t)(__shfl_sync(0xffffffffu, lst, k - 1) >> 32);
+  const uint16_t *kq = keys + q * npad;
+  int below, neq;
+  const uint32_t kth = warp_radix_kth<2>(
+      nlist, k, [&](int i) -> uint32_t { return __ldg(kq + i); }, s_hist[warp], s_sh[warp],
+      below, neq);
   const double rq = (double)qrho[q];
   const double E = 2.0 * (rmax + rq * cmax + rmax * rq) * (1.0 + 1e-3) + e_rest;
   const uint32_t thr = kth + (uint32_t)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1u;
-  uint64_t best = KEY_MAX;
-  for (int v0 = 0; v0 < nv; v0 += 32) {
-    const int vi = v0 + lane;
-    const uint4 u = vi < nv ? __ldg(kv + vi) : none;
-#pragma unroll 1
-    for (int e = 0; e < 8; ++e) {
-      const int c = vi * 8 + e;
-      uint64_t key = KEY_MAX;
-      if (c < nlist && key_of(u, e) <= thr) {
-        const float *x = cent + (int64_t)c * ldc;
-        float acc = 0.f;
+  auto score = [&](int c) -> uint64_t {
+    const float *x = cent + (int64_t)c * ldc;
+    float acc = 0.f;
 #pragma unroll 8
-        for (int t = 0; t < d_c; ++t) {
-          const float d = fmaf(-1.f, __ldg(x + t), s_q[warp][t]);
-          acc = fmaf(d, d, acc);
-        }
-        key = pack_key(acc, (uint32_t)c);
-      }
-      topk_insert(best, key, k);
+    for (int t = 0; t < d_c; ++t) {
+      const float d = fmaf(-1.f, __ldg(x + t), s_q[warp][t]);
+      acc = fmaf(d, d, acc);
+    }
+    return pack_key(acc, (uint32_t)c);
+  };
+  // candidates under the threshold, in list order
+  int nc = 0;
+  for (int c0 = 0; c0 < nlist; c0 += 32) {
+    const int c = c0 + lane;
+    const bool in = c < nlist && __ldg(kq + c) <= thr;
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    const int p = nc + __popc(m & lanemask_lt());
+    if (in && p < CP_CAND) s_cand[warp][p] = c;
+    nc += __popc(m);
+  }
+  __syncwarp();
+  uint64_t best = KEY_MAX;
+  if (nc <= CP_CAND) {
+    for (int j0 = 0; j0 < nc; j0 += 32) {
+      const int j = j0 + lane;
+      topk_insert(best, j < nc ? score(s_cand[warp][j]) : KEY_MAX, k);
+    }
+  } else {
+    for (int c0 = 0; c0 < nlist; c0 += 32) {
+      const int c = c0 + lane;
+      topk_insert(best, c < nlist && __ldg(kq + c) <= thr ? score(c) : KEY_MAX, k);
     }
   }
   if (lane < k) out[q * k + lane] = best;
@@ -585,7 +591,7 @@ int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t 
   const float e_rest = (float)(2.0 * nkb * 64 * std::ldexp(1.0, -22) +
                                8.0 * (d_c + 2) * std::ldexp(1.0, -24) + 1e-4);
   if (k <= CM_MAXK) {
-    coarse_pick_kernel<<<(unsigned)((B + 7) / 8), 256, 0, st>>>(
+    coarse_pick_kernel<<<(unsigned)((B + CP_WARPS - 1) / CP_WARPS), CP_WARPS * 32, 0, st>>>(
         keys, npad, nlist, qc, ldq, d_c, idx->centroids, idx->d_c, qrho,
         idx->cent_rmax[gi] * 1.001f, idx->cent_maxnorm * 1.001f, e_rest, B, k, out);
     ADN_LAUNCH("coarse_pick_kernel");

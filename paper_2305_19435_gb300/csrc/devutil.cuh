@@ -68,11 +68,56 @@ __device__ __forceinline__ void warp_find_bucket(const int *h, int base, int tar
   const unsigned m = __ballot_sync(0xffffffffu, base + inc >= target);
   const int L = m ? __ffs(m) - 1 : 31;
   if (lane == L) {
-    int c = base + inc - sum, j = 0;
-    while (j < 7 && c + v[j] < target) c += v[j++];
-    *b_out = L * 8 + j;
+    // first bucket j of the lane's 8 whose running count reaches target
+    int c = base + inc - sum, jb = 7;
+    bool found = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (!found) {
+        if (j == 7 || c + v[j] >= target) {
+          jb = j;
+          found = true;
+        } else {
+          c += v[j];
+        }
+      }
+    }
+    *b_out = L * 8 + jb;
     *below_out = c;
   }
+}
+
+// One warp: the kth smallest (1-based, 1 <= kth <= n) of n keys key(i) of
+// NPASS * 8 bits, by NPASS passes of 8-bit digits over the warp's 256-int
+// shared histogram hist (sh: 2 shared ints).  below = keys smaller than the
+// result, neq = keys equal to it.
+template <int NPASS, class KeyF>
+__device__ __forceinline__ uint32_t warp_radix_kth(int n, int kth, KeyF key, int *hist, int *sh,
+                                                   int &below, int &neq) {
+  const int lane = threadIdx.x & 31;
+  uint32_t prefix = 0, mask = 0;
+  int bl = 0;
+#pragma unroll 1
+  for (int pass = 0; pass < NPASS; ++pass) {
+    const int shift = 8 * (NPASS - 1 - pass);
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const uint32_t k = key(i);
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1);
+    }
+    __syncwarp();
+    warp_find_bucket(hist, bl, kth, sh, sh + 1);
+    __syncwarp();
+    const int digit = sh[0];
+    prefix |= (uint32_t)digit << shift;
+    mask |= 255u << shift;
+    bl = sh[1];
+    if (pass == NPASS - 1) neq = hist[digit];
+    __syncwarp();
+  }
+  below = bl;
+  return prefix;
 }
 
 // Block-wide radix select over n keys key(i) of NPASS * 8 bits: the kth

@@ -32,7 +32,7 @@ constexpr int SW_PF = 8;
 
 struct SwState {
   int hist[256];
-  int digit, below, n, cnt, ecnt;
+  int sh[2], n, cnt, ecnt;
   int lid[SW_MAXP], nl[SW_MAXP], pst[SW_MAXP + 1];
   union {
     uint16_t samp[SW_SAMPLE];
@@ -44,29 +44,9 @@ struct SwState {
 
 // the kth smallest (1-based, kth <= n) of n 16-bit keys, by one warp
 template <class KeyF>
-__device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, SwState &s, int &below, int &neq) {
-  const int lane = threadIdx.x & 31;
-  uint32_t prefix = 0;
-  int bl = 0;
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const int shift = pass == 0 ? 8 : 0;
-    for (int i = lane; i < 256; i += 32) s.hist[i] = 0;
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      const uint32_t k = key(i);
-      if (pass == 0 || (k >> 8) == (prefix >> 8)) atomicAdd(&s.hist[(k >> shift) & 255u], 1);
-    }
-    __syncwarp();
-    warp_find_bucket(s.hist, bl, kth, &s.digit, &s.below);
-    __syncwarp();
-    prefix |= (uint32_t)s.digit << shift;
-    bl = s.below;
-    if (pass == 1) neq = s.hist[s.digit];
-    __syncwarp();
-  }
-  below = bl;
-  return prefix;
+__device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, SwState &s, int &below,
+                                               int &neq) {
+  return warp_radix_kth<2>(n, kth, key, s.hist, s.sh, below, neq);
 }
 
 // The kk smallest of n keys into o[0, kk) (any order): key(i), database
