@@ -201,9 +201,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32) select16_kernel(
       //    (SWAR: d = (x | H) - (T & ~H) cannot borrow across the halves; the
       //    half x < T iff (~x_top & T_top) | (~(x_top ^ T_top) & ~d_top)); the
       //    survivor flags go to bit 8e + 7 of a 64-bit mask for key e of the
-      //    16-byte group, and a warp prefix sum gives every lane its slots
+      //    16-byte group; a lane with survivors claims its slots with one
+      //    shared-memory atomic
       const uint32_t TT = T | (T << 16), TL = TT & 0x7FFF7FFFu;
-      int nb = 0;  // survivors so far (the same in every lane)
       for (int c0 = 0; c0 < nvec; c0 += 32 * SW_PF) {
         uint4 v[SW_PF];
 #pragma unroll
@@ -223,30 +223,21 @@ __global__ void __launch_bounds__(SW_WARPS * 32) select16_kernel(
           }
           uint64_t M = ((uint64_t)__byte_perm(lt[2], lt[3], 0x7531) << 32) |
                        (uint64_t)__byte_perm(lt[0], lt[1], 0x7531);
-          const int cnt = __popcll(M);
-          int inc = cnt;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-          }
-          const int tot = __shfl_sync(0xffffffffu, inc, 31);
-          if (tot == 0) continue;
-          int p = nb + inc - cnt;
-          const uint64_t k01 = ((uint64_t)w[1] << 32) | w[0], k23 = ((uint64_t)w[3] << 32) | w[2];
-          while (M) {
-            const int e = (__ffsll((long long)M) - 1) >> 3;
-            M &= M - 1;
-            if (p < SW_BUF) {
-              s.bkey[p] = (uint16_t)(((e < 4 ? k01 : k23) >> (16 * (e & 3))) & 0xFFFFu);
-              s.bidx[p] = (uint32_t)(c * 8 + e);
+          if (M) {
+            int p = atomicAdd(&s.n, __popcll(M));
+            const uint64_t k01 = ((uint64_t)w[1] << 32) | w[0], k23 = ((uint64_t)w[3] << 32) | w[2];
+            while (M) {
+              const int e = (__ffsll((long long)M) - 1) >> 3;
+              M &= M - 1;
+              if (p < SW_BUF) {
+                s.bkey[p] = (uint16_t)(((e < 4 ? k01 : k23) >> (16 * (e & 3))) & 0xFFFFu);
+                s.bidx[p] = (uint32_t)(c * 8 + e);
+              }
+              ++p;
             }
-            ++p;
           }
-          nb += tot;
         }
       }
-      if (lane == 0) s.n = nb;
       __syncwarp();
       const int n = s.n;
       // 3. exact select on the buffer
