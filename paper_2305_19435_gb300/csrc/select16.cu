@@ -6,7 +6,7 @@
 //  1. a sample of up to 2,048 keys (256 evenly spaced 16-byte runs) gives a
 //     threshold T aimed at (kk + SW_BUF) / 2 smaller keys (radix select on
 //     the sample);
-//  2. one pass over the region (eight 16-byte loads in flight per lane)
+//  2. one pass over the region (sixteen 16-byte loads in flight per lane)
 //     compacts every key < T, with its position, into a per-warp buffer;
 //  3. if the buffer holds between kk and SW_BUF keys, an exact two-digit
 //     radix select on it fixes the cut; otherwise the same select runs over
@@ -28,7 +28,7 @@ constexpr int SW_SAMPLE = 2048;
 constexpr int SW_BUF = 1024;
 constexpr int SW_TIE = 256;
 constexpr int SW_MAXP = 128;
-constexpr int SW_PF = 8;
+constexpr int SW_PF = 16;
 
 struct SwState {
   int hist[256];
