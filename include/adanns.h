@@ -184,6 +184,11 @@ int adanns_kmeans_update(const float *points, int64_t n, int ld, int dim, int me
  *            probed with P_dc(q) against the first d_c coordinates of each
  *            centroid, taken as stored (not renormalised).
  *   storage  ADANNS_STORE_F32: the exact FP32 scan (rerank_k must be 0).
+ *            With few queries per probed list (B * nprobe / nlist <= 16,
+ *            nprobe <= 256) the lists are streamed once per 16-query tile
+ *            and the distances selected per query afterwards (4 bytes per
+ *            probed member of scratch); ADANNS_FP32_STREAM=0 keeps the
+ *            shared-memory tiled scan.  Both give the same result.
  *            ADANNS_STORE_BF16 / ADANNS_STORE_FP8E4M3 (tier built into the
  *            index, metric ADANNS_METRIC_L2_PREFIXNORM, nprobe <= 128): the
  *            probed lists are scanned on the tensor cores with FP32

@@ -385,6 +385,12 @@ int64_t adanns_search_scratch_bytes(const adanns_index *idx, int64_t B, int d_c,
     const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
     return Bc * per_q + (int64_t)idx->nlist * 64 + (64ll << 20);
   }
+  if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe)) {
+    const int64_t per_q = max_probe_members(idx, nprobe) * 4 + (int64_t)(dcp + dsp) * 4 +
+                          (int64_t)k * 8 + (int64_t)nprobe * 40 + 16;
+    const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
+    return Bc * per_q + (int64_t)idx->nlist * 64 + (16ll << 20);
+  }
   int tq, qt, nsplit;
   fp32_scan_shape(idx, B, d_s, nprobe, k, &tq, &qt, &nsplit);
   const int64_t per_q =
@@ -465,6 +471,9 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
   if (rerank_k != 0) return fail(ADANNS_ERR_ARG, "rerank_k must be 0 for the FP32 scan");
   if (B == 0) return ADANNS_OK;
   cudaStream_t st = S(cuda_stream);
+  if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe))
+    return search_f32_stream(idx, queries, B, d_c, d_s, nprobe, k, out_ids, out_dist, out_probes,
+                             st);
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
   int tq, qt, nsplit;

@@ -45,17 +45,6 @@ bool adc_select_enabled(int nprobe) {
   return nprobe <= 256 && !(env && env[0] == '0');
 }
 
-// the largest candidate segment one query can have: the n_p longest lists,
-// each padded to 8 members
-int64_t max_probe_members(const adanns_index *idx, int nprobe) {
-  std::vector<int64_t> len((size_t)idx->nlist);
-  for (int l = 0; l < idx->nlist; ++l)
-    len[(size_t)l] = (idx->h_list_off[l + 1] - idx->h_list_off[l] + 7) & ~7ll;
-  std::partial_sort(len.begin(), len.begin() + nprobe, len.end(), std::greater<int64_t>());
-  int64_t t = 0;
-  for (int s = 0; s < nprobe; ++s) t += len[(size_t)s];
-  return t;
-}
 
 uint64_t splitmix64(uint64_t &s) {
   uint64_t z = (s += 0x9E3779B97F4A7C15ull);

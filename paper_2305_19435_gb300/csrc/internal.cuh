@@ -82,6 +82,7 @@ extern std::atomic<long long> g_launches;  // kernels launched since load
 cudaMemPool_t scratch_pool();
 // Bytes of scratch one search call may hold at once (ADANNS_SCRATCH_GB, default 12).
 int64_t scratch_budget();
+int64_t max_probe_members(const adanns_index *idx, int nprobe);
 
 // Stream-ordered scratch allocation from that pool on the call's stream.
 struct Scratch {
@@ -236,6 +237,10 @@ int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int
 // FP32 distance bits) of its candidate segments, written as
 // (key << 32 | database id), KEY_MAX padding; ties at the cut go to the
 // smallest candidate positions.  nprobe <= 256.
+bool fp32_stream_enabled(double queries_per_list, int nprobe);
+int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
+                      int nprobe, int k, int64_t *out_ids, float *out_dist, int32_t *out_probes,
+                      cudaStream_t st);
 int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, int kk, int k, const float *qrho, float rmax,
                     float e_rest, int prune, int64_t B, int64_t *out, cudaStream_t st);

@@ -1,8 +1,11 @@
 // Query preparation, probe inversion into (list, query-tile) work, and the
 // cross-list top-k merge of AdANNS-IVF search (Algorithm 1 adannsInference).
+#include <algorithm>
 #include <cstdlib>
+#include <functional>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "devutil.cuh"
 #include "internal.cuh"
@@ -55,6 +58,18 @@ cudaMemPool_t scratch_pool() {
     pools[dev] = p;
   }
   return pools[dev];
+}
+
+// the largest candidate segment one query can have: the n_p longest lists,
+// each padded to 8 members
+int64_t max_probe_members(const adanns_index *idx, int nprobe) {
+  std::vector<int64_t> len((size_t)idx->nlist);
+  for (int l = 0; l < idx->nlist; ++l)
+    len[(size_t)l] = (idx->h_list_off[l + 1] - idx->h_list_off[l] + 7) & ~7ll;
+  std::partial_sort(len.begin(), len.begin() + nprobe, len.end(), std::greater<int64_t>());
+  int64_t t = 0;
+  for (int s = 0; s < nprobe; ++s) t += len[(size_t)s];
+  return t;
 }
 
 int64_t scratch_budget() {

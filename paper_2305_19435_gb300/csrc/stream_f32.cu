@@ -1,0 +1,261 @@
+// Exact FP32 list scan for the memory-bound regime: few queries probe each
+// list (Algorithm 1 linear scan when the batch is small against nlist), so a
+// member row is used by a handful of queries and the scan is a stream of the
+// probed lists' d_s prefixes.
+//
+// Work item = (query tile of up to 16 queries probing one list, member range).
+// One thread per member: the member's 16-coordinate prefix blocks are read
+// with 16-byte loads straight into registers (a warp covers 32 consecutive
+// members, 2 KB contiguous per block in the prefix-major layout), the next
+// block is in flight while one is used, and the distances to every query of
+// the tile are accumulated in registers.  No shared-memory staging and no
+// block barrier inside the stream.  The arithmetic is the FP32 scan's
+// (t = q_j - s_x x_j, acc += t * t over j ascending), so the distances are
+// bit-identical to it; each one is written as FP32 bits into the query's
+// candidate segment, and select32_kernel then keeps the k best by
+// (distance, id).
+#include <algorithm>
+
+#include "devutil.cuh"
+#include "internal.cuh"
+
+namespace adn {
+namespace {
+
+constexpr int SF_THREADS = 256;
+constexpr int SF_QT = 16;  // queries per work item
+
+struct StreamArgs {
+  const float *xpm;  // prefix-major FP32 lists
+  int d_pad, dims;
+  const int64_t *list_off;
+  const float *mscale;  // per-member scale (inverse prefix norm), or null
+  const float *qn;      // prepared query rows
+  int ldq;
+  const int32_t *tile_list, *tile_beg, *tile_cnt;
+  const int *ntiles_dev;
+  const int32_t *pair_q, *pair_out;
+  const int64_t *pbase;  // candidate segment start of each (query, probe) pair
+  uint32_t *cand;
+  int *counter;
+  int nsplit;  // member ranges per tile
+};
+
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg((const float4 *)p); }
+
+// acc[j] += sum over the block's coordinates (nd4 groups of 4) of (q - s x)^2
+template <bool FULL>
+__device__ __forceinline__ void block_step(float (&acc)[SF_QT], const float4 (&x)[4], float sc,
+                                           const float *const *qrow, int cnt, int off, int nd4) {
+#pragma unroll
+  for (int j = 0; j < SF_QT; ++j) {
+    if (j >= cnt) break;
+    const float *qb = qrow[j] + off;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (!FULL && s >= nd4) break;
+      const float4 q = ldg4(qb + 4 * s);
+      float t;
+      t = fmaf(-sc, x[s].x, q.x);
+      acc[j] = fmaf(t, t, acc[j]);
+      t = fmaf(-sc, x[s].y, q.y);
+      acc[j] = fmaf(t, t, acc[j]);
+      t = fmaf(-sc, x[s].z, q.z);
+      acc[j] = fmaf(t, t, acc[j]);
+      t = fmaf(-sc, x[s].w, q.w);
+      acc[j] = fmaf(t, t, acc[j]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SF_THREADS, 3) dist_f32_kernel(StreamArgs a) {
+  __shared__ int s_item;
+  __shared__ const float *s_qp[SF_QT];  // the tile's query rows
+  __shared__ int64_t s_pb[SF_QT];
+  const int tid = threadIdx.x;
+  const int ntiles = *a.ntiles_dev * a.nsplit;
+  const int nblk = (a.dims + 15) >> 4;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= ntiles) break;
+    const int tile = item / a.nsplit, range = item - tile * a.nsplit;
+    const int list = a.tile_list[tile], beg = a.tile_beg[tile], cnt = a.tile_cnt[tile];
+    if (tid < cnt) {
+      s_qp[tid] = a.qn + (int64_t)a.pair_q[beg + tid] * a.ldq;
+      s_pb[tid] = a.pbase[a.pair_out[beg + tid]];
+    }
+    __syncthreads();
+    const int64_t moff = a.list_off[list];
+    const int nl = (int)(a.list_off[list + 1] - moff), npad = (nl + 7) & ~7;
+    const float *lbase = a.xpm + moff * (int64_t)a.d_pad;
+    const int nchunk_all = (npad + SF_THREADS - 1) / SF_THREADS;
+    const int cper = (nchunk_all + a.nsplit - 1) / a.nsplit;
+    const int c1 = min(nchunk_all, (range + 1) * cper);
+    const float *const *qrow = s_qp;
+    for (int c = range * cper; c < c1; ++c) {
+      const int m = c * SF_THREADS + tid;
+      if (m >= npad) continue;
+      if (m >= nl) {  // the segment's padding
+        for (int j = 0; j < cnt; ++j) a.cand[s_pb[j] + m] = 0xFFFFFFFFu;
+        continue;
+      }
+      const float sc = a.mscale ? __ldg(a.mscale + moff + m) : 1.f;
+      const float *xr = lbase + (int64_t)m * 16;
+      const int64_t bstride = (int64_t)16 * nl;
+      float acc[SF_QT];
+#pragma unroll
+      for (int j = 0; j < SF_QT; ++j) acc[j] = 0.f;
+      float4 xa[4], xb[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) xa[s] = ldg4(xr + 4 * s);
+      int b = 0;
+      // two blocks per trip: the next block loads while this one is used
+      for (; b + 2 <= nblk; b += 2) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) xb[s] = ldg4(xr + (b + 1) * bstride + 4 * s);
+        block_step<true>(acc, xa, sc, qrow, cnt, 16 * b, 4);
+        if (b + 2 < nblk) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) xa[s] = ldg4(xr + (b + 2) * bstride + 4 * s);
+        }
+        const int nd4b = min(4, (a.dims - 16 * (b + 1)) >> 2);
+        if (nd4b == 4) block_step<true>(acc, xb, sc, qrow, cnt, 16 * (b + 1), 4);
+        else block_step<false>(acc, xb, sc, qrow, cnt, 16 * (b + 1), nd4b);
+      }
+      if (b < nblk) {  // odd block count: the last block is in xa
+        const int nd4 = min(4, (a.dims - 16 * b) >> 2);
+        if (nd4 == 4) block_step<true>(acc, xa, sc, qrow, cnt, 16 * b, 4);
+        else block_step<false>(acc, xa, sc, qrow, cnt, 16 * b, nd4);
+      }
+#pragma unroll
+      for (int j = 0; j < SF_QT; ++j)
+        if (j < cnt) a.cand[s_pb[j] + m] = __float_as_uint(acc[j]);
+    }
+    __syncthreads();  // s_qp / s_pb are rewritten by the next item
+  }
+}
+
+}  // namespace
+
+// Few queries per probed list: prefer the streaming scan (ADANNS_FP32_STREAM=0
+// keeps the shared-memory tiled scan everywhere)
+bool fp32_stream_enabled(double queries_per_list, int nprobe) {
+  const char *env = getenv("ADANNS_FP32_STREAM");
+  if (env && env[0] == '0') return false;
+  return queries_per_list <= 16.0 && nprobe <= 256;
+}
+
+int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
+                      int nprobe, int k, int64_t *out_ids, float *out_dist, int32_t *out_probes,
+                      cudaStream_t st) {
+  const int nlist = idx->nlist;
+  const int dcp = pad16(d_c), dsp = pad16(d_s);
+  const int64_t seg_q = max_probe_members(idx, nprobe);
+  const int64_t per_q =
+      seg_q * 4 + (int64_t)(dcp + dsp) * 4 + (int64_t)k * 8 + (int64_t)nprobe * 40 + 16;
+  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
+  const int64_t max_tiles = (Bc * nprobe + SF_QT - 1) / SF_QT + nlist;
+  Scratch s(st);
+  float *qc, *qs;
+  uint64_t *ckeys, *keys;
+  uint32_t *cand;
+  int64_t *qtot, *qbase, *pbase;
+  int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
+  int *ntiles, *counter;
+  int rc;
+  if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
+      (rc = s.get(&ckeys, (size_t)Bc * nprobe)) || (rc = s.get(&cand, (size_t)(Bc * seg_q))) ||
+      (rc = s.get(&keys, (size_t)Bc * k)) || (rc = s.get(&qtot, (size_t)Bc)) ||
+      (rc = s.get(&qbase, (size_t)Bc)) || (rc = s.get(&pbase, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&lcnt, nlist)) || (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) ||
+      (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
+      (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) ||
+      (rc = s.get(&counter, 2)))
+    return rc;
+  const float *mscale = idx->metric == ADANNS_METRIC_L2_PREFIXNORM
+                            ? idx->invn + (int64_t)gran_index(d_s) * idx->N
+                            : nullptr;
+  for (int64_t b0 = 0; b0 < B; b0 += Bc) {
+    const int64_t nb = std::min(Bc, B - b0);
+    {
+      StageTimer t(ST_PREP, st);
+      if ((rc = launch_prep_queries(queries + b0 * idx->d, nb, idx->d, d_c, d_s, idx->metric, qc,
+                                    dcp, qs, dsp, st)))
+        return rc;
+    }
+    ScanArgs c{};
+    c.xpm = idx->cent_pm;
+    c.d_pad = idx->dc_pad;  // stored centroid width; d_c <= built d_c (IVF-D)
+    c.dims = d_c;
+    c.list_off = idx->cent_off;
+    c.qn = qc;
+    c.ldq = dcp;
+    c.nq = (int)nb;
+    c.counter = counter;
+    c.k = nprobe;
+    c.out_keys = ckeys;
+    ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
+    {
+      StageTimer t(ST_COARSE, st);
+      if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, c, st))) return rc;
+    }
+    {
+      StageTimer t(ST_INVERT, st);
+      if ((rc = launch_invert_probes(ckeys, nb, nprobe, nlist, SF_QT, lcnt, lbeg, lfill, tbeg,
+                                     pair_q, pair_out, tl, tb, tc, ntiles,
+                                     out_probes ? out_probes + b0 * nprobe : nullptr, st)))
+        return rc;
+      if ((rc = launch_cand_segments(ckeys, nb, nprobe, idx->list_off, qtot, qbase, pbase, st)))
+        return rc;
+    }
+    {
+      StageTimer t(ST_SCAN, st);
+      StreamArgs a{};
+      a.xpm = idx->xpm;
+      a.d_pad = idx->d_pad;
+      a.dims = d_s;
+      a.list_off = idx->list_off;
+      a.mscale = mscale;
+      a.qn = qs;
+      a.ldq = dsp;
+      a.tile_list = tl;
+      a.tile_beg = tb;
+      a.tile_cnt = tc;
+      a.ntiles_dev = ntiles;
+      a.pair_q = pair_q;
+      a.pair_out = pair_out;
+      a.pbase = pbase;
+      a.cand = cand;
+      a.counter = counter + 1;
+      // enough items for every SM: each tile's members split into ranges
+      const int64_t tiles_est = std::min<int64_t>(nlist, nb * nprobe);
+      const int64_t target = (int64_t)num_sms() * 16;
+      a.nsplit = (int)std::max<int64_t>(
+          1, std::min<int64_t>((target + tiles_est - 1) / tiles_est,
+                               ((int64_t)idx->max_list + SF_THREADS - 1) / SF_THREADS));
+      int per_sm = 1;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dist_f32_kernel, SF_THREADS, 0) !=
+              cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      dist_f32_kernel<<<num_sms() * per_sm, SF_THREADS, 0, st>>>(a);
+      ADN_LAUNCH("dist_f32_kernel");
+    }
+    {
+      StageTimer t(ST_MERGE, st);
+      if ((rc = launch_select32(cand, ckeys, nprobe, qbase, idx->list_off, idx->list_ids, nb, k,
+                                keys, st)))
+        return rc;
+      if ((rc = launch_final_topk(keys, k, nb, k, out_ids + b0 * k, out_dist + b0 * k, st)))
+        return rc;
+    }
+  }
+  return ADANNS_OK;
+}
+
+}  // namespace adn

@@ -311,3 +311,22 @@ def test_tensor_core_cluster_mapping_is_exact(A, wide, d_c, nprobe, monkeypatch)
     g.status()
     g.free()
     search_parity(A, data["db"], data["queries"], o, d_c, 128, nprobe, 20, PN)
+
+
+@pytest.mark.parametrize("B,d_s,nprobe,k", [(40, 8, 1, 1), (100, 48, 4, 10), (500, 128, 1, 100),
+                                            (300, 96, 8, 33), (17, 128, 33, 50), (3, 16, 2, 5)])
+def test_fp32_stream_scan_equals_tiled_scan(A, wide, B, d_s, nprobe, k, monkeypatch):
+    """Few queries per probed list: the streaming scan (register accumulation,
+    distances written, then a per-query select) and the shared-memory tiled
+    scan compute the same FP32 distances and keep the same (distance, id)
+    top-k, bit for bit; d_s = 8 and 48 end in a partial 16-coordinate block."""
+    data, o = wide
+    g = import_index(A, data["db"], o, PN)
+    q = cu(data["queries"][:B])
+    i0, d0, p0 = A.search_ivf(g, q, 64, d_s, nprobe, k, return_probes=True)
+    monkeypatch.setenv("ADANNS_FP32_STREAM", "0")
+    i1, d1, p1 = A.search_ivf(g, q, 64, d_s, nprobe, k, return_probes=True)
+    assert torch.equal(p0, p1)
+    assert torch.equal(i0, i1)
+    assert torch.equal(d0.view(torch.int32), d1.view(torch.int32))
+    g.free()
