@@ -319,7 +319,9 @@ def scan_hbm_phase(P, torch, idx, q, oidx, args, hbm_peak, modes):
             stage = "scan" if mode == "f32" else "mma"
             t = prof.get(stage, (0.0, 1))[0] / 10
             gbs = int(sizes.sum()) * per_member / (t / 1e3) / 1e9 if t else None
-            out[f"{mode}_ds{d_s}"] = {"kernel": "scan_f32_kernel" if mode == "f32" else "mma_scan_kernel",
+            f32_kernel = ("dist_f32_kernel (streaming scan)"
+                          if os.environ.get("ADANNS_FP32_STREAM", "1") != "0" else "scan_f32_kernel")
+            out[f"{mode}_ds{d_s}"] = {"kernel": f32_kernel if mode == "f32" else "mma_scan_kernel",
                                       "kernel_ms": t, "step_ms": ms, "achieved_gbs": gbs,
                                       "frac_of_hbm": gbs / hbm_peak if gbs else None}
     return out
