@@ -293,6 +293,14 @@ __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, 
   }
 }
 
+// exclusive scan of n int64 values (one CTA); *total = their sum when non-null
+int launch_scan64(const int64_t *in, int64_t n, int64_t *out, int64_t *total, cudaStream_t st) {
+  if (n <= 0) return ADANNS_OK;
+  scan64_kernel<<<1, 1024, 0, st>>>(in, n, out, total);
+  ADN_LAUNCH("scan64_kernel");
+  return ADANNS_OK;
+}
+
 // per-query candidate segments: qtot, qbase (exclusive scan) and pbase
 int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int64_t *list_off,
                          int64_t *qtot, int64_t *qbase, int64_t *pbase, cudaStream_t st) {

@@ -3,17 +3,18 @@
 // member row is used by a handful of queries and the scan is a stream of the
 // probed lists' d_s prefixes.
 //
-// Work item = (query tile of up to 16 queries probing one list, member range).
-// One thread per member: the member's 16-coordinate prefix blocks are read
-// with 16-byte loads straight into registers (a warp covers 32 consecutive
+// Work unit = (probe tile, chunk of 256 members, group of up to 4 of the
+// tile's queries): units cost about the same whatever the list's popularity,
+// and are enumerated by an exclusive scan of each tile's unit count.  One
+// thread per member: the member's 16-coordinate prefix blocks are read with
+// 16-byte loads straight into registers (a warp covers 32 consecutive
 // members, 2 KB contiguous per block in the prefix-major layout), the next
-// block is in flight while one is used, and the distances to every query of
-// the tile are accumulated in registers.  No shared-memory staging and no
-// block barrier inside the stream.  The arithmetic is the FP32 scan's
-// (t = q_j - s_x x_j, acc += t * t over j ascending), so the distances are
-// bit-identical to it; each one is written as FP32 bits into the query's
-// candidate segment, and select32_kernel then keeps the k best by
-// (distance, id).
+// block in flight while one is used, and the distances to the group's
+// queries accumulate in registers; no barrier inside the stream.  The
+// arithmetic is the FP32 scan's (t = q_j - s_x x_j, acc += t * t over j
+// ascending), so the distances are bit-identical to it; each one is written
+// as FP32 bits into the query's candidate segment, and select32_kernel then
+// keeps the k best by (distance, id).
 #include <algorithm>
 
 #include "devutil.cuh"
@@ -22,8 +23,9 @@
 namespace adn {
 namespace {
 
-constexpr int SF_THREADS = 256;
-constexpr int SF_QT = 16;  // queries per work item
+constexpr int SF_THREADS = 256;  // one chunk of members per work unit
+constexpr int SF_QT = 16;        // queries per probe tile
+constexpr int SF_QG = 4;         // queries per work unit
 
 struct StreamArgs {
   const float *xpm;  // prefix-major FP32 lists
@@ -34,21 +36,37 @@ struct StreamArgs {
   int ldq;
   const int32_t *tile_list, *tile_beg, *tile_cnt;
   const int *ntiles_dev;
+  const int64_t *uoff;  // first work unit of each tile (exclusive scan of its units)
+  const int64_t *nunits;
   const int32_t *pair_q, *pair_out;
   const int64_t *pbase;  // candidate segment start of each (query, probe) pair
   uint32_t *cand;
   int *counter;
-  int nsplit;  // member ranges per tile
 };
 
 __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg((const float4 *)p); }
 
+// units of a tile: member chunks x query groups (0 past the tile count)
+__global__ void stream_units_kernel(const int32_t *__restrict__ tl, const int32_t *__restrict__ tc,
+                                    const int *__restrict__ ntiles, const int64_t *__restrict__ list_off,
+                                    int64_t max_tiles, int64_t *__restrict__ units) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= max_tiles) return;
+  int64_t u = 0;
+  if (t < *ntiles) {
+    const int l = tl[t];
+    const int64_t npad = (list_off[l + 1] - list_off[l] + 7) & ~7ll;
+    u = ((npad + SF_THREADS - 1) / SF_THREADS) * ((tc[t] + SF_QG - 1) / SF_QG);
+  }
+  units[t] = u;
+}
+
 // acc[j] += sum over the block's coordinates (nd4 groups of 4) of (q - s x)^2
 template <bool FULL>
-__device__ __forceinline__ void block_step(float (&acc)[SF_QT], const float4 (&x)[4], float sc,
+__device__ __forceinline__ void block_step(float (&acc)[SF_QG], const float4 (&x)[4], float sc,
                                            const float *const *qrow, int cnt, int off, int nd4) {
 #pragma unroll
-  for (int j = 0; j < SF_QT; ++j) {
+  for (int j = 0; j < SF_QG; ++j) {
     if (j >= cnt) break;
     const float *qb = qrow[j] + off;
 #pragma unroll
@@ -68,45 +86,47 @@ __device__ __forceinline__ void block_step(float (&acc)[SF_QT], const float4 (&x
   }
 }
 
-__global__ void __launch_bounds__(SF_THREADS, 3) dist_f32_kernel(StreamArgs a) {
+__global__ void __launch_bounds__(SF_THREADS, 4) dist_f32_kernel(StreamArgs a) {
   __shared__ int s_item;
-  __shared__ const float *s_qp[SF_QT];  // the tile's query rows
-  __shared__ int64_t s_pb[SF_QT];
+  __shared__ const float *s_qp[SF_QG];  // the unit's query rows
+  __shared__ int64_t s_pb[SF_QG];
   const int tid = threadIdx.x;
-  const int ntiles = *a.ntiles_dev * a.nsplit;
+  const int64_t nunits = *a.nunits;
+  const int ntiles = *a.ntiles_dev;
   const int nblk = (a.dims + 15) >> 4;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(a.counter, 1);
     __syncthreads();
-    const int item = s_item;
-    if (item >= ntiles) break;
-    const int tile = item / a.nsplit, range = item - tile * a.nsplit;
-    const int list = a.tile_list[tile], beg = a.tile_beg[tile], cnt = a.tile_cnt[tile];
+    const int64_t item = s_item;
+    if (item >= nunits) break;
+    // the tile holding this unit: the last tile whose first unit is <= item
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.uoff[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int tile = lo;
+    const int list = a.tile_list[tile], beg = a.tile_beg[tile], tcnt = a.tile_cnt[tile];
+    const int ngrp = (tcnt + SF_QG - 1) / SF_QG;
+    const int u = (int)(item - a.uoff[tile]);
+    const int chunk = u / ngrp, g = u - chunk * ngrp;
+    const int q0 = g * SF_QG, cnt = min(SF_QG, tcnt - q0);
     if (tid < cnt) {
-      s_qp[tid] = a.qn + (int64_t)a.pair_q[beg + tid] * a.ldq;
-      s_pb[tid] = a.pbase[a.pair_out[beg + tid]];
+      s_qp[tid] = a.qn + (int64_t)a.pair_q[beg + q0 + tid] * a.ldq;
+      s_pb[tid] = a.pbase[a.pair_out[beg + q0 + tid]];
     }
     __syncthreads();
     const int64_t moff = a.list_off[list];
     const int nl = (int)(a.list_off[list + 1] - moff), npad = (nl + 7) & ~7;
-    const float *lbase = a.xpm + moff * (int64_t)a.d_pad;
-    const int nchunk_all = (npad + SF_THREADS - 1) / SF_THREADS;
-    const int cper = (nchunk_all + a.nsplit - 1) / a.nsplit;
-    const int c1 = min(nchunk_all, (range + 1) * cper);
-    const float *const *qrow = s_qp;
-    for (int c = range * cper; c < c1; ++c) {
-      const int m = c * SF_THREADS + tid;
-      if (m >= npad) continue;
-      if (m >= nl) {  // the segment's padding
-        for (int j = 0; j < cnt; ++j) a.cand[s_pb[j] + m] = 0xFFFFFFFFu;
-        continue;
-      }
+    const int m = chunk * SF_THREADS + tid;
+    if (m < nl) {
       const float sc = a.mscale ? __ldg(a.mscale + moff + m) : 1.f;
-      const float *xr = lbase + (int64_t)m * 16;
+      const float *xr = a.xpm + moff * (int64_t)a.d_pad + (int64_t)m * 16;
       const int64_t bstride = (int64_t)16 * nl;
-      float acc[SF_QT];
+      const float *const *qrow = s_qp;
+      float acc[SF_QG];
 #pragma unroll
-      for (int j = 0; j < SF_QT; ++j) acc[j] = 0.f;
+      for (int j = 0; j < SF_QG; ++j) acc[j] = 0.f;
       float4 xa[4], xb[4];
 #pragma unroll
       for (int s = 0; s < 4; ++s) xa[s] = ldg4(xr + 4 * s);
@@ -130,10 +150,12 @@ __global__ void __launch_bounds__(SF_THREADS, 3) dist_f32_kernel(StreamArgs a) {
         else block_step<false>(acc, xa, sc, qrow, cnt, 16 * b, nd4);
       }
 #pragma unroll
-      for (int j = 0; j < SF_QT; ++j)
+      for (int j = 0; j < SF_QG; ++j)
         if (j < cnt) a.cand[s_pb[j] + m] = __float_as_uint(acc[j]);
+    } else if (m < npad) {  // the segment's padding
+      for (int j = 0; j < cnt; ++j) a.cand[s_pb[j] + m] = 0xFFFFFFFFu;
     }
-    __syncthreads();  // s_qp / s_pb are rewritten by the next item
+    __syncthreads();  // s_qp / s_pb are rewritten by the next unit
   }
 }
 
@@ -161,7 +183,7 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
   float *qc, *qs;
   uint64_t *ckeys, *keys;
   uint32_t *cand;
-  int64_t *qtot, *qbase, *pbase;
+  int64_t *qtot, *qbase, *pbase, *units, *uoff, *nunits;
   int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
   int *ntiles, *counter;
   int rc;
@@ -173,7 +195,8 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
       (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
       (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
       (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) ||
-      (rc = s.get(&counter, 2)))
+      (rc = s.get(&counter, 2)) || (rc = s.get(&units, max_tiles)) ||
+      (rc = s.get(&uoff, max_tiles)) || (rc = s.get(&nunits, 1)))
     return rc;
   const float *mscale = idx->metric == ADANNS_METRIC_L2_PREFIXNORM
                             ? idx->invn + (int64_t)gran_index(d_s) * idx->N
@@ -213,6 +236,10 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
     }
     {
       StageTimer t(ST_SCAN, st);
+      stream_units_kernel<<<(unsigned)((max_tiles + 255) / 256), 256, 0, st>>>(
+          tl, tc, ntiles, idx->list_off, max_tiles, units);
+      ADN_LAUNCH("stream_units_kernel");
+      if ((rc = launch_scan64(units, max_tiles, uoff, nunits, st))) return rc;
       StreamArgs a{};
       a.xpm = idx->xpm;
       a.d_pad = idx->d_pad;
@@ -225,17 +252,13 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
       a.tile_beg = tb;
       a.tile_cnt = tc;
       a.ntiles_dev = ntiles;
+      a.uoff = uoff;
+      a.nunits = nunits;
       a.pair_q = pair_q;
       a.pair_out = pair_out;
       a.pbase = pbase;
       a.cand = cand;
       a.counter = counter + 1;
-      // enough items for every SM: each tile's members split into ranges
-      const int64_t tiles_est = std::min<int64_t>(nlist, nb * nprobe);
-      const int64_t target = (int64_t)num_sms() * 16;
-      a.nsplit = (int)std::max<int64_t>(
-          1, std::min<int64_t>((target + tiles_est - 1) / tiles_est,
-                               ((int64_t)idx->max_list + SF_THREADS - 1) / SF_THREADS));
       int per_sm = 1;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dist_f32_kernel, SF_THREADS, 0) !=
               cudaSuccess ||
