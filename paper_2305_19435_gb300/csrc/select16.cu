@@ -6,7 +6,7 @@
 //  1. a sample of up to 2,048 keys (256 evenly spaced 16-byte runs) gives a
 //     threshold T aimed at (kk + SW_BUF) / 2 smaller keys (radix select on
 //     the sample);
-//  2. one pass over the region (sixteen 16-byte loads in flight per lane)
+//  2. one pass over the region (twelve 16-byte loads in flight per lane)
 //     compacts every key < T, with its position, into a per-warp buffer;
 //  3. if the buffer holds between kk and SW_BUF keys, an exact two-digit
 //     radix select on it fixes the cut; otherwise the same select runs over
@@ -26,27 +26,34 @@ namespace {
 constexpr int SW_WARPS = 4;
 constexpr int SW_SAMPLE = 2048;
 constexpr int SW_BUF = 1024;
-constexpr int SW_TIE = 256;
+constexpr int SW_TIE = 128;
 constexpr int SW_MAXP = 128;
-constexpr int SW_PF = 16;
+constexpr int SW_PF = 12;
 
+// Per-warp state, 8.6 KB, so that six CTAs of four warps fit on an SM.  The
+// histogram is dead when the ties at the cut are collected, and the sample is
+// dead when the compaction fills the buffer, so each pair shares its space.
 struct SwState {
-  int hist[256];
+  union {
+    int hist[256];
+    uint64_t ties[SW_TIE];  // (candidate position << 32 | index) of the keys at the cut
+  } h;
   int sh[2], n, cnt, ecnt;
   int lid[SW_MAXP], nl[SW_MAXP], pst[SW_MAXP + 1];
   union {
     uint16_t samp[SW_SAMPLE];
-    uint64_t ties[SW_TIE];  // (candidate position << 32 | index) of the keys at the cut
+    struct {
+      uint16_t key[SW_BUF];
+      uint32_t idx[SW_BUF];
+    } b;
   } u;
-  uint16_t bkey[SW_BUF];
-  uint32_t bidx[SW_BUF];
 };
 
 // the kth smallest (1-based, kth <= n) of n 16-bit keys, by one warp
 template <class KeyF>
 __device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, SwState &s, int &below,
                                                int &neq) {
-  return warp_radix_kth<2>(n, kth, key, s.hist, s.sh, below, neq);
+  return warp_radix_kth<2>(n, kth, key, s.h.hist, s.sh, below, neq);
 }
 
 // The kk smallest of n keys into o[0, kk) (any order): key(i), database
@@ -76,14 +83,14 @@ __device__ __forceinline__ bool warp_select16(int n, int kk, int kq, int prune_d
       o[atomicAdd(&s.cnt, 1)] = k <= keep_max ? id(i) : -1;
     } else if (k == T && few_ties) {
       const int p = atomicAdd(&s.ecnt, 1);
-      if (p < SW_TIE) s.u.ties[p] = ((uint64_t)(uint32_t)pos(i) << 32) | (uint32_t)i;
+      if (p < SW_TIE) s.h.ties[p] = ((uint64_t)(uint32_t)pos(i) << 32) | (uint32_t)i;
     }
   }
   __syncwarp();
   if (few_ties) {
-    warp_sort(s.u.ties, neq);
+    warp_sort(s.h.ties, neq);
     for (int j = lane; j < need_eq; j += 32)
-      o[below + j] = T <= keep_max ? id((int)(uint32_t)(s.u.ties[j] & 0xffffffffu)) : -1;
+      o[below + j] = T <= keep_max ? id((int)(uint32_t)(s.h.ties[j] & 0xffffffffu)) : -1;
   } else {
     // many ties, keys in position order: rank them with warp prefix counts
     int base = 0;
@@ -100,7 +107,7 @@ __device__ __forceinline__ bool warp_select16(int n, int kk, int kq, int prune_d
   return true;
 }
 
-__global__ void __launch_bounds__(SW_WARPS * 32) select16_kernel(
+__global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
     const uint16_t *__restrict__ cand, const uint64_t *__restrict__ ckeys, int nprobe,
     const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off, int kk, int k,
     const float *__restrict__ qrho, float rmax, float e_rest, int prune, int64_t B,
@@ -230,8 +237,8 @@ __global__ void __launch_bounds__(SW_WARPS * 32) select16_kernel(
               const int e = (__ffsll((long long)M) - 1) >> 3;
               M &= M - 1;
               if (p < SW_BUF) {
-                s.bkey[p] = (uint16_t)(((e < 4 ? k01 : k23) >> (16 * (e & 3))) & 0xFFFFu);
-                s.bidx[p] = (uint32_t)(c * 8 + e);
+                s.u.b.key[p] = (uint16_t)(((e < 4 ? k01 : k23) >> (16 * (e & 3))) & 0xFFFFu);
+                s.u.b.idx[p] = (uint32_t)(c * 8 + e);
               }
               ++p;
             }
@@ -243,9 +250,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32) select16_kernel(
       // 3. exact select on the buffer
       if (n >= kk && n <= SW_BUF &&
           warp_select16<false>(n, kk, kq, prune_delta,
-                               [&](int i) -> uint32_t { return s.bkey[i]; },
-                               [&](int i) -> int64_t { return id_at((int)s.bidx[i]); },
-                               [&](int i) -> int { return (int)s.bidx[i]; }, o, s))
+                               [&](int i) -> uint32_t { return s.u.b.key[i]; },
+                               [&](int i) -> int64_t { return id_at((int)s.u.b.idx[i]); },
+                               [&](int i) -> int { return (int)s.u.b.idx[i]; }, o, s))
         return;
     }
   }
