@@ -257,6 +257,23 @@ __global__ void csr_scatter_kernel(const int32_t *__restrict__ a, int64_t N, int
   }
 }
 
+// exclusive scan of n int32 counts (block sums, their scan, the per-block scan)
+int launch_scan_i32(const int32_t *v, int64_t n, int32_t *out, cudaStream_t st) {
+  if (n <= 0) return ADANNS_OK;
+  const int nb = (int)((n + SCAN_BLOCK - 1) / SCAN_BLOCK);
+  Scratch s(st);
+  int64_t *bsum;
+  int rc;
+  if ((rc = s.get(&bsum, nb))) return rc;
+  scan_reduce_kernel<<<nb, 1024, 0, st>>>(v, n, bsum);
+  ADN_LAUNCH("scan_reduce_kernel");
+  scan_bsum_kernel<<<1, 1024, 0, st>>>(bsum, nb);
+  ADN_LAUNCH("scan_bsum_kernel");
+  scan_apply_kernel<<<nb, 1024, 0, st>>>(v, n, bsum, out);
+  ADN_LAUNCH("scan_apply_kernel");
+  return ADANNS_OK;
+}
+
 int build_csr(const int32_t *assign, int64_t N, int nlist, int64_t *list_off, int32_t *list_ids,
               cudaStream_t st) {
   if (nlist > 32768) return fail(ADANNS_ERR_ARG, "nlist above 32768");

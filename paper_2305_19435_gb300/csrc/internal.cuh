@@ -237,6 +237,7 @@ int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int
 // FP32 distance bits) of its candidate segments, written as
 // (key << 32 | database id), KEY_MAX padding; ties at the cut go to the
 // smallest candidate positions.  nprobe <= 256.
+int launch_scan_i32(const int32_t *v, int64_t n, int32_t *out, cudaStream_t st);
 int launch_scan64(const int64_t *in, int64_t n, int64_t *out, int64_t *total, cudaStream_t st);
 bool fp32_stream_enabled(double queries_per_list, int nprobe);
 int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,

@@ -1,8 +1,9 @@
 // Member-major exact rerank of the shortlists (Sec. 4.3 shortlist-rerank).
 //
-// The B x k' shortlisted (query, member) pairs are grouped by list (stable
-// counting sort) and, inside each list, by member, so that a warp reads each
-// database row once from the prefix-major FP32 storage into shared memory and
+// The B x k' shortlisted (query, member) pairs are grouped by database member
+// (one counting sort over list-order member positions, so lists come out
+// grouped too), so that a CTA reads each database row once from the
+// prefix-major FP32 storage into shared memory and
 // re-scores it against every query that shortlisted it (the query rows, far
 // smaller than the database, are the gathered operand and stay in L2).  The
 // exact difference-form distances are written back to the pairs' slots and a
@@ -14,43 +15,39 @@
 
 namespace adn {
 
-// pair e = (query e / kr, rank e % kr), given as (list << 32 | member
-// position): its list (nlist for padding) and member index
-__global__ void pair_lists_kernel(const int64_t *__restrict__ cand, int64_t n, int nlist,
-                                  int32_t *__restrict__ plist, int32_t *__restrict__ pmem) {
+// Pairs grouped by database member with one counting sort over the list-order
+// member positions: pair e = (query e / kr, rank e % kr), given as
+// (list << 32 | member position) or -1 (padding, pruned).  Its position is
+// list_off[list] + member; the exclusive scan of the per-position counts is
+// both the sorted order's layout and each member's first pair (mstart).
+__global__ void pair_pos_kernel(const int64_t *__restrict__ cand, int64_t n,
+                                const int64_t *__restrict__ list_off, int32_t *__restrict__ ppos,
+                                int32_t *__restrict__ pmem, int32_t *__restrict__ cnt) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int64_t v = cand[e];
-  plist[e] = v < 0 ? nlist : (int32_t)(v >> 32);
-  pmem[e] = v < 0 ? 0 : (int32_t)(v & 0xffffffffll);
+  if (v < 0) {
+    ppos[e] = -1;
+    return;
+  }
+  const int m = (int)(v & 0xffffffffll);
+  const int32_t p = (int32_t)(list_off[v >> 32] + m);
+  ppos[e] = p;
+  pmem[e] = m;
+  atomicAdd(&cnt[p], 1);
 }
 
-// one CTA per list group: reorder that group's pairs by member index and
-// record where each member's pairs start (mstart, indexed like the lists'
-// member positions; mstart[N] = number of pairs before the padding group)
-__global__ void member_sort_kernel(const int64_t *__restrict__ goff, const int32_t *__restrict__ byl,
-                                   const int32_t *__restrict__ pmem,
-                                   const int64_t *__restrict__ list_off, int nlist,
-                                   int32_t *__restrict__ out, int32_t *__restrict__ mstart) {
-  extern __shared__ int hist[];
-  const int l = blockIdx.x;  // the padding group (l = nlist) is not reranked: not sorted
-  const int64_t lo = goff[l], hi = goff[l + 1];
-  const int nm = (int)(list_off[l + 1] - list_off[l]);
-  for (int i = threadIdx.x; i <= nm; i += blockDim.x) hist[i] = 0;
-  __syncthreads();
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&hist[pmem[byl[i]] + 1], 1);
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int i = 1; i <= nm; ++i) hist[i] += hist[i - 1];
-  __syncthreads();
-  for (int i = threadIdx.x; i < nm; i += blockDim.x) mstart[list_off[l] + i] = (int32_t)(lo + hist[i]);
-  if (l == 0 && threadIdx.x == 0) mstart[list_off[nlist]] = (int32_t)goff[nlist];
-  __syncthreads();  // every start is read before the scatter below advances it
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const int e = byl[i];
-    const int p = atomicAdd(&hist[pmem[e]], 1);
-    out[lo + p] = e;
-  }
+// order[cursor[p]++] = e for every kept pair (the order among one member's
+// pairs does not matter: each pair writes its own slot); npairs = the count
+__global__ void pair_scatter_kernel(const int32_t *__restrict__ ppos, int64_t n,
+                                    int32_t *__restrict__ cursor, int32_t *__restrict__ order,
+                                    const int32_t *__restrict__ mstart, int64_t N,
+                                    int64_t *__restrict__ npairs) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) *npairs = mstart[N];
+  if (e >= n) return;
+  const int32_t p = ppos[e];
+  if (p >= 0) order[atomicAdd(&cursor[p], 1)] = (int32_t)e;
 }
 
 // One CTA per (list, chunk of mc members): the chunk's member rows are read
@@ -234,26 +231,30 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
   const int64_t n = B * kr;
   if (n > INT32_MAX) return fail(ADANNS_ERR_ARG, "rerank slice too large");
   const int nlist = idx->nlist;
+  const int64_t N = idx->N;
   Scratch s(st);
-  int32_t *plist, *pmem, *byl, *order, *mstart;
-  int64_t *goff;
+  int32_t *ppos, *pmem, *order, *mstart, *cursor;
+  int64_t *npairs;
   uint64_t *keys;
   int rc;
-  if ((rc = s.get(&plist, n)) || (rc = s.get(&pmem, n)) || (rc = s.get(&byl, n)) ||
-      (rc = s.get(&order, n)) || (rc = s.get(&goff, (size_t)nlist + 2)) || (rc = s.get(&keys, n)) ||
-      (rc = s.get(&mstart, (size_t)idx->N + 1)))
+  if ((rc = s.get(&ppos, n)) || (rc = s.get(&pmem, n)) || (rc = s.get(&order, n)) ||
+      (rc = s.get(&keys, n)) || (rc = s.get(&mstart, (size_t)N + 1)) ||
+      (rc = s.get(&cursor, (size_t)N + 1)) || (rc = s.get(&npairs, 1)))
     return rc;
   {
     StageTimer t(ST_RR_SORT, st);
-    pair_lists_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, n, nlist, plist, pmem);
-    ADN_LAUNCH("pair_lists_kernel");
-    if ((rc = build_csr(plist, n, nlist + 1, goff, byl, st))) return rc;
-    const size_t hs = ((size_t)idx->max_list + 2) * 4;
-    ADN_CUDA(ensure_smem((const void *)member_sort_kernel, (size_t)(hs)));
-    member_sort_kernel<<<nlist, 256, hs, st>>>(goff, byl, pmem, idx->list_off, nlist, order, mstart);
-    ADN_LAUNCH("member_sort_kernel");
+    ADN_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (N + 1), st));
+    pair_pos_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, n, idx->list_off, ppos, pmem,
+                                                                  cursor);
+    ADN_LAUNCH("pair_pos_kernel");
+    if ((rc = launch_scan_i32(cursor, N + 1, mstart, st))) return rc;
+    ADN_CUDA(cudaMemcpyAsync(cursor, mstart, sizeof(int32_t) * (N + 1), cudaMemcpyDeviceToDevice,
+                             st));
+    pair_scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ppos, n, cursor, order, mstart,
+                                                                      N, npairs);
+    ADN_LAUNCH("pair_scatter_kernel");
   }
-  profile_count(PC_RERANK_PAIRS, goff + nlist, st);  // pairs left after pruning
+  profile_count(PC_RERANK_PAIRS, npairs, st);  // pairs left after pruning
   profile_count_host(PC_SHORTLIST_SLOTS, n);
   {
     StageTimer t(ST_RR_PAIRS, st);
