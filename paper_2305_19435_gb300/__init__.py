@@ -220,6 +220,18 @@ def index_create(db: torch.Tensor, centroids: torch.Tensor, assign: torch.Tensor
     return Index(h)
 
 
+def flat_index(db: torch.Tensor, metric: int = METRIC_L2_PREFIXNORM,
+               storage: int = STORE_F32) -> Index:
+    """Index whose single list holds every row.  IVF-OPQ search on it (d_c = 8,
+    nprobe = 1) is the exhaustive AdANNS-OPQ search of Sec. 4.2 (OPQ on the d_s
+    prefix, ADC over all N quantized vectors); the FP32 search is exact brute
+    force at d_s."""
+    _need(db, torch.float32, "db", 2)
+    cent = torch.zeros(1, 8, dtype=torch.float32, device=db.device)
+    assign = torch.zeros(db.shape[0], dtype=torch.int32, device=db.device)
+    return index_create(db, cent, assign, metric=metric, storage=storage)
+
+
 def kmeans_assign(points: torch.Tensor, centroids: torch.Tensor, dim: int,
                   metric: int = METRIC_L2_PREFIXNORM):
     """Nearest centroid of each point on the `dim` prefix -> (assign int32, dist f32)."""

@@ -249,8 +249,16 @@ int search_ivfopq_select(const adanns_index *idx, const float *queries, int64_t 
     }
     {
       StageTimer t(ST_ADC, st);
+      // few work items (few queries, or one long list as in the exhaustive
+      // search): split each list into member ranges so every SM has work
+      const int64_t tiles_est = (nb * nprobe + qa - 1) / qa;
+      const int64_t target = (int64_t)num_sms() * 4;
+      const int nsplit = tiles_est >= target
+                             ? 1
+                             : (int)std::min<int64_t>((target + tiles_est - 1) / tiles_est,
+                                                      ((int64_t)idx->max_list + 255) / 256);
       if ((rc = launch_adc_dist(idx->codes, idx->list_off, M, lut, tl, tb, tc, ntiles, counter + 1,
-                                pair_q, pair_out, pbase, cand, qa, st)))
+                                pair_q, pair_out, pbase, cand, qa, nsplit, st)))
         return rc;
     }
     {

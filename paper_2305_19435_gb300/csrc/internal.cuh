@@ -253,7 +253,7 @@ int adc_dist_query_tile(int M);
 int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const float *lut,
                     const int32_t *tl, const int32_t *tb, const int32_t *tc, const int *ntiles,
                     int *counter, const int32_t *pair_q, const int32_t *pair_out,
-                    const int64_t *pbase, uint32_t *cand, int qa, cudaStream_t st);
+                    const int64_t *pbase, uint32_t *cand, int qa, int nsplit, cudaStream_t st);
 int launch_select32(const uint32_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, const int32_t *list_ids, int64_t B, int kk,
                     uint64_t *out, cudaStream_t st);

@@ -601,6 +601,7 @@ struct AdcDistArgs {
   const int32_t *pair_q, *pair_out;
   const int64_t *pbase;     // candidate segment start of each pair
   uint32_t *cand;           // FP32 distance bits
+  int nsplit;               // member ranges per tile (work items = tiles x nsplit)
 };
 
 constexpr int AD_THREADS = 256;
@@ -636,12 +637,13 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
   __shared__ int64_t s_pb[AD_MAXQA];
   __shared__ int s_tile;
   const int tid = threadIdx.x;
-  const int ntiles = *a.ntiles_dev;
+  const int nitems = *a.ntiles_dev * a.nsplit;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(a.counter, 1);
     __syncthreads();
-    const int tile = s_tile;
-    if (tile >= ntiles) break;
+    const int item = s_tile;
+    if (item >= nitems) break;
+    const int tile = item / a.nsplit, range = item - tile * a.nsplit;
     const int list = a.tile_list[tile], beg = a.tile_beg[tile], cnt = a.tile_cnt[tile];
     const int ng = (cnt + G - 1) / G;
     if (tid < cnt) {
@@ -669,7 +671,11 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
     const int64_t off = a.list_off[list];
     const int nl = (int)(a.list_off[list + 1] - off);
     const int npad = (nl + 7) & ~7;
-    for (int m0 = 0; m0 < npad; m0 += AD_THREADS) {
+    // this item's chunks of AD_THREADS members: range `range` of nsplit
+    const int nch = (npad + AD_THREADS - 1) / AD_THREADS;
+    const int cper = (nch + a.nsplit - 1) / a.nsplit;
+    const int m_end = min(npad, min(nch, (range + 1) * cper) * AD_THREADS);
+    for (int m0 = range * cper * AD_THREADS; m0 < m_end; m0 += AD_THREADS) {
       const int mem = m0 + tid;
       if (mem < nl) {
         const uint8_t *cp = a.codes + (off + mem) * (int64_t)M;
@@ -738,8 +744,9 @@ int adc_dist_query_tile(int M) {
 int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const float *lut,
                     const int32_t *tl, const int32_t *tb, const int32_t *tc, const int *ntiles,
                     int *counter, const int32_t *pair_q, const int32_t *pair_out,
-                    const int64_t *pbase, uint32_t *cand, int qa, cudaStream_t st) {
+                    const int64_t *pbase, uint32_t *cand, int qa, int nsplit, cudaStream_t st) {
   AdcDistArgs a{};
+  a.nsplit = nsplit < 1 ? 1 : nsplit;
   a.codes = codes;
   a.list_off = list_off;
   a.M = M;

@@ -266,3 +266,47 @@ def test_adc_select_tie_rule(A, dup_case, nprobe, k, kr):
         n, fails = check_topk(ai, ad, orr["ids"], orr["dist"], k, skip_rows=amb)
         assert not fails, f"{len(fails)}/{n}: {fails[:2]}"
     g.free()
+
+
+@pytest.mark.parametrize("d_s,M,opq_iters", [(64, 16, 3), (32, 8, 3), (96, 32, 2), (64, 16, 0),
+                                             (48, 8, 0)])
+def test_flat_opq_exhaustive_parity(A, case, d_s, M, opq_iters):
+    """Exhaustive AdANNS-OPQ (Sec. 4.2: OPQ on the d_s prefix, ADC over every
+    quantized vector) as IVF-OPQ over an index with one list; opq_iters = 0 is
+    plain PQ (identity rotation).  Against the oracle's ADC over the same
+    one-list index and the same codes, at byte budgets 8 to 32."""
+    data = case["data"]
+    db, q = data["db"], data["queries"]
+    N = db.shape[0]
+    opq = oracle.train_opq(db, d_s, M, opq_iters, 3, 5, 4000, seed=21)
+    if opq_iters == 0:
+        assert np.array_equal(opq["R"], np.eye(d_s, dtype=np.float32))
+    codes = oracle.pq_encode(db, d_s, M, opq["R"], opq["codebooks"])
+    one = {"centroids": np.zeros((1, 8), np.float32), "list_off": np.array([0, N], np.int64),
+           "list_ids": np.arange(N, dtype=np.int32), "assign": np.zeros(N, np.int32),
+           "metric": PN}
+    g = A.flat_index(cu(db))
+    A.set_opq(g, d_s, M, cu(opq["R"]), cu(opq["codebooks"]), cu(codes))
+    for k in (10, 100):
+        gi, gd = A.search_ivfopq(g, cu(q), 8, 1, k)
+        orr = oracle.search_ivfopq(db, one, opq, codes, q, 8, 1, k + 40)
+        n, fails = check_topk(gi.cpu().numpy(), gd.cpu().numpy(), orr["ids"], orr["dist"], k)
+        assert n == len(q)
+        assert not fails, f"{len(fails)}/{n}: {fails[:2]}"
+    g.free()
+
+
+def test_flat_index_fp32_is_brute_force(A, case):
+    """The FP32 search over the one-list index is exact brute force at d_s."""
+    data = case["data"]
+    db, q = data["db"], data["queries"][:64]
+    N = db.shape[0]
+    one = {"centroids": np.zeros((1, 8), np.float32), "list_off": np.array([0, N], np.int64),
+           "list_ids": np.arange(N, dtype=np.int32), "assign": np.zeros(N, np.int32),
+           "metric": PN}
+    g = A.flat_index(cu(db))
+    gi, gd = A.search_ivf(g, cu(q), 8, 64, 1, 20)
+    exact = oracle.search_ivf(db, one, q, 8, 64, 1, 40)   # one list: brute force
+    n, fails = check_topk(gi.cpu().numpy(), gd.cpu().numpy(), exact["ids"], exact["dist"], 20)
+    assert n == len(q) and not fails, fails[:2]
+    g.free()
