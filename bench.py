@@ -68,6 +68,8 @@ def parse():
                    help="recall and distance error of every tier vs the FP64 oracle per "
                         "(d_c, d_s, nprobe) on a query sample, instead of the timed run")
     p.add_argument("--sweep-queries", type=int, default=500)
+    p.add_argument("--flat-opq", action="store_true",
+                   help="exhaustive AdANNS-OPQ byte-budget sweep on the ImageNet-shaped data")
     p.add_argument("--ivfopq", action="store_true",
                    help="IVF-OPQ on the NQ-shaped workload (build, QPS per (d_s, M, nprobe), "
                         "recall@10 against exact search on a query sample) instead of the timed run")
@@ -472,6 +474,61 @@ def ivfopq_bench(args):
                                           "(numpy over the whole database)"}))
 
 
+def flat_opq_bench(args):
+    """Exhaustive AdANNS-OPQ at byte budgets 8-64 (Sec. 4.2; the exact-search
+    OPQ table of the appendix): OPQ on the d_s prefix of the ImageNet-shaped
+    database, ADC over all N codes for every query (a one-list index), recall@10
+    against exact search at the same d_s."""
+    import torch
+    import paper_2305_19435_gb300 as P
+    P.build()
+    w = synthdata.WORKLOADS["imagenet"]
+    N = args.n or w.N
+    B = args.b or 10_000
+    data = synthdata.make("imagenet", n=N, b=B)
+    db_dev = torch.from_numpy(data["db"]).cuda()
+    q = torch.from_numpy(data["queries"]).cuda()
+    g = P.flat_index(db_dev)
+    S = min(args.gt_queries, B)
+    st = torch.cuda.current_stream()
+    rows = []
+    for d_s in (128, 512, 2048):
+        gt = exact_topk_prefixnorm(data["db"], data["queries"][:S], d_s, 10)
+        for M, opq_iters in ((8, 5), (16, 5), (32, 5), (64, 5), (16, 0)):
+            tb = time.time()
+            P.build_opq(g, db_dev, d_s, M, opq_iters, 4, 20, min(N, 65536), args.seed + 7)
+            torch.cuda.synchronize()
+            build_s = time.time() - tb
+            ids = torch.empty(B, 10, dtype=torch.int64, device="cuda")
+            dd = torch.empty(B, 10, dtype=torch.float32, device="cuda")
+
+            def step(ids=ids, dd=dd):
+                P.search_ivfopq(g, q, 8, 1, 10, out=(ids, dd))
+
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            ms, launches, prof = timed(P, torch, step, args.steps, st)
+            gi = ids[:S].cpu().numpy()
+            rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / 10.0
+                                 for a, b in zip(gi, gt)]))
+            adc_ms = prof.get("adc", (0.0, 1))[0] / args.steps
+            row = {"d_s": d_s, "bytes": M, "rotation": "OPQ" if opq_iters else "PQ (identity)",
+                   "qps": B / (ms / 1e3), "ms_per_step": ms,
+                   "lookups_per_s": B * N * M / (adc_ms / 1e3) if adc_ms else None,
+                   "stages_ms": {k2: v[0] / args.steps for k2, v in prof.items()},
+                   "recall10_vs_exact": rec, "build_s": build_s, "gpu_launches": launches}
+            rows.append(row)
+            log(json.dumps(row))
+    g.free()
+    print(json.dumps({"flat_opq": rows,
+                      "workload": f"exhaustive AdANNS-OPQ, ImageNet-shaped: N={N:,} d=2048 B={B:,} "
+                                  f"k=10 (one list, every code scanned per query)",
+                      "recall_sample": S,
+                      "recall_reference": "exact top-10 by L2 on normalised d_s prefixes "
+                                          "(numpy over the whole database)"}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -482,6 +539,9 @@ def main():
         return
     if args.ivfopq:
         ivfopq_bench(args)
+        return
+    if args.flat_opq:
+        flat_opq_bench(args)
         return
     import torch
     import torch.distributed as dist
