@@ -58,16 +58,15 @@ __device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, SwState
 
 // The kk smallest of n keys into o[0, kk) (any order): key(i), database
 // entry id(i), candidate position pos(i).  kq > 0: winners above the kq-th
-// smallest key + prune_delta become -1.  When the keys are not in position
-// order (ORDERED false) and more than SW_TIE tie at the cut, nothing is
-// written and false is returned.
+// smallest key + prune_delta become -1.  Keys equal to the cut are taken by
+// ascending position: a warp sort of up to SW_TIE of them, else a prefix count
+// (keys in position order) or a radix select on their positions.
 template <bool ORDERED, class KeyF, class IdF, class PosF>
 __device__ __forceinline__ bool warp_select16(int n, int kk, int kq, int prune_delta, KeyF key, IdF id, PosF pos,
                               int64_t *o, SwState &s) {
   const int lane = threadIdx.x & 31;
   int below, neq;
   const uint32_t T = warp_kth16(n, kk, key, s, below, neq);
-  if (!ORDERED && neq > SW_TIE) return false;
   uint32_t keep_max = 0xFFFFFFFFu;
   if (kq > 0) {
     int b2, n2;
@@ -91,7 +90,7 @@ __device__ __forceinline__ bool warp_select16(int n, int kk, int kq, int prune_d
     warp_sort(s.h.ties, neq);
     for (int j = lane; j < need_eq; j += 32)
       o[below + j] = T <= keep_max ? id((int)(uint32_t)(s.h.ties[j] & 0xffffffffu)) : -1;
-  } else {
+  } else if (ORDERED) {
     // many ties, keys in position order: rank them with warp prefix counts
     int base = 0;
     for (int i0 = 0; i0 < n && base < need_eq; i0 += 32) {
@@ -102,6 +101,20 @@ __device__ __forceinline__ bool warp_select16(int n, int kk, int kq, int prune_d
       if (eq && before < need_eq) o[below + before] = T <= keep_max ? id(i) : -1;
       base += __popc(b);
     }
+  } else {
+    // many ties, keys not in position order: the need_eq-th smallest position
+    // among them (positions are distinct) bounds the ones taken
+    int b2, n2;
+    const uint32_t posT = warp_radix_kth<4>(
+        n, need_eq, [&](int i) -> uint32_t { return key(i) == T ? (uint32_t)pos(i) : 0xFFFFFFFFu; },
+        s.h.hist, s.sh, b2, n2);
+    if (lane == 0) s.ecnt = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32)
+      if (key(i) == T && (uint32_t)pos(i) <= posT) {
+        const int p = atomicAdd(&s.ecnt, 1);
+        if (p < need_eq) o[below + p] = T <= keep_max ? id(i) : -1;
+      }
   }
   __syncwarp();
   return true;
