@@ -695,8 +695,8 @@ def main():
     # DRAM bytes (read + write) per launch from one ncu capture of the default
     # ImageNet-shaped bf16 step (profiles/mixed_bf16_imagenet_dram.md); reported
     # only for that workload, and to be removed whenever the kernel changes
-    traffic_table = {("bf16", "mma"): 2.434184960e9 + 2.332152576e9,
-                     ("bf16", "rerank"): 6.532207104e9 + 0.150063616e9}
+    traffic_table = {("bf16", "mma"): 2.434706432e9 + 2.332016640e9,
+                     ("bf16", "rerank"): 6.525888768e9 + 0.149626880e9}
     default_wl = (args.workload == "imagenet" and N == w.N and B == w.B and args.d_c == 32
                   and args.d_s == 512 and args.nprobe == 16 and args.k == 100
                   and args.nlist == 1024)
