@@ -158,6 +158,30 @@ def test_shortlist_ties_are_deterministic(A, storage):
     g.free()
 
 
+@pytest.mark.parametrize("kr", [40, 200])
+def test_shortlist_ties_inside_the_survivor_buffer(A, kr):
+    """300 identical rows (one list), queries equal to them: the shortlist cut
+    falls inside a group of 300 equal keys that all fit the survivor buffer
+    (more than its 128-entry tie sort), so the ties are ranked by a radix select
+    on their candidate positions.  The smallest positions are the smallest ids
+    of the group, so the result is the exact FP32 search's, run after run."""
+    data = synthdata.small(20_000, 64, 128, 32, 411)
+    db = data["db"].copy()
+    db[8000:8300] = db[8000]
+    q = np.repeat(db[8000:8001] * np.float32(1.25), 16, axis=0)
+    o = oracle.build_ivf(db, 32, 24, 5, 20_000, seed=29)
+    g = A.index_create(cu(db), cu(o["centroids"]), cu(o["assign"].astype(np.int32)),
+                       storage=1 | BF16)
+    args = (32, 128, 4, 10)
+    i1, d1 = A.search_ivf(g, cu(q), *args, storage=BF16, rerank_k=kr)
+    i2, _ = A.search_ivf(g, cu(q), *args, storage=BF16, rerank_k=kr)
+    ie, de = A.search_ivf(g, cu(q), *args)                       # exact FP32 scan
+    assert torch.equal(i1, i2)
+    assert torch.equal(i1, ie)
+    assert np.array_equal(i1[0].cpu().numpy(), np.arange(8000, 8010))
+    g.free()
+
+
 @pytest.mark.parametrize("storage,d_s,nprobe,k,kr", [(BF16, 256, 8, 100, 400), (BF16, 128, 12, 10, 40),
                                                     (BF16, 64, 4, 1, 2048), (FP8, 256, 8, 100, 400),
                                                     (FP8, 128, 6, 10, 40)])
