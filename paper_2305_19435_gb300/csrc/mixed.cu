@@ -465,18 +465,9 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     }
     {
       StageTimer t(ST_RERANK, st);
-      // the rerank gathers one query row per pair: slices of queries whose
-      // rows take about 40 MB stay resident in L2 next to the streamed member
-      // rows (each slice reads the member rows it needs again)
-      const int64_t qbytes = nb * (int64_t)dsp * 4;
-      const int64_t nsl = std::max<int64_t>(1, (qbytes + (40ll << 20) - 1) / (40ll << 20));
-      const int64_t sq = (nb + nsl - 1) / nsl;
-      for (int64_t s0 = 0; s0 < nb; s0 += sq) {
-        const int64_t ns = std::min(sq, nb - s0);
-        if ((rc = launch_rerank_lists(cids + s0 * kk, kk, ns, qs + s0 * dsp, dsp, d_s, idx, mscale,
-                                      k, out_ids + (b0 + s0) * k, out_dist + (b0 + s0) * k, st)))
-          return rc;
-      }
+      if ((rc = launch_rerank_lists(cids, kk, nb, qs, dsp, d_s, idx, mscale, k, out_ids + b0 * k,
+                                    out_dist + b0 * k, st)))
+        return rc;
     }
   }
   // a timed-out tensor-core pipeline sets the index's sticky status word,
