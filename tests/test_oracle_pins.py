@@ -271,6 +271,32 @@ def test_adc_is_distance_to_reconstruction():
         assert np.all(np.diff(res["dist"][i]) >= 0)
 
 
+@pytest.mark.parametrize("opq_iters", [2, 0])
+def test_one_list_ivfopq_is_exhaustive_adc(opq_iters):
+    """Exhaustive AdANNS-OPQ (Sec. 4.2: ADC over every quantized vector) read as
+    IVF-OPQ over an index with one list: the oracle's result is the full ADC
+    ranking of every row by (||z_q - decode(code_x)||^2, id), computed here from
+    the reconstructions.  opq_iters = 0 is plain PQ: the rotation stays I."""
+    data = synthdata.small(900, 10, 32, 6, 35)
+    db, q = data["db"], data["queries"]
+    N = db.shape[0]
+    opq = oracle.train_opq(db, 24, 6, opq_iters, 2, 3, 900, seed=8)
+    if opq_iters == 0:
+        assert np.array_equal(opq["R64"], np.eye(24))
+    codes = oracle.pq_encode(db, 24, 6, opq["R"], opq["codebooks"])
+    one = {"centroids": np.zeros((1, 8), np.float32), "list_off": np.array([0, N], np.int64),
+           "list_ids": np.arange(N, dtype=np.int32), "assign": np.zeros(N, np.int32),
+           "metric": PN}
+    res = oracle.search_ivfopq(db, one, opq, codes, q, 8, 1, 25)
+    Zq = oracle.prefix(q, 24) @ opq["R"].astype(np.float64)
+    rec = oracle.pq_decode(codes, opq["codebooks"].astype(np.float64))
+    for i in range(len(q)):
+        dd = ((Zq[i][None] - rec) ** 2).sum(1)
+        order = np.lexsort((np.arange(N), dd))[:25]
+        assert np.array_equal(res["ids"][i], order)
+        assert np.allclose(res["dist"][i], dd[order], rtol=1e-12, atol=1e-14)
+
+
 def test_small_training_set_makes_adc_exact():
     """With at most 256 training points each point is its own codeword and
     the Procrustes factor of the SPD matrix Y^T Y is I, so ADC on the training
