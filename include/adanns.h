@@ -121,6 +121,9 @@ int adanns_build_ivf(const float *db, int64_t N, int d, int d_c, int nlist, int 
  *   db         N x d FP32 (device), centroids nlist x d_c FP32 (device),
  *   assign     N int32 in [0, nlist) (device).
  * Members of each list are ordered by ascending id.  Synchronises the stream.
+ * With nlist = 1 (one list holding every row) a search with nprobe = 1 is
+ * exhaustive: adanns_search_ivfopq is then the exhaustive AdANNS-OPQ search of
+ * Sec. 4.2 (ADC over every code) and adanns_search_ivf brute force at d_s.
  */
 int adanns_index_create(const float *db, int64_t N, int d, const float *centroids, int nlist,
                         int d_c, const int32_t *assign, int metric, int storage_mask,
