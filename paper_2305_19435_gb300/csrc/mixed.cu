@@ -422,13 +422,8 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
                                      pair_out, tl, tb, tc, ntiles,
                                      out_probes ? out_probes + b0 * nprobe : nullptr, st)))
         return rc;
-      const unsigned g = (unsigned)((nb + 255) / 256);
-      cand_count_kernel<<<g, 256, 0, st>>>(ckeys, nb, nprobe, idx->list_off, qtot);
-      ADN_LAUNCH("cand_count_kernel");
-      scan64_kernel<<<1, 1024, 0, st>>>(qtot, nb, qbase, nullptr);
-      ADN_LAUNCH("scan64_kernel");
-      cand_base_kernel<<<g, 256, 0, st>>>(ckeys, nb, nprobe, idx->list_off, qbase, pbase);
-      ADN_LAUNCH("cand_base_kernel");
+      if ((rc = launch_cand_segments(ckeys, nb, nprobe, idx->list_off, qtot, qbase, pbase, st)))
+        return rc;
       gather_qtiles_kernel<<<dim3((unsigned)max_tiles, nkb), 256, 0, st>>>(qlow, nkb, tb, tc,
                                                                            ntiles, pair_q, qtile);
       ADN_LAUNCH("gather_qtiles_kernel");
