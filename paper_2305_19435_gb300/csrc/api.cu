@@ -508,21 +508,10 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
         return rc;
     }
     // cluster mapping: nprobe nearest centroids at d_c
-    ScanArgs c{};
-    c.xpm = idx->cent_pm;
-    c.d_pad = idx->dc_pad;  // stored centroid width; d_c <= built d_c (IVF-D)
-    c.dims = d_c;
-    c.list_off = idx->cent_off;
-    c.qn = qc;
-    c.ldq = dcp;
-    c.nq = (int)nb;
-    c.counter = counter;
-    c.k = nprobe;
-    c.out_keys = ckeys;
     ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
     {
       StageTimer t(ST_COARSE, st);
-      if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, c, st))) return rc;
+      if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, counter, st))) return rc;
     }
     {
       StageTimer t(ST_INVERT, st);

@@ -607,10 +607,24 @@ int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t 
 }
 
 int run_coarse(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
-               uint64_t *out, const ScanArgs &c, cudaStream_t st) {
+               uint64_t *out, int *counter, cudaStream_t st) {
   int rc = launch_coarse_tc(idx, qc, ldq, B, d_c, k, out, st);
   if (rc == 1) rc = launch_coarse(idx->centroids, idx->d_c, idx->nlist, d_c, qc, ldq, B, k, out, st);
-  if (rc == 1) rc = launch_scan_f32(c, st);
+  if (rc == 1) {
+    // the general scan over the prefix-major centroid table (one list)
+    ScanArgs c{};
+    c.xpm = idx->cent_pm;
+    c.d_pad = idx->dc_pad;  // stored centroid width; d_c <= built d_c (IVF-D)
+    c.dims = d_c;
+    c.list_off = idx->cent_off;
+    c.qn = qc;
+    c.ldq = ldq;
+    c.nq = (int)B;
+    c.counter = counter;
+    c.k = k;
+    c.out_keys = out;
+    rc = launch_scan_f32(c, st);
+  }
   return rc;
 }
 

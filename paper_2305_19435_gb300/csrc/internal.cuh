@@ -221,12 +221,14 @@ int launch_coarse(const float *cent, int ldc, int nlist, int d_c, const float *q
 // the query and centroid prefixes shortlist every centroid that can be among
 // the k nearest (a bound on the quantisation error), which are then scored
 // exactly in FP32 as above.  Returns 1, launching nothing, when the index has
-// no BF16 centroid copy, has fewer than 256 lists, or k > 32.
+// no BF16 centroid copy, has fewer than 256 lists, d_c > 64, k > 1024, or
+// k > 32 with more than 16,384 lists.
 int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
                      uint64_t *out, cudaStream_t st);
-// Both, in order of preference, then the general scan kernel with `c`.
+// Both, in order of preference, then the general scan over the prefix-major
+// centroid table (counter: the scan's work counter, zeroed by the caller).
 int run_coarse(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
-               uint64_t *out, const ScanArgs &c, cudaStream_t st);
+               uint64_t *out, int *counter, cudaStream_t st);
 int build_centroid_lowp(adanns_index *x, cudaStream_t st);
 // Candidate segments of a batch: per query, the probed lists' sizes rounded
 // up to 8, laid end to end (qtot: per-query total, qbase: its start, pbase:
