@@ -74,6 +74,8 @@ def parse():
                    help="IVF-OPQ on the NQ-shaped workload (build, QPS per (d_s, M, nprobe), "
                         "recall@10 against exact search on a query sample) instead of the timed run")
     p.add_argument("--gt-queries", type=int, default=100)
+    p.add_argument("--no-largest", action="store_true",
+                   help="skip the largest grid point (d_c = 64, d_s = 2048, nprobe = 32)")
     return p.parse_args()
 
 
@@ -209,6 +211,44 @@ def run_reference(args):
     }))
 
 
+# ---------------------------------------------------------------- DRAM traffic records
+KERNEL_SOURCES = {"mma_scan_kernel": ["mma_scan.cu"],
+                  "rerank_chunks_kernel": ["rerank_lists.cu"],
+                  "scan_f32_kernel": ["scan_f32.cu"],
+                  "dist_f32_kernel": ["stream_f32.cu"],
+                  "adc_dist_kernel": ["opq.cu"]}
+
+
+def kernel_source_hash(kernel):
+    """sha1 (first 16 hex digits) of the source files that define `kernel`."""
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, "paper_2305_19435_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel, mode, workload_key):
+    """DRAM bytes (read + write) per launch of `kernel` from a committed ncu
+    summary under profiles/ (a line `traffic-record: kernel=... mode=...
+    workload=... src_sha1=... bytes_per_launch=...`), used only when it was
+    captured on this workload from the current source of the kernel; else
+    None, so a stale capture is never reported."""
+    import glob
+    want = kernel_source_hash(kernel)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                line = line.strip().strip("`")
+                if not line.startswith("traffic-record:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                if (kv.get("kernel") == kernel and kv.get("mode") == mode
+                        and kv.get("workload") == workload_key and kv.get("src_sha1") == want):
+                    return float(kv["bytes_per_launch"])
+    return None
+
+
 # ---------------------------------------------------------------- GPU arm
 MODES = {"f32": (1, 0), "bf16": (2, 4), "fp8": (4, 4)}   # storage code, rerank multiple of k
 
@@ -322,10 +362,56 @@ def scan_hbm_phase(P, torch, idx, q, oidx, args, hbm_peak, modes):
             t = prof.get(stage, (0.0, 1))[0] / 10
             gbs = int(sizes.sum()) * per_member / (t / 1e3) / 1e9 if t else None
             f32_kernel = ("dist_f32_kernel (streaming scan)"
-                          if os.environ.get("ADANNS_FP32_STREAM", "1") != "0" else "scan_f32_kernel")
+                          if P.get_option(P.OPT_FP32_STREAM) else "scan_f32_kernel")
             out[f"{mode}_ds{d_s}"] = {"kernel": f32_kernel if mode == "f32" else "mma_scan_kernel",
                                       "kernel_ms": t, "step_ms": ms, "achieved_gbs": gbs,
                                       "frac_of_hbm": gbs / hbm_peak if gbs else None}
+    return out
+
+
+def largest_point_phase(P, torch, data, idx, oidx, q, args, N, B, modes, peaks):
+    """The largest point of the ImageNet-shaped grid (d_c = 64, d_s = 2048,
+    nprobe = 32, k = 100) on an index clustered at d_c = 64, every mode timed
+    over the full batch, recall@10 against the oracle on a query sample."""
+    import oracle
+    d_c, d_s, nprobe, k = 64, 2048, 32, args.k
+    steps = max(3, args.steps // 2)
+    _, _, probes = P.search_ivf(idx, q, d_c, d_s, nprobe, k, return_probes=True)
+    pairs = int(np.diff(oidx["list_off"])[probes.cpu().numpy()].sum())
+    S = min(200, B)
+    ref = oracle.search_ivf(data["db"], oidx, data["queries"][:S], d_c, d_s, nprobe, k)
+    out = {"workload": f"AdANNS-IVF {args.workload}-shaped: N={N:,} d=2048 B={B:,} "
+                       f"nlist={args.nlist} d_c={d_c} d_s={d_s} nprobe={nprobe} k={k} "
+                       "(largest point of the grid)", "pairs_per_step": pairs,
+           "recall_sample": S}
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    for mode in modes:
+        code, mult = MODES[mode]
+        ids = torch.empty(B, k, dtype=torch.int64, device="cuda")
+        dd = torch.empty(B, k, dtype=torch.float32, device="cuda")
+
+        def step(ids=ids, dd=dd, code=code, rr=mult * k):
+            P.search_ivf(idx, q, d_c, d_s, nprobe, k, storage=code, rerank_k=rr, out=(ids, dd))
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        ms, launches, prof = timed(P, torch, step, steps, torch.cuda.current_stream())
+        sm = {k2: v[0] / steps for k2, v in prof.items()}
+        gi = ids[:S].cpu().numpy()
+        rec = float(np.mean([len(set(a[:10].tolist()) & set(b[:10].tolist())) / 10.0
+                             for a, b in zip(gi, ref["ids"])]))
+        row = {"qps": B / (ms / 1e3), "ms_per_step": ms, "stages_ms": sm,
+               "recall_at_10_vs_oracle": rec, "gpu_launches": launches}
+        if mode != "f32" and sm.get("mma"):
+            peak = bf16_peak * (2.0 if mode == "fp8" else 1.0)
+            ach = 2.0 * pairs * d_s / (sm["mma"] / 1e3) / 1e12
+            row["mma_tflops"] = ach
+            row["mma_frac_of_peak"] = ach / peak
+        elif mode == "f32" and sm.get("scan"):
+            row["scan_tflops"] = 4.0 * pairs * d_s / (sm["scan"] / 1e3) / 1e12
+        out[mode] = row
+        log(json.dumps({"largest_point": mode, **row}))
     return out
 
 
@@ -603,6 +689,14 @@ def main():
         torch.cuda.synchronize()
         gpu_build_s = time.time() - tb
         gidx.free()
+    big = None
+    if not args.no_largest:
+        a64 = argparse.Namespace(**{**vars(args), "d_c": 64})
+        oidx64 = oracle_index(data, a64, N)
+        idx64 = P.index_create(db_dev, torch.from_numpy(oidx64["centroids"]).cuda(),
+                               torch.from_numpy(oidx64["assign"].astype(np.int32)).cuda(),
+                               storage=storage)
+        big = (idx64, oidx64)
     serving = None
     if args.serve_seconds > 0 and world == 1:
         serving = serving_phase(P, torch, data, db_dev, args, B)
@@ -692,17 +786,12 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     ffma_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
-    # DRAM bytes (read + write) per launch from one ncu capture of the default
-    # ImageNet-shaped bf16 step (profiles/mixed_bf16_imagenet_dram.md); reported
-    # only for that workload, and to be removed whenever the kernel changes
-    traffic_table = {("bf16", "mma"): 2.434706432e9 + 2.332016640e9,
-                     ("bf16", "rerank"): 6.525888768e9 + 0.149626880e9}
-    default_wl = (args.workload == "imagenet" and N == w.N and B == w.B and args.d_c == 32
-                  and args.d_s == 512 and args.nprobe == 16 and args.k == 100
-                  and args.nlist == 1024)
+    wl_key = (f"{args.workload}-N{N}-B{B}-nlist{args.nlist}-dc{args.d_c}-ds{args.d_s}"
+              f"-np{args.nprobe}-k{args.k}")
 
     def traffic(mode, kern):
-        return traffic_table.get((mode, kern)) if default_wl else None
+        return traffic_record({"mma": "mma_scan_kernel", "rerank": "rerank_chunks_kernel"}[kern],
+                              mode, wl_key)
 
     rooflines = {}
     for mode, r in results.items():
@@ -712,7 +801,9 @@ def main():
             ach = 4.0 * pairs * args.d_s / (t / 1e3) / 1e12
             rooflines[mode] = {"kernel": "scan_f32_kernel (list scan)", "bound": "alu",
                                "achieved": ach, "peak": ffma_peak, "unit": "TFLOP/s",
-                               "frac": ach / ffma_peak, "traffic": None, "kernel_ms": t,
+                               "frac": ach / ffma_peak,
+                               "traffic": traffic_record("scan_f32_kernel", "f32", wl_key),
+                               "kernel_ms": t,
                                "peak_source": f"derived FP32 FFMA peak: {sm_count} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz"}
         else:
             t = sm.get("mma", 0.0)
@@ -741,6 +832,12 @@ def main():
                 "note": "algorithmic bytes = (N + B) x d_s x 4: each database and query row "
                         "once; the query rows are gathered once per pair from L2"}
     scan_hbm = scan_hbm_phase(P, torch, idx, q, oidx, args, hbm_peak, list(results))
+    largest = None
+    if big is not None:
+        largest = largest_point_phase(P, torch, data, big[0], big[1], q, args, N, B,
+                                      list(results), peaks)
+        big[0].status()
+        big[0].free()
     main_roof = dict(rooflines[args.mode])
     # the dominant kernel of the step (largest stage) carries the headline roofline
     main_stages = main_r["stages_ms"]
@@ -766,6 +863,7 @@ def main():
            "graph_replay": {"ms_per_step": graph_ms, "qps": world * B / (graph_ms / 1000.0)},
            "serving": serving,
            "scan_hbm_regime": scan_hbm,
+           "largest_point": largest,
            "p50_ms": (serving or {}).get(args.mode, {}).get("p50_ms"),
            "p99_ms": (serving or {}).get(args.mode, {}).get("p99_ms"),
            "gpu_build_s": gpu_build_s, "index_layout_s": layout_s, "pairs_per_step": pairs,

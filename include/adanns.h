@@ -70,6 +70,51 @@ int adanns_version(void);
 int64_t adanns_launch_count(void);
 
 /*
+ * Runtime options (process-wide, every device; host-side, no device access).
+ * They select among kernels that compute the same result, bound scratch and
+ * waits, and hold test hooks.  The first call of any entry point seeds the
+ * first five from the environment variables ADANNS_FP32_STREAM,
+ * ADANNS_ADC_SELECT, ADANNS_COARSE_TC, ADANNS_RERANK_PRUNE ("0" turns the
+ * feature off) and ADANNS_SCRATCH_GB (GiB); nothing reads the environment
+ * after that.  A change applies to calls issued after it; a search plan keeps
+ * what it captured.
+ *   ADANNS_OPT_FP32_STREAM    1 (default): streaming FP32 scan where few
+ *                             queries share a probed list; 0: tiled scan always
+ *   ADANNS_OPT_ADC_SELECT     1 (default): IVF-OPQ distance-then-select stage
+ *                             for nprobe <= 256; 0: running top-k per list
+ *   ADANNS_OPT_COARSE_TC      1 (default): tensor-core cluster mapping where it
+ *                             applies; 0: FP32 kernels only
+ *   ADANNS_OPT_RERANK_PRUNE   1 (default): certified pruning of the shortlist
+ *                             before the exact rerank; 0: rerank all of it
+ *   ADANNS_OPT_SCRATCH_BYTES  scratch one search call may hold (default
+ *                             12 GiB, at least 1 MiB); larger batches are sliced
+ *   ADANNS_OPT_WAIT_LIMIT_NS  bound of every tensor-core pipeline wait
+ *                             (default 2e9 ns, within [1e5, 6e10]); a wait that
+ *                             runs out is reported by adanns_index_status
+ *   ADANNS_OPT_TEST_SKIP_LOAD test hook, -1 (default).  n >= 0 makes the next
+ *                             tensor-core scan launch (one launch; the option
+ *                             then returns to -1) leave out stage load n (in
+ *                             member-tile, K-block order) of its work item 0 --
+ *                             no copy and no arrival -- so that the MMA
+ *                             issuer's bounded wait runs out and the timeout
+ *                             path runs (nothing happens when item 0 has fewer
+ *                             loads).  That call's results are invalid.  Never
+ *                             needed outside tests.
+ * adanns_set_option returns ADANNS_ERR_ARG for an unknown option or a value
+ * out of range (the option keeps its value).
+ */
+#define ADANNS_OPT_FP32_STREAM 0
+#define ADANNS_OPT_ADC_SELECT 1
+#define ADANNS_OPT_COARSE_TC 2
+#define ADANNS_OPT_RERANK_PRUNE 3
+#define ADANNS_OPT_SCRATCH_BYTES 4
+#define ADANNS_OPT_WAIT_LIMIT_NS 5
+#define ADANNS_OPT_TEST_SKIP_LOAD 6
+#define ADANNS_OPT_COUNT 7
+int adanns_set_option(int option, int64_t value);
+int adanns_get_option(int option, int64_t *value);
+
+/*
  * Stage timing (diagnostics).  adanns_profile_enable(1) starts recording a
  * CUDA event pair, on the call's stream, around each stage of every search
  * (0 query prep, 1 cluster mapping, 2 probe inversion, 3 list scan, 4 merge,
@@ -347,11 +392,16 @@ void adanns_plan_free(adanns_plan *plan);
  * whose framework has reserved the whole device memory budget for its own
  * pool, latency-critical loops where an allocator call that may synchronise
  * or grow a pool is not acceptable, or hosts whose policy forbids the library
- * from using the allocator.  It computes exactly what adanns_search_ivf
- * computes with storage = ADANNS_STORE_F32 and rerank_k = 0, with the same
- * arguments, layouts and error codes, but takes all scratch from one fixed
- * file-scope device array of ADANNS_NOALLOC_SCRATCH_BYTES.  It calls no
- * cudaMalloc, cudaFree or allocating routine.
+ * from using the allocator.  It runs the FP32 search of adanns_search_ivf
+ * (storage = ADANNS_STORE_F32, rerank_k = 0) with the same arguments, layouts
+ * and error codes, but takes all scratch from one fixed file-scope device
+ * array of ADANNS_NOALLOC_SCRATCH_BYTES.  It calls no cudaMalloc, cudaFree or
+ * allocating routine.  It always takes the FP32 cluster mapping and the tiled
+ * list scan with the default work shape (never the tensor-core cluster
+ * mapping, the streaming scan, an autotuned shape or member-range splits), so
+ * its results agree with adanns_search_ivf's within the FP32 tolerance of the
+ * oracle comparison: distances within 1e-5 relative, ids equal except inside
+ * groups of distances that tie within that tolerance.
  *
  * Scratch needed, each piece rounded up to 256 bytes:
  *   B*pad16(d_c)*4 + B*pad16(d_s)*4 + B*nprobe*8 + B*nprobe*k*8

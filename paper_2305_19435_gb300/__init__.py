@@ -80,8 +80,46 @@ def lib():
         L.adanns_plan_free.restype = None
         L.adanns_map_ids.argtypes = [P, i64, P, i64, P]
         L.adanns_merge_shards.argtypes = [P, P, i32, i64, i32, P, P, P]
+        L.adanns_set_option.argtypes = [i32, i64]
+        L.adanns_get_option.argtypes = [i32, P]
         _lib = L
     return _lib
+
+
+# runtime options (include/adanns.h ADANNS_OPT_*)
+OPT_FP32_STREAM = 0
+OPT_ADC_SELECT = 1
+OPT_COARSE_TC = 2
+OPT_RERANK_PRUNE = 3
+OPT_SCRATCH_BYTES = 4
+OPT_WAIT_LIMIT_NS = 5
+OPT_TEST_SKIP_LOAD = 6
+
+
+def set_option(opt: int, value: int):
+    """Set a process-wide runtime option (kernel choices, scratch and wait bounds)."""
+    _check(lib().adanns_set_option(int(opt), int(value)))
+
+
+def get_option(opt: int) -> int:
+    v = ctypes.c_int64()
+    _check(lib().adanns_get_option(int(opt), ctypes.byref(v)))
+    return int(v.value)
+
+
+class option:
+    """Context manager: `with option(OPT_X, v): ...` sets an option and restores it."""
+
+    def __init__(self, opt: int, value: int):
+        self.opt, self.value = opt, value
+
+    def __enter__(self):
+        self.old = get_option(self.opt)
+        set_option(self.opt, self.value)
+        return self
+
+    def __exit__(self, *exc):
+        set_option(self.opt, self.old)
 
 
 def launch_count() -> int:

@@ -68,6 +68,8 @@ void free_index(adanns_index *x) {
     cudaFree(x->lowp_sx[i]);
     cudaFree(x->lowp_cx[i]);
   }
+  cudaFree(x->rr_order);
+  for (int i = 0; i < 4; ++i) cudaFree(x->rr_cstart[i]);
   delete[] x->h_list_off;
   delete x;
 }
@@ -214,11 +216,75 @@ int make_index(const float *db, int64_t N, int d, const float *centroids, int nl
   int64_t mx = 0;
   for (int l = 0; l < nlist; ++l) mx = std::max(mx, x->h_list_off[l + 1] - x->h_list_off[l]);
   x->max_list = (int)mx;
+  if ((rc = build_rerank_order(x, st))) return bail(rc);
   *out = x;
   return ADANNS_OK;
 }
 
 }  // namespace
+
+// Lists in a greedy nearest-neighbour chain of their centroids (start at list
+// 0, then repeatedly the nearest list not yet taken; ties to the lower id), so
+// lists next to each other in the order are probed by overlapping query sets.
+// Above 4,096 lists the chain's quadratic cost is not paid: identity order.
+int build_rerank_order(adanns_index *x, cudaStream_t st) {
+  const int nl = x->nlist, dc = x->d_c;
+  std::vector<int32_t> ord((size_t)nl);
+  for (int i = 0; i < nl; ++i) ord[(size_t)i] = i;
+  if (nl > 2 && nl <= 4096) {
+    std::vector<float> c((size_t)nl * dc);
+    ADN_CUDA(cudaMemcpyAsync(c.data(), x->centroids, sizeof(float) * c.size(),
+                             cudaMemcpyDeviceToHost, st));
+    ADN_CUDA(cudaStreamSynchronize(st));
+    std::vector<char> used((size_t)nl, 0);
+    int cur = 0;
+    used[0] = 1;
+    for (int i = 1; i < nl; ++i) {
+      const float *a = c.data() + (size_t)cur * dc;
+      int best = -1;
+      double bd = 0.0;
+      for (int j = 0; j < nl; ++j) {
+        if (used[(size_t)j]) continue;
+        const float *b = c.data() + (size_t)j * dc;
+        double dd = 0.0;
+        for (int t = 0; t < dc; ++t) {
+          const double u = (double)a[t] - (double)b[t];
+          dd += u * u;
+        }
+        if (best < 0 || dd < bd) {
+          best = j;
+          bd = dd;
+        }
+      }
+      used[(size_t)best] = 1;
+      ord[(size_t)i] = best;
+      cur = best;
+    }
+  }
+  int rc;
+  if ((rc = dmalloc(&x->rr_order, (size_t)nl))) return rc;
+  ADN_CUDA(cudaMemcpyAsync(x->rr_order, ord.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice,
+                           st));
+  std::vector<int32_t> cs[4];
+  for (int ci = 0; ci < 4; ++ci) {
+    const int mc = 64 >> ci;
+    cs[ci].resize((size_t)nl + 1);
+    int64_t t = 0;
+    for (int i = 0; i < nl; ++i) {
+      cs[ci][(size_t)i] = (int32_t)t;
+      const int l = ord[(size_t)i];
+      t += (x->h_list_off[l + 1] - x->h_list_off[l] + mc - 1) / mc;
+    }
+    cs[ci][(size_t)nl] = (int32_t)t;
+    x->rr_chunks[ci] = (int)t;
+    if ((rc = dmalloc(&x->rr_cstart[ci], (size_t)nl + 1))) return rc;
+    ADN_CUDA(cudaMemcpyAsync(x->rr_cstart[ci], cs[ci].data(), sizeof(int32_t) * (nl + 1),
+                             cudaMemcpyHostToDevice, st));
+  }
+  ADN_CUDA(cudaStreamSynchronize(st));  // the host tables go out of scope
+  return ADANNS_OK;
+}
+
 }  // namespace adn
 
 using namespace adn;
@@ -250,6 +316,15 @@ const char *adanns_last_error(void) { return adn::last_error(); }
 int adanns_version(void) { return 100; }
 
 int64_t adanns_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int adanns_set_option(int option, int64_t value) { return set_option(option, value); }
+
+int adanns_get_option(int option, int64_t *value) {
+  if (!value) return fail(ADANNS_ERR_ARG, "value is NULL");
+  if (option < 0 || option >= ADANNS_OPT_COUNT) return fail(ADANNS_ERR_ARG, "unknown option");
+  *value = adn::option(option);
+  return ADANNS_OK;
+}
 
 int adanns_index_create(const float *db, int64_t N, int d, const float *centroids, int nlist,
                         int d_c, const int32_t *assign, int metric, int storage_mask,

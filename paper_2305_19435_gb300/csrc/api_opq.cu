@@ -38,11 +38,10 @@ cudaStream_t S(void *p) { return (cudaStream_t)p; }
 
 // The ADC stage writes every probed member's distance and selects the top k'
 // per query afterwards (adc_dist_kernel + select32_kernel) when n_p <= 256;
-// ADANNS_ADC_SELECT=0 keeps a running top-k' per (query, list) instead
+// ADANNS_OPT_ADC_SELECT = 0 keeps a running top-k' per (query, list) instead
 // (adc_scan_kernel + merge).
 bool adc_select_enabled(int nprobe) {
-  const char *env = getenv("ADANNS_ADC_SELECT");
-  return nprobe <= 256 && !(env && env[0] == '0');
+  return nprobe <= 256 && option(ADANNS_OPT_ADC_SELECT) != 0;
 }
 
 

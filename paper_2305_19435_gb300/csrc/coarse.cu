@@ -532,10 +532,9 @@ int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t
 
 int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
                      uint64_t *out, cudaStream_t st) {
-  const char *env = getenv("ADANNS_COARSE_TC");
   // small tables stay on the FP32 kernels (they are cheap there, and the
   // tensor-core tile reads 256 centroid rows at a time)
-  if ((env && env[0] == '0') || !idx->cent_low || d_c > CM_MAXD || k > idx->nlist ||
+  if (!option(ADANNS_OPT_COARSE_TC) || !idx->cent_low || d_c > CM_MAXD || k > idx->nlist ||
       idx->nlist < 256 || k > CPB_MAXK || (k > CM_MAXK && idx->nlist > CPB_MAXLIST))
     return 1;
   if (B == 0) return ADANNS_OK;

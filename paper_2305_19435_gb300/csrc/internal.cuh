@@ -80,8 +80,13 @@ extern std::atomic<long long> g_launches;  // kernels launched since load
 // release threshold is unlimited, so scratch freed at the end of one call is
 // reused by the next without returning memory to the driver.
 cudaMemPool_t scratch_pool();
-// Bytes of scratch one search call may hold at once (ADANNS_SCRATCH_GB, default 12).
+// Bytes of scratch one search call may hold at once (ADANNS_OPT_SCRATCH_BYTES).
 int64_t scratch_budget();
+// Runtime options (ADANNS_OPT_*): current value; take_option returns it and
+// stores `reset` (one-shot test hooks); set_option validates.
+int64_t option(int opt);
+int64_t take_option(int opt, int64_t reset);
+int set_option(int opt, int64_t value);
 int64_t max_probe_members(const adanns_index *idx, int nprobe);
 
 // Stream-ordered scratch allocation from that pool on the call's stream.
@@ -205,6 +210,8 @@ struct MmaScanArgs {
   int *err;
   int *tile_counter;         // zeroed before the launch: next tile to take
   int fp8;
+  uint64_t wait_ns;          // bound of each pipeline wait (set by the launcher)
+  int skip_fill;             // test hook: stage load skip_fill of work item 0 is left out (-1: none)
 };
 // work counters recorded while profiling is on (adanns_profile_read_counters)
 enum ProfileCounter { PC_RERANK_PAIRS = 0, PC_SHORTLIST_SLOTS = 1, PC_NCOUNTER = 8 };
@@ -274,6 +281,11 @@ class StageTimer {
 };
 
 int build_lowp(adanns_index *x, const float *db, int which, cudaStream_t st);
+// chunk-table slot of a rerank member-chunk size (64, 32, 16, 8)
+inline int rerank_chunk_index(int mc) { return mc >= 64 ? 0 : mc >= 32 ? 1 : mc >= 16 ? 2 : 3; }
+// the rerank work order and chunk tables of an index (host copies of the
+// centroids and list offsets; synchronises the stream)
+int build_rerank_order(adanns_index *x, cudaStream_t st);
 int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
                  int nprobe, int k, int which, int kk, int64_t *out_ids, float *out_dist,
                  int32_t *out_probes, cudaStream_t st);
@@ -319,6 +331,13 @@ struct adanns_index {
   // per granularity g: max over members of nu_g(x) * |(x - s_x x~)[0:g]|, the
   // largest relative quantisation residual of a normalised prefix (host copy)
   float lowp_rmax[2][adn::NGRAN] = {};
+  // rerank work order: lists in a nearest-neighbour chain of the centroids
+  // (rr_order[i] = list at position i), and for the member-chunk sizes
+  // 64 / 32 / 16 / 8 the first chunk of each ordered list (nlist + 1 entries)
+  // and the chunk total
+  int32_t *rr_order = nullptr;
+  int32_t *rr_cstart[4] = {nullptr, nullptr, nullptr, nullptr};
+  int rr_chunks[4] = {0, 0, 0, 0};
   int64_t *h_list_off = nullptr;  // host copy of list offsets
   int *dev_err = nullptr;         // sticky device status word (tensor-core pipeline timeouts)
 };

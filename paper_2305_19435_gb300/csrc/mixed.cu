@@ -334,12 +334,9 @@ int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t
 // e_rest bounding the FP32 tensor-core accumulation (2 d_pad 2^-22), the FP32
 // norm and scale terms and the FP32 rerank's own rounding (8 (d_s + 2) 2^-24),
 // plus 1e-4.  Keys are round(16384 d_approx) (+-2^-15), so c can be dropped
-// when key_c > key_k + 2 * 16384 * (2^-15 + E_q).  Set ADANNS_RERANK_PRUNE=0
+// when key_c > key_k + 2 * 16384 * (2^-15 + E_q).  Set ADANNS_OPT_RERANK_PRUNE = 0
 // to rerank every shortlisted candidate.
-static bool shortlist_prune_enabled() {
-  const char *env = getenv("ADANNS_RERANK_PRUNE");
-  return !(env && env[0] == '0');
-}
+static bool shortlist_prune_enabled() { return option(ADANNS_OPT_RERANK_PRUNE) != 0; }
 
 static float shortlist_e_rest(int d_s, int d_pad) {
   return (float)(2.0 * d_pad * std::ldexp(1.0, -22) + 8.0 * (d_s + 2) * std::ldexp(1.0, -24) +

@@ -42,7 +42,6 @@ constexpr int STG_BYTES = 32 * EPI_SPAN * 2;    // a warp's 32 rows of 16-bit ke
 static_assert(EPI_SPAN == 64, "the key staging holds 8 16-byte chunks per row");
 constexpr int THREADS = 64 + EPI_THREADS;
 constexpr int TQD = 4;  // tile queue depth
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -68,15 +67,16 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// bounded wait for the phase with the given parity to complete (false on timeout)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait for the phase with the given parity to complete (false once
+// `limit_ns` of wall time has passed)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
   const uint32_t a = smem_u32(bar);
   uint64_t t0 = 0;
   for (uint32_t i = 0;; ++i) {
     if ((i & 1023) == 1023) {
       const uint64_t now = global_ns();
       if (t0 == 0) t0 = now;
-      else if (now - t0 > WAIT_LIMIT_NS) return false;
+      else if (now - t0 > limit_ns) return false;
     }
     uint32_t ok;
     asm volatile(
@@ -221,9 +221,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (;;) {
         int t = atomicAdd(a.tile_counter, 1);
         if (t >= ntiles || ld_abort(&abort_s)) t = -1;
-        if (!mbar_wait(&qempty[qs], qph ^ 1)) {
+        if (!mbar_wait(&qempty[qs], qph ^ 1, a.wait_ns)) {
           atomicExch(&abort_s, 1);
-          atomicExch(a.err, 6);
+          atomicCAS(a.err, 0, 6);
           break;
         }
         qids[qs] = t;
@@ -236,10 +236,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int nmt = (nl + BN - 1) / BN;
         for (int mt = 0; mt < nmt && !ld_abort(&abort_s); ++mt)
           for (int kb = 0; kb < a.nkb; ++kb) {
-            if (!mbar_wait(&empty[stage], phase ^ 1)) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, a.wait_ns)) {
               atomicExch(&abort_s, 1);
-              atomicExch(a.err, 1);
+              atomicCAS(a.err, 0, 1);
               break;
+            }
+            // test hook: leave this stage of work item 0 unfilled (no copy, no
+            // arrival), so the MMA issuer's bounded wait on it runs out
+            if (t == 0 && mt * a.nkb + kb == a.skip_fill) {
+              if (++stage == NSTAGE) { stage = 0; phase ^= 1; }
+              continue;
             }
             mbar_expect_tx(&full[stage], STAGE_BYTES);
             tma_load_2d(sA + stage * A_BYTES, &tmA, &full[stage], 0, (t * a.nkb + kb) * BM);
@@ -259,9 +265,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       int qs = 0;
       uint32_t qph = 0;
       while (!ld_abort(&abort_s)) {
-        if (!mbar_wait(&qfull[qs], qph)) {
+        if (!mbar_wait(&qfull[qs], qph, a.wait_ns)) {
           atomicExch(&abort_s, 1);
-          atomicExch(a.err, 7);
+          atomicCAS(a.err, 0, 7);
           break;
         }
         const int t = qids[qs];
@@ -272,17 +278,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int nl = (int)(a.list_off[list + 1] - a.list_off[list]);
         const int nmt = (nl + BN - 1) / BN;
         for (int mt = 0; mt < nmt && !ld_abort(&abort_s); ++mt) {
-          if (!mbar_wait(&tempty[acc], aphase ^ 1)) {
+          if (!mbar_wait(&tempty[acc], aphase ^ 1, a.wait_ns)) {
             atomicExch(&abort_s, 1);
-            atomicExch(a.err, 2);
+            atomicCAS(a.err, 0, 2);
             break;
           }
           tc_fence_after();
           const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
           for (int kb = 0; kb < a.nkb; ++kb) {
-            if (!mbar_wait(&full[stage], phase)) {
+            if (!mbar_wait(&full[stage], phase, a.wait_ns)) {
               atomicExch(&abort_s, 1);
-              atomicExch(a.err, 3);
+              atomicCAS(a.err, 0, 3);
               break;
             }
             tc_fence_after();
@@ -315,9 +321,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     int qs = 0;
     uint32_t qph = 0;
     for (;;) {
-      if (!mbar_wait(&qfull[qs], qph)) {
+      if (!mbar_wait(&qfull[qs], qph, a.wait_ns)) {
         atomicExch(&abort_s, 1);
-        atomicExch(a.err, 8);
+        atomicCAS(a.err, 0, 8);
         break;
       }
       const int t = qids[qs];
@@ -355,9 +361,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       };
       float2 terms = load_terms(0);
       for (int mt = 0; mt < nmt; ++mt) {
-        if (!mbar_wait(&tfull[acc], aphase)) {
+        if (!mbar_wait(&tfull[acc], aphase, a.wait_ns)) {
           atomicExch(&abort_s, 1);
-          atomicExch(a.err, 4);
+          atomicCAS(a.err, 0, 4);
           stop = true;
           break;
         }
@@ -370,60 +376,64 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           // hand-off through an mbarrier: a bounded wait, unlike bar.sync
           mbar_arrive(&sfull[acc]);
-          if (!mbar_wait(&sfull[acc], aphase)) {
+          if (!mbar_wait(&sfull[acc], aphase, a.wait_ns)) {
             atomicExch(&abort_s, 1);
-            atomicExch(a.err, 5);
+            atomicCAS(a.err, 0, 5);
             stop = true;
             break;
           }
         }
         if (mt + 1 < nmt) terms = load_terms(mt + 1);
-        const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
-        // this warp's 32 rows x 64 columns of keys are staged row-major in
-        // shared memory (16-byte chunks XOR-swizzled by row: conflict-free
-        // both ways), then stored as whole 128-byte row segments
-        uint4 *stg = (uint4 *)(sStage + (size_t)(warp - 2) * STG_BYTES);
+        // a lane quadrant with no valid query row (a tile with few queries)
+        // has nothing to drain: its warps skip the TMEM loads and the stores
+        if (quarter * 32 < cnt) {
+          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+          // this warp's 32 rows x 64 columns of keys are staged row-major in
+          // shared memory (16-byte chunks XOR-swizzled by row: conflict-free
+          // both ways), then stored as whole 128-byte row segments
+          uint4 *stg = (uint4 *)(sStage + (size_t)(warp - 2) * STG_BYTES);
 #pragma unroll 1
-        for (int c0 = 0; c0 < EPI_SPAN; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(tbase + c_lo + c0, r);
-          uint32_t packed[16];
+          for (int c0 = 0; c0 < EPI_SPAN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tbase + c_lo + c0, r);
+            uint32_t packed[16];
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            uint32_t kk[2];
+            for (int j = 0; j < 32; j += 2) {
+              uint32_t kk[2];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              // approximate squared distance as a 16-bit fixed-point key:
-              // round(d * 2^14), d clamped to [0, 4); members past the list
-              // end get the largest key
-              const int c = c_lo + c0 + j + u;
-              float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[j + u]), q2 + s_ca[acc][c]);
-              d = fminf(fmaxf(d, 0.f), 3.9999f);
-              kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
+              for (int u = 0; u < 2; ++u) {
+                // approximate squared distance as a 16-bit fixed-point key:
+                // round(d * 2^14), d clamped to [0, 4); members past the list
+                // end get the largest key
+                const int c = c_lo + c0 + j + u;
+                float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[j + u]), q2 + s_ca[acc][c]);
+                d = fminf(fmaxf(d, 0.f), 3.9999f);
+                kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
+              }
+              packed[j >> 1] = kk[0] | (kk[1] << 16);
             }
-            packed[j >> 1] = kk[0] | (kk[1] << 16);
-          }
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int ch = (c0 >> 3) + g;
-            stg[lane * 8 + (ch ^ (lane & 7))] =
-                make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2], packed[4 * g + 3]);
+            for (int g = 0; g < 4; ++g) {
+              const int ch = (c0 >> 3) + g;
+              stg[lane * 8 + (ch ^ (lane & 7))] =
+                  make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2], packed[4 * g + 3]);
+            }
           }
-        }
-        __syncwarp();
-        {
-          // 8 lanes per row: one instruction stores 4 rows x 128 bytes
-          const int m0 = mt * BN + c_lo, ch = lane & 7;
+          __syncwarp();
+          {
+            // 8 lanes per row: one instruction stores 4 rows x 128 bytes
+            const int m0 = mt * BN + c_lo, ch = lane & 7;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int rr = i * 4 + (lane >> 3);
-            const long long b = __shfl_sync(0xffffffffu, (long long)base, rr);
-            const int ok = __shfl_sync(0xffffffffu, valid ? 1 : 0, rr);
-            const uint4 v = stg[rr * 8 + (ch ^ (rr & 7))];
-            if (ok && m0 + 8 * ch < npad) *(uint4 *)(a.cand + b + m0 + 8 * ch) = v;
+            for (int i = 0; i < 8; ++i) {
+              const int rr = i * 4 + (lane >> 3);
+              const long long b = __shfl_sync(0xffffffffu, (long long)base, rr);
+              const int ok = __shfl_sync(0xffffffffu, valid ? 1 : 0, rr);
+              const uint4 v = stg[rr * 8 + (ch ^ (rr & 7))];
+              if (ok && m0 + 8 * ch < npad) *(uint4 *)(a.cand + b + m0 + 8 * ch) = v;
+            }
           }
+          __syncwarp();  // the staging buffer is rewritten for the next tile
         }
-        __syncwarp();  // the staging buffer is rewritten for the next tile
         tc_fence_before();
         mbar_arrive(&tempty[acc]);
         if (++acc == 2) { acc = 0; aphase ^= 1; }
@@ -496,7 +506,10 @@ int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t
   if ((rc = make_map(&tB, xlow, xrows, BN, a.fp8 != 0))) return rc;
   const size_t smem = mma_scan_smem();
   ADN_CUDA(ensure_smem((const void *)mma_scan_kernel, (size_t)(smem)));
-  mma_scan_kernel<<<num_sms(), THREADS, smem, st>>>(tA, tB, a);
+  MmaScanArgs b = a;
+  b.wait_ns = (uint64_t)option(ADANNS_OPT_WAIT_LIMIT_NS);
+  b.skip_fill = (int)take_option(ADANNS_OPT_TEST_SKIP_LOAD, -1);
+  mma_scan_kernel<<<num_sms(), THREADS, smem, st>>>(tA, tB, b);
   ADN_LAUNCH("mma_scan_kernel");
   return ADANNS_OK;
 }

@@ -55,15 +55,24 @@ __global__ void pair_scatter_kernel(const int32_t *__restrict__ ppos, int64_t n,
 // padded by 4 floats against bank conflicts); the chunk's pairs (consecutive
 // in the sorted order) are then scored by the CTA's half-warps, each prefetching
 // its next query row into registers while it scores the current one.  Only
-// the query rows are gathered (from L2: the whole query block is small).
+// the query rows are gathered.  CTA i takes chunk i of the lists laid end to
+// end in the index's rerank order (a nearest-neighbour chain of the
+// centroids), so the CTAs resident at one time cover a few neighbouring lists
+// and the query rows they gather -- those of the queries probing these lists
+// -- stay in L2 while they are reused.
 constexpr int RC_THREADS = 128;
 constexpr int RC_HW = RC_THREADS / 16;  // half-warps per CTA
 constexpr int RC_META = RC_THREADS;    // pairs whose metadata are staged at once
 constexpr int RC_MAX_MC = 64;
 
+// members per chunk: the largest of 64, 32, 16, 8 whose rows fit in 32 KB
+// (at least 8); the index keeps a chunk table for each of these sizes
 inline int rerank_chunk_members(int d_s) {
-  return std::max(8, std::min(RC_MAX_MC, 32768 / (d_s * 4)));
+  int mc = RC_MAX_MC;
+  while (mc > 8 && mc * d_s * 4 > 32768) mc >>= 1;
+  return mc;
 }
+static_assert(RC_MAX_MC == 64, "chunk sizes 64, 32, 16, 8 have precomputed chunk tables");
 
 // FULL: d_s is a multiple of 512 (every half-warp lane holds 8 whole float4
 // of each 512-coordinate segment), so no coordinate bound is checked.
@@ -73,25 +82,36 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
     const int32_t *__restrict__ pmem, const int32_t *__restrict__ list_ids, int kr,
     const float *__restrict__ qs, int ldq, int d_s, const float *__restrict__ xpm, int d_pad,
     const int64_t *__restrict__ list_off, const float *__restrict__ mscale, int mc,
+    const int32_t *__restrict__ lorder, const int32_t *__restrict__ cstart, int nlist,
     uint64_t *__restrict__ keys, int *__restrict__ err) {
   extern __shared__ __align__(16) float rows[];  // [mc][d_s + 4]
   __shared__ int s_e[RC_META], s_m[RC_META], s_q[RC_META];
   __shared__ float s_nu[RC_MAX_MC];
   __shared__ uint32_t s_id[RC_MAX_MC];
-  const int l = blockIdx.x;
+  // chunk -> (list, first member): the last order position whose first chunk
+  // is <= blockIdx.x (empty lists own no chunk and are passed over)
+  const int item = (int)blockIdx.x;
+  int lo = 0, hi = nlist - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cstart[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  const int l = lorder[lo];
   const int64_t off = list_off[l];
   const int nl = (int)(list_off[l + 1] - off);
+  const int m_first = (item - cstart[lo]) * mc;
   const int rs = d_s + 4, nseg = d_s >> 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = lane >> 4, hl = lane & 15, hw = warp * 2 + half;
   const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
   // the query block is re-read by every list: keep it in L2; member rows are read once
   const uint64_t keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
-  for (int m0 = blockIdx.y * mc; m0 < nl; m0 += gridDim.y * mc) {
+  {
+    const int m0 = m_first;
+    if (m0 >= nl) return;
     const int m1 = min(nl, m0 + mc), nm = m1 - m0;
     const int p0 = mstart[off + m0], p1 = mstart[off + m1];
-    if (p0 >= p1) continue;
-    __syncthreads();  // the previous chunk's rows are no longer read
+    if (p0 >= p1) return;
     // member rows: block b of the chunk is nm x 16 contiguous floats
     const int per_b = nm * 4;  // float4 per block
     for (int t = threadIdx.x; t < per_b * ((d_s + 15) >> 4); t += RC_THREADS) {
@@ -266,17 +286,21 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     ADN_CUDA(ensure_smem(fn, rs));
     // slots of padding or pruned candidates keep the empty key
     ADN_CUDA(cudaMemsetAsync(keys, 0xFF, sizeof(uint64_t) * n, st));
-    const int chunks = std::max(1, std::min(65535, (idx->max_list + mc - 1) / mc));
-    const dim3 grid((unsigned)nlist, (unsigned)chunks);
-    if (full)
-      rerank_chunks_kernel<true><<<grid, RC_THREADS, rs, st>>>(
-          order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad,
-          idx->list_off, mscale, mc, keys, idx->dev_err);
-    else
-      rerank_chunks_kernel<false><<<grid, RC_THREADS, rs, st>>>(
-          order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad,
-          idx->list_off, mscale, mc, keys, idx->dev_err);
-    ADN_LAUNCH("rerank_chunks_kernel");
+    const int ci = rerank_chunk_index(mc);
+    const int chunks = idx->rr_chunks[ci];
+    if (chunks > 0) {
+      if (full)
+        rerank_chunks_kernel<true><<<(unsigned)chunks, RC_THREADS, rs, st>>>(
+            order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad,
+            idx->list_off, mscale, mc, idx->rr_order, idx->rr_cstart[ci], nlist, keys,
+            idx->dev_err);
+      else
+        rerank_chunks_kernel<false><<<(unsigned)chunks, RC_THREADS, rs, st>>>(
+            order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad,
+            idx->list_off, mscale, mc, idx->rr_order, idx->rr_cstart[ci], nlist, keys,
+            idx->dev_err);
+      ADN_LAUNCH("rerank_chunks_kernel");
+    }
   }
   {
     StageTimer t(ST_RR_FINAL, st);

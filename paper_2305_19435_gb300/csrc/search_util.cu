@@ -72,15 +72,72 @@ int64_t max_probe_members(const adanns_index *idx, int nprobe) {
   return t;
 }
 
-int64_t scratch_budget() {
-  static int64_t b = [] {
+// Runtime options (adanns_set_option).  The first access seeds them from the
+// environment (ADANNS_FP32_STREAM, ADANNS_ADC_SELECT, ADANNS_COARSE_TC,
+// ADANNS_RERANK_PRUNE, ADANNS_SCRATCH_GB); later reads are one atomic load, so
+// no search call consults the environment.
+namespace {
+std::atomic<int64_t> g_opt[ADANNS_OPT_COUNT];
+std::once_flag g_opt_once;
+
+int64_t env_flag(const char *name, int64_t dflt) {
+  const char *e = getenv(name);
+  if (!e || !e[0]) return dflt;
+  return e[0] == '0' ? 0 : 1;
+}
+
+void init_options() {
+  std::call_once(g_opt_once, [] {
+    g_opt[ADANNS_OPT_FP32_STREAM] = env_flag("ADANNS_FP32_STREAM", 1);
+    g_opt[ADANNS_OPT_ADC_SELECT] = env_flag("ADANNS_ADC_SELECT", 1);
+    g_opt[ADANNS_OPT_COARSE_TC] = env_flag("ADANNS_COARSE_TC", 1);
+    g_opt[ADANNS_OPT_RERANK_PRUNE] = env_flag("ADANNS_RERANK_PRUNE", 1);
     const char *e = getenv("ADANNS_SCRATCH_GB");
     double gb = e ? atof(e) : 12.0;
     if (!(gb > 0.0)) gb = 12.0;
-    return (int64_t)(gb * (double)(1ll << 30));
-  }();
-  return b;
+    g_opt[ADANNS_OPT_SCRATCH_BYTES] = (int64_t)(gb * (double)(1ll << 30));
+    g_opt[ADANNS_OPT_WAIT_LIMIT_NS] = 2000000000ll;
+    g_opt[ADANNS_OPT_TEST_SKIP_LOAD] = -1;
+  });
 }
+}  // namespace
+
+int64_t option(int o) {
+  init_options();
+  return g_opt[o].load(std::memory_order_relaxed);
+}
+
+int64_t take_option(int o, int64_t reset) {
+  init_options();
+  return g_opt[o].exchange(reset);
+}
+
+int set_option(int o, int64_t v) {
+  init_options();
+  if (o < 0 || o >= ADANNS_OPT_COUNT) return fail(ADANNS_ERR_ARG, "unknown option");
+  switch (o) {
+    case ADANNS_OPT_FP32_STREAM:
+    case ADANNS_OPT_ADC_SELECT:
+    case ADANNS_OPT_COARSE_TC:
+    case ADANNS_OPT_RERANK_PRUNE:
+      if (v != 0 && v != 1) return fail(ADANNS_ERR_ARG, "this option takes 0 or 1");
+      break;
+    case ADANNS_OPT_SCRATCH_BYTES:
+      if (v < (1ll << 20)) return fail(ADANNS_ERR_ARG, "scratch budget below 1 MiB");
+      break;
+    case ADANNS_OPT_WAIT_LIMIT_NS:
+      if (v < 100000 || v > 60000000000ll)
+        return fail(ADANNS_ERR_ARG, "wait limit must be within [1e5, 6e10] ns");
+      break;
+    case ADANNS_OPT_TEST_SKIP_LOAD:
+      if (v < -1 || v > INT32_MAX) return fail(ADANNS_ERR_ARG, "bad skip index");
+      break;
+  }
+  g_opt[o].store(v);
+  return ADANNS_OK;
+}
+
+int64_t scratch_budget() { return option(ADANNS_OPT_SCRATCH_BYTES); }
 
 cudaError_t ensure_smem(const void *fn, size_t bytes) {
   static std::mutex mu;

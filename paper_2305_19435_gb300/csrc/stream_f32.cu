@@ -161,11 +161,10 @@ __global__ void __launch_bounds__(SF_THREADS, 4) dist_f32_kernel(StreamArgs a) {
 
 }  // namespace
 
-// Few queries per probed list: prefer the streaming scan (ADANNS_FP32_STREAM=0
+// Few queries per probed list: prefer the streaming scan (ADANNS_OPT_FP32_STREAM = 0
 // keeps the shared-memory tiled scan everywhere)
 bool fp32_stream_enabled(double queries_per_list, int nprobe) {
-  const char *env = getenv("ADANNS_FP32_STREAM");
-  if (env && env[0] == '0') return false;
+  if (!option(ADANNS_OPT_FP32_STREAM)) return false;
   return queries_per_list <= 16.0 && nprobe <= 256;
 }
 

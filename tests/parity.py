@@ -110,3 +110,24 @@ def recall(g_ids, o_ids, k):
             continue
         tot += len(bs & set(int(v) for v in a if v >= 0)) / len(bs)
     return tot / len(g_ids)
+
+
+def full_groups(o, rerun, k):
+    """Rows whose tie group at rank k-1 runs to the end of the oracle's list are
+    searched again with every candidate returned, so that group is complete."""
+    d = o["dist"]
+    last = d[:, -1]
+    trunc = np.isfinite(last) & (last - d[:, k - 1] <= tol(last))
+    if not trunc.any():
+        return o
+    rows = np.nonzero(trunc)[0]
+    kk = int(o["ncand"][rows].max()) if "ncand" in o else 4 * d.shape[1]
+    o2 = rerun(rows, max(kk, d.shape[1]))
+    K = o2["ids"].shape[1]
+    ids = np.full((d.shape[0], K), -1, dtype=np.int64)
+    dist = np.full((d.shape[0], K), np.inf)
+    ids[:, :d.shape[1]], dist[:, :d.shape[1]] = o["ids"], d
+    ids[rows], dist[rows] = o2["ids"], o2["dist"]
+    o = dict(o)
+    o["ids"], o["dist"] = ids, dist
+    return o

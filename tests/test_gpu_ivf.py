@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synthdata
-from parity import ambiguous_probe_rows, check_topk, recall, tol
+from parity import ambiguous_probe_rows, check_topk, full_groups, recall, tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -33,27 +33,6 @@ def cu(x):
 def import_index(A, db, oidx, metric):
     return A.index_create(cu(db), cu(oidx["centroids"]), cu(oidx["assign"].astype(np.int32)),
                           metric=metric)
-
-
-def full_groups(o, rerun, k):
-    """Rows whose tie group at rank k-1 runs to the end of the oracle's list are
-    searched again with every candidate returned, so that group is complete."""
-    d = o["dist"]
-    last = d[:, -1]
-    trunc = np.isfinite(last) & (last - d[:, k - 1] <= tol(last))
-    if not trunc.any():
-        return o
-    rows = np.nonzero(trunc)[0]
-    kk = int(o["ncand"][rows].max()) if "ncand" in o else 4 * d.shape[1]
-    o2 = rerun(rows, max(kk, d.shape[1]))
-    K = o2["ids"].shape[1]
-    ids = np.full((d.shape[0], K), -1, dtype=np.int64)
-    dist = np.full((d.shape[0], K), np.inf)
-    ids[:, :d.shape[1]], dist[:, :d.shape[1]] = o["ids"], d
-    ids[rows], dist[rows] = o2["ids"], o2["dist"]
-    o = dict(o)
-    o["ids"], o["dist"] = ids, dist
-    return o
 
 
 def search_parity(A, db, q, oidx, d_c, d_s, nprobe, k, metric, extra=24):
@@ -294,7 +273,7 @@ def wide(A):
 
 @pytest.mark.parametrize("d_c,nprobe", [(64, 1), (64, 16), (32, 32), (16, 8), (64, 33),
                                          (64, 100), (32, 300), (16, 64)])
-def test_tensor_core_cluster_mapping_is_exact(A, wide, d_c, nprobe, monkeypatch):
+def test_tensor_core_cluster_mapping_is_exact(A, wide, d_c, nprobe):
     """BF16 tensor-core shortlist + exact FP32 re-score of every centroid within
     the quantisation bound: the same probes and results as the FP32 cluster
     mapping (d_c < 64 is IVF-D on the d_c = 64 index), and oracle parity.
@@ -302,10 +281,10 @@ def test_tensor_core_cluster_mapping_is_exact(A, wide, d_c, nprobe, monkeypatch)
     data, o = wide
     g = import_index(A, data["db"], o, PN)
     q = cu(data["queries"])
-    monkeypatch.setenv("ADANNS_COARSE_TC", "0")
-    i0, d0, p0 = A.search_ivf(g, q, d_c, 128, nprobe, 20, return_probes=True)
-    monkeypatch.setenv("ADANNS_COARSE_TC", "1")
-    i1, d1, p1 = A.search_ivf(g, q, d_c, 128, nprobe, 20, return_probes=True)
+    with A.option(A.OPT_COARSE_TC, 0):
+        i0, d0, p0 = A.search_ivf(g, q, d_c, 128, nprobe, 20, return_probes=True)
+    with A.option(A.OPT_COARSE_TC, 1):
+        i1, d1, p1 = A.search_ivf(g, q, d_c, 128, nprobe, 20, return_probes=True)
     assert torch.equal(p0, p1)
     assert torch.equal(i0, i1) and torch.equal(d0, d1)
     g.status()
@@ -315,7 +294,7 @@ def test_tensor_core_cluster_mapping_is_exact(A, wide, d_c, nprobe, monkeypatch)
 
 @pytest.mark.parametrize("B,d_s,nprobe,k", [(40, 8, 1, 1), (100, 48, 4, 10), (500, 128, 1, 100),
                                             (300, 96, 8, 33), (17, 128, 33, 50), (3, 16, 2, 5)])
-def test_fp32_stream_scan_equals_tiled_scan(A, wide, B, d_s, nprobe, k, monkeypatch):
+def test_fp32_stream_scan_equals_tiled_scan(A, wide, B, d_s, nprobe, k):
     """Few queries per probed list: the streaming scan (register accumulation,
     distances written, then a per-query select) and the shared-memory tiled
     scan compute the same FP32 distances and keep the same (distance, id)
@@ -324,8 +303,8 @@ def test_fp32_stream_scan_equals_tiled_scan(A, wide, B, d_s, nprobe, k, monkeypa
     g = import_index(A, data["db"], o, PN)
     q = cu(data["queries"][:B])
     i0, d0, p0 = A.search_ivf(g, q, 64, d_s, nprobe, k, return_probes=True)
-    monkeypatch.setenv("ADANNS_FP32_STREAM", "0")
-    i1, d1, p1 = A.search_ivf(g, q, 64, d_s, nprobe, k, return_probes=True)
+    with A.option(A.OPT_FP32_STREAM, 0):
+        i1, d1, p1 = A.search_ivf(g, q, 64, d_s, nprobe, k, return_probes=True)
     assert torch.equal(p0, p1)
     assert torch.equal(i0, i1)
     assert torch.equal(d0.view(torch.int32), d1.view(torch.int32))

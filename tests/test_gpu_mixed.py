@@ -185,17 +185,17 @@ def test_shortlist_ties_inside_the_survivor_buffer(A, kr):
 @pytest.mark.parametrize("storage,d_s,nprobe,k,kr", [(BF16, 256, 8, 100, 400), (BF16, 128, 12, 10, 40),
                                                     (BF16, 64, 4, 1, 2048), (FP8, 256, 8, 100, 400),
                                                     (FP8, 128, 6, 10, 40)])
-def test_certified_pruning_changes_nothing(A, case, storage, d_s, nprobe, k, kr, monkeypatch):
+def test_certified_pruning_changes_nothing(A, case, storage, d_s, nprobe, k, kr):
     """The shortlist candidates dropped before the exact rerank (quantisation
     residual bound) cannot reach the top-k: results with and without the
     pruning are bit-identical, and the pruning does drop candidates (BF16)."""
     data, o, g = case
     q = cu(data["queries"])
-    monkeypatch.setenv("ADANNS_RERANK_PRUNE", "0")
-    i0, d0 = A.search_ivf(g, q, 32, d_s, nprobe, k, storage=storage, rerank_k=kr)
-    monkeypatch.setenv("ADANNS_RERANK_PRUNE", "1")
+    with A.option(A.OPT_RERANK_PRUNE, 0):
+        i0, d0 = A.search_ivf(g, q, 32, d_s, nprobe, k, storage=storage, rerank_k=kr)
     A.profile_enable(True)
-    i1, d1 = A.search_ivf(g, q, 32, d_s, nprobe, k, storage=storage, rerank_k=kr)
+    with A.option(A.OPT_RERANK_PRUNE, 1):
+        i1, d1 = A.search_ivf(g, q, 32, d_s, nprobe, k, storage=storage, rerank_k=kr)
     cnt = A.profile_read_counters()
     A.profile_enable(False)
     assert torch.equal(i0, i1)

@@ -194,13 +194,9 @@ def test_opq_errors(A, case):
 def _search_both(A, g, q, d_c, nprobe, k, kr=0):
     """The same IVF-OPQ search through the distance-then-select ADC stage and
     through the running per-(query, list) top-k ADC stage."""
-    import os
     a = [t.cpu().numpy() for t in A.search_ivfopq(g, q, d_c, nprobe, k, rerank_k=kr)]
-    os.environ["ADANNS_ADC_SELECT"] = "0"
-    try:
+    with A.option(A.OPT_ADC_SELECT, 0):
         b = [t.cpu().numpy() for t in A.search_ivfopq(g, q, d_c, nprobe, k, rerank_k=kr)]
-    finally:
-        del os.environ["ADANNS_ADC_SELECT"]
     return a, b
 
 
