@@ -64,9 +64,9 @@ def _load():
         lib.orc_assign.restype = None
         lib.orc_ivf_search.argtypes = [P, i64, i32, P, i32, i32, P, P, P, i64, i32, i32, i32, i32,
                                        i32, P, P, P, P, P, i32]
-        lib.orc_pq_encode.argtypes = [P, i64, i64, i32, i32, i32, P, P, P, i32]
+        lib.orc_pq_encode.argtypes = [P, i64, i64, i32, i32, i32, P, P, P, P, P, i32]
         lib.orc_ivfopq_search.argtypes = [P, i64, i32, P, i32, i32, P, P, P, P, P, i32, P, i64,
-                                          i32, i32, i32, i32, i32, i32, P, P, P, P, i32]
+                                          i32, i32, i32, i32, i32, i32, P, P, P, P, P, i32]
         _lib = lib
     return _lib
 
@@ -249,9 +249,28 @@ def distortion(Z: np.ndarray, C: np.ndarray, codes: np.ndarray) -> float:
     return float(((Z - pq_decode(codes, C)) ** 2).sum() / Z.shape[0])
 
 
+def list_centroids(db: np.ndarray, index: dict, d_s: int,
+                   metric: int = METRIC_L2_PREFIXNORM) -> np.ndarray:
+    """Residual centres of the IVF-OPQ composite: for every inverted list the
+    FP64 mean of its members' P_ds prefixes, rounded to FP32 (an empty list
+    gets the zero vector).  The coarse centroids live at d_c only, so the
+    residual that the codes of the d_s prefix encode is taken against these
+    d_s-dimensional list means (the reading of residual encoding used here)."""
+    X = prefix(db, d_s, metric)
+    nlist = index["nlist"]
+    a = np.asarray(index["assign"])
+    sums = np.zeros((nlist, d_s))
+    np.add.at(sums, a, X)
+    cnt = np.bincount(a, minlength=nlist)
+    out = np.zeros((nlist, d_s))
+    ne = cnt > 0
+    out[ne] = sums[ne] / cnt[ne, None]
+    return out.astype(np.float32)
+
+
 def train_opq(db: np.ndarray, d_s: int, M: int, opq_iters: int, pq_iters: int, final_iters: int,
               train_n: int, seed: int, metric: int = METRIC_L2_PREFIXNORM,
-              nthreads: int | None = None) -> dict:
+              nthreads: int | None = None, residual: dict | None = None) -> dict:
     """AdANNS-OPQ training on the d_s prefix (Sec. 3 "OPQ", Sec. 4.2).
 
     Y = P_ds(db[sample(seed + 2, N, train_n)]), R_0 = I.  Each outer iteration:
@@ -260,6 +279,8 @@ def train_opq(db: np.ndarray, d_s: int, M: int, opq_iters: int, pq_iters: int, f
     after); encode; R <- Procrustes(Y, Zhat).  Then `final_iters` Lloyd steps
     on Y R.  R and the codebooks are rounded to FP32 (the index values).
     `trace` records the distortion after every half-step; it never increases.
+    With residual = dict(lcent=list centroids [nlist, d_s], assign=list of each
+    row), the training rows are the residuals P_ds(x) - lcent[list(x)].
     """
     db = _c(db, np.float32)
     N = db.shape[0]
@@ -268,6 +289,9 @@ def train_opq(db: np.ndarray, d_s: int, M: int, opq_iters: int, pq_iters: int, f
     dsub = d_s // M
     S = sample(seed + 2, N, train_n)
     Y = prefix(db[S], d_s, metric)
+    if residual is not None:
+        Y = Y - np.asarray(residual["lcent"], dtype=np.float32)[
+            np.asarray(residual["assign"])[S]].astype(np.float64)
     n = Y.shape[0]
     perm = sample(seed + 3, n, min(256, n))
     init_rows = perm[np.arange(256) % len(perm)]
@@ -293,21 +317,29 @@ def train_opq(db: np.ndarray, d_s: int, M: int, opq_iters: int, pq_iters: int, f
     C = np.stack([lloyd(Z[:, m * dsub:(m + 1) * dsub], C[m], final_iters, nthreads)[0]
                   for m in range(M)])
     trace.append(distortion(Z, C, pq_assign(Z, C, M, nthreads)))
-    return {"R": R.astype(np.float32), "codebooks": C.astype(np.float32), "R64": R,
-            "codebooks64": C, "trace": trace, "train_idx": S, "d_s": d_s, "M": M,
-            "metric": metric}
+    out = {"R": R.astype(np.float32), "codebooks": C.astype(np.float32), "R64": R,
+           "codebooks64": C, "trace": trace, "train_idx": S, "d_s": d_s, "M": M,
+           "metric": metric}
+    if residual is not None:
+        out["lcent"] = np.asarray(residual["lcent"], dtype=np.float32)
+    return out
 
 
 def pq_encode(db: np.ndarray, d_s: int, M: int, R: np.ndarray, codebooks: np.ndarray,
-              metric: int = METRIC_L2_PREFIXNORM, nthreads: int | None = None) -> np.ndarray:
-    """codes uint8 [N, M] of z = P_ds(x) R under the given (FP32) R / codebooks."""
+              metric: int = METRIC_L2_PREFIXNORM, nthreads: int | None = None,
+              lcent: np.ndarray | None = None, assign: np.ndarray | None = None) -> np.ndarray:
+    """codes uint8 [N, M] of z = P_ds(x) R under the given (FP32) R / codebooks;
+    with list centroids lcent and the rows' lists assign, of the residual
+    z = (P_ds(x) - lcent[assign[x]]) R."""
     db = _c(db, np.float32)
     R64 = _c(np.asarray(R, dtype=np.float32).astype(np.float64), np.float64)
     C64 = _c(np.asarray(codebooks, dtype=np.float32).astype(np.float64), np.float64)
+    lc = None if lcent is None else _c(lcent, np.float32)
+    asg = None if lcent is None else _c(assign, np.int32)
     codes = np.empty((db.shape[0], M), dtype=np.uint8)
     rc = _load().orc_pq_encode(_p(db), db.shape[0], db.shape[1], d_s, M,
-                               int(metric == METRIC_L2_PREFIXNORM), _p(R64), _p(C64), _p(codes),
-                               _threads(nthreads))
+                               int(metric == METRIC_L2_PREFIXNORM), _p(R64), _p(C64), _p(lc),
+                               _p(asg), _p(codes), _threads(nthreads))
     if rc != 0:
         raise ValueError("bad encode arguments")
     return codes
@@ -318,7 +350,9 @@ def search_ivfopq(db: np.ndarray, index: dict, opq: dict, codes: np.ndarray, que
                   nthreads: int | None = None) -> dict:
     """AdANNS-IVFOPQ search: IVF at d_c, ADC distances on the rotated d_s
     prefix inside the probed lists, optional exact rerank of the rerank_k
-    best (Sec. 4.3; Table "formula" IVFOPQ row read as asymmetric lookup)."""
+    best (Sec. 4.3; Table "formula" IVFOPQ row read as asymmetric lookup).
+    When `opq` holds list centroids ("lcent"), the codes are of residuals and
+    each probed list l gets its own table from (P_ds(q) - lcent[l]) R."""
     metric = index["metric"] if metric is None else metric
     db = _c(db, np.float32)
     queries = _c(queries, np.float32)
@@ -336,8 +370,9 @@ def search_ivfopq(db: np.ndarray, index: dict, opq: dict, codes: np.ndarray, que
                                    _p(_c(index["list_off"], np.int64)),
                                    _p(_c(index["list_ids"], np.int32)), _p(R), _p(C), _p(codes),
                                    M, _p(queries), B, d_c, d_s, nprobe, k, rerank_k,
-                                   int(metric == METRIC_L2_PREFIXNORM), _p(ids), _p(dist),
-                                   _p(probes), _p(pd), _threads(nthreads))
+                                   int(metric == METRIC_L2_PREFIXNORM),
+                                   _p(_c(opq["lcent"], np.float32)) if "lcent" in opq else None,
+                                   _p(ids), _p(dist), _p(probes), _p(pd), _threads(nthreads))
     if rc != 0:
         raise ValueError("bad IVF-OPQ search arguments")
     return {"ids": ids, "dist": dist, "probes": probes, "probe_dist": pd}

@@ -283,6 +283,7 @@ static void rotate(const double *xs, int d_s, const double *R, double *z) {
 typedef struct {
     const float *x; int64_t ld; int d_s, M, normalize;
     const double *R, *C; uint8_t *codes;
+    const float *lcent; const int32_t *assign;
 } enc_ctx;
 
 static void enc_range(void *p, int64_t lo, int64_t hi) {
@@ -292,6 +293,10 @@ static void enc_range(void *p, int64_t lo, int64_t hi) {
     double *z = (double *)malloc(sizeof(double) * (size_t)c->d_s);
     for (int64_t i = lo; i < hi; ++i) {
         prefix_of(c->x + i * c->ld, c->d_s, c->normalize, xs);
+        if (c->lcent) {   /* residual: subtract the row's list centroid */
+            const float *cl = c->lcent + (int64_t)c->assign[i] * c->d_s;
+            for (int j = 0; j < c->d_s; ++j) xs[j] -= (double)cl[j];
+        }
         rotate(xs, c->d_s, c->R, z);
         for (int m = 0; m < c->M; ++m) {
             double best = INFINITY;
@@ -312,9 +317,10 @@ static void enc_range(void *p, int64_t lo, int64_t hi) {
 }
 
 int orc_pq_encode(const float *x, int64_t n, int64_t ld, int d_s, int M, int normalize,
-                  const double *R, const double *C, uint8_t *codes, int nthreads) {
-    if (M < 1 || d_s % M != 0) return -1;
-    enc_ctx c = {x, ld, d_s, M, normalize, R, C, codes};
+                  const double *R, const double *C, const float *lcent, const int32_t *assign,
+                  uint8_t *codes, int nthreads) {
+    if (M < 1 || d_s % M != 0 || (lcent && !assign)) return -1;
+    enc_ctx c = {x, ld, d_s, M, normalize, R, C, codes, lcent, assign};
     parallel_for(n, nthreads, enc_range, &c);
     return 0;
 }
@@ -334,7 +340,22 @@ typedef struct {
     const float *R; const float *C; const uint8_t *codes; int M;
     const float *queries; int d_c, d_s, nprobe, k_out, rerank_k, normalize;
     int64_t *out_ids; double *out_dist; int32_t *out_probes; double *out_pdist; int pstride;
+    const float *lcent;   /* residual codes: list centroids [nlist][d_s], else NULL */
 } opq_ctx;
+
+/* lut[m][c] = ||v_m - C_m[c]||^2 for the rotated vector v */
+static void build_lut(const double *v, const float *C, int M, int dsub, double *lut) {
+    for (int m = 0; m < M; ++m)
+        for (int cc = 0; cc < 256; ++cc) {
+            const float *cw = C + ((int64_t)m * 256 + cc) * dsub;
+            double acc = 0.0;
+            for (int t = 0; t < dsub; ++t) {
+                double diff = v[m * dsub + t] - (double)cw[t];
+                acc += diff * diff;
+            }
+            lut[m * 256 + cc] = acc;
+        }
+}
 
 static void opq_range(void *p, int64_t lo, int64_t hi) {
     opq_ctx *c = (opq_ctx *)p;
@@ -359,22 +380,26 @@ static void opq_range(void *p, int64_t lo, int64_t hi) {
             for (int i = 0; i < c->d_s; ++i) acc += qs[i] * (double)c->R[(int64_t)i * c->d_s + j];
             z[j] = acc;
         }
-        for (int m = 0; m < c->M; ++m)
-            for (int cc = 0; cc < 256; ++cc) {
-                const float *cw = c->C + ((int64_t)m * 256 + cc) * dsub;
-                double acc = 0.0;
-                for (int t = 0; t < dsub; ++t) {
-                    double diff = z[m * dsub + t] - (double)cw[t];
-                    acc += diff * diff;
-                }
-                lut[m * 256 + cc] = acc;
-            }
+        if (!c->lcent) build_lut(z, c->C, c->M, dsub, lut);
         int64_t ncand = 0;
         for (int i = 0; i < c->nprobe; ++i) ncand += c->off[probes[i] + 1] - c->off[probes[i]];
         cand *cs = (cand *)malloc(sizeof(cand) * (size_t)(ncand > 0 ? ncand : 1));
         int64_t w = 0;
         for (int i = 0; i < c->nprobe; ++i) {
             int l = probes[i];
+            if (c->lcent) {
+                /* residual codes: the query's rotated residual to list l,
+                   (P_ds(q) - c_l) R, gives this list's lookup table */
+                const float *cl = c->lcent + (int64_t)l * c->d_s;
+                for (int j = 0; j < c->d_s; ++j) xbuf[j] = qs[j] - (double)cl[j];
+                for (int j = 0; j < c->d_s; ++j) {
+                    double acc = 0.0;
+                    for (int t = 0; t < c->d_s; ++t)
+                        acc += xbuf[t] * (double)c->R[(int64_t)t * c->d_s + j];
+                    z[j] = acc;
+                }
+                build_lut(z, c->C, c->M, dsub, lut);
+            }
             for (int64_t p2 = c->off[l]; p2 < c->off[l + 1]; ++p2) {
                 int64_t id = c->ids[p2];
                 const uint8_t *code = c->codes + id * c->M;
@@ -411,15 +436,15 @@ int orc_ivfopq_search(const float *db, int64_t N, int d, const float *cent, int 
                       const int64_t *list_off, const int32_t *list_ids, const float *R,
                       const float *codebooks, const uint8_t *codes, int M,
                       const float *queries, int64_t B, int d_c, int d_s, int nprobe, int k_out,
-                      int rerank_k, int normalize, int64_t *out_ids, double *out_dist,
-                      int32_t *out_probes, double *out_pdist, int nthreads) {
+                      int rerank_k, int normalize, const float *lcent, int64_t *out_ids,
+                      double *out_dist, int32_t *out_probes, double *out_pdist, int nthreads) {
     (void)N;
     if (d_c < 1 || d_c > ldc || d_s < 1 || d_s > d || nprobe < 1 || nprobe > nlist ||
         k_out < 1 || M < 1 || d_s % M != 0 || rerank_k < 0)
         return -1;
     opq_ctx c = {db, d, cent, nlist, ldc, list_off, list_ids, R, codebooks, codes, M, queries,
                  d_c, d_s, nprobe, k_out, rerank_k, normalize, out_ids, out_dist, out_probes,
-                 out_pdist, nprobe + 1};
+                 out_pdist, nprobe + 1, lcent};
     parallel_for(B, nthreads, opq_range, &c);
     return 0;
 }

@@ -314,6 +314,107 @@ def test_small_training_set_makes_adc_exact():
     assert not fails
 
 
+def test_list_centroids_are_member_means():
+    """Residual centres: the mean of each list's normalised d_s prefixes,
+    computed here list by list with np.mean; an empty list gets zeros."""
+    data = synthdata.small(600, 5, 32, 4, 40)
+    db = data["db"]
+    idx = oracle.build_ivf(db, 8, 7, 3, 600, seed=9)
+    idx = dict(idx)
+    a = idx["assign"].copy()
+    a[a == 6] = 5                          # list 6 becomes empty
+    idx["assign"] = a
+    lc = oracle.list_centroids(db, idx, 24)
+    for l in range(7):
+        rows = db[a == l, :24].astype(np.float64)
+        if len(rows) == 0:
+            assert np.all(lc[l] == 0)
+            continue
+        rows /= np.linalg.norm(rows, axis=1, keepdims=True)
+        assert np.allclose(lc[l], rows.mean(0), rtol=1e-6, atol=1e-7)
+
+
+def _residual_case(seed, N=1500, d=48, d_s=48, M=6, nlist=6, train_n=1500):
+    data = synthdata.small(N, 12, d, 8, seed)
+    db, q = data["db"], data["queries"]
+    idx = oracle.build_ivf(db, 16, nlist, 4, N, seed=seed + 1)
+    lc = oracle.list_centroids(db, idx, d_s)
+    res = {"lcent": lc, "assign": idx["assign"]}
+    opq = oracle.train_opq(db, d_s, M, 2, 2, 3, train_n, seed=seed + 2, residual=res)
+    codes = oracle.pq_encode(db, d_s, M, opq["R"], opq["codebooks"], lcent=lc,
+                             assign=idx["assign"])
+    return db, q, idx, lc, opq, codes
+
+
+def test_residual_adc_is_distance_to_reconstruction():
+    """Residual IVF-OPQ: a member x of list l is reconstructed as
+    lcent[l] + decode(code_x) R^T, and its ADC score equals the squared
+    distance from P_ds(q) to that reconstruction (R orthogonal up to FP32
+    rounding), computed here directly in the unrotated space."""
+    db, q, idx, lc, opq, codes = _residual_case(41)
+    res = oracle.search_ivfopq(db, idx, opq, codes, q, 16, 3, 40)
+    Pq = oracle.prefix(q, 48)
+    R = opq["R"].astype(np.float64)
+    rec = oracle.pq_decode(codes, opq["codebooks"].astype(np.float64)) @ R.T + \
+        lc[idx["assign"]].astype(np.float64)
+    for i in range(len(q)):
+        dd = ((Pq[i][None] - rec[res["ids"][i]]) ** 2).sum(1)
+        assert np.allclose(dd, res["dist"][i], rtol=1e-5, atol=1e-7)
+        assert np.all(np.diff(res["dist"][i]) >= 0)
+        # every returned id lies in a probed list
+        assert set(idx["assign"][res["ids"][i]]) <= set(res["probes"][i])
+
+
+def test_residual_with_zero_centres_is_plain_ivfopq():
+    """With all list centres zero the residual codes and tables are the plain
+    ones: identical codes and results."""
+    data = synthdata.small(1000, 10, 32, 6, 42)
+    db, q = data["db"], data["queries"]
+    idx = oracle.build_ivf(db, 8, 5, 3, 1000, seed=3)
+    zero = np.zeros((5, 32), np.float32)
+    res = {"lcent": zero, "assign": idx["assign"]}
+    o1 = oracle.train_opq(db, 32, 4, 2, 2, 2, 1000, seed=4, residual=res)
+    o0 = oracle.train_opq(db, 32, 4, 2, 2, 2, 1000, seed=4)
+    assert np.array_equal(o1["R"], o0["R"]) and np.array_equal(o1["codebooks"], o0["codebooks"])
+    c1 = oracle.pq_encode(db, 32, 4, o1["R"], o1["codebooks"], lcent=zero, assign=idx["assign"])
+    c0 = oracle.pq_encode(db, 32, 4, o0["R"], o0["codebooks"])
+    assert np.array_equal(c1, c0)
+    a = oracle.search_ivfopq(db, idx, o1, c1, q, 8, 3, 10)
+    b = oracle.search_ivfopq(db, idx, o0, c0, q, 8, 3, 10)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["dist"], b["dist"])
+
+
+def test_residual_small_training_set_is_exact():
+    """At most 256 rows: every residual is its own codeword, so residual ADC is
+    the exact distance up to the rotation's FP32 orthogonality, and IVF-OPQ
+    ranks like IVF."""
+    data = synthdata.small(220, 10, 32, 4, 43)
+    db, q = data["db"], data["queries"]
+    idx = oracle.build_ivf(db, 8, 4, 3, 220, seed=5)
+    lc = oracle.list_centroids(db, idx, 16)
+    res = {"lcent": lc, "assign": idx["assign"]}
+    opq = oracle.train_opq(db, 16, 4, 2, 2, 2, 220, seed=6, residual=res)
+    codes = oracle.pq_encode(db, 16, 4, opq["R"], opq["codebooks"], lcent=lc, assign=idx["assign"])
+    a = oracle.search_ivfopq(db, idx, opq, codes, q, 8, 4, 15)
+    b = oracle.search_ivf(db, idx, q, 8, 16, 4, 15)
+    assert np.allclose(a["dist"], b["dist"], rtol=1e-5, atol=1e-6)
+    n, fails = check_topk(a["ids"], a["dist"], b["ids"], b["dist"], 15)
+    assert not fails
+
+
+def test_residual_pin_catches_a_wrong_sign():
+    """Planted slip: adding the list centre instead of subtracting it breaks
+    the reconstruction pin."""
+    db, q, idx, lc, opq, codes = _residual_case(44)
+    res = oracle.search_ivfopq(db, idx, opq, codes, q, 16, 3, 40)
+    Pq = oracle.prefix(q, 48)
+    R = opq["R"].astype(np.float64)
+    wrong = oracle.pq_decode(codes, opq["codebooks"].astype(np.float64)) @ R.T - \
+        lc[idx["assign"]].astype(np.float64)
+    dd = ((Pq[0][None] - wrong[res["ids"][0]]) ** 2).sum(1)
+    assert not np.allclose(dd, res["dist"][0], rtol=1e-5, atol=1e-7)
+
+
 def test_full_rerank_equals_exact_ivf():
     """Reranking every ADC candidate with the exact d_s distance gives the
     plain IVF result (Sec. 4.3 shortlist-rerank)."""
