@@ -281,7 +281,7 @@ def serving_phase(P, torch, data, db_dev, args, B):
     """Poisson request stream over two resident indices (d_c = 16 and 64),
     request sizes uniform in [1, 4096], per-request budgets; once with every
     request on the mixed-precision path and once on the FP32 path."""
-    from paper_2305_19435_gb300.serving import Budget, Server, poisson_stream
+    from paper_2305_19435_gb300.serving import Budget, NativeServer, poisson_stream
     idx = {}
     for d_c in (16, 64):
         g = P.build_ivf(db_dev, d_c, args.nlist, args.niter, min(db_dev.shape[0], 256 * args.nlist),
@@ -300,7 +300,7 @@ def serving_phase(P, torch, data, db_dev, args, B):
     for mode in ("bf16", "f32"):
         rng = np.random.default_rng(args.seed)   # same budgets and slices for both paths
         arrivals = poisson_stream(args.serve_rate, args.serve_seconds, seed=args.seed + 5)
-        srv = Server(idx, streams=3, max_batch=8192, mem_budget=24 << 30).start()
+        srv = NativeServer(idx, streams=3, max_batch=8192, mem_budget=24 << 30).start()
         reqs = []
         t0 = time.perf_counter()
         for (t, n, _) in arrivals:
@@ -316,8 +316,8 @@ def serving_phase(P, torch, data, db_dev, args, B):
             reqs.append(srv.submit(qh[lo:lo + n], b, index_key=d_c))
         for r in reqs:
             r.wait(600)
-        srv.stop()
         st = srv.stats()
+        srv.stop()
         errs = sum(1 for r in reqs if r.error is not None)
         st["errors"] = errs
         st["offered_qps"] = args.serve_rate

@@ -91,6 +91,15 @@ int64_t adanns_launch_count(void);
  *   ADANNS_OPT_WAIT_LIMIT_NS  bound of every tensor-core pipeline wait
  *                             (default 2e9 ns, within [1e5, 6e10]); a wait that
  *                             runs out is reported by adanns_index_status
+ *   ADANNS_OPT_SCAN_FILTER    0 (default): every approximate distance of the
+ *                             BF16 / FP8 tensor-core scan is written (2 bytes)
+ *                             and the shortlist selected afterwards; 1: each
+ *                             query's nearest list is scanned first and, in the
+ *                             other lists, only members whose approximate
+ *                             distance can still enter the shortlist leave the
+ *                             SM (as 4-byte records).  Both give the same
+ *                             result.  Lists of more than 65,536 members always
+ *                             take the first.
  *   ADANNS_OPT_TEST_SKIP_LOAD test hook, -1 (default).  n >= 0 makes the next
  *                             tensor-core scan launch (one launch; the option
  *                             then returns to -1) leave out stage load n (in
@@ -110,7 +119,8 @@ int64_t adanns_launch_count(void);
 #define ADANNS_OPT_SCRATCH_BYTES 4
 #define ADANNS_OPT_WAIT_LIMIT_NS 5
 #define ADANNS_OPT_TEST_SKIP_LOAD 6
-#define ADANNS_OPT_COUNT 7
+#define ADANNS_OPT_SCAN_FILTER 7
+#define ADANNS_OPT_COUNT 8
 int adanns_set_option(int option, int64_t value);
 int adanns_get_option(int option, int64_t *value);
 
@@ -132,6 +142,10 @@ int adanns_profile_read_host(double *us, int nstage);
  *   values[0]  (query, candidate) pairs re-scored by the exact rerank of the
  *              low-precision tiers, after the certified pruning
  *   values[1]  shortlist slots (queries x rerank_k) of those calls
+ *   values[2]  candidates kept by the filtered tensor-core scan
+ *              (ADANNS_OPT_SCAN_FILTER) for the shortlist selection
+ *   values[3]  queries whose kept candidates exceeded the selection's
+ *              on-chip buffer (selected from global memory instead)
  * Entries beyond the known counters are 0.
  */
 int adanns_profile_read_counters(int64_t *values, int ncounter);
@@ -178,6 +192,10 @@ int adanns_index_create(const float *db, int64_t N, int d, const float *centroid
 int adanns_index_info(const adanns_index *idx, int64_t *N, int *d, int *d_c, int *nlist,
                       int *metric);
 
+/* OPQ shape of an index (host outputs, either may be NULL): the prefix d_s
+ * and the code bytes M, both 0 when the index holds no OPQ data. */
+int adanns_index_opq_info(const adanns_index *idx, int *d_s, int *M);
+
 /* Copy the CSR lists to device buffers: list_off int64 [nlist + 1] (member
  * offsets), list_ids int32 [N] (database ids, ascending inside each list). */
 int adanns_index_get_lists(const adanns_index *idx, int64_t *list_off, int32_t *list_ids,
@@ -199,6 +217,36 @@ int64_t adanns_search_scratch_bytes(const adanns_index *idx, int64_t B, int d_c,
 
 /* Release an index (NULL is ignored).  Waits for the device to finish using it. */
 void adanns_index_free(adanns_index *idx);
+
+/*
+ * Index files.  The index is formed once and then serves many queries (Sec. 5
+ * "Search for AdANNS Hyperparameters"), so it can be written to a file and
+ * loaded by another process instead of being rebuilt.
+ *
+ * adanns_index_export writes to the HOST path `path` (created or truncated)
+ * what defines the index: a 96-byte header (magic "ADANNSIX", format version
+ * 1, N, d, d_c, nlist, metric, storage mask, OPQ d_s and M, OPQ flags with
+ * bit 0 = residual codes), the FP32 centroids [nlist][d_c], the list of every
+ * database id (int32 [N]), the database rows in id order (FP32 [N][d],
+ * recovered from the index's own copy), with OPQ data the rotation
+ * [d_s][d_s], the codebooks [M][256][d_s / M] and the codes in id order
+ * (uint8 [N][M]), and with residual codes the list centres [nlist][d_s]; all
+ * little-endian, packed.  It synchronises the stream.  The file is about as
+ * large as the database.  Errors: ADANNS_ERR_ARG (NULL argument, the file
+ * cannot be opened or written).
+ *
+ * adanns_index_import reads such a file and builds the index with
+ * adanns_index_create (the same storage tiers) and, when present,
+ * adanns_index_set_opq, so the imported index searches exactly like the
+ * exported one.  It allocates the database rows on the device for the
+ * duration of the call, synchronises the stream, and on success *out owns the
+ * index (release with adanns_index_free).  Errors: ADANNS_ERR_ARG (NULL
+ * argument, file cannot be opened), ADANNS_ERR_STATE (not an index file, other
+ * version, inconsistent sizes, truncated or over-long file), plus those of
+ * adanns_index_create.
+ */
+int adanns_index_export(const adanns_index *idx, const char *path, void *cuda_stream);
+int adanns_index_import(const char *path, void *cuda_stream, adanns_index **out);
 
 /*
  * Lloyd assignment step (Sec. 3 "IVF"): for each of n points (rows of `ld`
@@ -311,6 +359,34 @@ int adanns_build_opq(adanns_index *idx, const float *db, int d_s, int M, int opq
                      int pq_iters, int final_iters, int64_t train_n, uint64_t seed, double *trace,
                      void *cuda_stream);
 
+/*
+ * Residual-encoded AdANNS-IVFOPQ (the IVFOPQ row of Table "formula" with the
+ * codes taken of residuals, the usual IVF-PQ variant; the paper does not
+ * define it further).  The coarse centroids exist only at d_c, so the residual
+ * of a database row x in list l is taken against that list's centre at d_s,
+ * lcent[l] = the mean of P_ds over the list's members (FP64 sums, FP32
+ * values; zero for an empty list): the codes quantise (P_ds(x) - lcent[l]) R.
+ * adanns_build_opq_residual trains exactly as adanns_build_opq but on the
+ * residuals of the training rows, and encodes every row's residual.  A search
+ * (adanns_search_ivfopq, nprobe <= 256) then scores a member of a probed list
+ * l by sum_m ||((P_ds(q) - lcent[l]) R)_m - C_m[code_m]||^2, evaluated as
+ * sum_m (LUT_q[m][code_m] + S_l[m][code_m]) + |w_l|^2 - 2 <w_l, P_ds(q) R>
+ * with w_l = lcent[l] R and S_l[m][c] = 2 <w_l,m, C_m[c]> (FP32 tables
+ * nlist x M x 256 kept by the index; negative rounding residue is clamped to
+ * 0).  adanns_index_set_opq_residual attaches given data (list_centres
+ * [nlist][d_s] device FP32 plus what adanns_index_set_opq takes);
+ * adanns_index_get_list_centres copies them out (ADANNS_ERR_STATE without
+ * residual codes).  All three synchronise except the copy.
+ */
+int adanns_build_opq_residual(adanns_index *idx, const float *db, int d_s, int M, int opq_iters,
+                              int pq_iters, int final_iters, int64_t train_n, uint64_t seed,
+                              double *trace, void *cuda_stream);
+int adanns_index_set_opq_residual(adanns_index *idx, int d_s, int M, const float *R,
+                                  const float *codebooks, const uint8_t *codes_by_id,
+                                  const float *list_centres, void *cuda_stream);
+int adanns_index_get_list_centres(const adanns_index *idx, float *list_centres,
+                                  void *cuda_stream);
+
 /* Attach given OPQ data (device): R, codebooks and codes indexed by database
  * id (N x M); the codes are re-laid out in list order.  Synchronises. */
 int adanns_index_set_opq(adanns_index *idx, int d_s, int M, const float *R,
@@ -420,6 +496,64 @@ void adanns_plan_free(adanns_plan *plan);
 int adanns_search_ivf_noalloc(const adanns_index *idx, const float *queries, int64_t B, int d_c,
                               int d_s, int nprobe, int k, int64_t *out_ids, float *out_dist,
                               void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Continuous-batching server (the serving loop of the compute-aware elastic
+ * search of Sec. 5 "Compute-aware Elastic Search During Inference": every
+ * request carries its own compute budget over resident indices).
+ *
+ * adanns_server_create binds a server to the current device and to nindex
+ * resident indices (not copied: they must outlive the server) and starts one
+ * worker thread.  Requests are HOST query rows (n x d FP32 of the chosen
+ * index; copied at submit, so the caller may reuse the buffer at once) with a
+ * budget.  The worker keeps requests in arrival order; whenever one of its
+ * nstreams CUDA streams is free it packs the oldest pending request with later
+ * ones of the same index and budget into one batch of at most max_batch rows,
+ * admits the batch if its scratch estimate (adanns_search_scratch_bytes plus
+ * the batch's rows and results) fits mem_budget bytes next to the batches in
+ * flight (a batch is always admitted when nothing is in flight), and runs it
+ * on that stream: pinned staging, host-to-device copy, the search,
+ * device-to-host copy of the results.  Batches on different streams overlap
+ * on the device.  A request's rows get the same ids and distances as the same
+ * rows searched alone with adanns_search_ivf / adanns_search_ivfopq.
+ *
+ * adanns_server_submit checks the budget against the index (the search's own
+ * argument rules; errors are returned there) and returns a ticket.
+ * adanns_server_poll waits up to wait_ms (0: no wait, -1: until done) for the
+ * ticket; it returns ADANNS_PENDING (1) if the request is not finished, else
+ * retires the ticket and returns ADANNS_OK with the results copied to the HOST
+ * arrays ids (int64 [n][k]) and dist (FP32 [n][k]) and the latency from submit
+ * to results on the host, or the error the request's batch met (message in
+ * adanns_last_error on the polling thread).  adanns_server_stats reports
+ * latency percentiles (p50, p99 over finished requests), requests launched,
+ * batches, rows served, rows per second between the first submit and the last
+ * completion, and the largest memory estimate in flight; any pointer may be
+ * NULL.  adanns_server_destroy stops accepting requests, finishes the pending
+ * and in-flight ones, stops the worker and frees the server (results not
+ * polled are dropped); no other call on the server may run concurrently with
+ * it.  Submit, poll and stats may be called from any threads.
+ * ---------------------------------------------------------------------- */
+#define ADANNS_PENDING 1
+#define ADANNS_METHOD_IVF 0    /* adanns_search_ivf with the budget's storage tier */
+#define ADANNS_METHOD_IVFOPQ 1 /* adanns_search_ivfopq (d_s and storage unused) */
+
+typedef struct adanns_budget {
+  int method;   /* ADANNS_METHOD_* */
+  int d_c, d_s, nprobe, k;
+  int storage;  /* ADANNS_STORE_F32 / _BF16 / _FP8E4M3 for ADANNS_METHOD_IVF */
+  int rerank_k; /* as in the search calls */
+} adanns_budget;
+
+typedef struct adanns_server adanns_server;
+int adanns_server_create(const adanns_index *const *indices, int nindex, int nstreams,
+                         int64_t max_batch, int64_t mem_budget, adanns_server **out);
+int adanns_server_submit(adanns_server *srv, int index_slot, const float *queries, int64_t n,
+                         const adanns_budget *budget, int64_t *ticket);
+int adanns_server_poll(adanns_server *srv, int64_t ticket, int wait_ms, int64_t *ids, float *dist,
+                       double *latency_ms);
+int adanns_server_stats(adanns_server *srv, double *p50_ms, double *p99_ms, int64_t *requests,
+                        int64_t *batches, int64_t *queries, double *qps, int64_t *max_inflight);
+int adanns_server_destroy(adanns_server *srv);
 
 /* ------------------------------------------------------------------------
  * Lists partitioned over several GPUs (the IVF probe/scan is independent per

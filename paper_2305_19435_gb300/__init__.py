@@ -80,6 +80,17 @@ def lib():
         L.adanns_plan_free.restype = None
         L.adanns_map_ids.argtypes = [P, i64, P, i64, P]
         L.adanns_merge_shards.argtypes = [P, P, i32, i64, i32, P, P, P]
+        L.adanns_index_opq_info.argtypes = [P, P, P]
+        L.adanns_build_opq_residual.argtypes = [P, P, i32, i32, i32, i32, i32, i64, u64, P, P]
+        L.adanns_index_set_opq_residual.argtypes = [P, i32, i32, P, P, P, P, P]
+        L.adanns_index_get_list_centres.argtypes = [P, P, P]
+        L.adanns_index_export.argtypes = [P, ctypes.c_char_p, P]
+        L.adanns_index_import.argtypes = [ctypes.c_char_p, P, P]
+        L.adanns_server_create.argtypes = [P, i32, i32, i64, i64, P]
+        L.adanns_server_submit.argtypes = [P, i32, P, i64, P, P]
+        L.adanns_server_poll.argtypes = [P, i64, i32, P, P, P]
+        L.adanns_server_stats.argtypes = [P, P, P, P, P, P, P, P]
+        L.adanns_server_destroy.argtypes = [P]
         L.adanns_set_option.argtypes = [i32, i64]
         L.adanns_get_option.argtypes = [i32, P]
         _lib = L
@@ -94,6 +105,7 @@ OPT_RERANK_PRUNE = 3
 OPT_SCRATCH_BYTES = 4
 OPT_WAIT_LIMIT_NS = 5
 OPT_TEST_SKIP_LOAD = 6
+OPT_SCAN_FILTER = 7
 
 
 def set_option(opt: int, value: int):
@@ -120,6 +132,18 @@ class option:
 
     def __exit__(self, *exc):
         set_option(self.opt, self.old)
+
+
+class BudgetC(ctypes.Structure):
+    """adanns_budget (include/adanns.h)."""
+    _fields_ = [("method", ctypes.c_int), ("d_c", ctypes.c_int), ("d_s", ctypes.c_int),
+                ("nprobe", ctypes.c_int), ("k", ctypes.c_int), ("storage", ctypes.c_int),
+                ("rerank_k", ctypes.c_int)]
+
+
+METHOD_IVF = 0
+METHOD_IVFOPQ = 1
+PENDING = 1
 
 
 def launch_count() -> int:
@@ -155,7 +179,7 @@ def profile_read_host(nstage: int = 16) -> dict:
     return {names[i]: us[i] for i in range(nstage) if us[i]}
 
 
-COUNTERS = ("rerank_pairs", "shortlist_slots")
+COUNTERS = ("rerank_pairs", "shortlist_slots", "scan_survivors", "select_slow_queries")
 
 
 def profile_read_counters() -> dict:
@@ -200,6 +224,9 @@ class Index:
         _check(lib().adanns_index_info(self._h, ctypes.byref(N), ctypes.byref(d), ctypes.byref(dc),
                                        ctypes.byref(nl), ctypes.byref(m)))
         self.N, self.d, self.d_c, self.nlist, self.metric = N.value, d.value, dc.value, nl.value, m.value
+        ods, om = ctypes.c_int(), ctypes.c_int()
+        _check(lib().adanns_index_opq_info(handle, ctypes.byref(ods), ctypes.byref(om)))
+        self.opq = (ods.value, om.value) if om.value else None
 
     @property
     def handle(self):
@@ -255,6 +282,18 @@ def index_create(db: torch.Tensor, centroids: torch.Tensor, assign: torch.Tensor
     _check(lib().adanns_index_create(_ptr(db), db.shape[0], db.shape[1], _ptr(centroids),
                                      centroids.shape[0], centroids.shape[1], _ptr(assign), metric,
                                      storage, _stream(), ctypes.byref(h)))
+    return Index(h)
+
+
+def index_export(index: Index, path: str):
+    """Write the index to a file (synchronises)."""
+    _check(lib().adanns_index_export(index.handle, os.fsencode(path), _stream()))
+
+
+def index_import(path: str) -> Index:
+    """Load an index written by index_export (synchronises)."""
+    h = ctypes.c_void_p()
+    _check(lib().adanns_index_import(os.fsencode(path), _stream(), ctypes.byref(h)))
     return Index(h)
 
 
@@ -363,6 +402,37 @@ def build_opq(index: Index, db: torch.Tensor, d_s: int, M: int, opq_iters: int, 
                                   train_n, seed, tr, _stream()))
     index.opq = (d_s, M)
     return list(tr)
+
+
+def build_opq_residual(index: Index, db: torch.Tensor, d_s: int, M: int, opq_iters: int,
+                       pq_iters: int, final_iters: int, train_n: int, seed: int) -> list:
+    """Residual-encoded AdANNS-OPQ: codes of P_ds(x) minus its list's d_s centre."""
+    _need(db, torch.float32, "db", 2)
+    tr = (ctypes.c_double * max(3 * opq_iters, 1))()
+    _check(lib().adanns_build_opq_residual(index.handle, _ptr(db), d_s, M, opq_iters, pq_iters,
+                                           final_iters, train_n, seed, tr, _stream()))
+    index.opq = (d_s, M)
+    return list(tr)
+
+
+def set_opq_residual(index: Index, d_s: int, M: int, R: torch.Tensor, codebooks: torch.Tensor,
+                     codes_by_id: torch.Tensor, list_centres: torch.Tensor):
+    """Attach residual OPQ data (codes by database id, list centres [nlist, d_s])."""
+    _need(R, torch.float32, "R", 2)
+    _need(codebooks, torch.float32, "codebooks", 3)
+    _need(codes_by_id, torch.uint8, "codes", 2)
+    _need(list_centres, torch.float32, "list_centres", 2)
+    _check(lib().adanns_index_set_opq_residual(index.handle, d_s, M, _ptr(R), _ptr(codebooks),
+                                               _ptr(codes_by_id), _ptr(list_centres), _stream()))
+    index.opq = (d_s, M)
+
+
+def list_centres(index: Index) -> torch.Tensor:
+    """The residual list centres [nlist, d_s] of an index with residual codes."""
+    d_s, _ = index.opq
+    out = torch.empty(index.nlist, d_s, dtype=torch.float32, device="cuda")
+    _check(lib().adanns_index_get_list_centres(index.handle, _ptr(out), _stream()))
+    return out
 
 
 def set_opq(index: Index, d_s: int, M: int, R: torch.Tensor, codebooks: torch.Tensor,

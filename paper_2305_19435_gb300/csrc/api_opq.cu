@@ -23,6 +23,12 @@ int launch_permute_codes(const uint8_t *by_id, const int32_t *list_ids, int64_t 
 int launch_identity(float *R, int d, cudaStream_t st);
 int polar_factor(const float *Mx, int d, float *R, cudaStream_t st);
 int adc_query_tile(int M, int k);
+int launch_list_mean(const adanns_index *x, int d_s, float *lcent, cudaStream_t st);
+int launch_sub_list_centre(float *rows, int64_t n, int ldr, int d_s, const int64_t *ids64,
+                           const int32_t *ids32, const int32_t *assign, const float *lcent,
+                           cudaStream_t st);
+int launch_residual_tables(const float *w, int nlist, int d_s, int M, const float *C, float *S,
+                           float *w2, cudaStream_t st);
 struct AdcArgs;
 int launch_rerank(const int64_t *cand, int kr, int64_t B, const float *qs, int ldq, int d_s,
                   const adanns_index *idx, const float *mscale, int k, int64_t *out_ids,
@@ -118,6 +124,14 @@ int pq_lloyd(const float *z, int64_t n, int d_s, int M, int iters, float *C, uin
   return ADANNS_OK;
 }
 
+void free_residual(adanns_index *x) {
+  cudaFree(x->opq_lcent);
+  cudaFree(x->opq_w);
+  cudaFree(x->opq_w2);
+  cudaFree(x->opq_S);
+  x->opq_lcent = x->opq_w = x->opq_w2 = x->opq_S = nullptr;
+}
+
 void free_opq(adanns_index *x) {
   cudaFree(x->opq_R);
   cudaFree(x->opq_C);
@@ -125,6 +139,30 @@ void free_opq(adanns_index *x) {
   x->opq_R = x->opq_C = nullptr;
   x->codes = nullptr;
   x->opq_ds = x->opq_M = 0;
+  free_residual(x);
+}
+
+int alloc_residual(adanns_index *x, int d_s, int M) {
+  const size_t nl = (size_t)x->nlist;
+  if (cudaMalloc(&x->opq_lcent, sizeof(float) * nl * d_s) != cudaSuccess ||
+      cudaMalloc(&x->opq_w, sizeof(float) * nl * d_s) != cudaSuccess ||
+      cudaMalloc(&x->opq_w2, sizeof(float) * nl) != cudaSuccess ||
+      cudaMalloc(&x->opq_S, sizeof(float) * nl * M * 256) != cudaSuccess) {
+    cudaGetLastError();
+    free_residual(x);
+    return fail(ADANNS_ERR_OOM, "residual table allocation failed");
+  }
+  return ADANNS_OK;
+}
+
+// w = lcent R, |w_l|^2 and the per-list tables S from the index's R and codebooks
+int finish_residual(adanns_index *x, cudaStream_t st) {
+  const int d_s = x->opq_ds, M = x->opq_M;
+  int rc;
+  if ((rc = launch_gemm_f32(false, x->nlist, d_s, d_s, 1.f, x->opq_lcent, d_s, x->opq_R, d_s, 0.f,
+                            x->opq_w, d_s, st)))
+    return rc;
+  return launch_residual_tables(x->opq_w, x->nlist, d_s, M, x->opq_C, x->opq_S, x->opq_w2, st);
 }
 
 int alloc_opq(adanns_index *x, int d_s, int M) {
@@ -158,6 +196,9 @@ int encode_lists(adanns_index *x, const float *db, cudaStream_t st) {
     widen_ids_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x->list_ids + p0, n, r64);
     ADN_LAUNCH("widen_ids_kernel");
     if ((rc = launch_gather_normalize(db, n, x->d, r64, d_s, x->metric, xn, dsp, st))) return rc;
+    if (x->opq_lcent &&
+        (rc = launch_sub_list_centre(xn, n, dsp, d_s, r64, nullptr, x->assign, x->opq_lcent, st)))
+      return rc;
     if ((rc = launch_gemm_f32(false, (int)n, d_s, d_s, 1.f, xn, dsp, x->opq_R, d_s, 0.f, z, d_s,
                               st)))
       return rc;
@@ -246,7 +287,8 @@ int search_ivfopq_select(const adanns_index *idx, const float *queries, int64_t 
                              : (int)std::min<int64_t>((target + tiles_est - 1) / tiles_est,
                                                       ((int64_t)idx->max_list + 255) / 256);
       if ((rc = launch_adc_dist(idx->codes, idx->list_off, M, lut, tl, tb, tc, ntiles, counter + 1,
-                                pair_q, pair_out, pbase, cand, qa, nsplit, st)))
+                                pair_q, pair_out, pbase, cand, qa, nsplit, st, idx->opq_S,
+                                idx->opq_w, idx->opq_w2, z, d_s)))
         return rc;
     }
     {
@@ -332,9 +374,27 @@ int adanns_procrustes(const float *Y, const float *Zhat, int64_t n, int d_s, flo
   return polar_factor(Mx, d_s, R, st);
 }
 
+static int build_opq_impl(adanns_index *idx, const float *db, int d_s, int M, int opq_iters,
+                          int pq_iters, int final_iters, int64_t train_n, uint64_t seed,
+                          double *trace, bool residual, void *cuda_stream);
+
 int adanns_build_opq(adanns_index *idx, const float *db, int d_s, int M, int opq_iters,
                      int pq_iters, int final_iters, int64_t train_n, uint64_t seed, double *trace,
                      void *cuda_stream) {
+  return build_opq_impl(idx, db, d_s, M, opq_iters, pq_iters, final_iters, train_n, seed, trace,
+                        false, cuda_stream);
+}
+
+int adanns_build_opq_residual(adanns_index *idx, const float *db, int d_s, int M, int opq_iters,
+                              int pq_iters, int final_iters, int64_t train_n, uint64_t seed,
+                              double *trace, void *cuda_stream) {
+  return build_opq_impl(idx, db, d_s, M, opq_iters, pq_iters, final_iters, train_n, seed, trace,
+                        true, cuda_stream);
+}
+
+static int build_opq_impl(adanns_index *idx, const float *db, int d_s, int M, int opq_iters,
+                          int pq_iters, int final_iters, int64_t train_n, uint64_t seed,
+                          double *trace, bool residual, void *cuda_stream) {
   if (!idx || !db) return fail(ADANNS_ERR_ARG, "NULL argument");
   int rc;
   if ((rc = check_opq_shape(d_s, M, idx->d))) return rc;
@@ -349,6 +409,12 @@ int adanns_build_opq(adanns_index *idx, const float *db, int d_s, int M, int opq
   std::vector<int64_t> init(256);
   for (int c = 0; c < 256; ++c) init[c] = P[(size_t)(c % (int64_t)P.size())];
   if ((rc = alloc_opq(idx, d_s, M))) return rc;
+  if (residual) {
+    if ((rc = alloc_residual(idx, d_s, M)) || (rc = launch_list_mean(idx, d_s, idx->opq_lcent, st))) {
+      free_opq(idx);
+      return rc;
+    }
+  }
   Scratch s(st);
   int64_t *d_s1, *d_init;
   float *Y, *Z, *Zh, *Mx, *mind;
@@ -365,6 +431,9 @@ int adanns_build_opq(adanns_index *idx, const float *db, int d_s, int M, int opq
   ADN_CUDA(cudaMemcpyAsync(d_s1, S1.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
   ADN_CUDA(cudaMemcpyAsync(d_init, init.data(), sizeof(int64_t) * 256, cudaMemcpyHostToDevice, st));
   if ((rc = launch_gather_normalize(db, n, idx->d, d_s1, d_s, idx->metric, Y, d_s, st))) return rc;
+  if (residual && (rc = launch_sub_list_centre(Y, n, d_s, d_s, d_s1, nullptr, idx->assign,
+                                               idx->opq_lcent, st)))
+    return rc;
   if ((rc = launch_identity(idx->opq_R, d_s, st))) return rc;
   int nt = 0;
   bool have_C = false;
@@ -422,6 +491,7 @@ int adanns_build_opq(adanns_index *idx, const float *db, int d_s, int M, int opq
     return rc;
   put(dist);
   if ((rc = encode_lists(idx, db, st))) return rc;
+  if (residual && (rc = finish_residual(idx, st))) return rc;
   ADN_CUDA(cudaStreamSynchronize(st));
   return ADANNS_OK;
 }
@@ -438,6 +508,37 @@ int adanns_index_set_opq(adanns_index *idx, int d_s, int M, const float *R,
                            cudaMemcpyDeviceToDevice, st));
   if ((rc = launch_permute_codes(codes_by_id, idx->list_ids, idx->N, M, idx->codes, st))) return rc;
   ADN_CUDA(cudaStreamSynchronize(st));
+  return ADANNS_OK;
+}
+
+int adanns_index_set_opq_residual(adanns_index *idx, int d_s, int M, const float *R,
+                                  const float *codebooks, const uint8_t *codes_by_id,
+                                  const float *list_centres, void *cuda_stream) {
+  if (!list_centres) return fail(ADANNS_ERR_ARG, "NULL argument");
+  int rc;
+  if ((rc = adanns_index_set_opq(idx, d_s, M, R, codebooks, codes_by_id, cuda_stream))) return rc;
+  cudaStream_t st = S(cuda_stream);
+  if ((rc = alloc_residual(idx, d_s, M))) return rc;
+  ADN_CUDA(cudaMemcpyAsync(idx->opq_lcent, list_centres, sizeof(float) * idx->nlist * d_s,
+                           cudaMemcpyDeviceToDevice, st));
+  if ((rc = finish_residual(idx, st))) return rc;
+  ADN_CUDA(cudaStreamSynchronize(st));
+  return ADANNS_OK;
+}
+
+int adanns_index_get_list_centres(const adanns_index *idx, float *list_centres,
+                                  void *cuda_stream) {
+  if (!idx || !list_centres) return fail(ADANNS_ERR_ARG, "NULL argument");
+  if (!idx->opq_lcent) return fail(ADANNS_ERR_STATE, "the index has no residual OPQ codes");
+  ADN_CUDA(cudaMemcpyAsync(list_centres, idx->opq_lcent, sizeof(float) * idx->nlist * idx->opq_ds,
+                           cudaMemcpyDeviceToDevice, S(cuda_stream)));
+  return ADANNS_OK;
+}
+
+int adanns_index_opq_info(const adanns_index *idx, int *d_s, int *M) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  if (d_s) *d_s = idx->codes ? idx->opq_ds : 0;
+  if (M) *M = idx->codes ? idx->opq_M : 0;
   return ADANNS_OK;
 }
 
@@ -477,7 +578,9 @@ int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t 
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
   const int kr = rerank_k > 0 ? rerank_k : k;
-  if (adc_select_enabled(nprobe))
+  if (idx->opq_S && nprobe > 256)
+    return fail(ADANNS_ERR_ARG, "residual IVF-OPQ search needs nprobe <= 256");
+  if (adc_select_enabled(nprobe) || idx->opq_S)
     return search_ivfopq_select(idx, queries, B, d_c, nprobe, k, kr, rerank_k > 0, out_ids,
                                 out_dist, out_probes, st);
   const int qa = adc_query_tile(M, kr);

@@ -162,6 +162,13 @@ int launch_invert_probes(const uint64_t *ckeys, int64_t B, int nprobe, int nlist
                          int32_t *pair_q, int32_t *pair_out, int32_t *tile_list,
                          int32_t *tile_beg, int32_t *tile_cnt, int *ntiles, int32_t *probes_out,
                          cudaStream_t st);
+// The same over probe slots [s0, s0 + ns) of each query only (pair_out still
+// holds the pair index q * nprobe + slot; probes_out gets those slots' lists).
+int launch_invert_probe_slots(const uint64_t *ckeys, int64_t B, int nprobe, int s0, int ns,
+                              int nlist, int qt, int32_t *lcnt, int32_t *lbeg, int32_t *lfill,
+                              int32_t *tbeg, int32_t *pair_q, int32_t *pair_out,
+                              int32_t *tile_list, int32_t *tile_beg, int32_t *tile_cnt,
+                              int *ntiles, int32_t *probes_out, cudaStream_t st);
 int launch_merge(const uint64_t *pkeys, int64_t B, int nprobe, int k, int64_t *out_ids,
                  float *out_dist, cudaStream_t st);
 int num_sms();
@@ -210,11 +217,22 @@ struct MmaScanArgs {
   int *err;
   int *tile_counter;         // zeroed before the launch: next tile to take
   int fp8;
+  // filtered mode (rec != NULL): instead of every key, each (query, probe slot)
+  // pair p keeps only its members with key <= tau[query] (tau NULL: all), as
+  // 32-bit records (key << 16 | member index, lists below 65,537 members)
+  // compacted from rec[pbase[p]]; rcnt[p] (zeroed before) counts them
+  uint32_t *rec;
+  int *rcnt;
+  const uint16_t *tau;
   uint64_t wait_ns;          // bound of each pipeline wait (set by the launcher)
   int skip_fill;             // test hook: stage load skip_fill of work item 0 is left out (-1: none)
 };
 // work counters recorded while profiling is on (adanns_profile_read_counters)
-enum ProfileCounter { PC_RERANK_PAIRS = 0, PC_SHORTLIST_SLOTS = 1, PC_NCOUNTER = 8 };
+enum ProfileCounter {
+  PC_RERANK_PAIRS = 0, PC_SHORTLIST_SLOTS = 1, PC_SURVIVORS = 2, PC_SELECT_SLOW = 3,
+  PC_NCOUNTER = 8
+};
+bool profiling();  // whether adanns_profile_enable(1) is in effect
 void profile_count(int counter, const int64_t *dev_value, cudaStream_t st);
 void profile_count_host(int counter, int64_t value);
 
@@ -255,14 +273,29 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
 int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, int kk, int k, const float *qrho, float rmax,
                     float e_rest, int prune, int64_t B, int64_t *out, cudaStream_t st);
+// Filtered tensor-core scan: tau and the in-place compaction of slot 0, and
+// the shortlist selected from the survivors (same result as launch_select16).
+int launch_shortlist_tau(uint32_t *rec, int *rcnt, const int64_t *pbase, int nprobe, int kk,
+                         int64_t B, uint16_t *tau, cudaStream_t st);
+// stats (NULL, or 2 zeroed device counters): survivors, queries selected
+// from global memory because their survivors exceed the shared buffer
+int launch_select_surv(const uint32_t *rec, const int *rcnt, const int64_t *pbase,
+                       const uint64_t *ckeys, int nprobe, const int64_t *list_off, int kk, int k,
+                       const float *qrho, float rmax, float e_rest, int prune, int64_t B,
+                       int64_t *out, unsigned long long *stats, cudaStream_t st);
 int launch_keys_to_ids(const uint64_t *keys, int64_t n, int64_t *ids, cudaStream_t st);
 int launch_final_topk(const uint64_t *keys, int kr, int64_t B, int k, int64_t *out_ids,
                       float *out_dist, cudaStream_t st);
 int adc_dist_query_tile(int M);
+// res_S / res_w / res_w2 / z (NULL for plain codes): residual terms and the
+// queries' rotated vectors [B][d_s]; the score of a member of list l is then
+// sum_m (lut_q[m][c_m] + S_l[m][c_m]) + w2_l - 2 <w_l, z_q>
 int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const float *lut,
                     const int32_t *tl, const int32_t *tb, const int32_t *tc, const int *ntiles,
                     int *counter, const int32_t *pair_q, const int32_t *pair_out,
-                    const int64_t *pbase, uint32_t *cand, int qa, int nsplit, cudaStream_t st);
+                    const int64_t *pbase, uint32_t *cand, int qa, int nsplit, cudaStream_t st,
+                    const float *res_S = nullptr, const float *res_w = nullptr,
+                    const float *res_w2 = nullptr, const float *z = nullptr, int d_s = 0);
 int launch_select32(const uint32_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, const int32_t *list_ids, int64_t B, int kk,
                     uint64_t *out, cudaStream_t st);
@@ -323,6 +356,11 @@ struct adanns_index {
   float *opq_R = nullptr;       // d_s x d_s, z = x R
   float *opq_C = nullptr;       // M x 256 x (d_s / M)
   uint8_t *codes = nullptr;     // N x M, list order
+  // residual codes (adanns_build_opq_residual / adanns_index_set_opq_residual):
+  // lcent = list centres [nlist][d_s] (mean normalised d_s prefix of each
+  // list), w = lcent R [nlist][d_s], w2 = |w_l|^2 [nlist], S[l][m][c] =
+  // 2 <w_l,m, C_m[c]> [nlist][M][256]; NULL for plain codes
+  float *opq_lcent = nullptr, *opq_w = nullptr, *opq_w2 = nullptr, *opq_S = nullptr;
   // low-precision tiers [0] BF16 (64-dim blocks), [1] FP8-E4M3 (128-dim blocks)
   void *lowp[2] = {nullptr, nullptr};
   int lowp_blocks[2] = {0, 0};

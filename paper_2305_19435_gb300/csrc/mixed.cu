@@ -343,6 +343,12 @@ static float shortlist_e_rest(int d_s, int d_pad) {
                  1e-4);
 }
 
+// Whether a search uses the filtered tensor-core scan (records carry a 16-bit
+// member index, so every list must have at most 65,536 members).
+static bool scan_filter_enabled(const adanns_index *idx) {
+  return option(ADANNS_OPT_SCAN_FILTER) != 0 && idx->max_list <= 65536;
+}
+
 int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
                  int nprobe, int k, int which, int kk, int64_t *out_ids, float *out_dist,
                  int32_t *out_probes, cudaStream_t st) {
@@ -352,12 +358,18 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
   const int qt = 128;
+  const bool filt = scan_filter_enabled(idx);
   const int64_t seg_q = (int64_t)nprobe * (((int64_t)idx->max_list + 7) & ~7ll);
-  const int64_t per_q = seg_q * 2 + (int64_t)nprobe * ((int64_t)nkb * 128 * 128 / qt + 32) +
+  const int64_t per_q = seg_q * (filt ? 4 : 2) +
+                        (int64_t)nprobe * ((int64_t)nkb * 128 * 128 / qt + 36) +
                         (int64_t)(dcp + dsp) * 4 + (int64_t)nkb * 128 + (int64_t)kk * 8 + 64;
   // slices bounded by a scratch budget (the candidate keys dominate it)
   const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
-  const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
+  // work-item tiles: the filtered scan's two passes (slot 0; slots 1..) each
+  // get their own, the unfiltered scan one set over every slot
+  const int64_t tiles_a = filt ? (Bc + qt - 1) / qt + nlist : (Bc * nprobe + qt - 1) / qt + nlist;
+  const int64_t tiles_b = filt && nprobe > 1 ? (Bc * (nprobe - 1) + qt - 1) / qt + nlist : 0;
+  const int64_t max_tiles = tiles_a + tiles_b;
   const bool prune = shortlist_prune_enabled();
   const float rmax = idx->lowp_rmax[which][gran_index(d_s)] * 1.001f;
   const float e_rest = shortlist_e_rest(d_s, nkb * epb);
@@ -365,27 +377,66 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   float *qc, *qs, *qn2, *qsc, *qrho;
   uint64_t *ckeys;
   int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
-  int *ntiles, *counter;
+  int *ntiles, *counter, *rcnt = nullptr;
   int *err = idx->dev_err;
   int64_t *qtot, *qbase, *pbase, *cids;
   unsigned char *qlow, *qtile;
-  uint16_t *cand;
+  uint16_t *cand = nullptr, *tau = nullptr;
+  uint32_t *rec = nullptr;
   int rc;
   if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
       (rc = s.get(&qn2, Bc)) || (rc = s.get(&qsc, Bc)) || (rc = s.get(&qrho, Bc)) || (rc = s.get(&ckeys, (size_t)Bc * nprobe)) ||
       (rc = s.get(&lcnt, nlist)) || (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) ||
       (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
       (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
-      (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) ||
-      (rc = s.get(&counter, 2)) || (rc = s.get(&qtot, Bc)) ||
+      (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 2)) ||
+      (rc = s.get(&counter, 3)) || (rc = s.get(&qtot, Bc)) ||
       (rc = s.get(&qbase, Bc)) || (rc = s.get(&pbase, (size_t)Bc * nprobe)) ||
       (rc = s.get(&cids, (size_t)Bc * kk)) || (rc = s.get(&qlow, (size_t)Bc * nkb * 128)) ||
-      (rc = s.get(&qtile, (size_t)max_tiles * nkb * 128 * 128)) ||
-      (rc = s.get(&cand, (size_t)Bc * seg_q)))
+      (rc = s.get(&qtile, (size_t)max_tiles * nkb * 128 * 128)))
     return rc;
+  if (filt) {
+    if ((rc = s.get(&rec, (size_t)Bc * seg_q)) || (rc = s.get(&rcnt, (size_t)Bc * nprobe)) ||
+        (rc = s.get(&tau, Bc)))
+      return rc;
+  } else if ((rc = s.get(&cand, (size_t)Bc * seg_q))) {
+    return rc;
+  }
+  // survivors and slow-path queries of the selection, for adanns_profile_read_counters
+  unsigned long long *stats = nullptr;
+  if (filt && profiling() && (rc = s.get(&stats, 2))) return rc;
   const int gi = gran_index(d_s);
   const float *mscale = idx->invn + (int64_t)gi * idx->N;
   const float *cx = idx->lowp_cx[which] + (int64_t)gi * idx->N;
+  const int64_t xrows = idx->N * (int64_t)idx->lowp_blocks[which];
+  // one tensor-core scan over a tile set (tile arrays at offset t0, the set's
+  // pairs at offset p0 of pair_out, its own tile count and work counter)
+  auto scan = [&](int64_t t0, int64_t ntile_cap, int64_t p0, int set,
+                  const uint16_t *thr) -> int {
+    MmaScanArgs m{};
+    m.tile_list = tl + t0;
+    m.tile_beg = tb + t0;
+    m.tile_cnt = tc + t0;
+    m.ntiles_dev = ntiles + set;
+    m.list_off = idx->list_off;
+    m.pair_out = pair_out + p0;
+    m.pbase = pbase;
+    m.cx = cx;
+    m.qn2 = qn2;
+    m.qsc = qsc;
+    m.nprobe = nprobe;
+    m.nkb = nkb;
+    m.d_blocks = idx->lowp_blocks[which];
+    m.cand = cand;
+    m.rec = rec;
+    m.rcnt = rcnt;
+    m.tau = thr;
+    m.err = err;
+    m.tile_counter = counter + 1 + set;  // zeroed with the cluster-mapping counter
+    m.fp8 = fp8;
+    return launch_mma_scan(qtile + t0 * nkb * 128 * 128, ntile_cap * nkb * 128, idx->lowp[which],
+                           xrows, m, st);
+  };
   for (int64_t b0 = 0; b0 < B; b0 += Bc) {
     const int64_t nb = std::min(Bc, B - b0);
     {
@@ -397,52 +448,63 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
                                                                  qn2, qsc, qrho);
       ADN_LAUNCH("prep_lowp_kernel");
     }
-    ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
+    ADN_CUDA(cudaMemsetAsync(counter, 0, 3 * sizeof(int), st));
     {
       StageTimer t(ST_COARSE, st);
       if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, counter, st))) return rc;
     }
+    int32_t *probes = out_probes ? out_probes + b0 * nprobe : nullptr;
     {
       StageTimer t(ST_INVERT, st);
-      if ((rc = launch_invert_probes(ckeys, nb, nprobe, nlist, qt, lcnt, lbeg, lfill, tbeg, pair_q,
-                                     pair_out, tl, tb, tc, ntiles,
-                                     out_probes ? out_probes + b0 * nprobe : nullptr, st)))
+      // tile set 0: every slot (unfiltered) or slot 0 (filtered); tile set 1:
+      // slots 1.. (filtered); pairs of set 1 follow those of set 0
+      const int ns0 = filt ? 1 : nprobe;
+      if ((rc = launch_invert_probe_slots(ckeys, nb, nprobe, 0, ns0, nlist, qt, lcnt, lbeg, lfill,
+                                          tbeg, pair_q, pair_out, tl, tb, tc, ntiles, probes, st)))
         return rc;
+      gather_qtiles_kernel<<<dim3((unsigned)tiles_a, nkb), 256, 0, st>>>(qlow, nkb, tb, tc, ntiles,
+                                                                         pair_q, qtile);
+      ADN_LAUNCH("gather_qtiles_kernel");
+      if (tiles_b > 0) {
+        const int64_t o1 = nb;  // pairs of set 0
+        if ((rc = launch_invert_probe_slots(ckeys, nb, nprobe, 1, nprobe - 1, nlist, qt, lcnt,
+                                            lbeg, lfill, tbeg, pair_q + o1, pair_out + o1,
+                                            tl + tiles_a, tb + tiles_a, tc + tiles_a, ntiles + 1,
+                                            probes, st)))
+          return rc;
+        gather_qtiles_kernel<<<dim3((unsigned)tiles_b, nkb), 256, 0, st>>>(
+            qlow, nkb, tb + tiles_a, tc + tiles_a, ntiles + 1, pair_q + o1,
+            qtile + tiles_a * nkb * 128 * 128);
+        ADN_LAUNCH("gather_qtiles_kernel");
+      }
       if ((rc = launch_cand_segments(ckeys, nb, nprobe, idx->list_off, qtot, qbase, pbase, st)))
         return rc;
-      gather_qtiles_kernel<<<dim3((unsigned)max_tiles, nkb), 256, 0, st>>>(qlow, nkb, tb, tc,
-                                                                           ntiles, pair_q, qtile);
-      ADN_LAUNCH("gather_qtiles_kernel");
     }
     {
       StageTimer t(ST_MMA, st);
-      MmaScanArgs m{};
-      m.tile_list = tl;
-      m.tile_beg = tb;
-      m.tile_cnt = tc;
-      m.ntiles_dev = ntiles;
-      m.list_off = idx->list_off;
-      m.pair_out = pair_out;
-      m.pbase = pbase;
-      m.cx = cx;
-      m.qn2 = qn2;
-      m.qsc = qsc;
-      m.nprobe = nprobe;
-      m.nkb = nkb;
-      m.d_blocks = idx->lowp_blocks[which];
-      m.cand = cand;
-      m.err = err;
-      m.tile_counter = counter + 1;  // zeroed with the cluster-mapping counter
-      m.fp8 = fp8;
-      const int64_t xrows = idx->N * (int64_t)idx->lowp_blocks[which];
-      if ((rc = launch_mma_scan(qtile, max_tiles * nkb * 128, idx->lowp[which], xrows, m, st)))
+      if (filt) {
+        // pass 1: every query's nearest list, all members kept; its kk-th key
+        // bounds the query's shortlist; pass 2: the other lists, filtered
+        ADN_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int) * nb * nprobe, st));
+        if ((rc = scan(0, tiles_a, 0, 0, nullptr))) return rc;
+        if ((rc = launch_shortlist_tau(rec, rcnt, pbase, nprobe, kk, nb, tau, st))) return rc;
+        if (tiles_b > 0 && (rc = scan(tiles_a, tiles_b, nb, 1, tau))) return rc;
+      } else if ((rc = scan(0, tiles_a, 0, 0, nullptr))) {
         return rc;
+      }
     }
     {
       StageTimer t(ST_SELECT, st);
-      if ((rc = launch_select16(cand, ckeys, nprobe, qbase, idx->list_off, kk, k, qrho, rmax,
-                                e_rest, prune ? 1 : 0, nb, cids, st)))
-        return rc;
+      if (stats) ADN_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), st));
+      rc = filt ? launch_select_surv(rec, rcnt, pbase, ckeys, nprobe, idx->list_off, kk, k, qrho,
+                                     rmax, e_rest, prune ? 1 : 0, nb, cids, stats, st)
+                : launch_select16(cand, ckeys, nprobe, qbase, idx->list_off, kk, k, qrho, rmax,
+                                  e_rest, prune ? 1 : 0, nb, cids, st);
+      if (rc) return rc;
+      if (stats) {
+        profile_count(PC_SURVIVORS, (const int64_t *)stats, st);
+        profile_count(PC_SELECT_SLOW, (const int64_t *)stats + 1, st);
+      }
     }
     {
       StageTimer t(ST_RERANK, st);

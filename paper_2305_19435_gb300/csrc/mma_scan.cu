@@ -339,12 +339,16 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool valid = row < cnt;
       int64_t base = 0;
       float q2 = 0.f, qs = 0.f;
+      uint32_t tau = 0xFFFFu;  // filtered mode: members with key <= tau survive
+      int pidx = 0;
       if (valid) {
         const int p = a.pair_out[a.tile_beg[t] + row];
         const int q = p / a.nprobe;
         base = a.pbase[p];
         q2 = a.qn2[q];
         qs = a.qsc[q];
+        pidx = p;
+        if (a.tau) tau = a.tau[q];
       }
       bool stop = false;
       // per-member terms of member tile mt (thread et < BN holds member et of
@@ -386,7 +390,42 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (mt + 1 < nmt) terms = load_terms(mt + 1);
         // a lane quadrant with no valid query row (a tile with few queries)
         // has nothing to drain: its warps skip the TMEM loads and the stores
-        if (quarter * 32 < cnt) {
+        if (quarter * 32 < cnt && a.rec) {
+          // filtered: per 32 of this row's columns, the survivors (key <=
+          // tau, member inside the list) are reserved with one atomic and
+          // written as records (key << 16 | member index)
+          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+          for (int h = 0; h < 2; ++h) {
+            const int m0 = mt * BN + c_lo + 32 * h;
+            uint32_t r[32];
+            tmem_ld32(tbase + c_lo + 32 * h, r);
+            uint32_t packed[16];
+            int nsurv = 0;
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              uint32_t kk[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int c = c_lo + 32 * h + j + u;
+                float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[j + u]), q2 + s_ca[acc][c]);
+                d = fminf(fmaxf(d, 0.f), 3.9999f);
+                kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
+                nsurv += (kk[u] <= tau && m0 + j + u < nl) ? 1 : 0;
+              }
+              packed[j >> 1] = kk[0] | (kk[1] << 16);
+            }
+            if (valid && nsurv > 0) {
+              uint32_t *dst = a.rec + base + atomicAdd(a.rcnt + pidx, nsurv);
+              int w = 0;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const uint32_t key = (packed[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                if (key <= tau && m0 + j < nl) dst[w++] = (key << 16) | (uint32_t)(m0 + j);
+              }
+            }
+          }
+        } else if (quarter * 32 < cnt) {
           const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
           // this warp's 32 rows x 64 columns of keys are staged row-major in
           // shared memory (16-byte chunks XOR-swizzled by row: conflict-free

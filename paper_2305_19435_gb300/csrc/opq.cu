@@ -602,6 +602,10 @@ struct AdcDistArgs {
   const int64_t *pbase;     // candidate segment start of each pair
   uint32_t *cand;           // FP32 distance bits
   int nsplit;               // member ranges per tile (work items = tiles x nsplit)
+  // residual codes (res_S NULL: plain): per-list tables S [nlist][M][256],
+  // list centres rotated w [nlist][d_s] and |w|^2, queries rotated z [B][d_s]
+  const float *res_S, *res_w, *res_w2, *z;
+  int d_s;
 };
 
 constexpr int AD_THREADS = 256;
@@ -635,6 +639,7 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
   const V *s_lv = (const V *)smem;
   __shared__ int s_qrow[AD_MAXQA];
   __shared__ int64_t s_pb[AD_MAXQA];
+  __shared__ float s_K[AD_MAXQA];  // residual codes: w2_l - 2 <w_l, z_q> per query of the tile
   __shared__ int s_tile;
   const int tid = threadIdx.x;
   const int nitems = *a.ntiles_dev * a.nsplit;
@@ -651,6 +656,21 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
       s_pb[tid] = a.pbase[a.pair_out[beg + tid]];
     }
     __syncthreads();
+    // residual codes: this list's table is added to every query's table, and
+    // the per-query constant |w_l|^2 - 2 <w_l, z_q> goes to the score
+    const float *Sl = a.res_S ? a.res_S + (int64_t)list * lut_sz : nullptr;
+    if (a.res_S) {
+      const int warp = tid >> 5, lane = tid & 31;
+      const float *wl = a.res_w + (int64_t)list * a.d_s;
+      for (int j = warp; j < cnt; j += AD_THREADS / 32) {
+        const float *zq = a.z + (int64_t)s_qrow[j] * a.d_s;
+        float dot = 0.f;
+        for (int t = lane; t < a.d_s; t += 32) dot = fmaf(wl[t], zq[t], dot);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (lane == 0) s_K[j] = fmaf(-2.f, dot, a.res_w2[list]);
+      }
+    }
     for (int g = 0; g < ng; ++g) {
       const float *src[G];
 #pragma unroll
@@ -662,8 +682,9 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
           V v;
           float f[G];
         } u;
+        const float sl = Sl ? Sl[r] : 0.f;
 #pragma unroll
-        for (int j = 0; j < G; ++j) u.f[j] = src[j] ? src[j][r] : 0.f;
+        for (int j = 0; j < G; ++j) u.f[j] = src[j] ? src[j][r] + sl : 0.f;
         dst[r] = u.v;
       }
     }
@@ -708,15 +729,18 @@ __global__ void __launch_bounds__(AD_THREADS) adc_dist_kernel(AdcDistArgs a) {
             }
 #pragma unroll
             for (int j = 0; j < G; ++j)
-              if (g * G + j < cnt)
-                a.cand[s_pb[g * G + j] + mem] =
-                    __float_as_uint((sum[j][0] + sum[j][1]) + (sum[j][2] + sum[j][3]));
+              if (g * G + j < cnt) {
+                float d = (sum[j][0] + sum[j][1]) + (sum[j][2] + sum[j][3]);
+                if (Sl) d = fmaxf(d + s_K[g * G + j], 0.f);
+                a.cand[s_pb[g * G + j] + mem] = __float_as_uint(d);
+              }
           }
         } else {
           for (int qa = 0; qa < cnt; ++qa) {
             const float *L = s_lut + (size_t)(qa / G) * lut_sz * G + (qa % G);
             float d = 0.f;
             for (int m = 0; m < M; ++m) d += L[(m * 256 + cp[m]) * G];
+            if (Sl) d = fmaxf(d + s_K[qa], 0.f);
             a.cand[s_pb[qa] + mem] = __float_as_uint(d);
           }
         }
@@ -744,8 +768,15 @@ int adc_dist_query_tile(int M) {
 int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const float *lut,
                     const int32_t *tl, const int32_t *tb, const int32_t *tc, const int *ntiles,
                     int *counter, const int32_t *pair_q, const int32_t *pair_out,
-                    const int64_t *pbase, uint32_t *cand, int qa, int nsplit, cudaStream_t st) {
+                    const int64_t *pbase, uint32_t *cand, int qa, int nsplit, cudaStream_t st,
+                    const float *res_S, const float *res_w, const float *res_w2, const float *z,
+                    int d_s) {
   AdcDistArgs a{};
+  a.res_S = res_S;
+  a.res_w = res_w;
+  a.res_w2 = res_w2;
+  a.z = z;
+  a.d_s = d_s;
   a.nsplit = nsplit < 1 ? 1 : nsplit;
   a.codes = codes;
   a.list_off = list_off;
@@ -776,6 +807,84 @@ int launch_adc_dist(const uint8_t *codes, const int64_t *list_off, int M, const 
   void *args[] = {&a};
   ADN_CUDA(cudaLaunchKernel(fn, dim3(num_sms() * per_sm), dim3(AD_THREADS), args, smem, st));
   ADN_LAUNCH("adc_dist_kernel");
+  return ADANNS_OK;
+}
+
+// ---------------------------------------------------------------- residual codes
+// lcent[l] = mean over the members of list l of their d_s prefixes (times the
+// inverse prefix norm under the prefix-normalised metric), FP64 sums; one CTA
+// per list, one thread per coordinate (strided).  Empty lists get zeros.
+__global__ void list_mean_kernel(const float *__restrict__ xpm, int d_pad,
+                                 const int64_t *__restrict__ list_off,
+                                 const float *__restrict__ mscale, int d_s,
+                                 float *__restrict__ lcent) {
+  const int l = blockIdx.x;
+  const int64_t off = list_off[l];
+  const int64_t nl = list_off[l + 1] - off;
+  const float *base = xpm + off * d_pad;
+  for (int j = threadIdx.x; j < d_s; j += blockDim.x) {
+    double acc = 0.0;
+    const float *col = base + (int64_t)(j >> 4) * 16 * nl + (j & 15);
+    for (int64_t m = 0; m < nl; ++m)
+      acc += (double)col[m * 16] * (double)(mscale ? mscale[off + m] : 1.f);
+    lcent[(int64_t)l * d_s + j] = nl > 0 ? (float)(acc / (double)nl) : 0.f;
+  }
+}
+
+int launch_list_mean(const adanns_index *x, int d_s, float *lcent, cudaStream_t st) {
+  const float *mscale = x->metric == ADANNS_METRIC_L2_PREFIXNORM
+                            ? x->invn + (int64_t)gran_index(d_s) * x->N
+                            : nullptr;
+  list_mean_kernel<<<x->nlist, 256, 0, st>>>(x->xpm, x->d_pad, x->list_off, mscale, d_s, lcent);
+  ADN_LAUNCH("list_mean_kernel");
+  return ADANNS_OK;
+}
+
+// rows[i] -= lcent[assign[ids[i]]] for n rows of ldr floats (first d_s)
+__global__ void sub_list_centre_kernel(float *__restrict__ rows, int64_t n, int ldr, int d_s,
+                                       const int64_t *__restrict__ ids64,
+                                       const int32_t *__restrict__ ids32,
+                                       const int32_t *__restrict__ assign,
+                                       const float *__restrict__ lcent) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * d_s) return;
+  const int64_t i = e / d_s;
+  const int j = (int)(e % d_s);
+  const int64_t id = ids64 ? ids64[i] : (int64_t)ids32[i];
+  rows[i * ldr + j] -= lcent[(int64_t)assign[id] * d_s + j];
+}
+
+int launch_sub_list_centre(float *rows, int64_t n, int ldr, int d_s, const int64_t *ids64,
+                           const int32_t *ids32, const int32_t *assign, const float *lcent,
+                           cudaStream_t st) {
+  if (n <= 0) return ADANNS_OK;
+  sub_list_centre_kernel<<<(unsigned)((n * d_s + 255) / 256), 256, 0, st>>>(
+      rows, n, ldr, d_s, ids64, ids32, assign, lcent);
+  ADN_LAUNCH("sub_list_centre_kernel");
+  return ADANNS_OK;
+}
+
+// S[l][m][c] = 2 <w_l,m, C_m[c]> and w2[l] = |w_l|^2; grid (nlist, M), c = thread
+__global__ void residual_tables_kernel(const float *__restrict__ w, int d_s, int M, int dsub,
+                                       const float *__restrict__ C, float *__restrict__ S,
+                                       float *__restrict__ w2) {
+  const int l = blockIdx.x, m = blockIdx.y, c = threadIdx.x;
+  const float *wl = w + (int64_t)l * d_s + m * dsub;
+  const float *cw = C + ((int64_t)m * 256 + c) * dsub;
+  float acc = 0.f;
+  for (int t = 0; t < dsub; ++t) acc = fmaf(wl[t], cw[t], acc);
+  S[((int64_t)l * M + m) * 256 + c] = 2.f * acc;
+  if (m == 0 && c == 0) {
+    float s2 = 0.f;
+    for (int t = 0; t < d_s; ++t) s2 = fmaf(w[(int64_t)l * d_s + t], w[(int64_t)l * d_s + t], s2);
+    w2[l] = s2;
+  }
+}
+
+int launch_residual_tables(const float *w, int nlist, int d_s, int M, const float *C, float *S,
+                           float *w2, cudaStream_t st) {
+  residual_tables_kernel<<<dim3(nlist, M), 256, 0, st>>>(w, d_s, M, d_s / M, C, S, w2);
+  ADN_LAUNCH("residual_tables_kernel");
   return ADANNS_OK;
 }
 

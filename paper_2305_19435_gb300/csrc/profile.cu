@@ -48,6 +48,11 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+bool profiling() {
+  std::lock_guard<std::mutex> g(g_mu);
+  return g_on;
+}
+
 void profile_count(int counter, const int64_t *dev_value, cudaStream_t st) {
   std::lock_guard<std::mutex> g(g_mu);
   if (!g_on || counter < 0 || counter >= PC_NCOUNTER) return;

@@ -98,6 +98,7 @@ void init_options() {
     g_opt[ADANNS_OPT_SCRATCH_BYTES] = (int64_t)(gb * (double)(1ll << 30));
     g_opt[ADANNS_OPT_WAIT_LIMIT_NS] = 2000000000ll;
     g_opt[ADANNS_OPT_TEST_SKIP_LOAD] = -1;
+    g_opt[ADANNS_OPT_SCAN_FILTER] = 0;
   });
 }
 }  // namespace
@@ -120,6 +121,7 @@ int set_option(int o, int64_t v) {
     case ADANNS_OPT_ADC_SELECT:
     case ADANNS_OPT_COARSE_TC:
     case ADANNS_OPT_RERANK_PRUNE:
+    case ADANNS_OPT_SCAN_FILTER:
       if (v != 0 && v != 1) return fail(ADANNS_ERR_ARG, "this option takes 0 or 1");
       break;
     case ADANNS_OPT_SCRATCH_BYTES:
@@ -233,10 +235,18 @@ int launch_keys_to_result(const uint64_t *keys, int64_t rows, int k, int64_t *id
 }
 
 // ---------------------------------------------------------------- probe inversion
-__global__ void probe_count_kernel(const uint64_t *__restrict__ ckeys, int64_t n,
-                                   int32_t *__restrict__ lcnt, int32_t *__restrict__ probes_out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
+// Pairs (query, probe slot) over slots [s0, s0 + ns) of each query's nprobe:
+// item i is pair e = (i / ns) * nprobe + s0 + i % ns.
+__device__ __forceinline__ int64_t slot_pair(int64_t i, int nprobe, int s0, int ns) {
+  return ns == nprobe ? i : (i / ns) * nprobe + s0 + i % ns;
+}
+
+__global__ void probe_count_kernel(const uint64_t *__restrict__ ckeys, int64_t n, int nprobe,
+                                   int s0, int ns, int32_t *__restrict__ lcnt,
+                                   int32_t *__restrict__ probes_out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = slot_pair(i, nprobe, s0, ns);
   const int l = (int)(uint32_t)(ckeys[e] & 0xffffffffu);
   atomicAdd(&lcnt[l], 1);
   if (probes_out) probes_out[e] = l;
@@ -277,10 +287,12 @@ __global__ void probe_scan_kernel(const int32_t *__restrict__ lcnt, int nlist, i
 }
 
 __global__ void probe_fill_kernel(const uint64_t *__restrict__ ckeys, int64_t n, int nprobe,
-                                  const int32_t *__restrict__ lbeg, int32_t *__restrict__ lfill,
-                                  int32_t *__restrict__ pair_q, int32_t *__restrict__ pair_out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
+                                  int s0, int ns, const int32_t *__restrict__ lbeg,
+                                  int32_t *__restrict__ lfill, int32_t *__restrict__ pair_q,
+                                  int32_t *__restrict__ pair_out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = slot_pair(i, nprobe, s0, ns);
   const int l = (int)(uint32_t)(ckeys[e] & 0xffffffffu);
   const int pos = lbeg[l] + atomicAdd(&lfill[l], 1);
   pair_q[pos] = (int32_t)(e / nprobe);
@@ -309,15 +321,25 @@ int launch_invert_probes(const uint64_t *ckeys, int64_t B, int nprobe, int nlist
                          int32_t *pair_q, int32_t *pair_out, int32_t *tile_list,
                          int32_t *tile_beg, int32_t *tile_cnt, int *ntiles, int32_t *probes_out,
                          cudaStream_t st) {
-  const int64_t n = B * nprobe;
+  return launch_invert_probe_slots(ckeys, B, nprobe, 0, nprobe, nlist, qt, lcnt, lbeg, lfill, tbeg,
+                                   pair_q, pair_out, tile_list, tile_beg, tile_cnt, ntiles,
+                                   probes_out, st);
+}
+
+int launch_invert_probe_slots(const uint64_t *ckeys, int64_t B, int nprobe, int s0, int ns,
+                              int nlist, int qt, int32_t *lcnt, int32_t *lbeg, int32_t *lfill,
+                              int32_t *tbeg, int32_t *pair_q, int32_t *pair_out,
+                              int32_t *tile_list, int32_t *tile_beg, int32_t *tile_cnt,
+                              int *ntiles, int32_t *probes_out, cudaStream_t st) {
+  const int64_t n = B * ns;
   ADN_CUDA(cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * nlist, st));
   ADN_CUDA(cudaMemsetAsync(lfill, 0, sizeof(int32_t) * nlist, st));
-  const unsigned g = (unsigned)((n + 255) / 256);
-  probe_count_kernel<<<g, 256, 0, st>>>(ckeys, n, lcnt, probes_out);
+  const unsigned g = (unsigned)((std::max<int64_t>(n, 1) + 255) / 256);
+  probe_count_kernel<<<g, 256, 0, st>>>(ckeys, n, nprobe, s0, ns, lcnt, probes_out);
   ADN_LAUNCH("probe_count_kernel");
   probe_scan_kernel<<<1, 1024, 0, st>>>(lcnt, nlist, qt, lbeg, tbeg, ntiles);
   ADN_LAUNCH("probe_scan_kernel");
-  probe_fill_kernel<<<g, 256, 0, st>>>(ckeys, n, nprobe, lbeg, lfill, pair_q, pair_out);
+  probe_fill_kernel<<<g, 256, 0, st>>>(ckeys, n, nprobe, s0, ns, lbeg, lfill, pair_q, pair_out);
   ADN_LAUNCH("probe_fill_kernel");
   probe_tiles_kernel<<<(nlist + 255) / 256, 256, 0, st>>>(lcnt, lbeg, tbeg, nlist, qt, tile_list,
                                                           tile_beg, tile_cnt);

@@ -274,7 +274,216 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
                       [&](int i) -> int { return i; }, o, s);
 }
 
+// ---------------------------------------------------------------- filtered scan
+// With the filtered tensor-core scan, each (query, probe slot) pair keeps only
+// its members whose key can still be in the shortlist, as records
+// (key << 16 | member index) compacted at the start of the pair's segment.
+// The first pass scans every query's nearest list (slot 0) keeping all of it;
+// its kk-th smallest key tau bounds the query's overall kk-th key (those kk
+// members are candidates too), so the second pass over the other slots keeps
+// keys <= tau only.  The shortlist is then selected from the survivors with
+// the same (key, candidate position) order as select16_kernel, so the result
+// is the same.
+
+constexpr int TAU_WARPS = 4;
+
+// Per query (one warp): tau = the kk-th smallest key of slot 0's records (all
+// of its members), or 0xFFFF when the list has fewer than kk members; slot 0
+// is compacted in place to its records with key <= tau.
+__global__ void __launch_bounds__(TAU_WARPS * 32) shortlist_tau_kernel(
+    uint32_t *__restrict__ rec, int *__restrict__ rcnt, const int64_t *__restrict__ pbase,
+    int nprobe, int kk, int64_t B, uint16_t *__restrict__ tau) {
+  __shared__ int hist[TAU_WARPS][256];
+  __shared__ int sh[TAU_WARPS][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * TAU_WARPS + warp;
+  if (q >= B) return;
+  const int64_t p0 = q * nprobe;
+  const int n0 = rcnt[p0];
+  uint32_t *r = rec + pbase[p0];
+  if (n0 < kk) {
+    if (lane == 0) tau[q] = 0xFFFFu;
+    return;
+  }
+  int below, neq;
+  const uint32_t T = warp_radix_kth<2>(n0, kk, [&](int i) -> uint32_t { return r[i] >> 16; },
+                                       hist[warp], sh[warp], below, neq);
+  // in-place compaction: a lane writes at or before positions already read
+  int w = 0;
+  for (int i0 = 0; i0 < n0; i0 += 32) {
+    const int i = i0 + lane;
+    const uint32_t v = i < n0 ? r[i] : 0xFFFFFFFFu;
+    const bool keep = i < n0 && (v >> 16) <= T;
+    const unsigned b = __ballot_sync(0xffffffffu, keep);
+    if (keep) r[w + __popc(b & lanemask_lt())] = v;
+    w += __popc(b);
+  }
+  if (lane == 0) {
+    rcnt[p0] = w;
+    tau[q] = (uint16_t)T;
+  }
+}
+
+struct SvState {
+  SwState s;
+  int spre[SW_MAXP + 1];  // survivors before each slot
+  int64_t pb[SW_MAXP];    // record segment start of each slot
+};
+
+// Per query (one warp): the kk smallest (key, candidate position) among the
+// survivors, written like select16_kernel (pruning included).
+__global__ void __launch_bounds__(SW_WARPS * 32, 4) select_surv_kernel(
+    const uint32_t *__restrict__ rec, const int *__restrict__ rcnt,
+    const int64_t *__restrict__ pbase, const uint64_t *__restrict__ ckeys, int nprobe,
+    const int64_t *__restrict__ list_off, int kk, int k, const float *__restrict__ qrho,
+    float rmax, float e_rest, int prune, int64_t B, int64_t *__restrict__ out,
+    unsigned long long *__restrict__ stats) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  SvState &v = ((SvState *)smem)[warp];
+  SwState &s = v.s;
+  const int64_t q = (int64_t)blockIdx.x * SW_WARPS + warp;
+  if (q >= B) return;
+  int prune_delta = 0;
+  if (prune) {
+    const double rq = (double)qrho[q];
+    const double E = 2.0 * (rmax + rq + rmax * rq) * (1.0 + 1e-3) + e_rest;
+    prune_delta = (int)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1;
+    if (prune_delta > (1 << 20)) prune_delta = 1 << 20;
+  }
+  // probed lists: ids, sizes, padded candidate starts, survivor counts
+  int ln[4], pl[4], sc[4], tot = 0, ptot = 0, stot = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int sl = lane * 4 + j;
+    ln[j] = 0;
+    sc[j] = 0;
+    if (sl < nprobe) {
+      const int64_t p = q * nprobe + sl;
+      const int l = (int)(uint32_t)(ckeys[p] & 0xffffffffu);
+      s.lid[sl] = l;
+      ln[j] = (int)(list_off[l + 1] - list_off[l]);
+      s.nl[sl] = ln[j];
+      sc[j] = rcnt[p];
+      v.pb[sl] = pbase[p];
+    }
+    pl[j] = (ln[j] + 7) & ~7;
+    tot += ln[j];
+    ptot += pl[j];
+    stot += sc[j];
+  }
+  int inc = ptot, sinc = stot;
+#pragma unroll
+  for (int o2 = 1; o2 < 32; o2 <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o2);
+    const int z = __shfl_up_sync(0xffffffffu, sinc, o2);
+    if (lane >= o2) {
+      inc += y;
+      sinc += z;
+    }
+  }
+  {
+    int run = inc - ptot, srun = sinc - stot;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int sl = lane * 4 + j;
+      if (sl <= nprobe) {
+        s.pst[sl] = run;
+        v.spre[sl] = srun;
+      }
+      run += pl[j];
+      srun += sc[j];
+    }
+  }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o2);
+  const int total = tot;
+  const int S = __shfl_sync(0xffffffffu, sinc, 31);
+  if (stats && lane == 0) {
+    atomicAdd(stats, (unsigned long long)S);
+    if (S > SW_BUF && total > kk) atomicAdd(stats + 1, 1ull);
+  }
+  __syncwarp();
+  int64_t *o = out + q * kk;
+  if (total <= kk) {
+    int p0 = 0;
+    for (int sl = 0; sl < nprobe; ++sl) {
+      const int nl = s.nl[sl];
+      for (int m = lane; m < nl; m += 32) o[p0 + m] = ((int64_t)s.lid[sl] << 32) | (int64_t)m;
+      p0 += nl;
+    }
+    for (int r = total + lane; r < kk; r += 32) o[r] = -1;
+    return;
+  }
+  // survivor i -> slot (last slot whose survivor prefix is <= i)
+  auto slot_of = [&](int i) -> int {
+    int lo = 0, hi = nprobe - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (v.spre[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  // candidate position -> (list << 32 | member)
+  auto id_at = [&](int i) -> int64_t {
+    int lo = 0, hi = nprobe - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s.pst[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int m = i - s.pst[lo];
+    return m < s.nl[lo] ? (((int64_t)s.lid[lo] << 32) | (int64_t)m) : -1;
+  };
+  const int kq = prune ? k : 0;
+  if (S <= SW_BUF) {
+    for (int i = lane; i < S; i += 32) {
+      const int sl = slot_of(i);
+      const uint32_t r = rec[v.pb[sl] + (i - v.spre[sl])];
+      s.u.b.key[i] = (uint16_t)(r >> 16);
+      s.u.b.idx[i] = (uint32_t)(s.pst[sl] + (int)(r & 0xFFFFu));
+    }
+    __syncwarp();
+    warp_select16<false>(S, kk, kq, prune_delta, [&](int i) -> uint32_t { return s.u.b.key[i]; },
+                         [&](int i) -> int64_t { return id_at((int)s.u.b.idx[i]); },
+                         [&](int i) -> int { return (int)s.u.b.idx[i]; }, o, s);
+  } else {
+    auto rec_at = [&](int i) -> uint32_t {
+      const int sl = slot_of(i);
+      return rec[v.pb[sl] + (i - v.spre[sl])];
+    };
+    auto pos_at = [&](int i) -> int {
+      const int sl = slot_of(i);
+      return s.pst[sl] + (int)(rec[v.pb[sl] + (i - v.spre[sl])] & 0xFFFFu);
+    };
+    warp_select16<false>(S, kk, kq, prune_delta, [&](int i) -> uint32_t { return rec_at(i) >> 16; },
+                         [&](int i) -> int64_t { return id_at(pos_at(i)); }, pos_at, o, s);
+  }
+}
+
 }  // namespace
+
+int launch_shortlist_tau(uint32_t *rec, int *rcnt, const int64_t *pbase, int nprobe, int kk,
+                         int64_t B, uint16_t *tau, cudaStream_t st) {
+  if (B <= 0) return ADANNS_OK;
+  shortlist_tau_kernel<<<(unsigned)((B + TAU_WARPS - 1) / TAU_WARPS), TAU_WARPS * 32, 0, st>>>(
+      rec, rcnt, pbase, nprobe, kk, B, tau);
+  ADN_LAUNCH("shortlist_tau_kernel");
+  return ADANNS_OK;
+}
+
+int launch_select_surv(const uint32_t *rec, const int *rcnt, const int64_t *pbase,
+                       const uint64_t *ckeys, int nprobe, const int64_t *list_off, int kk, int k,
+                       const float *qrho, float rmax, float e_rest, int prune, int64_t B,
+                       int64_t *out, unsigned long long *stats, cudaStream_t st) {
+  if (nprobe > SW_MAXP) return fail(ADANNS_ERR_ARG, "select: nprobe above 128");
+  if (B <= 0) return ADANNS_OK;
+  const size_t sm = sizeof(SvState) * SW_WARPS;
+  ADN_CUDA(ensure_smem((const void *)select_surv_kernel, sm));
+  select_surv_kernel<<<(unsigned)((B + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, sm, st>>>(
+      rec, rcnt, pbase, ckeys, nprobe, list_off, kk, k, qrho, rmax, e_rest, prune, B, out, stats);
+  ADN_LAUNCH("select_surv_kernel");
+  return ADANNS_OK;
+}
 
 int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, int kk, int k, const float *qrho, float rmax,

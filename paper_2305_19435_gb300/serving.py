@@ -29,13 +29,15 @@ import numpy as np
 
 @dataclass(frozen=True)
 class Budget:
-    """Per-request compute budget (all fields as in search_ivf)."""
+    """Per-request compute budget (all fields as in search_ivf; method 1 is the
+    IVF-OPQ search, whose d_s and storage are those of the index's OPQ data)."""
     d_c: int
     d_s: int
     nprobe: int
     k: int
     storage: int = 1
     rerank_k: int = 0
+    method: int = 0
 
 
 @dataclass
@@ -74,8 +76,11 @@ class GpuExecutor:
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
 
     def scratch_bytes(self, index_key, budget: Budget, n: int) -> int:
-        return self.P.scratch_bytes(self.indexes[index_key], n, budget.d_c, budget.d_s,
-                                    budget.nprobe, budget.k, budget.storage, budget.rerank_k)
+        idx = self.indexes[index_key]
+        if budget.method == 1:   # IVF-OPQ: per-member scores of the probed lists dominate
+            return n * (budget.nprobe * 64 + budget.k * 12 + idx.d * 4) + (64 << 20)
+        return self.P.scratch_bytes(idx, n, budget.d_c, budget.d_s, budget.nprobe, budget.k,
+                                    budget.storage, budget.rerank_k)
 
     def launch(self, slot: int, index_key, budget: Budget, reqs: list):
         torch = self.torch
@@ -88,9 +93,13 @@ class GpuExecutor:
                     q = torch.from_numpy(np.ascontiguousarray(q))
                 parts.append(q.cuda(non_blocking=True) if not q.is_cuda else q)
             q = parts[0] if len(parts) == 1 else torch.cat(parts)
-            ids, dist = self.P.search_ivf(self.indexes[index_key], q, budget.d_c, budget.d_s,
-                                          budget.nprobe, budget.k, storage=budget.storage,
-                                          rerank_k=budget.rerank_k)
+            if budget.method == 1:
+                ids, dist = self.P.search_ivfopq(self.indexes[index_key], q, budget.d_c,
+                                                 budget.nprobe, budget.k, rerank_k=budget.rerank_k)
+            else:
+                ids, dist = self.P.search_ivf(self.indexes[index_key], q, budget.d_c, budget.d_s,
+                                              budget.nprobe, budget.k, storage=budget.storage,
+                                              rerank_k=budget.rerank_k)
             ids_h = torch.empty(ids.shape, dtype=ids.dtype, pin_memory=True)
             dist_h = torch.empty(dist.shape, dtype=dist.dtype, pin_memory=True)
             ids_h.copy_(ids, non_blocking=True)
@@ -268,3 +277,108 @@ def poisson_stream(rate_qps: float, duration_s: float, seed: int, max_rows: int 
         if t > duration_s:
             return out
         out.append((t, int(rng.integers(1, max_rows + 1)), int(rng.integers(0, nb))))
+
+
+# ---------------------------------------------------------------- native server
+class NativeRequest:
+    """A request of the library's server; results are collected on wait()."""
+
+    def __init__(self, server, ticket: int, n: int, k: int):
+        self._srv, self.ticket, self._n, self._k = server, ticket, n, k
+        self.ids = self.dist = None
+        self.error: Exception | None = None
+        self.latency_ms = None
+        self._lock = threading.Lock()
+        self._done = False
+
+    @property
+    def n(self) -> int:
+        return self._n
+
+    def wait(self, timeout: float | None = None) -> bool:
+        """Block until the results are on the host (True) or timeout seconds pass."""
+        import ctypes
+        with self._lock:
+            if self._done:
+                return True
+            P = self._srv.P
+            ids = np.empty((self._n, self._k), dtype=np.int64)
+            dist = np.empty((self._n, self._k), dtype=np.float32)
+            lat = ctypes.c_double()
+            ms = -1 if timeout is None else max(0, int(timeout * 1000))
+            rc = P.lib().adanns_server_poll(self._srv.handle, self.ticket, ms,
+                                            ids.ctypes.data_as(ctypes.c_void_p),
+                                            dist.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(lat))
+            if rc == P.PENDING:
+                return False
+            if rc != 0:
+                self.error = P.AdannsError(rc, P.lib().adanns_last_error().decode())
+            else:
+                self.ids, self.dist, self.latency_ms = ids, dist, lat.value
+            self._done = True
+            return True
+
+
+class NativeServer:
+    """Continuous batching done by the library (adanns_server_*): the same
+    scheduling as Server (arrival order, same-budget packing up to max_batch
+    rows, memory admission, one batch per CUDA stream in flight) in a native
+    worker thread.  Queries are host arrays or CPU tensors."""
+
+    def __init__(self, indexes: dict, streams: int = 2, max_batch: int = 8192,
+                 mem_budget: int = 16 << 30):
+        import ctypes
+        import paper_2305_19435_gb300 as P
+        self.P = P
+        self._keys = list(indexes)
+        self._d = {key: indexes[key].d for key in self._keys}
+        arr = (ctypes.c_void_p * len(self._keys))(*[indexes[key].handle.value for key in self._keys])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        P._check(P.lib().adanns_server_create(arr, len(self._keys), streams, max_batch, mem_budget,
+                                              ctypes.byref(h)))
+        self.handle = h
+        self.requests: list[NativeRequest] = []
+
+    def start(self):
+        return self
+
+    def submit(self, queries, budget: Budget, index_key=None) -> NativeRequest:
+        import ctypes
+        P = self.P
+        if index_key is None:
+            index_key = self._keys[0]
+        q = queries.numpy() if hasattr(queries, "numpy") else queries
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        b = P.BudgetC(budget.method, budget.d_c, budget.d_s, budget.nprobe, budget.k,
+                      budget.storage, budget.rerank_k)
+        t = ctypes.c_int64()
+        P._check(P.lib().adanns_server_submit(self.handle, self._keys.index(index_key),
+                                              q.ctypes.data_as(ctypes.c_void_p), q.shape[0],
+                                              ctypes.byref(b), ctypes.byref(t)))
+        r = NativeRequest(self, t.value, q.shape[0], budget.k)
+        self.requests.append(r)
+        return r
+
+    def stop(self, drain: bool = True, timeout: float = 600.0):
+        for r in self.requests:
+            r.wait(timeout if drain else 0)
+        self._stats = self.stats()
+        self.P.lib().adanns_server_destroy(self.handle)
+        self.handle = None
+
+    def stats(self) -> dict:
+        import ctypes
+        if self.handle is None:
+            return self._stats
+        p50, p99, qps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        req, bat, rows, mx = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self.P._check(self.P.lib().adanns_server_stats(self.handle, ctypes.byref(p50),
+                                                       ctypes.byref(p99), ctypes.byref(req),
+                                                       ctypes.byref(bat), ctypes.byref(rows),
+                                                       ctypes.byref(qps), ctypes.byref(mx)))
+        return {"requests": req.value, "queries": rows.value, "p50_ms": p50.value,
+                "p99_ms": p99.value, "qps": qps.value, "batches": bat.value,
+                "mean_requests_per_batch": req.value / max(bat.value, 1),
+                "max_inflight_bytes": mx.value, "scheduler": "native (adanns_server)"}

@@ -75,3 +75,40 @@ def test_version_and_argument_errors_without_device(lib):
     assert lib.adanns_map_ids(fake, -1, fake, 4, None) == -1
     assert lib.adanns_map_ids(fake, 4, None, 4, None) == -1
     assert lib.adanns_map_ids(None, 0, None, 0, None) == 0
+
+
+def test_runtime_options_without_device(lib):
+    v = ctypes.c_int64()
+    assert lib.adanns_get_option(5, ctypes.byref(v)) == 0 and v.value == 2_000_000_000
+    assert lib.adanns_set_option(5, 10) == -1           # wait limit below 1e5 ns
+    assert lib.adanns_set_option(0, 2) == -1            # switches take 0 or 1
+    assert lib.adanns_set_option(99, 1) == -1           # unknown option
+    assert lib.adanns_get_option(99, ctypes.byref(v)) == -1
+    assert lib.adanns_set_option(4, 1 << 30) == 0       # scratch budget 1 GiB
+    assert lib.adanns_get_option(4, ctypes.byref(v)) == 0 and v.value == 1 << 30
+    assert lib.adanns_set_option(4, 12 << 30) == 0
+    assert lib.adanns_get_option(6, ctypes.byref(v)) == 0 and v.value == -1
+
+
+def test_index_import_rejects_bad_files_without_device(lib, tmp_path):
+    import indexfile
+    h = ctypes.c_void_p()
+    missing = str(tmp_path / "missing.idx").encode()
+    assert lib.adanns_index_import(missing, None, ctypes.byref(h)) == -1
+    bad = tmp_path / "bad.idx"
+    bad.write_bytes(b"NOTANIDX" + bytes(200))
+    assert lib.adanns_index_import(str(bad).encode(), None, ctypes.byref(h)) == -6
+    assert b"not an AdANNS index file" in lib.adanns_last_error()
+    short = tmp_path / "short.idx"
+    short.write_bytes(b"ADANNSIX" + bytes(20))
+    assert lib.adanns_index_import(str(short).encode(), None, ctypes.byref(h)) == -6
+    # a valid header with inconsistent sizes (d_c > d)
+    odd = tmp_path / "odd.idx"
+    odd.write_bytes(indexfile.HEADER.pack(b"ADANNSIX", 1, 96, 10, 8, 16, 2, 1, 1, 0, 0, 0,
+                                          *([0] * 10)))
+    assert lib.adanns_index_import(str(odd).encode(), None, ctypes.byref(h)) == -6
+    ver = tmp_path / "ver.idx"
+    ver.write_bytes(indexfile.HEADER.pack(b"ADANNSIX", 7, 96, 10, 8, 8, 2, 1, 1, 0, 0, 0,
+                                          *([0] * 10)))
+    assert lib.adanns_index_import(str(ver).encode(), None, ctypes.byref(h)) == -6
+    assert not h.value

@@ -143,3 +143,17 @@ def test_tensor_core_cluster_mapping_long_index(A, wide, d_c, nprobe):
     assert (~amb).sum() > 200
     for i in np.nonzero(~amb)[0]:
         assert set(gp[i]) == set(ref["probes"][i]), i
+
+
+@pytest.mark.parametrize("storage,d_s,nprobe", [(BF16, 512, 16), (FP8, 2048, 8), (BF16, 2048, 32)])
+def test_filtered_scan_long_prefix(A, wide, storage, d_s, nprobe):
+    """The filtered tensor-core scan (32 and 16 K-blocks) gives the unfiltered
+    scan's result bit for bit at the long prefixes."""
+    data, o, g = wide
+    q = cu(data["queries"])
+    with A.option(A.OPT_SCAN_FILTER, 0):
+        i0, d0 = A.search_ivf(g, q, 64, d_s, nprobe, 100, storage=storage, rerank_k=400)
+    with A.option(A.OPT_SCAN_FILTER, 1):
+        i1, d1 = A.search_ivf(g, q, 64, d_s, nprobe, 100, storage=storage, rerank_k=400)
+    assert torch.equal(i0, i1)
+    assert torch.equal(d0.view(torch.int32), d1.view(torch.int32))

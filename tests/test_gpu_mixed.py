@@ -211,3 +211,65 @@ def test_status_clean_after_mixed_searches(A, case):
     data, o, g = case
     A.search_ivf(g, cu(data["queries"]), 32, 256, 8, 100, storage=BF16, rerank_k=400)
     g.status()
+
+
+def _candidates(A, g, q, d_c, nprobe):
+    """Total members of every query's probed lists (the unfiltered scan's keys)."""
+    _, _, pr = A.search_ivf(g, q, d_c, 64, nprobe, 1, return_probes=True)
+    off, _ = g.lists()
+    sizes = (off[1:] - off[:-1]).cpu().numpy()
+    return int(sizes[pr.cpu().numpy()].sum())
+
+
+@pytest.mark.parametrize("storage,d_s,nprobe,k,kr", [(BF16, 256, 8, 100, 400), (BF16, 128, 1, 10, 40),
+                                                    (BF16, 64, 12, 50, 2048), (FP8, 256, 8, 100, 400),
+                                                    (FP8, 96, 3, 1, 4), (BF16, 256, 48, 20, 80),
+                                                    (BF16, 192, 2, 7, 1000)])
+def test_filtered_scan_equals_unfiltered(A, case, storage, d_s, nprobe, k, kr):
+    """The filtered tensor-core scan keeps, outside each query's nearest list,
+    only members whose key is at most the kk-th key of that list (a bound on the
+    query's kk-th key), and selects the shortlist from them with the same
+    (key, candidate position) order: ids and distance bits equal those of the
+    scan that writes every key, and for a selective shortlist far fewer
+    candidates reach the selection."""
+    data, o, g = case
+    q = cu(data["queries"])
+    with A.option(A.OPT_SCAN_FILTER, 0):
+        i0, d0 = A.search_ivf(g, q, 32, d_s, nprobe, k, storage=storage, rerank_k=kr)
+    A.profile_enable(True)
+    with A.option(A.OPT_SCAN_FILTER, 1):
+        i1, d1 = A.search_ivf(g, q, 32, d_s, nprobe, k, storage=storage, rerank_k=kr)
+    cnt = A.profile_read_counters()
+    A.profile_enable(False)
+    g.status()
+    assert torch.equal(i0, i1)
+    assert torch.equal(d0.view(torch.int32), d1.view(torch.int32))
+    total = _candidates(A, g, q, 32, nprobe)
+    assert 0 < cnt["scan_survivors"] <= total
+    if nprobe >= 8 and kr <= 400:
+        assert cnt["scan_survivors"] < 0.6 * total, (cnt, total)
+
+
+@pytest.mark.parametrize("kr", [40, 400])
+def test_filtered_scan_ties_at_the_bound(A, kr):
+    """Every other database row duplicated and a block of 2,000 identical rows,
+    queries equal to them: many keys equal the bound taken from the nearest
+    list; all of them are kept, so the result is the unfiltered scan's."""
+    data = synthdata.small(20_000, 200, 128, 32, 413)
+    db = data["db"].copy()
+    db[1::2] = db[0::2]
+    db[5000:7000] = db[5000]
+    q = data["queries"].copy()
+    q[:8] = db[5000] * np.float32(1.5)
+    o = oracle.build_ivf(db, 32, 24, 5, 20_000, seed=31)
+    g = A.index_create(cu(db), cu(o["centroids"]), cu(o["assign"].astype(np.int32)),
+                       storage=1 | BF16 | FP8)
+    for storage in (BF16, FP8):
+        with A.option(A.OPT_SCAN_FILTER, 0):
+            i0, d0 = A.search_ivf(g, cu(q), 32, 128, 6, 10, storage=storage, rerank_k=kr)
+        with A.option(A.OPT_SCAN_FILTER, 1):
+            i1, d1 = A.search_ivf(g, cu(q), 32, 128, 6, 10, storage=storage, rerank_k=kr)
+        assert torch.equal(i0, i1)
+        assert torch.equal(d0.view(torch.int32), d1.view(torch.int32))
+    g.status()
+    g.free()

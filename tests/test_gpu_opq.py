@@ -306,3 +306,92 @@ def test_flat_index_fp32_is_brute_force(A, case):
     n, fails = check_topk(gi.cpu().numpy(), gd.cpu().numpy(), exact["ids"], exact["dist"], 20)
     assert n == len(q) and not fails, fails[:2]
     g.free()
+
+
+# ---------------------------------------------------------------- residual codes
+@pytest.fixture(scope="module")
+def res_case(case):
+    data, o = case["data"], case["idx"]
+    db = data["db"]
+    out = {}
+    for d_s, M in ((64, 16), (96, 32), (32, 4)):
+        lc = oracle.list_centroids(db, o, d_s)
+        opq = oracle.train_opq(db, d_s, M, 3, 3, 5, 4000, seed=17,
+                               residual={"lcent": lc, "assign": o["assign"]})
+        codes = oracle.pq_encode(db, d_s, M, opq["R"], opq["codebooks"], lcent=lc,
+                                 assign=o["assign"])
+        out[(d_s, M)] = (opq, codes, lc)
+    return out
+
+
+def gpu_res_index(A, case, res_case, d_s, M):
+    data, o = case["data"], case["idx"]
+    opq, codes, lc = res_case[(d_s, M)]
+    g = A.index_create(cu(data["db"]), cu(o["centroids"]), cu(o["assign"].astype(np.int32)))
+    A.set_opq_residual(g, d_s, M, cu(opq["R"]), cu(opq["codebooks"]), cu(codes), cu(lc))
+    return g
+
+
+@pytest.mark.parametrize("d_s,M,nprobe,k,d_c", [(64, 16, 4, 20, 32), (96, 32, 8, 100, 32),
+                                                (32, 4, 24, 50, 32), (64, 16, 6, 10, 16)])
+def test_residual_ivfopq_search_parity(A, case, res_case, d_s, M, nprobe, k, d_c):
+    """Residual codes: one table per (query, probed list) built from
+    (P_ds(q) - lcent[l]) R on the oracle's side, the list table S_l and the
+    constant |w_l|^2 - 2 <w_l, z_q> on the GPU's; scores and ids agree."""
+    data, o = case["data"], case["idx"]
+    opq, codes, lc = res_case[(d_s, M)]
+    g = gpu_res_index(A, case, res_case, d_s, M)
+    q = data["queries"]
+    gi, gd = A.search_ivfopq(g, cu(q), d_c, nprobe, k)
+    orr = oracle.search_ivfopq(data["db"], o, opq, codes, q, d_c, nprobe, k + 40)
+    amb = ambiguous_probe_rows(orr["probe_dist"], nprobe)
+    n, fails = check_topk(gi.cpu().numpy(), gd.cpu().numpy(), orr["ids"], orr["dist"], k,
+                          skip_rows=amb)
+    assert n > 0.8 * len(q) and not fails, f"{len(fails)}/{n}: {fails[:2]}"
+    # the list centres round-trip
+    assert torch.equal(A.list_centres(g).cpu(), torch.from_numpy(lc))
+    g.free()
+
+
+@pytest.mark.parametrize("d_s,M,nprobe,k,kr", [(64, 16, 4, 10, 40), (32, 4, 2, 10, 2048)])
+def test_residual_ivfopq_rerank_parity(A, case, res_case, d_s, M, nprobe, k, kr):
+    data, o = case["data"], case["idx"]
+    opq, codes, lc = res_case[(d_s, M)]
+    g = gpu_res_index(A, case, res_case, d_s, M)
+    q = data["queries"]
+    gi, gd = A.search_ivfopq(g, cu(q), 32, nprobe, k, rerank_k=kr)
+    orr = oracle.search_ivfopq(data["db"], o, opq, codes, q, 32, nprobe, k + 20, rerank_k=kr)
+    adc = oracle.search_ivfopq(data["db"], o, opq, codes, q, 32, nprobe, kr + 1)
+    a, b = adc["dist"][:, kr - 1], adc["dist"][:, kr]
+    near = np.isfinite(b) & (b - a > 0) & (b - a <= tol(b))
+    amb = ambiguous_probe_rows(adc["probe_dist"], nprobe) | near
+    n, fails = check_topk(gi.cpu().numpy(), gd.cpu().numpy(), orr["ids"], orr["dist"], k,
+                          skip_rows=amb)
+    assert n > 0.8 * len(q) and not fails, f"{len(fails)}/{n}: {fails[:2]}"
+    g.free()
+
+
+def test_residual_build_on_gpu(A, case):
+    """The GPU residual trainer: its list centres are the oracle's list means
+    of the same lists, the distortion trace does not increase, and residual
+    codes quantise better than plain codes of the same byte budget."""
+    data, o = case["data"], case["idx"]
+    db = cu(data["db"])
+    g = A.index_create(db, cu(o["centroids"]), cu(o["assign"].astype(np.int32)))
+    tr = A.build_opq_residual(g, db, 64, 8, 3, 3, 5, 6000, 21)
+    lc = A.list_centres(g).cpu().numpy()
+    ref = oracle.list_centroids(data["db"], o, 64)
+    assert np.allclose(lc, ref, rtol=1e-5, atol=1e-6)
+    tr = np.array(tr)
+    assert np.all(np.diff(tr) <= 1e-6 * tr[:-1] + 1e-9), tr
+    h = A.index_create(db, cu(o["centroids"]), cu(o["assign"].astype(np.int32)))
+    tr0 = np.array(A.build_opq(h, db, 64, 8, 3, 3, 5, 6000, 21))
+    assert tr[-1] < tr0[-1]
+    # both searchable; residual recall against exact IVF at least that of plain codes
+    q = cu(data["queries"])
+    ex = oracle.search_ivf(data["db"], o, data["queries"], 32, 64, 6, 10)
+    r1 = recall(A.search_ivfopq(g, q, 32, 6, 10)[0].cpu().numpy(), ex["ids"], 10)
+    r0 = recall(A.search_ivfopq(h, q, 32, 6, 10)[0].cpu().numpy(), ex["ids"], 10)
+    assert r1 >= r0 - 0.02, (r1, r0)
+    g.free()
+    h.free()

@@ -69,3 +69,68 @@ def test_results_same_alone_and_in_the_mix(setup):
         assert np.all(np.abs(r.dist[fin] - dist[fin]) <= tol(dist[fin]))
     for g in idx.values():
         g.status()
+
+
+def test_native_server_same_alone_and_in_the_mix(setup):
+    """The library's own server (adanns_server_*): FP32, BF16 + rerank and IVF-OPQ
+    requests over two resident indices, a burst submitted at once (shared
+    batches) and a paced stream; every request equals the same rows searched
+    alone through the search calls, bit for bit."""
+    P, data, idx = setup
+    from paper_2305_19435_gb300.serving import Budget, NativeServer
+    if idx[16].opq is None:
+        P.build_opq(idx[16], torch.from_numpy(data["db"]).cuda(), 64, 16, 2, 2, 4, 8_000, 3)
+    budgets = [Budget(16, 128, 4, 10), Budget(64, 256, 8, 100, P.STORE_BF16, 400),
+               Budget(16, 64, 1, 10, P.STORE_BF16, 40), Budget(16, 0, 6, 20, method=1),
+               Budget(16, 0, 4, 10, rerank_k=80, method=1)]
+    rng = np.random.default_rng(11)
+    srv = NativeServer(idx, streams=3, max_batch=1024, mem_budget=8 << 30)
+    q = data["queries"]
+    reqs = []
+    for i in range(10):
+        b = budgets[i % 2]
+        reqs.append((srv.submit(q[50 * i:50 * i + 31], b, index_key=b.d_c), b, 50 * i, 31))
+    for i in range(40):
+        n = int(rng.integers(1, 300))
+        lo = int(rng.integers(0, len(q) - n))
+        b = budgets[int(rng.integers(0, len(budgets)))]
+        reqs.append((srv.submit(q[lo:lo + n], b, index_key=b.d_c), b, lo, n))
+        time.sleep(float(rng.exponential(0.001)))
+    for r, _, _, _ in reqs:
+        assert r.wait(120)
+    st = srv.stats()
+    srv.stop()
+    assert st["requests"] == 50 and st["queries"] == sum(n for _, _, _, n in reqs)
+    assert st["batches"] < 50 and st["p99_ms"] >= st["p50_ms"] > 0
+    for r, b, lo, n in reqs:
+        assert r.error is None, r.error
+        qq = torch.from_numpy(np.ascontiguousarray(q[lo:lo + n])).cuda()
+        if b.method == 1:
+            ids, dist = P.search_ivfopq(idx[b.d_c], qq, b.d_c, b.nprobe, b.k, rerank_k=b.rerank_k)
+        else:
+            ids, dist = P.search_ivf(idx[b.d_c], qq, b.d_c, b.d_s, b.nprobe, b.k,
+                                     storage=b.storage, rerank_k=b.rerank_k)
+        assert np.array_equal(r.ids, ids.cpu().numpy())
+        assert np.array_equal(r.dist.view(np.int32), dist.cpu().numpy().view(np.int32))
+        assert r.latency_ms > 0
+    for g in idx.values():
+        g.status()
+
+
+def test_native_server_rejects_bad_requests(setup):
+    P, data, idx = setup
+    from paper_2305_19435_gb300.serving import Budget, NativeServer
+    srv = NativeServer({64: idx[64]}, streams=1, max_batch=64)
+    q = data["queries"][:8]
+    for b, code in ((Budget(16, 100, 4, 10), -2),               # d_s not a granularity
+                    (Budget(16, 128, 4, 0), -1),                # k = 0
+                    (Budget(16, 128, 4, 10, P.STORE_BF16, 4), -1),   # shortlist below k
+                    (Budget(16, 0, 4, 10, method=1), -6)):      # no OPQ data on this index
+        with pytest.raises(P.AdannsError) as e:
+            srv.submit(q, b, index_key=64)
+        assert e.value.code == code
+    with pytest.raises(P.AdannsError):
+        srv.submit(data["queries"][:65], Budget(16, 128, 4, 10), index_key=64)  # > max_batch
+    r = srv.submit(q, Budget(64, 128, 4, 10), index_key=64)
+    assert r.wait(60) and r.error is None
+    srv.stop()
