@@ -35,15 +35,17 @@ METRIC_L2_PREFIXNORM = 1
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_liboracle.so")
 _SRC = os.path.join(_HERE, "oracle_core.c")
+_SRCS = [_SRC, os.path.join(_HERE, "graph_core.c")]
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile the C part of the oracle in place (gcc, no arch-specific flags)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or \
+            any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in _SRCS):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -67,6 +69,12 @@ def _load():
         lib.orc_pq_encode.argtypes = [P, i64, i64, i32, i32, i32, P, P, P, P, P, i32]
         lib.orc_ivfopq_search.argtypes = [P, i64, i32, P, i32, i32, P, P, P, P, P, i32, P, i64,
                                           i32, i32, i32, i32, i32, i32, P, P, P, P, P, i32]
+        lib.orc_knn_graph.argtypes = [P, i64, i32, i32, ctypes.c_double, ctypes.c_double, P, P, P,
+                                      i32]
+        lib.orc_graph_build.argtypes = [P, i64, i32, i32, i32, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, P, P, P, i32]
+        lib.orc_graph_search.argtypes = [P, i64, i32, P, i32, i64, P, i64, i32, i32,
+                                         ctypes.c_double, ctypes.c_double, P, P, P, P, i32]
         _lib = lib
     return _lib
 
@@ -388,3 +396,80 @@ def mflops_per_query(d_c: int, d_s: int, nlist: int, nprobe: int, N: int) -> dic
     read = d_c * nlist + nprobe * d_s * N / nlist
     literal = d_s * nlist + nprobe * d_s * N / nlist
     return {"mflops": read / 1e6, "mflops_literal": literal / 1e6}
+
+
+# ----------------------------------------------------------------------------
+# low-d graph shortlist + high-d rerank (AdANNS-DiskANN, Sec. 4.3)
+# ----------------------------------------------------------------------------
+# Ties within this tolerance make a decision "ambiguous" for a comparison with
+# an FP32 implementation (the parity rule's relative tolerance and floor).
+AMB_REL, AMB_ABS = 1e-5, 2.4e-7
+
+
+def knn_graph(db: np.ndarray, d_g: int, K: int, metric: int = METRIC_L2_PREFIXNORM,
+              nthreads: int | None = None):
+    """The K nearest other rows of every row at the d_g prefix, by (distance,
+    id): (ids int32 [N, K], distances FP64, ambiguity flag of the K-th cut)."""
+    X = prefix(db, d_g, metric)
+    N = X.shape[0]
+    nbr = np.empty((N, K), dtype=np.int32)
+    dist = np.empty((N, K), dtype=np.float64)
+    amb = np.empty(N, dtype=np.uint8)
+    if _load().orc_knn_graph(_p(X), N, d_g, K, AMB_REL, AMB_ABS, _p(nbr), _p(dist), _p(amb),
+                             _threads(nthreads)) != 0:
+        raise ValueError("bad kNN graph arguments")
+    return nbr, dist, amb.astype(bool)
+
+
+def build_graph(db: np.ndarray, d_g: int, K: int, R: int, alpha: float,
+                metric: int = METRIC_L2_PREFIXNORM, nthreads: int | None = None) -> dict:
+    """AdANNS-DiskANN graph formed with the low-d MR (Sec. 4.3): at the d_g
+    prefix, every row's K nearest other rows are robust-pruned (factor alpha)
+    to at most R out-neighbours, every edge offers its source to its target,
+    and rows holding more than R are pruned again over the union.  Returns
+    dict(graph int32 [N, R] (-1 padding, rows by (distance, id)), entry (row
+    nearest to the mean), amb (rows with a decision within tolerance))."""
+    X = prefix(db, d_g, metric)
+    N = X.shape[0]
+    g = np.empty((N, R), dtype=np.int32)
+    amb = np.empty(N, dtype=np.uint8)
+    entry = ctypes.c_int64()
+    if _load().orc_graph_build(_p(X), N, d_g, K, R, float(alpha), AMB_REL, AMB_ABS, _p(g),
+                               _p(amb), ctypes.byref(entry), _threads(nthreads)) != 0:
+        raise ValueError("bad graph build arguments")
+    return {"graph": g, "entry": int(entry.value), "amb": amb.astype(bool), "d_g": d_g, "R": R,
+            "K": K, "alpha": alpha, "metric": metric}
+
+
+def search_graph(db: np.ndarray, gr: dict, queries: np.ndarray, L: int, d_s: int, k: int,
+                 rerank_k: int, nthreads: int | None = None) -> dict:
+    """Best-first search of the graph at the d_g prefix with a candidate list
+    of L, then the rerank_k nearest of the list re-scored with dist_ds (the
+    high-d MR, Sec. 4.3 shortlist-rerank) and the k best by (distance, id).
+    Returns ids, dist (FP64, -1 / +inf padding), the graph stage's shortlist
+    (short_ids, short_dist), amb (a traversal decision within tolerance) and
+    the number of expanded rows per query."""
+    metric = gr["metric"]
+    X = prefix(db, gr["d_g"], metric)
+    Q = prefix(queries, gr["d_g"], metric)
+    B = Q.shape[0]
+    sid = np.empty((B, rerank_k), dtype=np.int64)
+    sd = np.empty((B, rerank_k), dtype=np.float64)
+    amb = np.empty(B, dtype=np.uint8)
+    nexp = np.empty(B, dtype=np.int64)
+    if _load().orc_graph_search(_p(X), X.shape[0], gr["d_g"], _p(_c(gr["graph"], np.int32)),
+                                gr["R"], gr["entry"], _p(Q), B, L, rerank_k, AMB_REL, AMB_ABS,
+                                _p(sid), _p(sd), _p(amb), _p(nexp), _threads(nthreads)) != 0:
+        raise ValueError("bad graph search arguments")
+    ids = np.full((B, k), -1, dtype=np.int64)
+    dist = np.full((B, k), np.inf)
+    Ps = prefix(queries, d_s, metric)
+    for i in range(B):
+        c = sid[i][sid[i] >= 0]
+        if len(c) == 0:
+            continue
+        d = ((prefix(db[c], d_s, metric) - Ps[i][None]) ** 2).sum(1)
+        o = np.lexsort((c, d))[:k]
+        ids[i, :len(o)], dist[i, :len(o)] = c[o], d[o]
+    return {"ids": ids, "dist": dist, "short_ids": sid, "short_dist": sd,
+            "amb": amb.astype(bool), "expanded": nexp}
