@@ -120,6 +120,48 @@ int top1_sweep(const float *pts, int64_t n, int ldq, const float *cent_pm, const
   return launch_scan_f32(a, st);
 }
 
+// Nearest of nc centroids (nc x dim FP32 row-major `cent`, also prefix-major
+// in cent_pm / cent_off) for n prepared points (rows of ldq floats):
+// keys[i] = (distance bits << 32 | centroid), ties to the lower centroid.
+// The Lloyd assignment step as a tensor-core GEMM: with at least 256
+// centroids, dim <= 64 and the prefix-normalised metric, BF16 products of the
+// points and a BF16 copy of the centroids (tcgen05) shortlist every centroid
+// within the quantisation error bound of the best, and those are scored
+// exactly in FP32 -- the cluster mapping's path with n_p = 1, so the result is
+// the FP32 scan's.  Otherwise the FP32 scan.  err: the device status word of
+// the tensor-core pipeline.
+int nearest_centroid(const float *cent, int nc, int dim, int metric, const float *cent_pm,
+                     const int64_t *cent_off, const float *pts, int64_t n, int ldq,
+                     uint64_t *keys, int *counter, int *err, cudaStream_t st) {
+  if (n <= 0) return ADANNS_OK;
+  if (metric == ADANNS_METRIC_L2_PREFIXNORM && nc >= 256 && dim <= 64 &&
+      option(ADANNS_OPT_COARSE_TC)) {
+    adanns_index shell;
+    shell.centroids = const_cast<float *>(cent);
+    shell.nlist = nc;
+    shell.d_c = dim;
+    shell.dc_pad = pad16(dim);
+    shell.metric = metric;
+    shell.cent_pm = const_cast<float *>(cent_pm);
+    shell.cent_off = const_cast<int64_t *>(cent_off);
+    shell.dev_err = err;
+    int rc = build_centroid_lowp(&shell, st);
+    if (rc == ADANNS_OK) {
+      // slices keep the 2-byte keys of (point, centroid) pairs near 1 GiB
+      const int64_t rows = std::max<int64_t>(CT_SLICE_MIN, (1ll << 29) / ((nc + 7) & ~7));
+      for (int64_t i0 = 0; i0 < n && rc == ADANNS_OK; i0 += rows)
+        rc = launch_coarse_tc(&shell, pts + i0 * ldq, ldq, std::min(rows, n - i0), dim, 1,
+                              keys + i0, st);
+    }
+    cudaStreamSynchronize(st);  // the table copies are released below
+    cudaFree(shell.cent_low);
+    cudaFree(shell.cent_sc);
+    cudaFree(shell.cent_n2);
+    if (rc != 1) return rc;  // 1: the shape does not fit the tensor-core path
+  }
+  return top1_sweep(pts, n, ldq, cent_pm, cent_off, nc, dim, keys, counter, st);
+}
+
 int make_cent_off(int64_t **off, int nc, cudaStream_t st) {
   int rc = dmalloc(off, 2);
   if (rc) return rc;
@@ -131,9 +173,10 @@ int make_cent_off(int64_t **off, int nc, cudaStream_t st) {
 constexpr int64_t SWEEP_ROWS = 1 << 20;  // points per assignment slice
 
 // assign all N rows of db (first d_c coordinates, normalised per metric) to
-// the nearest of nc centroids (prefix-major table)
-int assign_all(const float *db, int64_t N, int ld, int d_c, int metric, const float *cent_pm,
-               const int64_t *cent_off, int nc, int32_t *assign, float *dist, cudaStream_t st) {
+// the nearest of nc centroids (row-major cent and its prefix-major table)
+int assign_all(const float *db, int64_t N, int ld, int d_c, int metric, const float *cent,
+               const float *cent_pm, const int64_t *cent_off, int nc, int32_t *assign,
+               float *dist, int *err, cudaStream_t st) {
   Scratch s(st);
   const int dcp = pad16(d_c);
   const int64_t rows = std::min<int64_t>(N, SWEEP_ROWS);
@@ -148,7 +191,9 @@ int assign_all(const float *db, int64_t N, int ld, int d_c, int metric, const fl
     const int64_t n = std::min(rows, N - b0);
     if ((rc = launch_gather_normalize(db + b0 * ld, n, ld, nullptr, d_c, metric, pn, dcp, st)))
       return rc;
-    if ((rc = top1_sweep(pn, n, dcp, cent_pm, cent_off, nc, d_c, keys, counter, st))) return rc;
+    if ((rc = nearest_centroid(cent, nc, d_c, metric, cent_pm, cent_off, pn, n, dcp, keys, counter,
+                               err, st)))
+      return rc;
     if ((rc = launch_keys_to_result(keys, n, 1, nullptr, assign + b0, dist ? dist + b0 : nullptr,
                                     st)))
       return rc;
@@ -366,15 +411,16 @@ int adanns_build_ivf(const float *db, int64_t N, int d, int d_c, int nlist, int 
   uint64_t *keys;
   int32_t *asg, *counts, *asg_all;
   double *sums, *obj;
-  int *counter;
+  int *counter, *err;
   if ((rc = s.get(&d_s1, train_n)) || (rc = s.get(&d_s2, nlist)) ||
       (rc = s.get(&tn, (size_t)train_n * dcp)) || (rc = s.get(&cent, (size_t)nlist * d_c)) ||
       (rc = s.get(&cent_pm, (size_t)nlist * dcp)) || (rc = s.get(&keys, train_n)) ||
       (rc = s.get(&asg, train_n)) || (rc = s.get(&counts, nlist)) ||
       (rc = s.get(&sums, (size_t)nlist * d_c)) || (rc = s.get(&obj, 1)) ||
       (rc = s.get(&counter, 1)) || (rc = s.get(&cent_off, 2)) || (rc = s.get(&asg_all, N)) ||
-      (rc = s.get(&kd, 1)))
+      (rc = s.get(&kd, 1)) || (rc = s.get(&err, 1)))
     return rc;
+  ADN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   ADN_CUDA(cudaMemcpyAsync(d_s1, S1.data(), sizeof(int64_t) * train_n, cudaMemcpyHostToDevice, st));
   ADN_CUDA(cudaMemcpyAsync(d_s2, S2.data(), sizeof(int64_t) * nlist, cudaMemcpyHostToDevice, st));
   const int64_t h_off[2] = {0, (int64_t)nlist};
@@ -384,7 +430,8 @@ int adanns_build_ivf(const float *db, int64_t N, int d, int d_c, int nlist, int 
     return rc;
   for (int it = 0; it < niter; ++it) {
     if ((rc = centroids_pm(cent, nlist, d_c, cent_pm, st))) return rc;
-    if ((rc = top1_sweep(tn, train_n, dcp, cent_pm, cent_off, nlist, d_c, keys, counter, st)))
+    if ((rc = nearest_centroid(cent, nlist, d_c, metric, cent_pm, cent_off, tn, train_n, dcp, keys,
+                               counter, err, st)))
       return rc;
     if ((rc = launch_sum_keys(keys, train_n, obj, st))) return rc;
     if ((rc = launch_keys_to_result(keys, train_n, 1, nullptr, asg, nullptr, st))) return rc;
@@ -396,8 +443,15 @@ int adanns_build_ivf(const float *db, int64_t N, int d, int d_c, int nlist, int 
     if (objective) objective[it] = J;
   }
   if ((rc = centroids_pm(cent, nlist, d_c, cent_pm, st))) return rc;
-  if ((rc = assign_all(db, N, d, d_c, metric, cent_pm, cent_off, nlist, asg_all, nullptr, st)))
+  if ((rc = assign_all(db, N, d, d_c, metric, cent, cent_pm, cent_off, nlist, asg_all, nullptr,
+                       err, st)))
     return rc;
+  {
+    int h = 0;
+    ADN_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ADN_CUDA(cudaStreamSynchronize(st));
+    if (h) return fail(ADANNS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out in the k-means assignment");
+  }
   return make_index(db, N, d, cent, nlist, d_c, asg_all, metric, storage_mask, st, out);
 }
 
@@ -496,7 +550,17 @@ int adanns_kmeans_assign(const float *points, int64_t n, int ld, int dim, int me
   const int64_t h_off[2] = {0, (int64_t)nc};
   ADN_CUDA(cudaMemcpyAsync(coff, h_off, sizeof(h_off), cudaMemcpyHostToDevice, st));
   if ((rc = centroids_pm(centroids, nc, dim, cpm, st))) return rc;
-  return assign_all(points, n, ld, dim, metric, cpm, coff, nc, out_assign, out_dist, st);
+  int *err;
+  if ((rc = s.get(&err, 1))) return rc;
+  ADN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  if ((rc = assign_all(points, n, ld, dim, metric, centroids, cpm, coff, nc, out_assign, out_dist,
+                       err, st)))
+    return rc;
+  int h = 0;
+  ADN_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ADN_CUDA(cudaStreamSynchronize(st));
+  if (h) return fail(ADANNS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out in the assignment");
+  return ADANNS_OK;
 }
 
 int adanns_kmeans_update(const float *points, int64_t n, int ld, int dim, int metric,

@@ -254,6 +254,7 @@ int launch_coarse_tc(const adanns_index *idx, const float *qc, int ldq, int64_t 
 // centroid table (counter: the scan's work counter, zeroed by the caller).
 int run_coarse(const adanns_index *idx, const float *qc, int ldq, int64_t B, int d_c, int k,
                uint64_t *out, int *counter, cudaStream_t st);
+constexpr int64_t CT_SLICE_MIN = 4096;  // fewest points per tensor-core assignment slice
 int build_centroid_lowp(adanns_index *x, cudaStream_t st);
 // Candidate segments of a batch: per query, the probed lists' sizes rounded
 // up to 8, laid end to end (qtot: per-query total, qbase: its start, pbase:

@@ -202,9 +202,12 @@ def teacher_forced_case(seed=106, n=6000, d=64, d_c=32, nc=50):
     return x, T, C0
 
 
-def test_kmeans_assign_step_matches_oracle(A):
-    x, T, C0 = teacher_forced_case()
-    a, dist = A.kmeans_assign(cu(x), cu(C0), 32)
+@pytest.mark.parametrize("nc,d_c", [(50, 32), (300, 32), (1024, 64), (256, 16)])
+def test_kmeans_assign_step_matches_oracle(A, nc, d_c):
+    """From 256 centroids up (d_c <= 64) the assignment runs on the tensor cores
+    (BF16 products, exact FP32 re-score within the error bound)."""
+    x, T, C0 = teacher_forced_case(d_c=d_c, nc=nc)
+    a, dist = A.kmeans_assign(cu(x), cu(C0), d_c)
     a, dist = a.cpu().numpy(), dist.cpu().numpy()
     oa, ob, os2 = oracle.assign(T, C0.astype(np.float64))
     tied = os2 - ob <= tol(os2)
@@ -238,15 +241,33 @@ def test_build_ivf_free_running_objective(A, tiny):
     off, ids = g.lists()
     off, ids = off.cpu().numpy(), ids.cpu().numpy()
     assert off[-1] == 10_000 and sorted(ids.tolist()) == list(range(10_000))
-    # the GPU's final assignment is the nearest of its own centroids (oracle check)
+    # the GPU's final assignment is the nearest of its own centroids (a
+    # property, checked with a plain FP64 distance table, not the oracle)
     C = g.centroids().cpu().numpy().astype(np.float64)
     X = oracle.prefix(data["db"], 16)
-    oa, ob, os2 = oracle.assign(X, C)
+    D = ((X[:, None, :] - C[None, :, :]) ** 2).sum(-1)
+    srt = np.sort(D, axis=1)
+    oa, ob, os2 = np.argmin(D, axis=1), srt[:, 0], srt[:, 1]
     lab = np.empty(10_000, dtype=np.int64)
     for l in range(64):
         lab[ids[off[l]:off[l + 1]]] = l
     tied = os2 - ob <= tol(os2)
     assert np.array_equal(lab[~tied], oa[~tied])
+    g.free()
+
+
+def test_build_ivf_tensor_core_assignment_objective(A):
+    """A build with 256 lists (assignment on the tensor cores): the same sample
+    and initialisation as the oracle's give the same first objective, the
+    free-running trace stays within 1e-4 and never increases."""
+    data = synthdata.small(30_000, 1, 64, 300, 117)
+    o = oracle.build_ivf(data["db"], 32, 256, 8, 30_000, seed=7)
+    g = A.build_ivf(cu(data["db"]), 32, 256, 8, 30_000, 7)
+    Jg, Jo = np.array(g.objective), np.array(o["objectives"])
+    assert abs(Jg[0] - Jo[0]) <= 1e-5 * Jo[0]
+    assert abs(Jg[-1] - Jo[-1]) <= 1e-4 * Jo[-1]
+    assert np.all(Jg[1:] <= Jg[:-1] * (1 + 1e-6))
+    g.status()
     g.free()
 
 
