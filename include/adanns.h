@@ -498,6 +498,48 @@ int adanns_search_ivf_noalloc(const adanns_index *idx, const float *queries, int
                               void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Low-d graph shortlist + high-d rerank (AdANNS-DiskANN, Sec. 4.3 "AdANNS for
+ * Composite Indices": the search graph is formed with a low-d MR, its
+ * shortlist is re-ranked with a high-d MR).
+ *
+ * adanns_graph_build forms a DiskANN-style pruned proximity graph on the d_g
+ * prefix (P_dg under ADANNS_METRIC_L2_PREFIXNORM) of the N x d FP32 rows db
+ * (device; copied, so the caller may free it): every row's K nearest other
+ * rows (exact, ties to the lower id) are robust-pruned with factor alpha to at
+ * most R out-neighbours (take the nearest remaining candidate c, drop every
+ * remaining v with alpha * d(c, v) <= d(row, v)); every edge offers its
+ * source to its target, and a row whose own and offered neighbours exceed R is
+ * pruned again over their union by (distance, id).  The entry point is the
+ * row nearest to the mean of the P_dg rows.  Limits: d_g in G and <= 64,
+ * 1 <= R <= 64, 1 <= K <= 256, K < N, alpha >= 1; a row offered more than
+ * 4,096 edges returns ADANNS_ERR_ARG.  Synchronises the stream.
+ * adanns_graph_create takes a given graph instead (device int32 [N][R], -1
+ * padding; an id outside [-1, N) returns ADANNS_ERR_ARG) and entry point.  adanns_graph_info / adanns_graph_get report it.
+ *
+ * adanns_graph_search: per query, a best-first search at d_g with a
+ * candidate list of L entries (1 <= L <= 512) -- expand the nearest entry not
+ * yet expanded, score its neighbours that are not in the list, keep the L
+ * nearest by (distance, id) -- until every entry is expanded; the rerank_k
+ * (k <= rerank_k <= min(L, 1024)) nearest entries are re-scored with the exact
+ * FP32 dist_ds (d_s in G, <= d) and the k best by (distance, id) are returned
+ * in out_ids / out_dist (device, [B][k], -1 / +inf padding); out_shortlist
+ * (optional, device int64 [B][rerank_k]) receives the graph stage's list.
+ * All distances are FP32 in difference form.  Asynchronous on the stream.
+ */
+typedef struct adanns_graph adanns_graph;
+int adanns_graph_build(const float *db, int64_t N, int d, int d_g, int K, int R, float alpha,
+                       int metric, void *cuda_stream, adanns_graph **out);
+int adanns_graph_create(const float *db, int64_t N, int d, int d_g, const int32_t *graph, int R,
+                        int64_t entry, int metric, void *cuda_stream, adanns_graph **out);
+int adanns_graph_info(const adanns_graph *g, int64_t *N, int *d, int *d_g, int *R,
+                      int64_t *entry);
+int adanns_graph_get(const adanns_graph *g, int32_t *graph, void *cuda_stream);
+int adanns_graph_search(const adanns_graph *g, const float *queries, int64_t B, int L, int d_s,
+                        int k, int rerank_k, int64_t *out_ids, float *out_dist,
+                        int64_t *out_shortlist, void *cuda_stream);
+void adanns_graph_free(adanns_graph *g);
+
+/* ------------------------------------------------------------------------
  * Continuous-batching server (the serving loop of the compute-aware elastic
  * search of Sec. 5 "Compute-aware Elastic Search During Inference": every
  * request carries its own compute budget over resident indices).

@@ -91,6 +91,13 @@ def lib():
         L.adanns_server_poll.argtypes = [P, i64, i32, P, P, P]
         L.adanns_server_stats.argtypes = [P, P, P, P, P, P, P, P]
         L.adanns_server_destroy.argtypes = [P]
+        L.adanns_graph_build.argtypes = [P, i64, i32, i32, i32, i32, ctypes.c_float, i32, P, P]
+        L.adanns_graph_create.argtypes = [P, i64, i32, i32, P, i32, i64, i32, P, P]
+        L.adanns_graph_info.argtypes = [P, P, P, P, P, P]
+        L.adanns_graph_get.argtypes = [P, P, P]
+        L.adanns_graph_search.argtypes = [P, P, i64, i32, i32, i32, i32, P, P, P, P]
+        L.adanns_graph_free.argtypes = [P]
+        L.adanns_graph_free.restype = None
         L.adanns_set_option.argtypes = [i32, i64]
         L.adanns_get_option.argtypes = [i32, P]
         _lib = L
@@ -295,6 +302,76 @@ def index_import(path: str) -> Index:
     h = ctypes.c_void_p()
     _check(lib().adanns_index_import(os.fsencode(path), _stream(), ctypes.byref(h)))
     return Index(h)
+
+
+class Graph:
+    """A low-d proximity graph with the rows for the high-d rerank (library-owned)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        N, d, dg, R, e = (ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(),
+                          ctypes.c_int64())
+        _check(lib().adanns_graph_info(handle, ctypes.byref(N), ctypes.byref(d), ctypes.byref(dg),
+                                       ctypes.byref(R), ctypes.byref(e)))
+        self.N, self.d, self.d_g, self.R, self.entry = N.value, d.value, dg.value, R.value, e.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("graph already freed")
+        return self._h
+
+    def neighbours(self) -> torch.Tensor:
+        out = torch.empty(self.N, self.R, dtype=torch.int32, device="cuda")
+        _check(lib().adanns_graph_get(self.handle, _ptr(out), _stream()))
+        return out
+
+    def free(self):
+        if self._h is not None:
+            lib().adanns_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def graph_build(db: torch.Tensor, d_g: int, K: int, R: int, alpha: float,
+                metric: int = METRIC_L2_PREFIXNORM) -> Graph:
+    """AdANNS-DiskANN graph on the d_g prefix (K candidates, R out-degree, prune factor alpha)."""
+    _need(db, torch.float32, "db", 2)
+    h = ctypes.c_void_p()
+    _check(lib().adanns_graph_build(_ptr(db), db.shape[0], db.shape[1], d_g, K, R, float(alpha),
+                                    metric, _stream(), ctypes.byref(h)))
+    return Graph(h)
+
+
+def graph_create(db: torch.Tensor, d_g: int, graph: torch.Tensor, entry: int,
+                 metric: int = METRIC_L2_PREFIXNORM) -> Graph:
+    """A graph from given neighbour lists (int32 [N, R], -1 padding) and entry point."""
+    _need(db, torch.float32, "db", 2)
+    _need(graph, torch.int32, "graph", 2)
+    h = ctypes.c_void_p()
+    _check(lib().adanns_graph_create(_ptr(db), db.shape[0], db.shape[1], d_g, _ptr(graph),
+                                     graph.shape[1], int(entry), metric, _stream(),
+                                     ctypes.byref(h)))
+    return Graph(h)
+
+
+def graph_search(g: Graph, queries: torch.Tensor, L: int, d_s: int, k: int, rerank_k: int,
+                 return_shortlist: bool = False):
+    """Graph shortlist at d_g, exact rerank at d_s -> (ids, dist[, shortlist])."""
+    _need(queries, torch.float32, "queries", 2)
+    B = queries.shape[0]
+    ids = torch.empty(B, k, dtype=torch.int64, device=queries.device)
+    dist = torch.empty(B, k, dtype=torch.float32, device=queries.device)
+    sl = torch.empty(B, rerank_k, dtype=torch.int64, device=queries.device) \
+        if return_shortlist else None
+    _check(lib().adanns_graph_search(g.handle, _ptr(queries), B, L, d_s, k, rerank_k, _ptr(ids),
+                                     _ptr(dist), _ptr(sl), _stream()))
+    return (ids, dist, sl) if return_shortlist else (ids, dist)
 
 
 def flat_index(db: torch.Tensor, metric: int = METRIC_L2_PREFIXNORM,
