@@ -74,6 +74,8 @@ def parse():
                    help="IVF-OPQ on the NQ-shaped workload (build, QPS per (d_s, M, nprobe), "
                         "recall@10 against exact search on a query sample) instead of the timed run")
     p.add_argument("--gt-queries", type=int, default=100)
+    p.add_argument("--graph", action="store_true",
+                   help="AdANNS-DiskANN graph shortlist + rerank on the ImageNet-shaped data")
     p.add_argument("--no-largest", action="store_true",
                    help="skip the largest grid point (d_c = 64, d_s = 2048, nprobe = 32)")
     return p.parse_args()
@@ -617,8 +619,65 @@ def flat_opq_bench(args):
                                           "(numpy over the whole database)"}))
 
 
+def graph_bench(args):
+    """AdANNS-DiskANN on the ImageNet-shaped workload (Sec. 4.3): a graph formed
+    at the low-d MR (d_g = 16), best-first shortlist at d_g, exact rerank with
+    the high-d MR; QPS and recall@10 against exact search at the rerank's d_s."""
+    import torch
+    import paper_2305_19435_gb300 as P
+    P.build()
+    w = synthdata.WORKLOADS["imagenet"]
+    N = args.n or w.N
+    B = args.b or 10_000
+    data = synthdata.make("imagenet", n=N, b=B)
+    db_dev = torch.from_numpy(data["db"]).cuda()
+    q = torch.from_numpy(data["queries"]).cuda()
+    torch.cuda.synchronize()
+    tb = time.time()
+    g = P.graph_build(db_dev, 16, 64, 32, 1.2)
+    torch.cuda.synchronize()
+    build_s = time.time() - tb
+    log(f"graph build {build_s:.1f}s")
+    del db_dev
+    torch.cuda.empty_cache()
+    S = min(args.gt_queries, B)
+    st = torch.cuda.current_stream()
+    rows = []
+    for d_s in (512, 2048):
+        gt = exact_topk_prefixnorm(data["db"], data["queries"][:S], d_s, 10)
+        for L, kr in ((32, 32), (64, 40), (128, 100), (256, 200)):
+            ids = torch.empty(B, 10, dtype=torch.int64, device="cuda")
+
+            def step(L=L, kr=kr):
+                P.graph_search(g, q, L, d_s, 10, kr)
+
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            ms, launches, prof = timed(P, torch, step, args.steps, st)
+            gi, _ = P.graph_search(g, q[:S], L, d_s, 10, kr)
+            gi = gi.cpu().numpy()
+            rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / 10.0
+                                 for a, b in zip(gi, gt)]))
+            row = {"d_g": 16, "d_s": d_s, "L": L, "rerank_k": kr, "qps": B / (ms / 1e3),
+                   "ms_per_step": ms, "stages_ms": {k2: v[0] / args.steps for k2, v in prof.items()},
+                   "recall10_vs_exact": rec, "gpu_launches": launches}
+            rows.append(row)
+            log(json.dumps(row))
+    g.free()
+    print(json.dumps({"graph": rows, "build_s": build_s,
+                      "workload": f"AdANNS-DiskANN, ImageNet-shaped: N={N:,} d=2048 B={B:,} k=10, "
+                                  "graph at d_g=16 (K=64 candidates, R=32, alpha=1.2)",
+                      "recall_sample": S,
+                      "recall_reference": "exact top-10 by L2 on normalised d_s prefixes "
+                                          "(numpy over the whole database)"}))
+
+
 def main():
     args = parse()
+    if getattr(args, "graph", False):
+        graph_bench(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

@@ -60,24 +60,26 @@ __global__ void pair_scatter_kernel(const int32_t *__restrict__ ppos, int64_t n,
 // centroids), so the CTAs resident at one time cover a few neighbouring lists
 // and the query rows they gather -- those of the queries probing these lists
 // -- stay in L2 while they are reused.
-constexpr int RC_THREADS = 128;
-constexpr int RC_HW = RC_THREADS / 16;  // half-warps per CTA
-constexpr int RC_META = RC_THREADS;    // pairs whose metadata are staged at once
 constexpr int RC_MAX_MC = 64;
 
-// members per chunk: the largest of 64, 32, 16, 8 whose rows fit in 32 KB
-// (at least 8); the index keeps a chunk table for each of these sizes
+// members per chunk: the largest of 64, 32, 16, 8 whose rows fit in 16 KB
+// (at least 8), so that eight CTAs share an SM; the index keeps a chunk table
+// for each of these sizes
 inline int rerank_chunk_members(int d_s) {
   int mc = RC_MAX_MC;
-  while (mc > 8 && mc * d_s * 4 > 32768) mc >>= 1;
+  while (mc > 8 && mc * d_s * 4 > 16384) mc >>= 1;
   return mc;
 }
 static_assert(RC_MAX_MC == 64, "chunk sizes 64, 32, 16, 8 have precomputed chunk tables");
 
 // FULL: d_s is a multiple of 512 (every half-warp lane holds 8 whole float4
 // of each 512-coordinate segment), so no coordinate bound is checked.
-template <bool FULL>
-__global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
+// NT threads (a half-warp per pair in flight), at least MINB CTAs per SM: the
+// query-row gathers are latency-bound, so more resident warps each holding one
+// row in flight beat fewer warps double-buffering two (measured: 1.71 against
+// 2.03 ms at d_s = 512, 9.25 against 10.41 ms at d_s = 2048)
+template <bool FULL, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
     const int32_t *__restrict__ order, const int32_t *__restrict__ mstart,
     const int32_t *__restrict__ pmem, const int32_t *__restrict__ list_ids, int kr,
     const float *__restrict__ qs, int ldq, int d_s, const float *__restrict__ xpm, int d_pad,
@@ -85,7 +87,8 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
     const int32_t *__restrict__ lorder, const int32_t *__restrict__ cstart, int nlist,
     uint64_t *__restrict__ keys, int *__restrict__ err) {
   extern __shared__ __align__(16) float rows[];  // [mc][d_s + 4]
-  __shared__ int s_e[RC_META], s_m[RC_META], s_q[RC_META];
+  constexpr int HW = NT / 16;  // half-warps per CTA
+  __shared__ int s_e[NT], s_m[NT], s_q[NT];
   __shared__ float s_nu[RC_MAX_MC];
   __shared__ uint32_t s_id[RC_MAX_MC];
   // chunk -> (list, first member): the last order position whose first chunk
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
     if (p0 >= p1) return;
     // member rows: block b of the chunk is nm x 16 contiguous floats
     const int per_b = nm * 4;  // float4 per block
-    for (int t = threadIdx.x; t < per_b * ((d_s + 15) >> 4); t += RC_THREADS) {
+    for (int t = threadIdx.x; t < per_b * ((d_s + 15) >> 4); t += NT) {
       const int b = t / per_b, w = t - b * per_b, mm = w >> 2, part = w & 3;
       if (4 * b + part >= nseg) continue;  // d_s = 8: half of the last block
       cp_async16_hint(rows + (size_t)mm * rs + 16 * b + 4 * part,
@@ -122,12 +125,12 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
                       stream);
     }
     cp_async_commit();  // the copies land while the first metadata batch loads
-    for (int t = threadIdx.x; t < nm; t += RC_THREADS) {
+    for (int t = threadIdx.x; t < nm; t += NT) {
       s_nu[t] = mscale ? mscale[off + m0 + t] : 1.f;
       s_id[t] = (uint32_t)list_ids[off + m0 + t];
     }
-    for (int base = p0; base < p1; base += RC_META) {
-      const int nb = min(RC_META, p1 - base);
+    for (int base = p0; base < p1; base += NT) {
+      const int nb = min(NT, p1 - base);
       if (base != p0) __syncthreads();  // previous metadata consumed
       if ((int)threadIdx.x < nb) {
         const int e = order[base + threadIdx.x];
@@ -180,20 +183,11 @@ __global__ void __launch_bounds__(RC_THREADS) rerank_chunks_kernel(
         for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(hmask, acc, o);
         if (hl == 0) keys[s_e[t]] = pack_key(acc, s_id[mm]);
       };
-      // the half-warp's pairs t = hw, hw + RC_HW, ...: the next pair's query
-      // row loads into the other register buffer while this one is scored
-      float4 qa[8], qb[8];
-      int t = hw;
-      if (t < nb) load_first(t, qa);
-      while (t < nb) {
-        const int t2 = t + RC_HW;
-        if (t2 < nb) load_first(t2, qb);
+      // the half-warp's pairs t = hw, hw + HW, ...
+      float4 qa[8];
+      for (int t = hw; t < nb; t += HW) {
+        load_first(t, qa);
         score(t, qa);
-        if (t2 >= nb) break;
-        const int t3 = t2 + RC_HW;
-        if (t3 < nb) load_first(t3, qa);
-        score(t2, qb);
-        t = t3;
       }
     }
   }
@@ -281,24 +275,31 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     const int mc = rerank_chunk_members(d_s);
     const size_t rs = (size_t)mc * (d_s + 4) * 4;
     const bool full = d_s % 512 == 0;
-    const void *fn = full ? (const void *)rerank_chunks_kernel<true>
-                          : (const void *)rerank_chunks_kernel<false>;
-    ADN_CUDA(ensure_smem(fn, rs));
     // slots of padding or pruned candidates keep the empty key
     ADN_CUDA(cudaMemsetAsync(keys, 0xFF, sizeof(uint64_t) * n, st));
     const int ci = rerank_chunk_index(mc);
     const int chunks = idx->rr_chunks[ci];
     if (chunks > 0) {
+      // long prefixes (eight-member chunks of up to 64 KB of rows): 256 threads
+      // share a chunk; shorter ones: 128 threads, eight CTAs per SM
+      auto go = [&](auto kern, int nt) -> cudaError_t {
+        cudaError_t e = ensure_smem((const void *)kern, rs);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)chunks, nt, rs, st>>>(order, mstart, pmem, idx->list_ids, kr, qs, ldq,
+                                               d_s, idx->xpm, idx->d_pad, idx->list_off, mscale,
+                                               mc, idx->rr_order, idx->rr_cstart[ci], nlist, keys,
+                                               idx->dev_err);
+        return cudaSuccess;
+      };
+      const bool wide = d_s >= 1024;
+      cudaError_t e;
       if (full)
-        rerank_chunks_kernel<true><<<(unsigned)chunks, RC_THREADS, rs, st>>>(
-            order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad,
-            idx->list_off, mscale, mc, idx->rr_order, idx->rr_cstart[ci], nlist, keys,
-            idx->dev_err);
+        e = wide ? go(rerank_chunks_kernel<true, 256, 4>, 256)
+                 : go(rerank_chunks_kernel<true, 128, 8>, 128);
       else
-        rerank_chunks_kernel<false><<<(unsigned)chunks, RC_THREADS, rs, st>>>(
-            order, mstart, pmem, idx->list_ids, kr, qs, ldq, d_s, idx->xpm, idx->d_pad,
-            idx->list_off, mscale, mc, idx->rr_order, idx->rr_cstart[ci], nlist, keys,
-            idx->dev_err);
+        e = wide ? go(rerank_chunks_kernel<false, 256, 4>, 256)
+                 : go(rerank_chunks_kernel<false, 128, 8>, 128);
+      if (e != cudaSuccess) return cuda_fail(e, "rerank attribute");
       ADN_LAUNCH("rerank_chunks_kernel");
     }
   }
