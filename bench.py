@@ -63,6 +63,9 @@ def parse():
                    help="length of each serving run (0 disables the serving phase)")
     p.add_argument("--serve-rate", type=float, default=20000.0,
                    help="mean offered load of the serving runs, queries/s")
+    p.add_argument("--serve-rate-small", type=float, default=200000.0,
+                   help="query rate of the small-request serving load (above what one "
+                        "request per launch sustains, so requests queue and share batches)")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--accuracy-sweep", action="store_true",
                    help="recall and distance error of every tier vs the FP64 oracle per "
@@ -280,9 +283,12 @@ def timed(P, torch, step, steps, stream):
 
 
 def serving_phase(P, torch, data, db_dev, args, B):
-    """Poisson request stream over two resident indices (d_c = 16 and 64),
-    request sizes uniform in [1, 4096], per-request budgets; once with every
-    request on the mixed-precision path and once on the FP32 path."""
+    """Poisson request streams over two resident indices (d_c = 16 and 64) with
+    per-request budgets, each once with every request on the mixed-precision
+    path and once on the FP32 path: request sizes uniform in [1, 4096] at the
+    offered rate, and small interactive requests (uniform in [1, 64]) at ten
+    times that rate, more requests than one launch per request sustains, so they
+    queue and share batches."""
     from paper_2305_19435_gb300.serving import Budget, NativeServer, poisson_stream
     idx = {}
     for d_c in (16, 64):
@@ -298,39 +304,44 @@ def serving_phase(P, torch, data, db_dev, args, B):
         g.free()
     grans = [m for m in P.GRANULARITIES if 64 <= m <= db_dev.shape[1]]
     qh = torch.from_numpy(data["queries"]).pin_memory()
+    loads = {"sizes_1_4096": (4096, args.serve_seconds, args.serve_rate),
+             "sizes_1_64": (64, min(args.serve_seconds, 2.0), args.serve_rate_small)}
     out = {}
-    for mode in ("bf16", "f32"):
-        rng = np.random.default_rng(args.seed)   # same budgets and slices for both paths
-        arrivals = poisson_stream(args.serve_rate, args.serve_seconds, seed=args.seed + 5)
-        srv = NativeServer(idx, streams=3, max_batch=8192, mem_budget=24 << 30).start()
-        reqs = []
-        t0 = time.perf_counter()
-        for (t, n, _) in arrivals:
-            d_c = int(rng.choice([16, 64]))
-            d_s = int(rng.choice(grans))
-            nprobe = int(rng.integers(1, 129))
-            k = int(rng.choice([10, 100]))
-            b = Budget(d_c, d_s, nprobe, k, P.STORE_BF16, 4 * k) if mode == "bf16" else \
-                Budget(d_c, d_s, nprobe, k)
-            lo = int(rng.integers(0, B - n + 1))
-            while time.perf_counter() - t0 < t:
-                time.sleep(2e-4)
-            reqs.append(srv.submit(qh[lo:lo + n], b, index_key=d_c))
-        for r in reqs:
-            r.wait(600)
-        st = srv.stats()
-        srv.stop()
-        errs = sum(1 for r in reqs if r.error is not None)
-        st["errors"] = errs
-        st["offered_qps"] = args.serve_rate
-        out[mode] = st
+    for load, (max_rows, seconds, rate) in loads.items():
+        out[load] = {}
+        for mode in ("bf16", "f32"):
+            rng = np.random.default_rng(args.seed)   # same budgets and slices for both paths
+            arrivals = poisson_stream(rate, seconds, seed=args.seed + 5, max_rows=max_rows)
+            srv = NativeServer(idx, streams=3, max_batch=8192, mem_budget=24 << 30).start()
+            reqs = []
+            t0 = time.perf_counter()
+            for (t, n, _) in arrivals:
+                d_c = int(rng.choice([16, 64]))
+                d_s = int(rng.choice(grans))
+                nprobe = int(rng.integers(1, 129))
+                k = int(rng.choice([10, 100]))
+                b = Budget(d_c, d_s, nprobe, k, P.STORE_BF16, 4 * k) if mode == "bf16" else \
+                    Budget(d_c, d_s, nprobe, k)
+                lo = int(rng.integers(0, B - n + 1))
+                while time.perf_counter() - t0 < t:
+                    time.sleep(2e-4)
+                reqs.append(srv.submit(qh[lo:lo + n], b, index_key=d_c))
+            for r in reqs:
+                r.wait(600)
+            st = srv.stats()
+            srv.stop()
+            st["errors"] = sum(1 for r in reqs if r.error is not None)
+            st["offered_qps"] = rate
+            out[load][mode] = st
     for g in idx.values():
         g.status()
         g.free()
-    return {"workload": f"Poisson arrivals, mean {args.serve_rate:.0f} queries/s for "
-                        f"{args.serve_seconds:.0f} s, request sizes U[1, 4096], budgets d_c in "
+    return {"workload": "Poisson arrivals; budgets d_c in "
                         "{16, 64}, d_s in G within [64, 2048], nprobe U[1, 128], k in {10, 100}; "
-                        "bf16 = BF16 tensor-core scan + FP32 rerank of 4k, f32 = exact FP32 scan",
+                        "bf16 = BF16 tensor-core scan + FP32 rerank of 4k, f32 = exact FP32 "
+                        "scan; the native server packs requests whose budgets share a pass",
+            "loads": {key: f"request sizes U[1, {v[0]}], mean {v[2]:.0f} queries/s for "
+                           f"{v[1]:.0f} s" for key, v in loads.items()},
             **out}
 
 
@@ -923,8 +934,8 @@ def main():
            "serving": serving,
            "scan_hbm_regime": scan_hbm,
            "largest_point": largest,
-           "p50_ms": (serving or {}).get(args.mode, {}).get("p50_ms"),
-           "p99_ms": (serving or {}).get(args.mode, {}).get("p99_ms"),
+           "p50_ms": (serving or {}).get("sizes_1_4096", {}).get(args.mode, {}).get("p50_ms"),
+           "p99_ms": (serving or {}).get("sizes_1_4096", {}).get(args.mode, {}).get("p99_ms"),
            "gpu_build_s": gpu_build_s, "index_layout_s": layout_s, "pairs_per_step": pairs,
            "unique_lists_per_step": int(len(probed)),
            "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "queries/s",

@@ -306,6 +306,32 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
                       int d_s, int nprobe, int k, int storage, int rerank_k, int64_t *out_ids,
                       float *out_dist, int32_t *out_probes, void *cuda_stream);
 
+/* AdANNS-IVF search of a batch whose queries carry their own budgets (Sec. 5
+ * "Compute-aware Elastic Search During Inference": each query picks its
+ * d_s, nprobe and k at run time over one resident index), in one pass of the
+ * search's kernels instead of one call per budget.
+ *   d_s, nprobe, k  HOST int32 arrays of B entries, read before the call
+ *            returns: query i is searched with d_s[i], nprobe[i], k[i] under
+ *            the rules of adanns_search_ivf, and k[i] <= k_max <= 1024.
+ *   storage  ADANNS_STORE_F32 (rerank_k 0, nprobe[i] <= 256): the streaming
+ *            FP32 scan, every query at its own d_s.  ADANNS_STORE_BF16 /
+ *            ADANNS_STORE_FP8E4M3: every d_s[i] must be equal (the
+ *            tensor-core scan tiles share one K extent) and
+ *            k_max <= rerank_k <= 2048, nprobe[i] <= 128; the shortlist is
+ *            the rerank_k best of each query's own probed lists.
+ *   out_ids  int64 [B x k_max], out_dist FP32 [B x k_max] (device): row i
+ *            holds query i's k[i] results, then (-1, +inf) up to k_max.
+ * Row i equals the first k[i] entries of adanns_search_ivf on query i alone
+ * with (d_c, d_s[i], nprobe[i], k_max, storage, rerank_k): for the FP32 tier
+ * that is its exact top-k[i]; for the low-precision tiers the top-k[i] of the
+ * re-scored shortlist.  ADANNS_ERR_ARG / ADANNS_ERR_DIM for a bad entry (its
+ * index in the message); nothing is launched then.
+ */
+int adanns_search_ivf_budgets(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                              const int32_t *d_s, const int32_t *nprobe, const int32_t *k,
+                              int k_max, int storage, int rerank_k, int64_t *out_ids,
+                              float *out_dist, void *cuda_stream);
+
 /* ------------------------------------------------------------------------
  * AdANNS-OPQ on the d_s prefix and the AdANNS-IVFOPQ composite
  * (Sec. 3 "OPQ": M sub-vectors, 2^8 codewords each, m bytes per vector,

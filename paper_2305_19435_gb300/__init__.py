@@ -61,6 +61,7 @@ def lib():
         L.adanns_kmeans_assign.argtypes = [P, i64, i32, i32, i32, P, i32, P, P, P]
         L.adanns_kmeans_update.argtypes = [P, i64, i32, i32, i32, P, i32, P, P]
         L.adanns_search_ivf.argtypes = [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, P, P]
+        L.adanns_search_ivf_budgets.argtypes = [P, P, i64, i32, P, P, P, i32, i32, i32, P, P, P]
         L.adanns_opq_encode.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P]
         L.adanns_pq_update.argtypes = [P, i64, i32, i32, P, P, P]
         L.adanns_procrustes.argtypes = [P, P, i64, i32, P, P]
@@ -435,6 +436,43 @@ def search_ivf(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: 
     _check(lib().adanns_search_ivf(index.handle, _ptr(queries), B, d_c, d_s, nprobe, k, storage,
                                    rerank_k, _ptr(ids), _ptr(dist), _ptr(probes), _stream()))
     return (ids, dist, probes) if return_probes else (ids, dist)
+
+
+def search_ivf_budgets(index: Index, queries: torch.Tensor, d_c: int, d_s, nprobe, k,
+                       k_max: int | None = None, storage: int = STORE_F32, rerank_k: int = 0,
+                       out: tuple | None = None):
+    """AdANNS-IVF search with a budget per query (d_s, nprobe, k: sequences of B
+    ints, or one int for all) -> (ids int64 [B,k_max], dist f32 [B,k_max]); row i
+    holds query i's k[i] results, then (-1, +inf)."""
+    _need(queries, torch.float32, "queries", 2)
+    if queries.shape[1] != index.d:
+        raise ValueError(f"queries must have {index.d} columns")
+    B = queries.shape[0]
+
+    def arr(v, what):
+        a = (ctypes.c_int32 * B)()
+        if isinstance(v, int):
+            for i in range(B):
+                a[i] = v
+        else:
+            v = [int(x) for x in v]
+            if len(v) != B:
+                raise ValueError(f"{what} needs {B} entries")
+            a[:] = v
+        return a
+
+    ds_a, np_a, k_a = arr(d_s, "d_s"), arr(nprobe, "nprobe"), arr(k, "k")
+    if k_max is None:
+        k_max = max(k_a) if B else 1
+    if out is None:
+        ids = torch.empty(B, k_max, dtype=torch.int64, device=queries.device)
+        dist = torch.empty(B, k_max, dtype=torch.float32, device=queries.device)
+    else:
+        ids, dist = out
+    _check(lib().adanns_search_ivf_budgets(index.handle, _ptr(queries), B, d_c, ds_a, np_a, k_a,
+                                           k_max, storage, rerank_k, _ptr(ids), _ptr(dist),
+                                           _stream()))
+    return ids, dist
 
 
 # ---------------------------------------------------------------- OPQ / IVF-OPQ

@@ -500,6 +500,19 @@ int adanns_index_status(const adanns_index *idx, void *cuda_stream) {
   return ADANNS_OK;
 }
 
+}  // extern "C"
+
+namespace adn {
+int64_t stream_scratch_bytes(const adanns_index *idx, int64_t B, int d_c, int d_s, int nprobe,
+                             int k) {
+  const int64_t per_q = max_probe_members(idx, nprobe) * 4 + (int64_t)(pad16(d_c) + pad16(d_s)) * 4 +
+                        (int64_t)k * 8 + (int64_t)nprobe * 40 + 16;
+  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
+  return Bc * per_q + (int64_t)idx->nlist * 64 + (16ll << 20);
+}
+}  // namespace adn
+
+extern "C" {
 int64_t adanns_search_scratch_bytes(const adanns_index *idx, int64_t B, int d_c, int d_s,
                                     int nprobe, int k, int storage, int rerank_k) {
   if (!idx || B < 0 || nprobe < 1 || k < 1) return -1;
@@ -514,12 +527,8 @@ int64_t adanns_search_scratch_bytes(const adanns_index *idx, int64_t B, int d_c,
     const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
     return Bc * per_q + (int64_t)idx->nlist * 64 + (64ll << 20);
   }
-  if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe)) {
-    const int64_t per_q = max_probe_members(idx, nprobe) * 4 + (int64_t)(dcp + dsp) * 4 +
-                          (int64_t)k * 8 + (int64_t)nprobe * 40 + 16;
-    const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
-    return Bc * per_q + (int64_t)idx->nlist * 64 + (16ll << 20);
-  }
+  if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe))
+    return stream_scratch_bytes(idx, B, d_c, d_s, nprobe, k);
   int tq, qt, nsplit;
   fp32_scan_shape(idx, B, d_s, nprobe, k, &tq, &qt, &nsplit);
   const int64_t per_q =
@@ -692,6 +701,72 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
     }
   }
   return ADANNS_OK;
+}
+
+int adanns_search_ivf_budgets(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                              const int32_t *d_s, const int32_t *nprobe, const int32_t *k,
+                              int k_max, int storage, int rerank_k, int64_t *out_ids,
+                              float *out_dist, void *cuda_stream) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  if (B < 0 || B > INT32_MAX) return fail(ADANNS_ERR_ARG, "bad batch size");
+  if (B > 0 && (!queries || !out_ids || !out_dist || !d_s || !nprobe || !k))
+    return fail(ADANNS_ERR_ARG, "NULL argument");
+  if (gran_index(d_c) < 0 || d_c > idx->d_c)
+    return fail(ADANNS_ERR_DIM, "d_c must be an MR granularity <= the index's clustering prefix " +
+                                    std::to_string(idx->d_c));
+  if (k_max < 1 || k_max > 1024) return fail(ADANNS_ERR_ARG, "need 1 <= k_max <= 1024");
+  const bool lowp = storage == ADANNS_STORE_BF16 || storage == ADANNS_STORE_FP8E4M3;
+  if (!lowp && storage != ADANNS_STORE_F32) return fail(ADANNS_ERR_ARG, "unknown storage tier");
+  const int np_cap = lowp ? 128 : 256;
+  int ds_max = 0, np_max = 0, rc;
+  // one staging array: d_s, granularity index, nprobe, k of every query
+  std::vector<int32_t> h((size_t)B * 4);
+  for (int64_t i = 0; i < B; ++i) {
+    const std::string at = " (query " + std::to_string(i) + ")";
+    if ((rc = check_gran(d_s[i], idx->d, "d_s"))) return fail(rc, adanns_last_error() + at);
+    if (nprobe[i] < 1 || nprobe[i] > idx->nlist || nprobe[i] > np_cap)
+      return fail(ADANNS_ERR_ARG, "need 1 <= nprobe <= min(nlist, " + std::to_string(np_cap) +
+                                      ")" + at);
+    if (k[i] < 1 || k[i] > k_max) return fail(ADANNS_ERR_ARG, "need 1 <= k <= k_max" + at);
+    if (lowp && d_s[i] != d_s[0])
+      return fail(ADANNS_ERR_ARG, "the low-precision tiers need one d_s per batch" + at);
+    ds_max = std::max(ds_max, (int)d_s[i]);
+    np_max = std::max(np_max, (int)nprobe[i]);
+    h[(size_t)i] = d_s[i];
+    h[(size_t)(B + i)] = gran_index(d_s[i]);
+    h[(size_t)(2 * B + i)] = nprobe[i];
+    h[(size_t)(3 * B + i)] = k[i];
+  }
+  int which = 0;
+  if (lowp) {
+    which = storage == ADANNS_STORE_BF16 ? 0 : 1;
+    if (!idx->lowp[which]) return fail(ADANNS_ERR_STATE, "the index has no such storage tier");
+    if (idx->metric != ADANNS_METRIC_L2_PREFIXNORM)
+      return fail(ADANNS_ERR_STATE, "low-precision search needs the prefix-normalised metric");
+    if (rerank_k < k_max || rerank_k > 2048)
+      return fail(ADANNS_ERR_ARG, "low-precision search needs k_max <= rerank_k <= 2048");
+  } else if (rerank_k != 0) {
+    return fail(ADANNS_ERR_ARG, "rerank_k must be 0 for the FP32 scan");
+  }
+  if (B == 0) return ADANNS_OK;
+  cudaStream_t st = S(cuda_stream);
+  Scratch s(st);
+  int32_t *dq;
+  if ((rc = s.get(&dq, h.size()))) return rc;
+  // pageable source: staged by the copy call itself, so h may go when it returns
+  ADN_CUDA(cudaMemcpyAsync(dq, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  QueryBudgets qb;
+  qb.ds = dq;
+  qb.gi = dq + B;
+  qb.np = dq + 2 * B;
+  qb.k = dq + 3 * B;
+  if (lowp) {
+    qb.ds = qb.gi = nullptr;  // one d_s for the batch
+    return search_mixed(idx, queries, B, d_c, ds_max, np_max, k_max, which, rerank_k, out_ids,
+                        out_dist, nullptr, st, &qb);
+  }
+  return search_f32_stream(idx, queries, B, d_c, ds_max, np_max, k_max, out_ids, out_dist, nullptr,
+                           st, &qb);
 }
 
 }  // extern "C"

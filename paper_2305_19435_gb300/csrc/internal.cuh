@@ -14,6 +14,35 @@ namespace adn {
 
 constexpr uint64_t KEY_MAX = ~0ull;  // empty slot / padding key
 
+// A probe key (coarse distance bits << 32 | list) of a masked slot: a query
+// with its own, smaller nprobe than the batch's keeps its first nprobe slots
+// and the rest hold PROBE_NONE, which every consumer reads as an empty list.
+constexpr uint64_t PROBE_NONE = ~0ull;
+__host__ __device__ inline int probe_list(uint64_t key) {
+  return key == PROBE_NONE ? -1 : (int)(uint32_t)(key & 0xffffffffu);
+}
+
+// Per-query budgets of one batch (Sec. 5, compute-aware elastic search):
+// device arrays of one entry per query, or null where the batch shares the
+// call's value.  ds: scan prefix d_s; gi: its granularity index; np: nprobe;
+// k: neighbours kept (a prefix of the batch's k results).
+struct QueryBudgets {
+  const int32_t *ds = nullptr, *gi = nullptr, *np = nullptr, *k = nullptr;
+  QueryBudgets at(int64_t b0) const {
+    QueryBudgets r;
+    r.ds = ds ? ds + b0 : nullptr;
+    r.gi = gi ? gi + b0 : nullptr;
+    r.np = np ? np + b0 : nullptr;
+    r.k = k ? k + b0 : nullptr;
+    return r;
+  }
+};
+// slots at or past np[q] of each query's nprobe probe keys -> PROBE_NONE
+int launch_mask_probes(uint64_t *ckeys, int64_t B, int nprobe, const int32_t *np, cudaStream_t st);
+// entries at or past k[q] of each row of k_max results -> (-1, +inf)
+int launch_pad_rows(int64_t *ids, float *dist, int64_t B, int k_max, const int32_t *k,
+                    cudaStream_t st);
+
 // bits of an index's sticky device error word (adanns_index_status); the low
 // byte is the tensor-core pipeline stage whose wait timed out
 constexpr int ADANNS_DEVERR_RERANK = 0x100;  // rerank pair outside its member chunk
@@ -153,8 +182,10 @@ int scan_query_tile(int k, int tq = 0);  // queries per work item
 int tuned_scan_tq(int k, int d_s, double queries_per_list);
 
 // ---------------------------------------------------------------- helpers
+// dims_b_q (or null): a per-query dims_b for the second copy
 int launch_prep_queries(const float *q, int64_t B, int ld, int dims_a, int dims_b, int metric,
-                        float *qa, int lda, float *qb, int ldb, cudaStream_t st);
+                        float *qa, int lda, float *qb, int ldb, cudaStream_t st,
+                        const int32_t *dims_b_q = nullptr);
 int launch_keys_to_result(const uint64_t *keys, int64_t rows, int k, int64_t *ids, int32_t *ids32,
                           float *dist, cudaStream_t st);
 int launch_invert_probes(const uint64_t *ckeys, int64_t B, int nprobe, int nlist, int qt,
@@ -268,9 +299,13 @@ int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int
 int launch_scan_i32(const int32_t *v, int64_t n, int32_t *out, cudaStream_t st);
 int launch_scan64(const int64_t *in, int64_t n, int64_t *out, int64_t *total, cudaStream_t st);
 bool fp32_stream_enabled(double queries_per_list, int nprobe);
+// scratch bytes of search_f32_stream for these arguments (host arithmetic)
+int64_t stream_scratch_bytes(const adanns_index *idx, int64_t B, int d_c, int d_s, int nprobe,
+                             int k);
+// qb (or null): per-query d_s / nprobe / k at most the call's d_s, nprobe, k
 int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
                       int nprobe, int k, int64_t *out_ids, float *out_dist, int32_t *out_probes,
-                      cudaStream_t st);
+                      cudaStream_t st, const QueryBudgets *qb = nullptr);
 int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, int kk, int k, const float *qrho, float rmax,
                     float e_rest, int prune, int64_t B, int64_t *out, cudaStream_t st);
@@ -320,9 +355,10 @@ inline int rerank_chunk_index(int mc) { return mc >= 64 ? 0 : mc >= 32 ? 1 : mc 
 // the rerank work order and chunk tables of an index (host copies of the
 // centroids and list offsets; synchronises the stream)
 int build_rerank_order(adanns_index *x, cudaStream_t st);
+// qb (or null): per-query nprobe / k at most the call's (d_s is the batch's)
 int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
                  int nprobe, int k, int which, int kk, int64_t *out_ids, float *out_dist,
-                 int32_t *out_probes, cudaStream_t st);
+                 int32_t *out_probes, cudaStream_t st, const QueryBudgets *qb = nullptr);
 
 }  // namespace adn
 

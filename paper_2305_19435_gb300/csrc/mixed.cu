@@ -228,8 +228,8 @@ __global__ void cand_count_kernel(const uint64_t *__restrict__ ckeys, int64_t B,
   if (q >= B) return;
   int64_t t = 0;
   for (int s = 0; s < nprobe; ++s) {
-    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
-    t += (list_off[l + 1] - list_off[l] + 7) & ~7ll;
+    const int l = probe_list(ckeys[q * nprobe + s]);
+    if (l >= 0) t += (list_off[l + 1] - list_off[l] + 7) & ~7ll;
   }
   qtot[q] = t;
 }
@@ -287,9 +287,9 @@ __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, 
   if (q >= B) return;
   int64_t t = qbase[q];
   for (int s = 0; s < nprobe; ++s) {
-    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
+    const int l = probe_list(ckeys[q * nprobe + s]);
     pbase[q * nprobe + s] = t;
-    t += (list_off[l + 1] - list_off[l] + 7) & ~7ll;
+    if (l >= 0) t += (list_off[l + 1] - list_off[l] + 7) & ~7ll;
   }
 }
 
@@ -351,7 +351,7 @@ static bool scan_filter_enabled(const adanns_index *idx) {
 
 int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
                  int nprobe, int k, int which, int kk, int64_t *out_ids, float *out_dist,
-                 int32_t *out_probes, cudaStream_t st) {
+                 int32_t *out_probes, cudaStream_t st, const QueryBudgets *qb) {
   const int fp8 = which == 1;
   const int epb = fp8 ? 128 : 64;
   const int nkb = (d_s + epb - 1) / epb;
@@ -452,6 +452,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     {
       StageTimer t(ST_COARSE, st);
       if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, counter, st))) return rc;
+      if (qb && (rc = launch_mask_probes(ckeys, nb, nprobe, qb->at(b0).np, st))) return rc;
     }
     int32_t *probes = out_probes ? out_probes + b0 * nprobe : nullptr;
     {
@@ -510,6 +511,9 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
       StageTimer t(ST_RERANK, st);
       if ((rc = launch_rerank_lists(cids, kk, nb, qs, dsp, d_s, idx, mscale, k, out_ids + b0 * k,
                                     out_dist + b0 * k, st)))
+        return rc;
+      if (qb && (rc = launch_pad_rows(out_ids + b0 * k, out_dist + b0 * k, nb, k, qb->at(b0).k,
+                                      st)))
         return rc;
     }
   }

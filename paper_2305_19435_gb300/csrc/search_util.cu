@@ -173,11 +173,13 @@ int num_sms() {
 // of squares, lane-strided then a shuffle tree) and the two scaled, zero
 // padded copies q * nu_a (rows of lda) and q * nu_b (rows of ldb).
 __global__ void prep_queries_kernel(const float *__restrict__ q, int64_t B, int ld, int da,
-                                    int db, int metric, float *__restrict__ qa, int lda,
-                                    float *__restrict__ qb, int ldb) {
+                                    int db0, int metric, float *__restrict__ qa, int lda,
+                                    float *__restrict__ qb, int ldb,
+                                    const int32_t *__restrict__ dbq) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= B) return;
+  const int db = dbq ? dbq[row] : db0;
   const float *src = q + row * ld;
   float sa = 0.f, sb = 0.f;
   const int dm = max(da, db);
@@ -203,11 +205,11 @@ __global__ void prep_queries_kernel(const float *__restrict__ q, int64_t B, int 
 }
 
 int launch_prep_queries(const float *q, int64_t B, int ld, int da, int db, int metric, float *qa,
-                        int lda, float *qb, int ldb, cudaStream_t st) {
+                        int lda, float *qb, int ldb, cudaStream_t st, const int32_t *dbq) {
   if (B <= 0) return ADANNS_OK;
   const int wpb = 8;
-  prep_queries_kernel<<<(unsigned)((B + wpb - 1) / wpb), wpb * 32, 0, st>>>(q, B, ld, da, db,
-                                                                           metric, qa, lda, qb, ldb);
+  prep_queries_kernel<<<(unsigned)((B + wpb - 1) / wpb), wpb * 32, 0, st>>>(
+      q, B, ld, da, db, metric, qa, lda, qb, ldb, dbq);
   ADN_LAUNCH("prep_queries_kernel");
   return ADANNS_OK;
 }
@@ -247,9 +249,9 @@ __global__ void probe_count_kernel(const uint64_t *__restrict__ ckeys, int64_t n
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t e = slot_pair(i, nprobe, s0, ns);
-  const int l = (int)(uint32_t)(ckeys[e] & 0xffffffffu);
-  atomicAdd(&lcnt[l], 1);
+  const int l = probe_list(ckeys[e]);
   if (probes_out) probes_out[e] = l;
+  if (l >= 0) atomicAdd(&lcnt[l], 1);
 }
 
 // single CTA: lbeg = exclusive scan of lcnt; per-list tile counts and their scan
@@ -293,7 +295,8 @@ __global__ void probe_fill_kernel(const uint64_t *__restrict__ ckeys, int64_t n,
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t e = slot_pair(i, nprobe, s0, ns);
-  const int l = (int)(uint32_t)(ckeys[e] & 0xffffffffu);
+  const int l = probe_list(ckeys[e]);
+  if (l < 0) return;  // a masked slot has no pair
   const int pos = lbeg[l] + atomicAdd(&lfill[l], 1);
   pair_q[pos] = (int32_t)(e / nprobe);
   pair_out[pos] = (int32_t)e;
@@ -344,6 +347,42 @@ int launch_invert_probe_slots(const uint64_t *ckeys, int64_t B, int nprobe, int 
   probe_tiles_kernel<<<(nlist + 255) / 256, 256, 0, st>>>(lcnt, lbeg, tbeg, nlist, qt, tile_list,
                                                           tile_beg, tile_cnt);
   ADN_LAUNCH("probe_tiles_kernel");
+  return ADANNS_OK;
+}
+
+// ---------------------------------------------------------------- per-query budgets
+__global__ void mask_probes_kernel(uint64_t *__restrict__ ckeys, int64_t n, int nprobe,
+                                   const int32_t *__restrict__ np) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  if ((int)(e % nprobe) >= np[e / nprobe]) ckeys[e] = PROBE_NONE;
+}
+
+int launch_mask_probes(uint64_t *ckeys, int64_t B, int nprobe, const int32_t *np,
+                       cudaStream_t st) {
+  const int64_t n = B * nprobe;
+  if (n <= 0 || !np) return ADANNS_OK;
+  mask_probes_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ckeys, n, nprobe, np);
+  ADN_LAUNCH("mask_probes_kernel");
+  return ADANNS_OK;
+}
+
+__global__ void pad_rows_kernel(int64_t *__restrict__ ids, float *__restrict__ dist, int64_t n,
+                                int k_max, const int32_t *__restrict__ k) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if ((int)(i % k_max) >= k[i / k_max]) {
+    ids[i] = -1;
+    dist[i] = __int_as_float(0x7f800000);
+  }
+}
+
+int launch_pad_rows(int64_t *ids, float *dist, int64_t B, int k_max, const int32_t *k,
+                    cudaStream_t st) {
+  const int64_t n = B * k_max;
+  if (n <= 0 || !k) return ADANNS_OK;
+  pad_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ids, dist, n, k_max, k);
+  ADN_LAUNCH("pad_rows_kernel");
   return ADANNS_OK;
 }
 

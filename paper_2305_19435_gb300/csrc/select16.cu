@@ -144,9 +144,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
     const int sl = lane * 4 + j;
     ln[j] = 0;
     if (sl < nprobe) {
-      const int l = (int)(uint32_t)(ckeys[q * nprobe + sl] & 0xffffffffu);
+      const int l = probe_list(ckeys[q * nprobe + sl]);
       s.lid[sl] = l;
-      ln[j] = (int)(list_off[l + 1] - list_off[l]);
+      ln[j] = l >= 0 ? (int)(list_off[l + 1] - list_off[l]) : 0;
       s.nl[sl] = ln[j];
     }
     pl[j] = (ln[j] + 7) & ~7;
@@ -360,9 +360,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) select_surv_kernel(
     sc[j] = 0;
     if (sl < nprobe) {
       const int64_t p = q * nprobe + sl;
-      const int l = (int)(uint32_t)(ckeys[p] & 0xffffffffu);
+      const int l = probe_list(ckeys[p]);
       s.lid[sl] = l;
-      ln[j] = (int)(list_off[l + 1] - list_off[l]);
+      ln[j] = l >= 0 ? (int)(list_off[l + 1] - list_off[l]) : 0;
       s.nl[sl] = ln[j];
       sc[j] = rcnt[p];
       v.pb[sl] = pbase[p];

@@ -94,9 +94,9 @@ __global__ void __launch_bounds__(S32_THREADS) select32_kernel(
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
   for (int s = tid; s < nprobe; s += S32_THREADS) {
-    const int l = (int)(uint32_t)(ckeys[q * nprobe + s] & 0xffffffffu);
-    s_off[s] = list_off[l];
-    s_nl[s] = (int)(list_off[l + 1] - list_off[l]);
+    const int l = probe_list(ckeys[q * nprobe + s]);
+    s_off[s] = l >= 0 ? list_off[l] : 0;
+    s_nl[s] = l >= 0 ? (int)(list_off[l + 1] - list_off[l]) : 0;
   }
   __syncthreads();
   if (tid == 0) {

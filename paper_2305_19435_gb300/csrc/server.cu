@@ -5,8 +5,9 @@
 //
 // Requests are host query batches submitted at any time.  A worker thread
 // keeps them in arrival order and, whenever one of the server's CUDA streams
-// is free, packs the oldest request with later requests of the same index and
-// budget into one batch of at most max_batch rows, admits the batch only if
+// is free, packs the oldest request with later requests of the same index whose
+// budgets can share one pass of the search (below) into one batch of at most
+// max_batch rows, admits the batch only if
 // its scratch estimate fits the memory budget next to the batches in flight
 // (a batch is always admitted when nothing is in flight), and launches it on
 // that stream: the rows are staged in pinned memory, copied to the device,
@@ -14,6 +15,12 @@
 // different streams overlap on the device; the worker polls their events and
 // hands each request its rows.  Callers collect results with
 // adanns_server_poll.
+//
+// Budgets that share a pass (adanns_search_ivf_budgets): with the FP32 tier,
+// any d_s, nprobe (<= 256) and k at one d_c; with a low-precision tier, any
+// nprobe and k at one d_c, d_s and rerank_k.  A batch of one budget runs the
+// plain search call, a mixed one the per-query-budget call; IVF-OPQ requests
+// batch with identical budgets only.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -80,6 +87,7 @@ struct Lane {
   bool busy = false;
   std::vector<std::shared_ptr<Request>> reqs;
   int64_t bytes = 0;
+  int kstride = 0;  // result columns per row of the batch (its largest k)
   Buf qh{nullptr, 0, true}, ih{nullptr, 0, true}, dh{nullptr, 0, true};
   Buf qd, id, dd;
 };
@@ -87,6 +95,16 @@ struct Lane {
 bool same_budget(const adanns_budget &a, const adanns_budget &b) {
   return a.method == b.method && a.d_c == b.d_c && a.d_s == b.d_s && a.nprobe == b.nprobe &&
          a.k == b.k && a.storage == b.storage && a.rerank_k == b.rerank_k;
+}
+
+// whether requests with budgets a and b can run in one pass of the search
+bool shareable(const adanns_budget &a, const adanns_budget &b) {
+  if (same_budget(a, b)) return true;
+  if (a.method != ADANNS_METHOD_IVF || b.method != ADANNS_METHOD_IVF || a.d_c != b.d_c ||
+      a.storage != b.storage || a.rerank_k != b.rerank_k)
+    return false;
+  if (a.storage == ADANNS_STORE_F32) return a.nprobe <= 256 && b.nprobe <= 256;
+  return a.d_s == b.d_s;
 }
 
 }  // namespace
@@ -128,9 +146,13 @@ void adanns_server::finish(Lane &L) {
       r->status = ADANNS_ERR_CUDA;
       r->msg = std::string("batch failed: ") + cudaGetErrorString(e);
     } else {
-      const int k = r->b.k;
-      r->ids.assign((const int64_t *)L.ih.p + off * k, (const int64_t *)L.ih.p + (off + r->n) * k);
-      r->dist.assign((const float *)L.dh.p + off * k, (const float *)L.dh.p + (off + r->n) * k);
+      const int k = r->b.k, ks = L.kstride;  // the request's first k of each row
+      r->ids.resize((size_t)(r->n * k));
+      r->dist.resize((size_t)(r->n * k));
+      for (int64_t i = 0; i < r->n; ++i) {
+        memcpy(r->ids.data() + i * k, (const int64_t *)L.ih.p + (off + i) * ks, sizeof(int64_t) * k);
+        memcpy(r->dist.data() + i * k, (const float *)L.dh.p + (off + i) * ks, sizeof(float) * k);
+      }
       r->status = ADANNS_OK;
       lat_ms.push_back(t - r->t_arrive);
       queries += r->n;
@@ -156,7 +178,7 @@ bool adanns_server::launch_one(Lane &L) {
     const auto head = pending.front();
     std::deque<std::shared_ptr<Request>> keep;
     for (auto &r : pending) {
-      if (r->slot == head->slot && same_budget(r->b, head->b) &&
+      if (r->slot == head->slot && shareable(r->b, head->b) &&
           (batch.empty() || rows + r->n <= max_batch)) {
         batch.push_back(r);
         rows += r->n;
@@ -165,13 +187,23 @@ bool adanns_server::launch_one(Lane &L) {
       }
     }
     const adanns_index *idx = indices[(size_t)head->slot];
-    const adanns_budget &b = head->b;
-    bytes = b.method == ADANNS_METHOD_IVFOPQ
-                ? rows * (int64_t)(b.nprobe * 64 + b.k * 12 + idx->d * 4) + (64ll << 20)
-                : adanns_search_scratch_bytes(idx, rows, b.d_c, b.d_s, b.nprobe, b.k, b.storage,
-                                              b.rerank_k);
+    adanns_budget b = head->b;  // the batch's largest d_s, nprobe and k
+    bool mixed = false;
+    for (auto &r : batch) {
+      mixed = mixed || !same_budget(r->b, b);
+      b.d_s = std::max(b.d_s, r->b.d_s);
+      b.nprobe = std::max(b.nprobe, r->b.nprobe);
+      b.k = std::max(b.k, r->b.k);
+    }
+    if (b.method == ADANNS_METHOD_IVFOPQ)
+      bytes = rows * (int64_t)(b.nprobe * 64 + b.k * 12 + idx->d * 4) + (64ll << 20);
+    else if (mixed && b.storage == ADANNS_STORE_F32)
+      bytes = stream_scratch_bytes(idx, rows, b.d_c, b.d_s, b.nprobe, b.k);
+    else
+      bytes = adanns_search_scratch_bytes(idx, rows, b.d_c, b.d_s, b.nprobe, b.k, b.storage,
+                                          b.rerank_k);
     if (bytes < 0) bytes = 0;
-    bytes += rows * (int64_t)(idx->d * 4 + b.k * 12);
+    bytes += rows * (int64_t)(idx->d * 4 + b.k * 12 + (mixed ? 16 : 0));
     const bool any_busy = std::any_of(lanes.begin(), lanes.end(),
                                       [](const std::unique_ptr<Lane> &x) { return x->busy; });
     if (any_busy && inflight + bytes > mem_budget) return false;  // wait for memory
@@ -182,7 +214,12 @@ bool adanns_server::launch_one(Lane &L) {
     batch_requests += (int64_t)batch.size();
   }
   const adanns_index *idx = indices[(size_t)batch[0]->slot];
-  const adanns_budget b = batch[0]->b;
+  adanns_budget b = batch[0]->b;
+  bool mixed = false;
+  for (auto &r : batch) {
+    mixed = mixed || !same_budget(r->b, b);
+    b.k = std::max(b.k, r->b.k);
+  }
   const int d = idx->d, k = b.k;
   int rc = ADANNS_OK;
   std::string msg;
@@ -200,6 +237,18 @@ bool adanns_server::launch_one(Lane &L) {
                                     cudaMemcpyHostToDevice, L.st);
     if (e != cudaSuccess) {
       rc = cuda_fail(e, "server query copy");
+    } else if (mixed) {
+      std::vector<int32_t> ds((size_t)rows), np((size_t)rows), kq((size_t)rows);
+      int64_t o = 0;
+      for (auto &r : batch)
+        for (int64_t i = 0; i < r->n; ++i, ++o) {
+          ds[(size_t)o] = r->b.d_s;
+          np[(size_t)o] = r->b.nprobe;
+          kq[(size_t)o] = r->b.k;
+        }
+      rc = adanns_search_ivf_budgets(idx, (const float *)L.qd.p, rows, b.d_c, ds.data(), np.data(),
+                                     kq.data(), k, b.storage, b.rerank_k, (int64_t *)L.id.p,
+                                     (float *)L.dd.p, L.st);
     } else if (b.method == ADANNS_METHOD_IVFOPQ) {
       rc = adanns_search_ivfopq(idx, (const float *)L.qd.p, rows, b.d_c, b.nprobe, k, b.rerank_k,
                                 (int64_t *)L.id.p, (float *)L.dd.p, nullptr, L.st);
@@ -232,6 +281,7 @@ bool adanns_server::launch_one(Lane &L) {
   }
   L.reqs = std::move(batch);
   L.bytes = bytes;
+  L.kstride = k;
   L.busy = true;
   return true;
 }

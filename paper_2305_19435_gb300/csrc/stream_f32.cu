@@ -15,6 +15,13 @@
 // ascending), so the distances are bit-identical to it; each one is written
 // as FP32 bits into the query's candidate segment, and select32_kernel then
 // keeps the k best by (distance, id).
+//
+// A batch of queries with their own budgets (d_s, nprobe, k per query) runs
+// as one launch of each kernel: masked probe slots make no pairs, a unit
+// streams its member rows up to the largest d_s of its queries while each
+// query stops accumulating at its own d_s (with its own per-member scale at
+// that prefix), and the selection keeps the batch's largest k, of which a
+// query's own k results are the prefix.
 #include <algorithm>
 
 #include "devutil.cuh"
@@ -34,6 +41,12 @@ struct StreamArgs {
   const float *mscale;  // per-member scale (inverse prefix norm), or null
   const float *qn;      // prepared query rows
   int ldq;
+  // per-query prefixes (or null: every query scans a.dims): d_s of each query
+  // and the index's inverse prefix norms [granularity][N] with each query's
+  // granularity index (null with the raw metric)
+  const int32_t *qds, *qgi;
+  const float *invn;
+  int64_t N;
   const int32_t *tile_list, *tile_beg, *tile_cnt;
   const int *ntiles_dev;
   const int64_t *uoff;  // first work unit of each tile (exclusive scan of its units)
@@ -83,6 +96,114 @@ __device__ __forceinline__ void block_step(float (&acc)[SF_QG], const float4 (&x
       t = fmaf(-sc, x[s].w, q.w);
       acc[j] = fmaf(t, t, acc[j]);
     }
+  }
+}
+
+// The same for a group whose queries stop at their own prefixes: query j
+// takes the block's coordinates below ds[j] (multiples of 4), scaled by its
+// own sc[j].
+__device__ __forceinline__ void block_step_var(float (&acc)[SF_QG], const float4 (&x)[4],
+                                               const float (&sc)[SF_QG],
+                                               const float *const *qrow, const int (&ds)[SF_QG],
+                                               int cnt, int off) {
+#pragma unroll
+  for (int j = 0; j < SF_QG; ++j) {
+    if (j >= cnt) break;
+    const int nd4 = min(4, (ds[j] - off) >> 2);
+    const float *qb = qrow[j] + off;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (s >= nd4) break;
+      const float4 q = ldg4(qb + 4 * s);
+      float t;
+      t = fmaf(-sc[j], x[s].x, q.x);
+      acc[j] = fmaf(t, t, acc[j]);
+      t = fmaf(-sc[j], x[s].y, q.y);
+      acc[j] = fmaf(t, t, acc[j]);
+      t = fmaf(-sc[j], x[s].z, q.z);
+      acc[j] = fmaf(t, t, acc[j]);
+      t = fmaf(-sc[j], x[s].w, q.w);
+      acc[j] = fmaf(t, t, acc[j]);
+    }
+  }
+}
+
+// Per-query prefixes: units as in dist_f32_kernel; a unit's member rows are
+// streamed to the largest d_s of its queries.
+__global__ void __launch_bounds__(SF_THREADS, 4) dist_f32_var_kernel(StreamArgs a) {
+  __shared__ int s_item;
+  __shared__ const float *s_qp[SF_QG];
+  __shared__ const float *s_sp[SF_QG];  // each query's per-member scales (or null)
+  __shared__ int64_t s_pb[SF_QG];
+  __shared__ int s_ds[SF_QG];
+  const int tid = threadIdx.x;
+  const int64_t nunits = *a.nunits;
+  const int ntiles = *a.ntiles_dev;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= nunits) break;
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.uoff[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int tile = lo;
+    const int list = a.tile_list[tile], beg = a.tile_beg[tile], tcnt = a.tile_cnt[tile];
+    const int ngrp = (tcnt + SF_QG - 1) / SF_QG;
+    const int u = (int)(item - a.uoff[tile]);
+    const int chunk = u / ngrp, g = u - chunk * ngrp;
+    const int q0 = g * SF_QG, cnt = min(SF_QG, tcnt - q0);
+    if (tid < cnt) {
+      const int q = a.pair_q[beg + q0 + tid];
+      s_qp[tid] = a.qn + (int64_t)q * a.ldq;
+      s_pb[tid] = a.pbase[a.pair_out[beg + q0 + tid]];
+      s_ds[tid] = a.qds[q];
+      s_sp[tid] = a.invn ? a.invn + (int64_t)a.qgi[q] * a.N : nullptr;
+    }
+    __syncthreads();
+    const int64_t moff = a.list_off[list];
+    const int nl = (int)(a.list_off[list + 1] - moff), npad = (nl + 7) & ~7;
+    const int m = chunk * SF_THREADS + tid;
+    if (m < nl) {
+      int ds[SF_QG], dmax = 0;
+      float sc[SF_QG];
+#pragma unroll
+      for (int j = 0; j < SF_QG; ++j) {
+        ds[j] = j < cnt ? s_ds[j] : 0;
+        sc[j] = j < cnt && s_sp[j] ? __ldg(s_sp[j] + moff + m) : 1.f;
+        dmax = max(dmax, ds[j]);
+      }
+      const int nblk = (dmax + 15) >> 4;
+      const float *xr = a.xpm + moff * (int64_t)a.d_pad + (int64_t)m * 16;
+      const int64_t bstride = (int64_t)16 * nl;
+      const float *const *qrow = s_qp;
+      float acc[SF_QG];
+#pragma unroll
+      for (int j = 0; j < SF_QG; ++j) acc[j] = 0.f;
+      float4 xa[4], xb[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) xa[s] = ldg4(xr + 4 * s);
+      int b = 0;
+      for (; b + 2 <= nblk; b += 2) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) xb[s] = ldg4(xr + (b + 1) * bstride + 4 * s);
+        block_step_var(acc, xa, sc, qrow, ds, cnt, 16 * b);
+        if (b + 2 < nblk) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) xa[s] = ldg4(xr + (b + 2) * bstride + 4 * s);
+        }
+        block_step_var(acc, xb, sc, qrow, ds, cnt, 16 * (b + 1));
+      }
+      if (b < nblk) block_step_var(acc, xa, sc, qrow, ds, cnt, 16 * b);
+#pragma unroll
+      for (int j = 0; j < SF_QG; ++j)
+        if (j < cnt) a.cand[s_pb[j] + m] = __float_as_uint(acc[j]);
+    } else if (m < npad) {
+      for (int j = 0; j < cnt; ++j) a.cand[s_pb[j] + m] = 0xFFFFFFFFu;
+    }
+    __syncthreads();
   }
 }
 
@@ -170,7 +291,7 @@ bool fp32_stream_enabled(double queries_per_list, int nprobe) {
 
 int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
                       int nprobe, int k, int64_t *out_ids, float *out_dist, int32_t *out_probes,
-                      cudaStream_t st) {
+                      cudaStream_t st, const QueryBudgets *qb) {
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
   const int64_t seg_q = max_probe_members(idx, nprobe);
@@ -202,16 +323,18 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
                             : nullptr;
   for (int64_t b0 = 0; b0 < B; b0 += Bc) {
     const int64_t nb = std::min(Bc, B - b0);
+    const QueryBudgets bq = qb ? qb->at(b0) : QueryBudgets{};
     {
       StageTimer t(ST_PREP, st);
       if ((rc = launch_prep_queries(queries + b0 * idx->d, nb, idx->d, d_c, d_s, idx->metric, qc,
-                                    dcp, qs, dsp, st)))
+                                    dcp, qs, dsp, st, bq.ds)))
         return rc;
     }
     ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
     {
       StageTimer t(ST_COARSE, st);
       if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, counter, st))) return rc;
+      if ((rc = launch_mask_probes(ckeys, nb, nprobe, bq.np, st))) return rc;
     }
     {
       StageTimer t(ST_INVERT, st);
@@ -247,15 +370,20 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
       a.pbase = pbase;
       a.cand = cand;
       a.counter = counter + 1;
+      a.qds = bq.ds;
+      a.qgi = bq.gi;
+      a.invn = idx->metric == ADANNS_METRIC_L2_PREFIXNORM ? idx->invn : nullptr;
+      a.N = idx->N;
+      auto kern = bq.ds ? dist_f32_var_kernel : dist_f32_kernel;
       int per_sm = 1;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dist_f32_kernel, SF_THREADS, 0) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SF_THREADS, 0) !=
               cudaSuccess ||
           per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
       }
-      dist_f32_kernel<<<num_sms() * per_sm, SF_THREADS, 0, st>>>(a);
-      ADN_LAUNCH("dist_f32_kernel");
+      kern<<<num_sms() * per_sm, SF_THREADS, 0, st>>>(a);
+      ADN_LAUNCH(bq.ds ? "dist_f32_var_kernel" : "dist_f32_kernel");
     }
     {
       StageTimer t(ST_MERGE, st);
@@ -264,6 +392,7 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
         return rc;
       if ((rc = launch_final_topk(keys, k, nb, k, out_ids + b0 * k, out_dist + b0 * k, st)))
         return rc;
+      if ((rc = launch_pad_rows(out_ids + b0 * k, out_dist + b0 * k, nb, k, bq.k, st))) return rc;
     }
   }
   return ADANNS_OK;

@@ -322,9 +322,11 @@ class NativeRequest:
 
 class NativeServer:
     """Continuous batching done by the library (adanns_server_*): the same
-    scheduling as Server (arrival order, same-budget packing up to max_batch
-    rows, memory admission, one batch per CUDA stream in flight) in a native
-    worker thread.  Queries are host arrays or CPU tensors."""
+    scheduling as Server (arrival order, memory admission, one batch per CUDA
+    stream in flight) in a native worker thread, and it also packs requests
+    whose budgets differ but can share one pass (adanns_search_ivf_budgets:
+    FP32 requests of one index and d_c; low-precision ones of one d_c, d_s and
+    shortlist) up to max_batch rows.  Queries are host arrays or CPU tensors."""
 
     def __init__(self, indexes: dict, streams: int = 2, max_batch: int = 8192,
                  mem_budget: int = 16 << 30):

@@ -117,6 +117,49 @@ def test_native_server_same_alone_and_in_the_mix(setup):
         g.status()
 
 
+def test_native_server_packs_mixed_budgets(setup):
+    """Requests of one index with different d_s / nprobe / k (FP32 tier) and
+    with different nprobe / k at one d_s (BF16 tier) share batches: a burst
+    queued behind a long request is served in a few launches of the
+    per-query-budget search, and every request equals the same rows searched
+    alone, bit for bit."""
+    P, data, idx = setup
+    from paper_2305_19435_gb300.serving import Budget, NativeServer
+    rng = np.random.default_rng(13)
+    q = data["queries"]
+    srv = NativeServer(idx, streams=1, max_batch=2048, mem_budget=8 << 30)
+    reqs = [(srv.submit(q[:1500], Budget(64, 256, 48, 100), index_key=64),
+             Budget(64, 256, 48, 100), 0, 1500)]
+    for i in range(24):
+        n = int(rng.integers(1, 60))
+        lo = int(rng.integers(0, len(q) - n))
+        if i % 2:
+            b = Budget(64, int(rng.choice([64, 128, 192, 256])), int(rng.integers(1, 30)),
+                       int(rng.choice([1, 10, 100])))
+        else:
+            b = Budget(16, 128, int(rng.integers(1, 30)), int(rng.choice([5, 10])),
+                       P.STORE_BF16, 40)
+        reqs.append((srv.submit(q[lo:lo + n], b, index_key=b.d_c), b, lo, n))
+    for r, _, _, _ in reqs:
+        assert r.wait(120)
+    st = srv.stats()
+    srv.stop()
+    assert st["requests"] == 25
+    assert st["batches"] <= 6, st      # the burst shares launches across budgets
+    for r, b, lo, n in reqs:
+        assert r.error is None, r.error
+        qq = torch.from_numpy(np.ascontiguousarray(q[lo:lo + n])).cuda()
+        # BF16: the batch's shortlist is pruned against its largest k, which keeps
+        # a superset of what the request's own k keeps (certified pruning)
+        ids, dist = P.search_ivf(idx[b.d_c], qq, b.d_c, b.d_s, b.nprobe, b.k, storage=b.storage,
+                                 rerank_k=b.rerank_k)
+        assert np.array_equal(r.ids, ids.cpu().numpy())
+        assert np.array_equal(r.dist.view(np.int32),
+                              np.ascontiguousarray(dist.cpu().numpy()).view(np.int32))
+    for g in idx.values():
+        g.status()
+
+
 def test_native_server_rejects_bad_requests(setup):
     P, data, idx = setup
     from paper_2305_19435_gb300.serving import Budget, NativeServer
