@@ -503,6 +503,101 @@ int adanns_index_status(const adanns_index *idx, void *cuda_stream) {
 }  // extern "C"
 
 namespace adn {
+int search_f32_tiled(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
+                     int nprobe, int k, int64_t *out_ids, float *out_dist, int32_t *out_probes,
+                     cudaStream_t st, const QueryBudgets *qb, const int32_t *rows) {
+  int rc;
+  const int nlist = idx->nlist;
+  const int dcp = pad16(d_c), dsp = pad16(d_s);
+  int tq, qt, nsplit;
+  fp32_scan_shape(idx, B, d_s, nprobe, k, &tq, &qt, &nsplit);
+  // slice the batch so that the per-(query, probe) partial results stay ~2 GiB
+  const int64_t per_q =
+      (int64_t)nprobe * nsplit * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
+  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (2ll << 30) / per_q));
+  const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
+  Scratch s(st);
+  float *qc, *qs;
+  uint64_t *ckeys, *pkeys;
+  int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
+  int *ntiles, *counter;
+  if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
+      (rc = s.get(&ckeys, (size_t)Bc * nprobe)) || (rc = s.get(&pkeys, (size_t)Bc * nprobe * nsplit * k)) ||
+      (rc = s.get(&lcnt, nlist)) || (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) ||
+      (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
+      (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
+      (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) ||
+      (rc = s.get(&counter, 2)))
+    return rc;
+  const float *mscale = idx->metric == ADANNS_METRIC_L2_PREFIXNORM
+                            ? idx->invn + (int64_t)gran_index(d_s) * idx->N
+                            : nullptr;
+  for (int64_t b0 = 0; b0 < B; b0 += Bc) {
+    const int64_t nb = std::min(Bc, B - b0);
+    const QueryBudgets bq = qb ? qb->at(b0) : QueryBudgets{};
+    const int32_t *rws = rows ? rows + b0 : nullptr;
+    {
+      StageTimer t(ST_PREP, st);
+      if ((rc = launch_prep_queries(rws ? queries : queries + b0 * idx->d, nb, idx->d, d_c, d_s,
+                                    idx->metric, qc, dcp, qs, dsp, st, nullptr, rws)))
+        return rc;
+    }
+    // cluster mapping: nprobe nearest centroids at d_c
+    ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
+    {
+      StageTimer t(ST_COARSE, st);
+      if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, counter, st))) return rc;
+      if ((rc = launch_mask_probes(ckeys, nb, nprobe, bq.np, st))) return rc;
+    }
+    {
+      StageTimer t(ST_INVERT, st);
+      if ((rc = launch_invert_probes(ckeys, nb, nprobe, nlist, qt, lcnt, lbeg, lfill, tbeg, pair_q,
+                                     pair_out, tl, tb, tc, ntiles,
+                                     out_probes ? out_probes + b0 * nprobe : nullptr, st)))
+        return rc;
+    }
+    // linear scan of the probed lists at d_s
+    ScanArgs l{};
+    l.xpm = idx->xpm;
+    l.d_pad = idx->d_pad;
+    l.dims = d_s;
+    l.list_off = idx->list_off;
+    l.list_ids = idx->list_ids;
+    l.mscale = mscale;
+    l.qn = qs;
+    l.ldq = dsp;
+    l.tile_list = tl;
+    l.tile_beg = tb;
+    l.tile_cnt = tc;
+    l.ntiles_dev = ntiles;
+    l.counter = counter + 1;
+    l.pair_q = pair_q;
+    l.pair_out = pair_out;
+    l.k = k;
+    l.out_keys = pkeys;
+    l.tq = tq;
+    l.nsplit = nsplit;
+    {
+      StageTimer t(ST_SCAN, st);
+      if ((rc = launch_scan_f32(l, st))) return rc;
+    }
+    {
+      StageTimer t(ST_MERGE, st);
+      MergeMask mm;
+      if (bq.np) {
+        mm.ckeys = ckeys;
+        mm.nsplit = nsplit;
+      }
+      mm.kq = bq.k;
+      mm.orow = rws;
+      if ((rc = launch_merge(pkeys, nb, nprobe * nsplit, k, rws ? out_ids : out_ids + b0 * k,
+                             rws ? out_dist : out_dist + b0 * k, st, mm)))
+        return rc;
+    }
+  }
+  return ADANNS_OK;
+}
+
 int64_t stream_scratch_bytes(const adanns_index *idx, int64_t B, int d_c, int d_s, int nprobe,
                              int k) {
   const int64_t per_q = max_probe_members(idx, nprobe) * 4 + (int64_t)(pad16(d_c) + pad16(d_s)) * 4 +
@@ -622,85 +717,8 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
   if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe))
     return search_f32_stream(idx, queries, B, d_c, d_s, nprobe, k, out_ids, out_dist, out_probes,
                              st);
-  const int nlist = idx->nlist;
-  const int dcp = pad16(d_c), dsp = pad16(d_s);
-  int tq, qt, nsplit;
-  fp32_scan_shape(idx, B, d_s, nprobe, k, &tq, &qt, &nsplit);
-  // slice the batch so that the per-(query, probe) partial results stay ~2 GiB
-  const int64_t per_q =
-      (int64_t)nprobe * nsplit * k * 8 + (int64_t)(dcp + dsp) * 4 + nprobe * 24;
-  const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, (2ll << 30) / per_q));
-  const int64_t max_tiles = (Bc * nprobe + qt - 1) / qt + nlist;
-  Scratch s(st);
-  float *qc, *qs;
-  uint64_t *ckeys, *pkeys;
-  int32_t *lcnt, *lbeg, *lfill, *tbeg, *pair_q, *pair_out, *tl, *tb, *tc;
-  int *ntiles, *counter;
-  if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
-      (rc = s.get(&ckeys, (size_t)Bc * nprobe)) || (rc = s.get(&pkeys, (size_t)Bc * nprobe * nsplit * k)) ||
-      (rc = s.get(&lcnt, nlist)) || (rc = s.get(&lbeg, nlist)) || (rc = s.get(&lfill, nlist)) ||
-      (rc = s.get(&tbeg, nlist)) || (rc = s.get(&pair_q, (size_t)Bc * nprobe)) ||
-      (rc = s.get(&pair_out, (size_t)Bc * nprobe)) || (rc = s.get(&tl, max_tiles)) ||
-      (rc = s.get(&tb, max_tiles)) || (rc = s.get(&tc, max_tiles)) || (rc = s.get(&ntiles, 1)) ||
-      (rc = s.get(&counter, 2)))
-    return rc;
-  const float *mscale = idx->metric == ADANNS_METRIC_L2_PREFIXNORM
-                            ? idx->invn + (int64_t)gran_index(d_s) * idx->N
-                            : nullptr;
-  for (int64_t b0 = 0; b0 < B; b0 += Bc) {
-    const int64_t nb = std::min(Bc, B - b0);
-    {
-      StageTimer t(ST_PREP, st);
-      if ((rc = launch_prep_queries(queries + b0 * idx->d, nb, idx->d, d_c, d_s, idx->metric, qc,
-                                    dcp, qs, dsp, st)))
-        return rc;
-    }
-    // cluster mapping: nprobe nearest centroids at d_c
-    ADN_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), st));
-    {
-      StageTimer t(ST_COARSE, st);
-      if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, counter, st))) return rc;
-    }
-    {
-      StageTimer t(ST_INVERT, st);
-      if ((rc = launch_invert_probes(ckeys, nb, nprobe, nlist, qt, lcnt, lbeg, lfill, tbeg, pair_q,
-                                     pair_out, tl, tb, tc, ntiles,
-                                     out_probes ? out_probes + b0 * nprobe : nullptr, st)))
-        return rc;
-    }
-    // linear scan of the probed lists at d_s
-    ScanArgs l{};
-    l.xpm = idx->xpm;
-    l.d_pad = idx->d_pad;
-    l.dims = d_s;
-    l.list_off = idx->list_off;
-    l.list_ids = idx->list_ids;
-    l.mscale = mscale;
-    l.qn = qs;
-    l.ldq = dsp;
-    l.tile_list = tl;
-    l.tile_beg = tb;
-    l.tile_cnt = tc;
-    l.ntiles_dev = ntiles;
-    l.counter = counter + 1;
-    l.pair_q = pair_q;
-    l.pair_out = pair_out;
-    l.k = k;
-    l.out_keys = pkeys;
-    l.tq = tq;
-    l.nsplit = nsplit;
-    {
-      StageTimer t(ST_SCAN, st);
-      if ((rc = launch_scan_f32(l, st))) return rc;
-    }
-    {
-      StageTimer t(ST_MERGE, st);
-      if ((rc = launch_merge(pkeys, nb, nprobe * nsplit, k, out_ids + b0 * k, out_dist + b0 * k,
-                             st)))
-        return rc;
-    }
-  }
-  return ADANNS_OK;
+  return search_f32_tiled(idx, queries, B, d_c, d_s, nprobe, k, out_ids, out_dist, out_probes,
+                          st);
 }
 
 int adanns_search_ivf_budgets(const adanns_index *idx, const float *queries, int64_t B, int d_c,
@@ -719,8 +737,10 @@ int adanns_search_ivf_budgets(const adanns_index *idx, const float *queries, int
   if (!lowp && storage != ADANNS_STORE_F32) return fail(ADANNS_ERR_ARG, "unknown storage tier");
   const int np_cap = lowp ? 128 : 256;
   int ds_max = 0, np_max = 0, rc;
-  // one staging array: d_s, granularity index, nprobe, k of every query
-  std::vector<int32_t> h((size_t)B * 4);
+  int64_t np_sum = 0;
+  // one staging array: d_s, granularity index, nprobe, k of every query, then
+  // the queries in d_s order with their nprobe and k (the tiled FP32 groups)
+  std::vector<int32_t> h((size_t)B * 7);
   for (int64_t i = 0; i < B; ++i) {
     const std::string at = " (query " + std::to_string(i) + ")";
     if ((rc = check_gran(d_s[i], idx->d, "d_s"))) return fail(rc, adanns_last_error() + at);
@@ -732,6 +752,7 @@ int adanns_search_ivf_budgets(const adanns_index *idx, const float *queries, int
       return fail(ADANNS_ERR_ARG, "the low-precision tiers need one d_s per batch" + at);
     ds_max = std::max(ds_max, (int)d_s[i]);
     np_max = std::max(np_max, (int)nprobe[i]);
+    np_sum += nprobe[i];
     h[(size_t)i] = d_s[i];
     h[(size_t)(B + i)] = gran_index(d_s[i]);
     h[(size_t)(2 * B + i)] = nprobe[i];
@@ -749,6 +770,24 @@ int adanns_search_ivf_budgets(const adanns_index *idx, const float *queries, int
     return fail(ADANNS_ERR_ARG, "rerank_k must be 0 for the FP32 scan");
   }
   if (B == 0) return ADANNS_OK;
+  // FP32 with many queries per probed list: the tiled scan, one launch
+  // sequence per distinct d_s over that group of queries (rows in place)
+  const bool tiled = !lowp && !fp32_stream_enabled((double)np_sum / idx->nlist, np_max);
+  std::vector<std::pair<int64_t, int64_t>> grp;  // [begin, end) of each d_s group in the order
+  if (tiled) {
+    std::vector<int32_t> perm((size_t)B);
+    for (int64_t i = 0; i < B; ++i) perm[(size_t)i] = (int32_t)i;
+    std::stable_sort(perm.begin(), perm.end(),
+                     [&](int32_t a, int32_t b) { return d_s[a] < d_s[b]; });
+    for (int64_t i = 0; i < B; ++i) {
+      const int32_t r = perm[(size_t)i];
+      h[(size_t)(4 * B + i)] = r;
+      h[(size_t)(5 * B + i)] = nprobe[r];
+      h[(size_t)(6 * B + i)] = k[r];
+      if (i == 0 || d_s[r] != d_s[perm[(size_t)i - 1]]) grp.push_back({i, i + 1});
+      else grp.back().second = i + 1;
+    }
+  }
   cudaStream_t st = S(cuda_stream);
   Scratch s(st);
   int32_t *dq;
@@ -764,6 +803,22 @@ int adanns_search_ivf_budgets(const adanns_index *idx, const float *queries, int
     qb.ds = qb.gi = nullptr;  // one d_s for the batch
     return search_mixed(idx, queries, B, d_c, ds_max, np_max, k_max, which, rerank_k, out_ids,
                         out_dist, nullptr, st, &qb);
+  }
+  if (tiled) {
+    for (const auto &g : grp) {
+      const int32_t *perm = dq + 4 * B + g.first;
+      int gnp = 0;
+      for (int64_t i = g.first; i < g.second; ++i)
+        gnp = std::max(gnp, (int)h[(size_t)(5 * B + i)]);
+      QueryBudgets gb;
+      gb.np = dq + 5 * B + g.first;
+      gb.k = dq + 6 * B + g.first;
+      if ((rc = search_f32_tiled(idx, queries, g.second - g.first, d_c,
+                                 d_s[h[(size_t)(4 * B + g.first)]], gnp, k_max, out_ids, out_dist,
+                                 nullptr, st, &gb, perm)))
+        return rc;
+    }
+    return ADANNS_OK;
   }
   return search_f32_stream(idx, queries, B, d_c, ds_max, np_max, k_max, out_ids, out_dist, nullptr,
                            st, &qb);

@@ -182,10 +182,11 @@ int scan_query_tile(int k, int tq = 0);  // queries per work item
 int tuned_scan_tq(int k, int d_s, double queries_per_list);
 
 // ---------------------------------------------------------------- helpers
-// dims_b_q (or null): a per-query dims_b for the second copy
+// dims_b_q (or null): a per-query dims_b for the second copy; rows (or null):
+// prepared row i is query row rows[i] of q
 int launch_prep_queries(const float *q, int64_t B, int ld, int dims_a, int dims_b, int metric,
                         float *qa, int lda, float *qb, int ldb, cudaStream_t st,
-                        const int32_t *dims_b_q = nullptr);
+                        const int32_t *dims_b_q = nullptr, const int32_t *rows = nullptr);
 int launch_keys_to_result(const uint64_t *keys, int64_t rows, int k, int64_t *ids, int32_t *ids32,
                           float *dist, cudaStream_t st);
 int launch_invert_probes(const uint64_t *ckeys, int64_t B, int nprobe, int nlist, int qt,
@@ -200,8 +201,15 @@ int launch_invert_probe_slots(const uint64_t *ckeys, int64_t B, int nprobe, int 
                               int32_t *tbeg, int32_t *pair_q, int32_t *pair_out,
                               int32_t *tile_list, int32_t *tile_beg, int32_t *tile_cnt,
                               int *ntiles, int32_t *probes_out, cudaStream_t st);
+// Per-query budgets in the merge (all null: none): ckeys / nsplit mark the runs
+// of masked probe slots, kq the per-query k, orow each query's output row.
+struct MergeMask {
+  const uint64_t *ckeys = nullptr;
+  int nsplit = 1;
+  const int32_t *kq = nullptr, *orow = nullptr;
+};
 int launch_merge(const uint64_t *pkeys, int64_t B, int nprobe, int k, int64_t *out_ids,
-                 float *out_dist, cudaStream_t st);
+                 float *out_dist, cudaStream_t st, const MergeMask &mm = MergeMask{});
 int num_sms();
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (device, kernel, size)
 cudaError_t ensure_smem(const void *fn, size_t bytes);
@@ -302,6 +310,14 @@ bool fp32_stream_enabled(double queries_per_list, int nprobe);
 // scratch bytes of search_f32_stream for these arguments (host arithmetic)
 int64_t stream_scratch_bytes(const adanns_index *idx, int64_t B, int d_c, int d_s, int nprobe,
                              int k);
+// The tiled FP32 scan (many queries per probed list).  qb (or null): per-query
+// nprobe / k at most the call's, one d_s for the batch; rows (or null): query
+// i of the batch is row rows[i] of `queries` and its results go to output row
+// rows[i] (rows of k entries).
+int search_f32_tiled(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
+                     int nprobe, int k, int64_t *out_ids, float *out_dist, int32_t *out_probes,
+                     cudaStream_t st, const QueryBudgets *qb = nullptr,
+                     const int32_t *rows = nullptr);
 // qb (or null): per-query d_s / nprobe / k at most the call's d_s, nprobe, k
 int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,
                       int nprobe, int k, int64_t *out_ids, float *out_dist, int32_t *out_probes,

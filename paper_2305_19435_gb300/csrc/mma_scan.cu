@@ -12,11 +12,18 @@
 // fixed-point key round(d * 2^14) into the query's candidate segment.  A selection kernel then keeps each query's best k' candidates and
 // the exact FP32 rerank (Sec. 4.3 shortlist-rerank) produces the result.
 //
-// Warp roles (576 threads): warp 0 issues TMA tile loads into a 3-stage
-// shared-memory ring; warp 1 owns tensor memory (512 columns: two 256-column
-// accumulators) and one elected thread issues the MMAs; warps 2-17 drain the
-// accumulators (four warps per TMEM lane quadrant, 64 columns each).  Every mbarrier wait is bounded: on timeout the kernel records
-// an error, stops issuing work, lets in-flight copies land and frees TMEM.
+// Warp roles (576 threads): warp 0 issues TMA tile loads into an NS-stage
+// shared-memory ring (a stage is one K-block of 128 bytes per row of the query
+// tile and of 256 members, 48 KB); warp 1 owns tensor memory (512 columns: two
+// 256-column accumulators) and one elected thread issues the MMAs; warps 2-17
+// drain the accumulators (four warps per TMEM lane quadrant, 64 columns each),
+// staging SC key columns at a time in shared memory for row-segment stores.
+// BF16 (a third of a microsecond of MMA work per stage) takes four stages, so
+// that more loads are in flight, and 16-column staging to make room for them;
+// FP8 (twice the MMA rate, the drain is the limit) keeps three stages and
+// 64-column staging, whose stores are fewer and wider.  Every mbarrier wait is
+// bounded: on timeout the kernel records an error, stops issuing work, lets
+// in-flight copies land and frees TMEM.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -31,15 +38,15 @@ namespace {
 constexpr int BM = 128;          // queries per tile (TMEM lanes)
 constexpr int BN = 256;          // members per MMA tile (TMEM columns per accumulator)
 constexpr int ROWB = 128;        // bytes per K-block row (one 128-byte swizzle atom row)
-constexpr int NSTAGE = 3;
 constexpr int A_BYTES = BM * ROWB;    // 16 KB
 constexpr int B_BYTES = BN * ROWB;    // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 16;                 // four per TMEM lane quadrant
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int EPI_SPAN = BN / (EPI_WARPS / 4);  // accumulator columns per epilogue warp
-constexpr int STG_BYTES = 32 * EPI_SPAN * 2;    // a warp's 32 rows of 16-bit keys
-static_assert(EPI_SPAN == 64, "the key staging holds 8 16-byte chunks per row");
+static_assert(EPI_SPAN == 64, "an epilogue warp drains 64 accumulator columns");
+// a warp's key staging tile: 32 rows x SC keys (SC 16 or 64)
+constexpr int stg_bytes(int sc) { return 32 * sc * 2; }
 constexpr int THREADS = 64 + EPI_THREADS;
 constexpr int TQD = 4;  // tile queue depth
 
@@ -159,15 +166,17 @@ __device__ __forceinline__ void tc_fence_after() {
 
 
 
+template <int NS, int SC>
 __global__ void __launch_bounds__(THREADS, 1)
     mma_scan_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     MmaScanArgs a) {
+  static_assert(SC == 16 || SC == 64, "staging of 16 or 64 key columns");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *sA = smem;                              // NSTAGE x 16 KB
-  unsigned char *sB = smem + NSTAGE * A_BYTES;           // NSTAGE x 32 KB
-  unsigned char *sStage = smem + NSTAGE * STAGE_BYTES;   // EPI_WARPS x 4 KB key staging
-  __shared__ uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], sfull[2];
+  unsigned char *sA = smem;                          // NS x 16 KB
+  unsigned char *sB = smem + NS * A_BYTES;           // NS x 32 KB
+  unsigned char *sStage = smem + NS * STAGE_BYTES;   // EPI_WARPS x stg_bytes(SC) key staging
+  __shared__ uint64_t full[NS], empty[NS], tfull[2], tempty[2], sfull[2];
   // tile queue: the producer takes tiles from a global counter (dynamic load
   // balance) and hands their ids to the MMA issuer and the epilogue in order
   __shared__ uint64_t qfull[TQD], qempty[TQD];
@@ -178,7 +187,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -244,14 +253,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             // test hook: leave this stage of work item 0 unfilled (no copy, no
             // arrival), so the MMA issuer's bounded wait on it runs out
             if (t == 0 && mt * a.nkb + kb == a.skip_fill) {
-              if (++stage == NSTAGE) { stage = 0; phase ^= 1; }
+              if (++stage == NS) { stage = 0; phase ^= 1; }
               continue;
             }
             mbar_expect_tx(&full[stage], STAGE_BYTES);
             tma_load_2d(sA + stage * A_BYTES, &tmA, &full[stage], 0, (t * a.nkb + kb) * BM);
             tma_load_2d(sB + stage * B_BYTES, &tmB, &full[stage], 0,
                         (int)(off * a.d_blocks) + kb * nl + mt * BN);
-            if (++stage == NSTAGE) { stage = 0; phase ^= 1; }
+            if (++stage == NS) { stage = 0; phase ^= 1; }
           }
       }
     }
@@ -301,7 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         (kb > 0 || ks > 0) ? 1u : 0u, a.fp8 != 0);
             }
             mma_commit(&empty[stage]);
-            if (++stage == NSTAGE) { stage = 0; phase ^= 1; }
+            if (++stage == NS) { stage = 0; phase ^= 1; }
           }
           mma_commit(&tfull[acc]);
           if (++acc == 2) { acc = 0; aphase ^= 1; }
@@ -427,10 +436,16 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         } else if (quarter * 32 < cnt) {
           const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
-          // this warp's 32 rows x 64 columns of keys are staged row-major in
-          // shared memory (16-byte chunks XOR-swizzled by row: conflict-free
-          // both ways), then stored as whole 128-byte row segments
-          uint4 *stg = (uint4 *)(sStage + (size_t)(warp - 2) * STG_BYTES);
+          // this warp's 32 rows of keys pass through a shared-memory tile of SC
+          // columns (CPR 16-byte chunks per row, chunks XOR-swizzled by row so
+          // that both the row-per-lane writes and the row-segment reads are
+          // conflict-free) and are stored as SC * 2-byte row segments
+          constexpr int CPR = SC / 8, LPR = CPR, RPI = 32 / LPR;
+          uint4 *stg = (uint4 *)(sStage + (size_t)(warp - 2) * stg_bytes(SC));
+          auto swz = [](int row, int ch) -> int {
+            return CPR == 8 ? (ch ^ (row & 7)) : (ch ^ ((row >> 2) & 1));
+          };
+          const int chl = lane % LPR;
 #pragma unroll 1
           for (int c0 = 0; c0 < EPI_SPAN; c0 += 32) {
             uint32_t r[32];
@@ -453,25 +468,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
-              const int ch = (c0 >> 3) + g;
-              stg[lane * 8 + (ch ^ (lane & 7))] =
+              const int col = c0 + 8 * g;  // column of this chunk in the warp's span
+              stg[lane * CPR + swz(lane, (col % SC) / 8)] =
                   make_uint4(packed[4 * g], packed[4 * g + 1], packed[4 * g + 2], packed[4 * g + 3]);
-            }
-          }
-          __syncwarp();
-          {
-            // 8 lanes per row: one instruction stores 4 rows x 128 bytes
-            const int m0 = mt * BN + c_lo, ch = lane & 7;
+              if ((col + 8) % SC == 0) {
+                __syncwarp();
+                // LPR lanes per row: one instruction stores RPI rows x SC * 2 bytes
+                const int m0 = mt * BN + c_lo + col + 8 - SC;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int rr = i * 4 + (lane >> 3);
-              const long long b = __shfl_sync(0xffffffffu, (long long)base, rr);
-              const int ok = __shfl_sync(0xffffffffu, valid ? 1 : 0, rr);
-              const uint4 v = stg[rr * 8 + (ch ^ (rr & 7))];
-              if (ok && m0 + 8 * ch < npad) *(uint4 *)(a.cand + b + m0 + 8 * ch) = v;
+                for (int i = 0; i < 32 / RPI; ++i) {
+                  const int rr = i * RPI + lane / LPR;
+                  const long long b = __shfl_sync(0xffffffffu, (long long)base, rr);
+                  const int ok = __shfl_sync(0xffffffffu, valid ? 1 : 0, rr);
+                  const uint4 v = stg[rr * CPR + swz(rr, chl)];
+                  if (ok && m0 + 8 * chl < npad) *(uint4 *)(a.cand + b + m0 + 8 * chl) = v;
+                }
+                __syncwarp();  // the staging tile is rewritten next
+              }
             }
           }
-          __syncwarp();  // the staging buffer is rewritten for the next tile
         }
         tc_fence_before();
         mbar_arrive(&tempty[acc]);
@@ -535,7 +550,11 @@ int make_map(CUtensorMap *m, const void *base, int64_t rows, int box_rows, bool 
 }
 }  // namespace
 
-size_t mma_scan_smem() { return (size_t)NSTAGE * STAGE_BYTES + (size_t)EPI_WARPS * STG_BYTES + 1024; }
+// stage count and staging width per element type (see the kernel's notes)
+constexpr int NS_BF16 = 4, SC_BF16 = 16, NS_FP8 = 3, SC_FP8 = 64;
+size_t mma_scan_smem(int ns, int sc) {
+  return (size_t)ns * STAGE_BYTES + (size_t)EPI_WARPS * stg_bytes(sc) + 1024;
+}
 
 int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
                     const MmaScanArgs &a, cudaStream_t st) {
@@ -543,12 +562,18 @@ int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t
   int rc;
   if ((rc = make_map(&tA, qtiles, qrows, BM, a.fp8 != 0))) return rc;
   if ((rc = make_map(&tB, xlow, xrows, BN, a.fp8 != 0))) return rc;
-  const size_t smem = mma_scan_smem();
-  ADN_CUDA(ensure_smem((const void *)mma_scan_kernel, (size_t)(smem)));
   MmaScanArgs b = a;
   b.wait_ns = (uint64_t)option(ADANNS_OPT_WAIT_LIMIT_NS);
   b.skip_fill = (int)take_option(ADANNS_OPT_TEST_SKIP_LOAD, -1);
-  mma_scan_kernel<<<num_sms(), THREADS, smem, st>>>(tA, tB, b);
+  if (a.fp8) {
+    const size_t smem = mma_scan_smem(NS_FP8, SC_FP8);
+    ADN_CUDA(ensure_smem((const void *)mma_scan_kernel<NS_FP8, SC_FP8>, smem));
+    mma_scan_kernel<NS_FP8, SC_FP8><<<num_sms(), THREADS, smem, st>>>(tA, tB, b);
+  } else {
+    const size_t smem = mma_scan_smem(NS_BF16, SC_BF16);
+    ADN_CUDA(ensure_smem((const void *)mma_scan_kernel<NS_BF16, SC_BF16>, smem));
+    mma_scan_kernel<NS_BF16, SC_BF16><<<num_sms(), THREADS, smem, st>>>(tA, tB, b);
+  }
   ADN_LAUNCH("mma_scan_kernel");
   return ADANNS_OK;
 }

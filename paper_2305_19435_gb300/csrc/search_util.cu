@@ -175,12 +175,13 @@ int num_sms() {
 __global__ void prep_queries_kernel(const float *__restrict__ q, int64_t B, int ld, int da,
                                     int db0, int metric, float *__restrict__ qa, int lda,
                                     float *__restrict__ qb, int ldb,
-                                    const int32_t *__restrict__ dbq) {
+                                    const int32_t *__restrict__ dbq,
+                                    const int32_t *__restrict__ rows) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= B) return;
   const int db = dbq ? dbq[row] : db0;
-  const float *src = q + row * ld;
+  const float *src = q + (rows ? (int64_t)rows[row] : row) * ld;
   float sa = 0.f, sb = 0.f;
   const int dm = max(da, db);
   for (int j = lane; j < dm; j += 32) {
@@ -205,11 +206,12 @@ __global__ void prep_queries_kernel(const float *__restrict__ q, int64_t B, int 
 }
 
 int launch_prep_queries(const float *q, int64_t B, int ld, int da, int db, int metric, float *qa,
-                        int lda, float *qb, int ldb, cudaStream_t st, const int32_t *dbq) {
+                        int lda, float *qb, int ldb, cudaStream_t st, const int32_t *dbq,
+                        const int32_t *rows) {
   if (B <= 0) return ADANNS_OK;
   const int wpb = 8;
   prep_queries_kernel<<<(unsigned)((B + wpb - 1) / wpb), wpb * 32, 0, st>>>(
-      q, B, ld, da, db, metric, qa, lda, qb, ldb, dbq);
+      q, B, ld, da, db, metric, qa, lda, qb, ldb, dbq, rows);
   ADN_LAUNCH("prep_queries_kernel");
   return ADANNS_OK;
 }
@@ -390,21 +392,28 @@ int launch_pad_rows(int64_t *ids, float *dist, int64_t B, int k_max, const int32
 // Per query (one warp): the nprobe sorted per-list top-k runs -> the k best.
 // tau starts at the smallest k-th key over the runs, an upper bound of the
 // final k-th key, so only keys <= tau are buffered; the buffer is sorted and
-// trimmed to k whenever it fills.
+// trimmed to k whenever it fills.  Per-query budgets (m.ckeys non-null): run r
+// belongs to probe slot r / m.nsplit, and runs of masked slots (PROBE_NONE,
+// never scanned) are skipped; m.kq: the query keeps its first kq[q] results
+// and pads the rest; m.orow: the query's output row.
 constexpr int MERGE_WPB = 4;
 
 __global__ void merge_kernel(const uint64_t *__restrict__ pkeys, int64_t B, int nprobe, int k,
                              int cap, int64_t *__restrict__ out_ids,
-                             float *__restrict__ out_dist) {
+                             float *__restrict__ out_dist, MergeMask m) {
   extern __shared__ uint64_t msmem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t qi = (int64_t)blockIdx.x * MERGE_WPB + warp;
   if (qi >= B) return;
   uint64_t *buf = msmem + (size_t)warp * cap;
   const uint64_t *src = pkeys + qi * (int64_t)nprobe * k;
+  const int nslot = m.ckeys ? nprobe / m.nsplit : 0;
+  auto masked = [&](int run) -> bool {
+    return m.ckeys && m.ckeys[qi * nslot + run / m.nsplit] == PROBE_NONE;
+  };
   uint64_t tau = KEY_MAX;
   for (int s = lane; s < nprobe; s += 32) {
-    const uint64_t v = src[(int64_t)s * k + k - 1];
+    const uint64_t v = masked(s) ? KEY_MAX : src[(int64_t)s * k + k - 1];
     tau = v < tau ? v : tau;
   }
   tau = warp_min_u64(tau);
@@ -412,7 +421,7 @@ __global__ void merge_kernel(const uint64_t *__restrict__ pkeys, int64_t B, int 
   const int total = nprobe * k;
   for (int base = 0; base < total; base += 32) {
     const int i = base + lane;
-    const uint64_t key = i < total ? src[i] : KEY_MAX;
+    const uint64_t key = i < total && !masked(i / k) ? src[i] : KEY_MAX;
     const bool take = key != KEY_MAX && key <= tau;
     const unsigned m = __ballot_sync(0xffffffffu, take);
     if (take) buf[n + __popc(m & lanemask_lt())] = key;
@@ -431,8 +440,10 @@ __global__ void merge_kernel(const uint64_t *__restrict__ pkeys, int64_t B, int 
   __syncwarp();
   warp_sort(buf, n);
   if (n > k) n = k;
+  if (m.kq && n > m.kq[qi]) n = m.kq[qi];
+  const int64_t orow = m.orow ? (int64_t)m.orow[qi] : qi;
   for (int r = lane; r < k; r += 32) {
-    const int64_t o = qi * k + r;
+    const int64_t o = orow * k + r;
     if (r < n) {
       const uint64_t key = buf[r];
       out_ids[o] = (int64_t)(uint32_t)(key & 0xffffffffu);
@@ -445,7 +456,7 @@ __global__ void merge_kernel(const uint64_t *__restrict__ pkeys, int64_t B, int 
 }
 
 int launch_merge(const uint64_t *pkeys, int64_t B, int nprobe, int k, int64_t *out_ids,
-                 float *out_dist, cudaStream_t st) {
+                 float *out_dist, cudaStream_t st, const MergeMask &mm) {
   if (B <= 0) return ADANNS_OK;
   int kp = 1;
   while (kp < k) kp <<= 1;
@@ -455,7 +466,7 @@ int launch_merge(const uint64_t *pkeys, int64_t B, int nprobe, int k, int64_t *o
   cudaError_t e = ensure_smem((const void *)merge_kernel, smem);
   if (e != cudaSuccess) return cuda_fail(e, "merge attribute");
   merge_kernel<<<(unsigned)((B + MERGE_WPB - 1) / MERGE_WPB), MERGE_WPB * 32, smem, st>>>(
-      pkeys, B, nprobe, k, cap, out_ids, out_dist);
+      pkeys, B, nprobe, k, cap, out_ids, out_dist, mm);
   ADN_LAUNCH("merge_kernel");
   return ADANNS_OK;
 }

@@ -48,13 +48,19 @@ def groups(*cols):
     return {k: np.array(v) for k, v in out.items()}
 
 
-def test_budgets_f32_match_oracle_per_query(A, setup):
+# FP32 routes: about 10 queries per probed list take the streaming scan with a
+# d_s per query; about 80 take the tiled scan, one pass per d_s group
+F32_PROBES = {"stream": [1, 2, 3], "tiled": [1, 2, 5, 13, 40]}
+
+
+@pytest.mark.parametrize("route", ["stream", "tiled"])
+def test_budgets_f32_match_oracle_per_query(A, setup, route):
     data, o, g = setup
     db, q = data["db"], data["queries"]
     rng = np.random.default_rng(3)
     B = len(q)
     ds = rng.choice([8, 16, 48, 64, 96, 192, 256, 512], B).astype(np.int32)
-    npb = rng.choice([1, 2, 5, 13, 40], B).astype(np.int32)
+    npb = rng.choice(F32_PROBES[route], B).astype(np.int32)
     kq = rng.choice([1, 7, 10, 33], B).astype(np.int32)
     gi, gd = A.search_ivf_budgets(g, cu(q), 32, ds, npb, kq, k_max=40)
     gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
@@ -73,13 +79,14 @@ def test_budgets_f32_match_oracle_per_query(A, setup):
     assert checked > 0.9 * B
 
 
-def test_budgets_f32_equal_single_budget_calls(A, setup):
+@pytest.mark.parametrize("route", ["stream", "tiled"])
+def test_budgets_f32_equal_single_budget_calls(A, setup, route):
     data, o, g = setup
     q = data["queries"]
     rng = np.random.default_rng(4)
     B = len(q)
     ds = rng.choice([16, 64, 128, 384, 512], B).astype(np.int32)
-    npb = rng.choice([1, 3, 8, 40], B).astype(np.int32)
+    npb = rng.choice(F32_PROBES[route], B).astype(np.int32)
     kq = rng.choice([5, 50, 100], B).astype(np.int32)
     gi, gd = A.search_ivf_budgets(g, cu(q), 16, ds, npb, kq)   # IVF-D: d_c below the built 32
     gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
