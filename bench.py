@@ -81,6 +81,9 @@ def parse():
                    help="AdANNS-DiskANN graph shortlist + rerank on the ImageNet-shaped data")
     p.add_argument("--no-largest", action="store_true",
                    help="skip the largest grid point (d_c = 64, d_s = 2048, nprobe = 32)")
+    p.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
+                   help="set a library run-time option first (e.g. SCAN_FILTER=1); recorded in "
+                        "the config")
     return p.parse_args()
 
 
@@ -728,6 +731,11 @@ def main():
     barrier()
     P.build()
     props = torch.cuda.get_device_properties(local)
+    options = {}
+    for kv in args.option:
+        name, val = kv.split("=", 1)
+        P.set_option(getattr(P, "OPT_" + name.upper()), int(val))
+        options[name.upper()] = int(val)
 
     w = synthdata.WORKLOADS[args.workload]
     N = args.n or w.N
@@ -920,6 +928,8 @@ def main():
                      "mma": {k2: v for k2, v in rooflines[args.mode].items() if k2 != "rerank"}}
 
     cfg = workload_config(args, N, B)
+    if options:
+        cfg["options"] = options
     out = {"metric": "QPS at recall@10 vs oracle", "value": main_r["qps"], "unit": "queries/s",
            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
            "ms_per_step": main_r["ms"], "higher_is_better": True, "scaling": "weak",

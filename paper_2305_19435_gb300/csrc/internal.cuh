@@ -244,6 +244,8 @@ struct MmaScanArgs {
   const int64_t *list_off;
   const int32_t *pair_out;   // pair index (q * nprobe + slot) of each tile row
   const int64_t *pbase;      // candidate segment start of each pair (multiple of 8)
+  int64_t pstride;           // > 0: key segment of pair p at (p / nprobe) * pstride instead
+                             // (one segment per query: a scan of the nearest list only)
   const float *cx;           // per member (list order): s_x * nu_x(d_s), 0 for a zero prefix
   const float *qn2;          // per query: |P_ds(q)|^2
   const float *qsc;          // per query: operand scale s_q
@@ -256,10 +258,12 @@ struct MmaScanArgs {
   int *err;
   int *tile_counter;         // zeroed before the launch: next tile to take
   int fp8;
-  // filtered mode (rec != NULL): instead of every key, each (query, probe slot)
-  // pair p keeps only its members with key <= tau[query] (tau NULL: all), as
-  // 32-bit records (key << 16 | member index, lists below 65,537 members)
-  // compacted from rec[pbase[p]]; rcnt[p] (zeroed before) counts them
+  // filtered mode (rec != NULL, tau != NULL): instead of every key, each
+  // (query, probe slot) pair p keeps only its members with key <= tau[query],
+  // as 32-bit records (key << 16 | member index, lists below 65,537 members)
+  // compacted from rec[pbase[p]]; the CTA counts them per tile row in shared
+  // memory and writes the count to rcnt[p] once the pair's work item is done
+  // (rcnt zeroed before, for pairs of empty lists)
   uint32_t *rec;
   int *rcnt;
   const uint16_t *tau;
@@ -325,10 +329,14 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
 int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, int kk, int k, const float *qrho, float rmax,
                     float e_rest, int prune, int64_t B, int64_t *out, cudaStream_t st);
-// Filtered tensor-core scan: tau and the in-place compaction of slot 0, and
-// the shortlist selected from the survivors (same result as launch_select16).
-int launch_shortlist_tau(uint32_t *rec, int *rcnt, const int64_t *pbase, int nprobe, int kk,
-                         int64_t B, uint16_t *tau, cudaStream_t st);
+// Filtered tensor-core scan: from the keys of each query's nearest list
+// (cand0 + q * stride0, the list of probe slot 0), tau = their kk-th smallest
+// (0xFFFF with fewer than kk members) and slot 0's records with key <= tau;
+// then the shortlist selected from the survivors (same result as
+// launch_select16).
+int launch_shortlist_tau(const uint16_t *cand0, int64_t stride0, const uint64_t *ckeys,
+                         const int64_t *list_off, uint32_t *rec, int *rcnt, const int64_t *pbase,
+                         int nprobe, int kk, int64_t B, uint16_t *tau, cudaStream_t st);
 // stats (NULL, or 2 zeroed device counters): survivors, queries selected
 // from global memory because their survivors exceed the shared buffer
 int launch_select_surv(const uint32_t *rec, const int *rcnt, const int64_t *pbase,

@@ -360,7 +360,9 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   const int qt = 128;
   const bool filt = scan_filter_enabled(idx);
   const int64_t seg_q = (int64_t)nprobe * (((int64_t)idx->max_list + 7) & ~7ll);
-  const int64_t per_q = seg_q * (filt ? 4 : 2) +
+  // filtered: the keys of each query's nearest list, one segment per query
+  const int64_t stride0 = ((int64_t)idx->max_list + 7) & ~7ll;
+  const int64_t per_q = (filt ? seg_q * 4 + stride0 * 2 : seg_q * 2) +
                         (int64_t)nprobe * ((int64_t)nkb * 128 * 128 / qt + 36) +
                         (int64_t)(dcp + dsp) * 4 + (int64_t)nkb * 128 + (int64_t)kk * 8 + 64;
   // slices bounded by a scratch budget (the candidate keys dominate it)
@@ -381,7 +383,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   int *err = idx->dev_err;
   int64_t *qtot, *qbase, *pbase, *cids;
   unsigned char *qlow, *qtile;
-  uint16_t *cand = nullptr, *tau = nullptr;
+  uint16_t *cand = nullptr, *tau = nullptr, *cand0 = nullptr;
   uint32_t *rec = nullptr;
   int rc;
   if ((rc = s.get(&qc, (size_t)Bc * dcp)) || (rc = s.get(&qs, (size_t)Bc * dsp)) ||
@@ -397,7 +399,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     return rc;
   if (filt) {
     if ((rc = s.get(&rec, (size_t)Bc * seg_q)) || (rc = s.get(&rcnt, (size_t)Bc * nprobe)) ||
-        (rc = s.get(&tau, Bc)))
+        (rc = s.get(&tau, Bc)) || (rc = s.get(&cand0, (size_t)(Bc * stride0))))
       return rc;
   } else if ((rc = s.get(&cand, (size_t)Bc * seg_q))) {
     return rc;
@@ -411,8 +413,10 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   const int64_t xrows = idx->N * (int64_t)idx->lowp_blocks[which];
   // one tensor-core scan over a tile set (tile arrays at offset t0, the set's
   // pairs at offset p0 of pair_out, its own tile count and work counter)
-  auto scan = [&](int64_t t0, int64_t ntile_cap, int64_t p0, int set,
-                  const uint16_t *thr) -> int {
+  // (thr non-null: the filtered second pass; keys0: the first pass's keys of
+  // each query's nearest list, one segment of stride0 per query)
+  auto scan = [&](int64_t t0, int64_t ntile_cap, int64_t p0, int set, const uint16_t *thr,
+                  uint16_t *keys0) -> int {
     MmaScanArgs m{};
     m.tile_list = tl + t0;
     m.tile_beg = tb + t0;
@@ -427,9 +431,10 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     m.nprobe = nprobe;
     m.nkb = nkb;
     m.d_blocks = idx->lowp_blocks[which];
-    m.cand = cand;
-    m.rec = rec;
-    m.rcnt = rcnt;
+    m.cand = keys0 ? keys0 : cand;
+    m.pstride = keys0 ? stride0 : 0;
+    m.rec = thr ? rec : nullptr;
+    m.rcnt = thr ? rcnt : nullptr;
     m.tau = thr;
     m.err = err;
     m.tile_counter = counter + 1 + set;  // zeroed with the cluster-mapping counter
@@ -484,13 +489,15 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     {
       StageTimer t(ST_MMA, st);
       if (filt) {
-        // pass 1: every query's nearest list, all members kept; its kk-th key
+        // pass 1: every query's nearest list, every key written; its kk-th key
         // bounds the query's shortlist; pass 2: the other lists, filtered
         ADN_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int) * nb * nprobe, st));
-        if ((rc = scan(0, tiles_a, 0, 0, nullptr))) return rc;
-        if ((rc = launch_shortlist_tau(rec, rcnt, pbase, nprobe, kk, nb, tau, st))) return rc;
-        if (tiles_b > 0 && (rc = scan(tiles_a, tiles_b, nb, 1, tau))) return rc;
-      } else if ((rc = scan(0, tiles_a, 0, 0, nullptr))) {
+        if ((rc = scan(0, tiles_a, 0, 0, nullptr, cand0))) return rc;
+        if ((rc = launch_shortlist_tau(cand0, stride0, ckeys, idx->list_off, rec, rcnt, pbase,
+                                       nprobe, kk, nb, tau, st)))
+          return rc;
+        if (tiles_b > 0 && (rc = scan(tiles_a, tiles_b, nb, 1, tau, nullptr))) return rc;
+      } else if ((rc = scan(0, tiles_a, 0, 0, nullptr, nullptr))) {
         return rc;
       }
     }

@@ -156,6 +156,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 __device__ __forceinline__ int ld_abort(const int *flag) { return *(const volatile int *)flag; }
 
+// bit e set for each of the 8 16-bit keys of v (key e in half e & 1 of word
+// e >> 1) that is <= tau: two keys per word against T = tau + 1 (with
+// d = (x | H) - (T & ~H) no borrow crosses the halves, and a half x < T iff
+// (~x_top & T_top) | (~(x_top ^ T_top) & ~d_top))
+__device__ __forceinline__ uint32_t keys_le8(const uint4 &v, uint32_t tau) {
+  if (tau >= 0xFFFFu) return 0xFFu;
+  const uint32_t T = tau + 1, TT = T | (T << 16), TL = TT & 0x7FFF7FFFu;
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint32_t m = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t x = w[i], d = (x | 0x80008000u) - TL;
+    const uint32_t lt = ((~x & TT) | (~(x ^ TT) & ~d)) & 0x80008000u;
+    m |= ((lt >> 15) & 1u) << (2 * i) | (lt >> 31) << (2 * i + 1);
+  }
+  return m;
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -182,6 +200,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ uint64_t qfull[TQD], qempty[TQD];
   __shared__ int qids[TQD];
   __shared__ float s_cb[2][BN], s_ca[2][BN];  // per member of the tile: -2 s_x nu_x, |x|^2
+  // filtered mode: survivors per tile row of the current and the previous work item
+  __shared__ int s_rc[2][BM];
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
 
@@ -201,6 +221,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&qempty[s], 1 + EPI_THREADS);
     }
     abort_s = 0;
+    for (int i = 0; i < 2 * BM; ++i) s_rc[i / BM][i % BM] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -218,6 +239,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                                : ((1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                   ((uint32_t)(BM >> 4) << 24));
 
+  // filtered mode: the last work item with member tiles whose survivor counts
+  // this epilogue thread still has to write (see the epilogue)
+  const bool filt = a.rec != nullptr && a.tau != nullptr;
+  bool fl_pv = false;
+  int fl_pp = 0, fl_buf = 0;
   if (warp == 0) {
     // ---------------- TMA producer
     if (lane == 0) {
@@ -329,6 +355,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t aphase = 0;
     int qs = 0;
     uint32_t qph = 0;
+    // filtered mode: a pair's survivors are counted in s_rc[ib & 1][row] (shared
+    // atomics of the row's four column warps) while its work item, the ib-th
+    // with member tiles, is drained; at the next such item's first tile, after
+    // the hand-off barrier that every epilogue thread passes only once done
+    // with the previous tile, the first column warp of each quadrant writes
+    // the count to rcnt and clears its slot for the item after that
+    int ib = 0;
     for (;;) {
       if (!mbar_wait(&qfull[qs], qph, a.wait_ns)) {
         atomicExch(&abort_s, 1);
@@ -353,12 +386,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (valid) {
         const int p = a.pair_out[a.tile_beg[t] + row];
         const int q = p / a.nprobe;
-        base = a.pbase[p];
+        base = a.pstride ? (int64_t)(p / a.nprobe) * a.pstride : a.pbase[p];
         q2 = a.qn2[q];
         qs = a.qsc[q];
         pidx = p;
         if (a.tau) tau = a.tau[q];
       }
+      const int cbuf = ib & 1;
       bool stop = false;
       // per-member terms of member tile mt (thread et < BN holds member et of
       // the tile), loaded one tile ahead so the loads overlap the drain
@@ -396,50 +430,23 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
         }
+        if (filt && mt == 0 && ib > 0 && c_lo == 0) {
+          if (fl_pv) a.rcnt[fl_pp] = s_rc[fl_buf][row];
+          s_rc[fl_buf][row] = 0;
+        }
         if (mt + 1 < nmt) terms = load_terms(mt + 1);
         // a lane quadrant with no valid query row (a tile with few queries)
         // has nothing to drain: its warps skip the TMEM loads and the stores
-        if (quarter * 32 < cnt && a.rec) {
-          // filtered: per 32 of this row's columns, the survivors (key <=
-          // tau, member inside the list) are reserved with one atomic and
-          // written as records (key << 16 | member index)
-          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
-#pragma unroll 1
-          for (int h = 0; h < 2; ++h) {
-            const int m0 = mt * BN + c_lo + 32 * h;
-            uint32_t r[32];
-            tmem_ld32(tbase + c_lo + 32 * h, r);
-            uint32_t packed[16];
-            int nsurv = 0;
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              uint32_t kk[2];
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const int c = c_lo + 32 * h + j + u;
-                float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[j + u]), q2 + s_ca[acc][c]);
-                d = fminf(fmaxf(d, 0.f), 3.9999f);
-                kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
-                nsurv += (kk[u] <= tau && m0 + j + u < nl) ? 1 : 0;
-              }
-              packed[j >> 1] = kk[0] | (kk[1] << 16);
-            }
-            if (valid && nsurv > 0) {
-              uint32_t *dst = a.rec + base + atomicAdd(a.rcnt + pidx, nsurv);
-              int w = 0;
-#pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const uint32_t key = (packed[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-                if (key <= tau && m0 + j < nl) dst[w++] = (key << 16) | (uint32_t)(m0 + j);
-              }
-            }
-          }
-        } else if (quarter * 32 < cnt) {
+        if (quarter * 32 < cnt) {
           const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
           // this warp's 32 rows of keys pass through a shared-memory tile of SC
           // columns (CPR 16-byte chunks per row, chunks XOR-swizzled by row so
           // that both the row-per-lane writes and the row-segment reads are
-          // conflict-free) and are stored as SC * 2-byte row segments
+          // conflict-free) and are stored as SC * 2-byte row segments; in the
+          // filtered pass a lane instead compares each 8-key chunk it reads
+          // with its row's tau (two keys per word) and writes only the
+          // survivors, as records, after one shared-memory atomic on the row's
+          // count
           constexpr int CPR = SC / 8, LPR = CPR, RPI = 32 / LPR;
           uint4 *stg = (uint4 *)(sStage + (size_t)(warp - 2) * stg_bytes(SC));
           auto swz = [](int row, int ch) -> int {
@@ -480,8 +487,28 @@ __global__ void __launch_bounds__(THREADS, 1)
                   const int rr = i * RPI + lane / LPR;
                   const long long b = __shfl_sync(0xffffffffu, (long long)base, rr);
                   const int ok = __shfl_sync(0xffffffffu, valid ? 1 : 0, rr);
+                  const uint32_t tr = __shfl_sync(0xffffffffu, tau, rr);
                   const uint4 v = stg[rr * CPR + swz(rr, chl)];
-                  if (ok && m0 + 8 * chl < npad) *(uint4 *)(a.cand + b + m0 + 8 * chl) = v;
+                  const int mb = m0 + 8 * chl;
+                  if (!filt) {
+                    if (ok && mb < npad) *(uint4 *)(a.cand + b + mb) = v;
+                  } else if (ok && mb < nl) {
+                    uint32_t msk = keys_le8(v, tr);
+                    if (mb + 8 > nl) msk &= (1u << (nl - mb)) - 1u;  // members past the list end
+                    if (msk) {
+                      uint32_t *dst =
+                          a.rec + b + atomicAdd(&s_rc[cbuf][quarter * 32 + rr], __popc(msk));
+                      const uint64_t k01 = ((uint64_t)v.y << 32) | v.x,
+                                     k23 = ((uint64_t)v.w << 32) | v.z;
+                      while (msk) {
+                        const int e = __ffs(msk) - 1;
+                        msk &= msk - 1;
+                        const uint32_t key =
+                            (uint32_t)(((e < 4 ? k01 : k23) >> (16 * (e & 3))) & 0xFFFFu);
+                        *dst++ = (key << 16) | (uint32_t)(mb + e);
+                      }
+                    }
+                  }
                 }
                 __syncwarp();  // the staging tile is rewritten next
               }
@@ -493,11 +520,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (++acc == 2) { acc = 0; aphase ^= 1; }
       }
       if (stop) break;
+      if (nmt > 0) {
+        fl_pv = valid;
+        fl_pp = pidx;
+        fl_buf = cbuf;
+        ++ib;
+      }
       if (ld_abort(&abort_s)) break;
     }
   }
 
   __syncthreads();
+  // filtered mode: the last work item's survivor counts (every epilogue thread
+  // is past the block barrier, so they are final)
+  if (filt && warp >= 2 && (warp - 2) / 4 == 0 && fl_pv && !ld_abort(&abort_s))
+    a.rcnt[fl_pp] = s_rc[fl_buf][(warp & 3) * 32 + lane];
   if (ld_abort(&abort_s)) {
     // let any copy still in flight land before the shared memory is released
     for (int i = 0; i < 1 << 14; ++i) __nanosleep(1000);

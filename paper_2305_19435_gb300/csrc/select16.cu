@@ -30,10 +30,13 @@ constexpr int SW_TIE = 128;
 constexpr int SW_MAXP = 128;
 constexpr int SW_PF = 12;
 
-// Per-warp state, 8.6 KB, so that six CTAs of four warps fit on an SM.  The
+// Per-warp state with a buffer of BUF keys (8.6 KB for the 1,024 of
+// select16_kernel, so that six CTAs of four warps fit on an SM).  The
 // histogram is dead when the ties at the cut are collected, and the sample is
 // dead when the compaction fills the buffer, so each pair shares its space.
-struct SwState {
+template <int BUF>
+struct SwStateT {
+  static constexpr int kBuf = BUF;
   union {
     int hist[256];
     uint64_t ties[SW_TIE];  // (candidate position << 32 | index) of the keys at the cut
@@ -43,15 +46,19 @@ struct SwState {
   union {
     uint16_t samp[SW_SAMPLE];
     struct {
-      uint16_t key[SW_BUF];
-      uint32_t idx[SW_BUF];
+      uint16_t key[BUF];
+      uint32_t idx[BUF];
     } b;
   } u;
 };
+using SwState = SwStateT<SW_BUF>;
+// the survivors of the filtered scan: about kk from the nearest list plus those
+// of the other lists under its bound, over 1,024 for a few percent of queries
+constexpr int SV_BUF = 2048;
 
 // the kth smallest (1-based, kth <= n) of n 16-bit keys, by one warp
-template <class KeyF>
-__device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, SwState &s, int &below,
+template <class KeyF, class St>
+__device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, St &s, int &below,
                                                int &neq) {
   return warp_radix_kth<2>(n, kth, key, s.h.hist, s.sh, below, neq);
 }
@@ -61,9 +68,9 @@ __device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, SwState
 // smallest key + prune_delta become -1.  Keys equal to the cut are taken by
 // ascending position: a warp sort of up to SW_TIE of them, else a prefix count
 // (keys in position order) or a radix select on their positions.
-template <bool ORDERED, class KeyF, class IdF, class PosF>
+template <bool ORDERED, class KeyF, class IdF, class PosF, class St>
 __device__ __forceinline__ bool warp_select16(int n, int kk, int kq, int prune_delta, KeyF key, IdF id, PosF pos,
-                              int64_t *o, SwState &s) {
+                              int64_t *o, St &s) {
   const int lane = threadIdx.x & 31;
   int below, neq;
   const uint32_t T = warp_kth16(n, kk, key, s, below, neq);
@@ -278,44 +285,45 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
 // With the filtered tensor-core scan, each (query, probe slot) pair keeps only
 // its members whose key can still be in the shortlist, as records
 // (key << 16 | member index) compacted at the start of the pair's segment.
-// The first pass scans every query's nearest list (slot 0) keeping all of it;
-// its kk-th smallest key tau bounds the query's overall kk-th key (those kk
-// members are candidates too), so the second pass over the other slots keeps
-// keys <= tau only.  The shortlist is then selected from the survivors with
-// the same (key, candidate position) order as select16_kernel, so the result
-// is the same.
+// A first pass scans every query's nearest list (slot 0) and writes all of its
+// keys; their kk-th smallest, tau, bounds the query's overall kk-th key (those
+// kk members are candidates too), so slot 0 keeps its records with key <= tau
+// and the second pass over the other slots keeps keys <= tau only.  The
+// shortlist is then selected from the survivors with the same (key, candidate
+// position) order as select16_kernel, so the result is the same.
 
 constexpr int TAU_WARPS = 4;
 
-// Per query (one warp): tau = the kk-th smallest key of slot 0's records (all
-// of its members), or 0xFFFF when the list has fewer than kk members; slot 0
-// is compacted in place to its records with key <= tau.
+// Per query (one warp): tau = the kk-th smallest of slot 0's n0 keys (0xFFFF
+// when n0 < kk) and slot 0's records with key <= tau, in member order.
 __global__ void __launch_bounds__(TAU_WARPS * 32) shortlist_tau_kernel(
-    uint32_t *__restrict__ rec, int *__restrict__ rcnt, const int64_t *__restrict__ pbase,
-    int nprobe, int kk, int64_t B, uint16_t *__restrict__ tau) {
+    const uint16_t *__restrict__ cand0, int64_t stride0, const uint64_t *__restrict__ ckeys,
+    const int64_t *__restrict__ list_off, uint32_t *__restrict__ rec, int *__restrict__ rcnt,
+    const int64_t *__restrict__ pbase, int nprobe, int kk, int64_t B,
+    uint16_t *__restrict__ tau) {
   __shared__ int hist[TAU_WARPS][256];
   __shared__ int sh[TAU_WARPS][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t q = (int64_t)blockIdx.x * TAU_WARPS + warp;
   if (q >= B) return;
   const int64_t p0 = q * nprobe;
-  const int n0 = rcnt[p0];
-  uint32_t *r = rec + pbase[p0];
-  if (n0 < kk) {
-    if (lane == 0) tau[q] = 0xFFFFu;
-    return;
+  const int l = probe_list(ckeys[p0]);  // slot 0 is never masked
+  const int n0 = l >= 0 ? (int)(list_off[l + 1] - list_off[l]) : 0;
+  const uint16_t *keys = cand0 + q * stride0;
+  uint32_t T = 0xFFFFu;
+  if (n0 >= kk) {
+    int below, neq;
+    T = warp_radix_kth<2>(n0, kk, [&](int i) -> uint32_t { return keys[i]; }, hist[warp],
+                          sh[warp], below, neq);
   }
-  int below, neq;
-  const uint32_t T = warp_radix_kth<2>(n0, kk, [&](int i) -> uint32_t { return r[i] >> 16; },
-                                       hist[warp], sh[warp], below, neq);
-  // in-place compaction: a lane writes at or before positions already read
+  uint32_t *r = rec + pbase[p0];
   int w = 0;
   for (int i0 = 0; i0 < n0; i0 += 32) {
     const int i = i0 + lane;
-    const uint32_t v = i < n0 ? r[i] : 0xFFFFFFFFu;
-    const bool keep = i < n0 && (v >> 16) <= T;
+    const uint32_t k = i < n0 ? keys[i] : 0xFFFFFFFFu;
+    const bool keep = i < n0 && k <= T;
     const unsigned b = __ballot_sync(0xffffffffu, keep);
-    if (keep) r[w + __popc(b & lanemask_lt())] = v;
+    if (keep) r[w + __popc(b & lanemask_lt())] = (k << 16) | (uint32_t)i;
     w += __popc(b);
   }
   if (lane == 0) {
@@ -325,14 +333,14 @@ __global__ void __launch_bounds__(TAU_WARPS * 32) shortlist_tau_kernel(
 }
 
 struct SvState {
-  SwState s;
+  SwStateT<SV_BUF> s;
   int spre[SW_MAXP + 1];  // survivors before each slot
   int64_t pb[SW_MAXP];    // record segment start of each slot
 };
 
 // Per query (one warp): the kk smallest (key, candidate position) among the
 // survivors, written like select16_kernel (pruning included).
-__global__ void __launch_bounds__(SW_WARPS * 32, 4) select_surv_kernel(
+__global__ void __launch_bounds__(SW_WARPS * 32, 3) select_surv_kernel(
     const uint32_t *__restrict__ rec, const int *__restrict__ rcnt,
     const int64_t *__restrict__ pbase, const uint64_t *__restrict__ ckeys, int nprobe,
     const int64_t *__restrict__ list_off, int kk, int k, const float *__restrict__ qrho,
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) select_surv_kernel(
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   SvState &v = ((SvState *)smem)[warp];
-  SwState &s = v.s;
+  auto &s = v.s;
   const int64_t q = (int64_t)blockIdx.x * SW_WARPS + warp;
   if (q >= B) return;
   int prune_delta = 0;
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) select_surv_kernel(
   const int S = __shfl_sync(0xffffffffu, sinc, 31);
   if (stats && lane == 0) {
     atomicAdd(stats, (unsigned long long)S);
-    if (S > SW_BUF && total > kk) atomicAdd(stats + 1, 1ull);
+    if (S > SV_BUF && total > kk) atomicAdd(stats + 1, 1ull);
   }
   __syncwarp();
   int64_t *o = out + q * kk;
@@ -435,7 +443,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) select_surv_kernel(
     return m < s.nl[lo] ? (((int64_t)s.lid[lo] << 32) | (int64_t)m) : -1;
   };
   const int kq = prune ? k : 0;
-  if (S <= SW_BUF) {
+  if (S <= SV_BUF) {
     for (int i = lane; i < S; i += 32) {
       const int sl = slot_of(i);
       const uint32_t r = rec[v.pb[sl] + (i - v.spre[sl])];
@@ -462,11 +470,12 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) select_surv_kernel(
 
 }  // namespace
 
-int launch_shortlist_tau(uint32_t *rec, int *rcnt, const int64_t *pbase, int nprobe, int kk,
-                         int64_t B, uint16_t *tau, cudaStream_t st) {
+int launch_shortlist_tau(const uint16_t *cand0, int64_t stride0, const uint64_t *ckeys,
+                         const int64_t *list_off, uint32_t *rec, int *rcnt, const int64_t *pbase,
+                         int nprobe, int kk, int64_t B, uint16_t *tau, cudaStream_t st) {
   if (B <= 0) return ADANNS_OK;
   shortlist_tau_kernel<<<(unsigned)((B + TAU_WARPS - 1) / TAU_WARPS), TAU_WARPS * 32, 0, st>>>(
-      rec, rcnt, pbase, nprobe, kk, B, tau);
+      cand0, stride0, ckeys, list_off, rec, rcnt, pbase, nprobe, kk, B, tau);
   ADN_LAUNCH("shortlist_tau_kernel");
   return ADANNS_OK;
 }
