@@ -193,6 +193,41 @@ __global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
   }
 }
 
+// Ascending bitonic sort of 256 keys held 8 per lane (lane l holds positions
+// 8l .. 8l + 7): strides below 8 compare within a lane, larger ones across
+// lanes by shuffles; the direction of each compare-exchange is that of the
+// block of `size` positions holding it (ascending for even blocks).
+__device__ __forceinline__ void warp_sort256(uint64_t (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= 8) {
+        const int ls = stride >> 3;
+        const bool lower = (lane & ls) == 0;
+        const bool asc = ((lane * 8) & size) == 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint64_t o = __shfl_xor_sync(0xffffffffu, v[j], ls);
+          const uint64_t lo = o < v[j] ? o : v[j], hi = o < v[j] ? v[j] : o;
+          v[j] = lower == asc ? lo : hi;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j & stride) continue;
+          const bool asc = ((lane * 8 + j) & size) == 0;
+          const uint64_t a = v[j], b = v[j | stride];
+          const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+          v[j] = asc ? lo : hi;
+          v[j | stride] = asc ? hi : lo;
+        }
+      }
+    }
+  }
+}
+
 // per query (one warp): sort its kr keys, write the k best
 __global__ void final_topk_kernel(const uint64_t *__restrict__ keys, int kr, int64_t B, int k,
                                   int64_t *__restrict__ out_ids, float *__restrict__ out_dist) {
@@ -218,6 +253,30 @@ __global__ void final_topk_kernel(const uint64_t *__restrict__ keys, int kr, int
     }
   }
   __syncwarp();
+  if (n <= 256) {
+    // the common case (pruned shortlists): sorted in registers
+    uint64_t v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = lane * 8 + j;
+      v[j] = r < n ? buf[r] : KEY_MAX;
+    }
+    warp_sort256(v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = lane * 8 + j;
+      if (r < k) {
+        out_ids[q * k + r] = v[j] == KEY_MAX ? -1 : (int64_t)(uint32_t)(v[j] & 0xffffffffu);
+        out_dist[q * k + r] = v[j] == KEY_MAX ? __int_as_float(0x7f800000)
+                                              : __uint_as_float((uint32_t)(v[j] >> 32));
+      }
+    }
+    for (int r = 256 + lane; r < k; r += 32) {  // k above the 256 sorted positions: padding
+      out_ids[q * k + r] = -1;
+      out_dist[q * k + r] = __int_as_float(0x7f800000);
+    }
+    return;
+  }
   warp_sort(buf, n);
   for (int r = lane; r < k; r += 32) {
     const uint64_t key = r < n ? buf[r] : KEY_MAX;
