@@ -306,6 +306,21 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
                       int d_s, int nprobe, int k, int storage, int rerank_k, int64_t *out_ids,
                       float *out_dist, int32_t *out_probes, void *cuda_stream);
 
+/* AdANNS-IVF search of HOST queries with HOST results: adanns_search_ivf's
+ * arguments and rules, but queries (B x d FP32), out_ids (int64 B x k) and
+ * out_dist (FP32 B x k) are host memory.  The batch is cut into slices of
+ * `slice` rows (0: four slices); slice i+1's queries are copied to the device
+ * on an internal stream while slice i is searched on cuda_stream, and slice
+ * i's results are copied back while slice i+1 is searched.  Returns once the
+ * work is queued; the results are on the host when cuda_stream reaches the
+ * point of the call (synchronise it, or an event recorded after the call).
+ * Page-locked host buffers let the copies overlap the search; pageable ones
+ * work but their copies run synchronously.  The host buffers must stay valid
+ * until then.  Results equal adanns_search_ivf on the same rows. */
+int adanns_search_ivf_host(const adanns_index *idx, const float *queries, int64_t B, int d_c,
+                           int d_s, int nprobe, int k, int storage, int rerank_k,
+                           int64_t *out_ids, float *out_dist, int64_t slice, void *cuda_stream);
+
 /* AdANNS-IVF search of a batch whose queries carry their own budgets (Sec. 5
  * "Compute-aware Elastic Search During Inference": each query picks its
  * d_s, nprobe and k at run time over one resident index), in one pass of the
@@ -441,6 +456,22 @@ int adanns_index_get_opq(const adanns_index *idx, float *R, float *codebooks,
 int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t B, int d_c,
                          int nprobe, int k, int rerank_k, int64_t *out_ids, float *out_dist,
                          int32_t *out_probes, void *cuda_stream);
+
+/* AdANNS-IVFOPQ search of a batch whose queries carry their own nprobe and k
+ * (Sec. 5 compute-aware elastic search over the IVF-OPQ composite), in one
+ * pass of the distance-then-select ADC stage.
+ *   nprobe, k  HOST int32 arrays of B entries, read before the call returns:
+ *            1 <= nprobe[i] <= min(nlist, 256), 1 <= k[i] <= k_max <= 1024.
+ *   rerank_k 0, or k_max <= rerank_k <= 2048 (the shortlist of every query).
+ *   out_ids  int64 [B x k_max], out_dist FP32 [B x k_max] (device): row i
+ *            holds query i's k[i] results, then (-1, +inf) up to k_max.
+ * Row i equals the first k[i] entries of adanns_search_ivfopq on query i alone
+ * with (d_c, nprobe[i], k_max, rerank_k).  ADANNS_ERR_ARG for a bad entry (its
+ * index in the message); nothing is launched then. */
+int adanns_search_ivfopq_budgets(const adanns_index *idx, const float *queries, int64_t B,
+                                 int d_c, const int32_t *nprobe, const int32_t *k, int k_max,
+                                 int rerank_k, int64_t *out_ids, float *out_dist,
+                                 void *cuda_stream);
 
 /* ------------------------------------------------------------------------
  * Autotuning of the exact FP32 list scan.  adanns_autotune_search runs the

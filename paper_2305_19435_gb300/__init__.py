@@ -62,6 +62,8 @@ def lib():
         L.adanns_kmeans_update.argtypes = [P, i64, i32, i32, i32, P, i32, P, P]
         L.adanns_search_ivf.argtypes = [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, P, P]
         L.adanns_search_ivf_budgets.argtypes = [P, P, i64, i32, P, P, P, i32, i32, i32, P, P, P]
+        L.adanns_search_ivf_host.argtypes = [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, i64, P]
+        L.adanns_search_ivfopq_budgets.argtypes = [P, P, i64, i32, P, P, i32, i32, P, P, P]
         L.adanns_opq_encode.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P]
         L.adanns_pq_update.argtypes = [P, i64, i32, i32, P, P, P]
         L.adanns_procrustes.argtypes = [P, P, i64, i32, P, P]
@@ -438,6 +440,31 @@ def search_ivf(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: 
     return (ids, dist, probes) if return_probes else (ids, dist)
 
 
+def search_ivf_host(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: int, k: int,
+                    storage: int = STORE_F32, rerank_k: int = 0, out: tuple | None = None,
+                    slice_rows: int = 0):
+    """AdANNS-IVF search of HOST queries (a CPU float32 tensor, page-locked for
+    overlap) into HOST results (ids int64 [B,k], dist f32 [B,k]); the copies of
+    each slice overlap the search of its neighbours.  Returns when the work is
+    queued: synchronise the current stream before reading the results."""
+    if not isinstance(queries, torch.Tensor) or queries.is_cuda or queries.dtype != torch.float32:
+        raise TypeError("queries must be a CPU float32 tensor")
+    if queries.dim() != 2 or queries.shape[1] != index.d or not queries.is_contiguous():
+        raise ValueError(f"queries must be contiguous [B, {index.d}]")
+    B = queries.shape[0]
+    if out is None:
+        ids = torch.empty(B, k, dtype=torch.int64, pin_memory=True)
+        dist = torch.empty(B, k, dtype=torch.float32, pin_memory=True)
+    else:
+        ids, dist = out
+        if ids.is_cuda or dist.is_cuda:
+            raise TypeError("results must be CPU tensors")
+    _check(lib().adanns_search_ivf_host(index.handle, _ptr(queries), B, d_c, d_s, nprobe, k,
+                                        storage, rerank_k, _ptr(ids), _ptr(dist), slice_rows,
+                                        _stream()))
+    return ids, dist
+
+
 def search_ivf_budgets(index: Index, queries: torch.Tensor, d_c: int, d_s, nprobe, k,
                        k_max: int | None = None, storage: int = STORE_F32, rerank_k: int = 0,
                        out: tuple | None = None):
@@ -449,19 +476,8 @@ def search_ivf_budgets(index: Index, queries: torch.Tensor, d_c: int, d_s, nprob
         raise ValueError(f"queries must have {index.d} columns")
     B = queries.shape[0]
 
-    def arr(v, what):
-        a = (ctypes.c_int32 * B)()
-        if isinstance(v, int):
-            for i in range(B):
-                a[i] = v
-        else:
-            v = [int(x) for x in v]
-            if len(v) != B:
-                raise ValueError(f"{what} needs {B} entries")
-            a[:] = v
-        return a
-
-    ds_a, np_a, k_a = arr(d_s, "d_s"), arr(nprobe, "nprobe"), arr(k, "k")
+    ds_a = _budget_array(d_s, B, "d_s")
+    np_a, k_a = _budget_array(nprobe, B, "nprobe"), _budget_array(k, B, "k")
     if k_max is None:
         k_max = max(k_a) if B else 1
     if out is None:
@@ -473,6 +489,42 @@ def search_ivf_budgets(index: Index, queries: torch.Tensor, d_c: int, d_s, nprob
                                            k_max, storage, rerank_k, _ptr(ids), _ptr(dist),
                                            _stream()))
     return ids, dist
+
+
+def search_ivfopq_budgets(index: Index, queries: torch.Tensor, d_c: int, nprobe, k,
+                          k_max: int | None = None, rerank_k: int = 0, out: tuple | None = None):
+    """AdANNS-IVFOPQ search with nprobe and k per query (sequences of B ints,
+    or one int for all) -> (ids int64 [B,k_max], dist f32 [B,k_max]); row i
+    holds query i's k[i] results, then (-1, +inf)."""
+    _need(queries, torch.float32, "queries", 2)
+    if queries.shape[1] != index.d:
+        raise ValueError(f"queries must have {index.d} columns")
+    B = queries.shape[0]
+    np_a, k_a = _budget_array(nprobe, B, "nprobe"), _budget_array(k, B, "k")
+    if k_max is None:
+        k_max = max(k_a) if B else 1
+    if out is None:
+        ids = torch.empty(B, k_max, dtype=torch.int64, device=queries.device)
+        dist = torch.empty(B, k_max, dtype=torch.float32, device=queries.device)
+    else:
+        ids, dist = out
+    _check(lib().adanns_search_ivfopq_budgets(index.handle, _ptr(queries), B, d_c, np_a, k_a,
+                                              k_max, rerank_k, _ptr(ids), _ptr(dist), _stream()))
+    return ids, dist
+
+
+def _budget_array(v, B: int, what: str):
+    """a ctypes int32 array of B entries from one int or a sequence"""
+    a = (ctypes.c_int32 * B)()
+    if isinstance(v, int):
+        for i in range(B):
+            a[i] = v
+    else:
+        v = [int(x) for x in v]
+        if len(v) != B:
+            raise ValueError(f"{what} needs {B} entries")
+        a[:] = v
+    return a
 
 
 # ---------------------------------------------------------------- OPQ / IVF-OPQ

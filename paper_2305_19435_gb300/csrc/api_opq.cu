@@ -213,9 +213,11 @@ int encode_lists(adanns_index *x, const float *db, cudaStream_t st) {
 // items -> LUTs -> every probed member's ADC distance into the query's
 // candidate segment -> the k' smallest (distance, id) per query -> the k best
 // (no rerank) or the exact FP32 rerank of the k'.
+// qb (or null): per-query nprobe and k, at most the call's nprobe and k (rows
+// of k entries, a query's own k results first, then padding)
 int search_ivfopq_select(const adanns_index *idx, const float *queries, int64_t B, int d_c,
                          int nprobe, int k, int kr, bool rerank, int64_t *out_ids, float *out_dist,
-                         int32_t *out_probes, cudaStream_t st) {
+                         int32_t *out_probes, cudaStream_t st, const QueryBudgets *qb = nullptr) {
   const int d_s = idx->opq_ds, M = idx->opq_M, dsub = d_s / M;
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
@@ -259,6 +261,7 @@ int search_ivfopq_select(const adanns_index *idx, const float *queries, int64_t 
     {
       StageTimer t(ST_COARSE, st);
       if ((rc = run_coarse(idx, qc, dcp, nb, d_c, nprobe, ckeys, counter, st))) return rc;
+      if (qb && (rc = launch_mask_probes(ckeys, nb, nprobe, qb->at(b0).np, st))) return rc;
     }
     {
       StageTimer t(ST_INVERT, st);
@@ -307,6 +310,8 @@ int search_ivfopq_select(const adanns_index *idx, const float *queries, int64_t 
                               out_dist + b0 * k, st)))
         return rc;
     }
+    if (qb && (rc = launch_pad_rows(out_ids + b0 * k, out_dist + b0 * k, nb, k, qb->at(b0).k, st)))
+      return rc;
   }
   return ADANNS_OK;
 }
@@ -657,6 +662,49 @@ int adanns_search_ivfopq(const adanns_index *idx, const float *queries, int64_t 
     }
   }
   return ADANNS_OK;
+}
+
+int adanns_search_ivfopq_budgets(const adanns_index *idx, const float *queries, int64_t B,
+                                 int d_c, const int32_t *nprobe, const int32_t *k, int k_max,
+                                 int rerank_k, int64_t *out_ids, float *out_dist,
+                                 void *cuda_stream) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  if (!idx->codes) return fail(ADANNS_ERR_STATE, "the index has no OPQ data");
+  if (B < 0 || B > INT32_MAX) return fail(ADANNS_ERR_ARG, "bad batch size");
+  if (B > 0 && (!queries || !out_ids || !out_dist || !nprobe || !k))
+    return fail(ADANNS_ERR_ARG, "NULL argument");
+  if (gran_index(d_c) < 0 || d_c > idx->d_c)
+    return fail(ADANNS_ERR_DIM, "d_c must be an MR granularity <= the index's clustering prefix " +
+                                    std::to_string(idx->d_c));
+  if (k_max < 1 || k_max > 1024) return fail(ADANNS_ERR_ARG, "need 1 <= k_max <= 1024");
+  if (rerank_k != 0 && (rerank_k < k_max || rerank_k > 2048))
+    return fail(ADANNS_ERR_ARG, "need rerank_k = 0 or k_max <= rerank_k <= 2048");
+  int np_max = 0;
+  // staging array: nprobe, then k, of every query
+  std::vector<int32_t> h((size_t)B * 2);
+  for (int64_t i = 0; i < B; ++i) {
+    const std::string at = " (query " + std::to_string(i) + ")";
+    if (nprobe[i] < 1 || nprobe[i] > idx->nlist || nprobe[i] > 256)
+      return fail(ADANNS_ERR_ARG, "need 1 <= nprobe <= min(nlist, 256)" + at);
+    if (k[i] < 1 || k[i] > k_max) return fail(ADANNS_ERR_ARG, "need 1 <= k <= k_max" + at);
+    np_max = std::max(np_max, (int)nprobe[i]);
+    h[(size_t)i] = nprobe[i];
+    h[(size_t)(B + i)] = k[i];
+  }
+  if (B == 0) return ADANNS_OK;
+  cudaStream_t st = S(cuda_stream);
+  Scratch s(st);
+  int32_t *dq;
+  int rc;
+  if ((rc = s.get(&dq, h.size()))) return rc;
+  // pageable source: staged by the copy call itself, so h may go when it returns
+  ADN_CUDA(cudaMemcpyAsync(dq, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  QueryBudgets qb;
+  qb.np = dq;
+  qb.k = dq + B;
+  const int kr = rerank_k > 0 ? rerank_k : k_max;
+  return search_ivfopq_select(idx, queries, B, d_c, np_max, k_max, kr, rerank_k > 0, out_ids,
+                              out_dist, nullptr, st, &qb);
 }
 
 }  // extern "C"

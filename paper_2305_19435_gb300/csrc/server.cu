@@ -16,11 +16,12 @@
 // hands each request its rows.  Callers collect results with
 // adanns_server_poll.
 //
-// Budgets that share a pass (adanns_search_ivf_budgets): with the FP32 tier,
-// any d_s, nprobe (<= 256) and k at one d_c; with a low-precision tier, any
-// nprobe and k at one d_c, d_s and rerank_k.  A batch of one budget runs the
-// plain search call, a mixed one the per-query-budget call; IVF-OPQ requests
-// batch with identical budgets only.
+// Budgets that share a pass (adanns_search_ivf_budgets /
+// adanns_search_ivfopq_budgets): with the FP32 tier, any d_s, nprobe (<= 256)
+// and k at one d_c; with a low-precision tier, any nprobe and k at one d_c,
+// d_s and rerank_k; IVF-OPQ, any nprobe (<= 256) and k at one d_c and
+// rerank_k.  A batch of one budget runs the plain search call, a mixed one the
+// per-query-budget call.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -100,9 +101,9 @@ bool same_budget(const adanns_budget &a, const adanns_budget &b) {
 // whether requests with budgets a and b can run in one pass of the search
 bool shareable(const adanns_budget &a, const adanns_budget &b) {
   if (same_budget(a, b)) return true;
-  if (a.method != ADANNS_METHOD_IVF || b.method != ADANNS_METHOD_IVF || a.d_c != b.d_c ||
-      a.storage != b.storage || a.rerank_k != b.rerank_k)
-    return false;
+  if (a.method != b.method || a.d_c != b.d_c || a.rerank_k != b.rerank_k) return false;
+  if (a.method == ADANNS_METHOD_IVFOPQ) return a.nprobe <= 256 && b.nprobe <= 256;
+  if (a.method != ADANNS_METHOD_IVF || a.storage != b.storage) return false;
   if (a.storage == ADANNS_STORE_F32) return a.nprobe <= 256 && b.nprobe <= 256;
   return a.d_s == b.d_s;
 }
@@ -246,9 +247,13 @@ bool adanns_server::launch_one(Lane &L) {
           np[(size_t)o] = r->b.nprobe;
           kq[(size_t)o] = r->b.k;
         }
-      rc = adanns_search_ivf_budgets(idx, (const float *)L.qd.p, rows, b.d_c, ds.data(), np.data(),
-                                     kq.data(), k, b.storage, b.rerank_k, (int64_t *)L.id.p,
-                                     (float *)L.dd.p, L.st);
+      rc = b.method == ADANNS_METHOD_IVFOPQ
+               ? adanns_search_ivfopq_budgets(idx, (const float *)L.qd.p, rows, b.d_c, np.data(),
+                                              kq.data(), k, b.rerank_k, (int64_t *)L.id.p,
+                                              (float *)L.dd.p, L.st)
+               : adanns_search_ivf_budgets(idx, (const float *)L.qd.p, rows, b.d_c, ds.data(),
+                                           np.data(), kq.data(), k, b.storage, b.rerank_k,
+                                           (int64_t *)L.id.p, (float *)L.dd.p, L.st);
     } else if (b.method == ADANNS_METHOD_IVFOPQ) {
       rc = adanns_search_ivfopq(idx, (const float *)L.qd.p, rows, b.d_c, b.nprobe, k, b.rerank_k,
                                 (int64_t *)L.id.p, (float *)L.dd.p, nullptr, L.st);

@@ -147,3 +147,62 @@ def test_budgets_argument_errors(A, setup):
     # an empty batch is a no-op
     ids, dist = A.search_ivf_budgets(g, q[:0], 32, [], [], [], k_max=5)
     assert ids.shape == (0, 5)
+
+
+@pytest.fixture(scope="module")
+def opq_case(A):
+    """an IVF-OPQ index (d = 96, d_s = 64, M = 16) built by the oracle"""
+    data = synthdata.small(12_000, 240, 96, 48, 821)
+    db = data["db"]
+    o = oracle.build_ivf(db, 32, 24, 6, 12_000, seed=9)
+    opq = oracle.train_opq(db, 64, 16, 3, 3, 5, 4000, seed=13)
+    codes = oracle.pq_encode(db, 64, 16, opq["R"], opq["codebooks"])
+    g = A.index_create(cu(db), cu(o["centroids"]), cu(o["assign"].astype(np.int32)))
+    A.set_opq(g, 64, 16, cu(opq["R"]), cu(opq["codebooks"]), cu(codes))
+    yield data, o, opq, codes, g
+    g.free()
+
+
+def test_budgets_ivfopq_match_oracle_and_single_calls(A, opq_case):
+    data, o, opq, codes, g = opq_case
+    db, q = data["db"], data["queries"]
+    rng = np.random.default_rng(6)
+    B = len(q)
+    npb = rng.choice([1, 3, 8, 24], B).astype(np.int32)
+    kq = rng.choice([1, 10, 30], B).astype(np.int32)
+    gi, gd = A.search_ivfopq_budgets(g, cu(q), 32, npb, kq, k_max=30)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    for (nprobe, k), rows in groups(npb, kq).items():
+        assert np.all(gi[rows, k:] == -1) and np.all(np.isinf(gd[rows, k:]))
+        si, sd = A.search_ivfopq(g, cu(q[rows]), 32, nprobe, k)
+        assert np.array_equal(gi[rows, :k], si.cpu().numpy())
+        assert np.array_equal(gd[rows, :k].view(np.int32), sd.cpu().numpy().view(np.int32))
+        orr = oracle.search_ivfopq(db, o, opq, codes, q[rows], 32, nprobe, k + 20)
+        amb = ambiguous_probe_rows(orr["probe_dist"], nprobe)
+        n, fails = check_topk(gi[rows, :k], gd[rows, :k], orr["ids"], orr["dist"], k,
+                              skip_rows=amb)
+        assert not fails, (nprobe, k, fails[:2])
+
+
+def test_budgets_ivfopq_rerank_equal_single_calls(A, opq_case):
+    data, o, opq, codes, g = opq_case
+    q = data["queries"]
+    rng = np.random.default_rng(7)
+    B = len(q)
+    npb = rng.choice([2, 6, 24], B).astype(np.int32)
+    kq = rng.choice([5, 10], B).astype(np.int32)
+    gi, gd = A.search_ivfopq_budgets(g, cu(q), 32, npb, kq, k_max=10, rerank_k=40)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    for (nprobe, k), rows in groups(npb, kq).items():
+        # the shortlist is the rerank_k best by ADC for every k: the k best of
+        # the re-scored shortlist are a prefix of the k_max best
+        si, sd = A.search_ivfopq(g, cu(q[rows]), 32, nprobe, 10, rerank_k=40)
+        assert np.array_equal(gi[rows, :k], si.cpu().numpy()[:, :k])
+        assert np.array_equal(gd[rows, :k].view(np.int32),
+                              np.ascontiguousarray(sd.cpu().numpy()[:, :k]).view(np.int32))
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivfopq_budgets(g, cu(q[:3]), 32, [1, 300, 2], 5)     # nprobe above 256
+    assert e.value.code == -1
+    with pytest.raises(A.AdannsError) as e:
+        A.search_ivfopq_budgets(g, cu(q[:3]), 32, 2, [5, 5, 5], k_max=5, rerank_k=4)
+    assert e.value.code == -1

@@ -118,24 +118,28 @@ def test_native_server_same_alone_and_in_the_mix(setup):
 
 
 def test_native_server_packs_mixed_budgets(setup):
-    """Requests of one index with different d_s / nprobe / k (FP32 tier) and
-    with different nprobe / k at one d_s (BF16 tier) share batches: a burst
-    queued behind a long request is served in a few launches of the
-    per-query-budget search, and every request equals the same rows searched
-    alone, bit for bit."""
+    """Requests of one index with different d_s / nprobe / k (FP32 tier), with
+    different nprobe / k at one d_s (BF16 tier) and with different nprobe / k
+    (IVF-OPQ) share batches: a burst queued behind a long request is served in
+    a few launches of the per-query-budget searches, and every request equals
+    the same rows searched alone, bit for bit."""
     P, data, idx = setup
     from paper_2305_19435_gb300.serving import Budget, NativeServer
+    if idx[16].opq is None:
+        P.build_opq(idx[16], torch.from_numpy(data["db"]).cuda(), 64, 16, 2, 2, 4, 8_000, 3)
     rng = np.random.default_rng(13)
     q = data["queries"]
     srv = NativeServer(idx, streams=1, max_batch=2048, mem_budget=8 << 30)
     reqs = [(srv.submit(q[:1500], Budget(64, 256, 48, 100), index_key=64),
              Budget(64, 256, 48, 100), 0, 1500)]
-    for i in range(24):
+    for i in range(36):
         n = int(rng.integers(1, 60))
         lo = int(rng.integers(0, len(q) - n))
-        if i % 2:
+        if i % 3 == 1:
             b = Budget(64, int(rng.choice([64, 128, 192, 256])), int(rng.integers(1, 30)),
                        int(rng.choice([1, 10, 100])))
+        elif i % 3 == 2:
+            b = Budget(16, 0, int(rng.integers(1, 30)), int(rng.choice([5, 20])), method=1)
         else:
             b = Budget(16, 128, int(rng.integers(1, 30)), int(rng.choice([5, 10])),
                        P.STORE_BF16, 40)
@@ -144,15 +148,18 @@ def test_native_server_packs_mixed_budgets(setup):
         assert r.wait(120)
     st = srv.stats()
     srv.stop()
-    assert st["requests"] == 25
-    assert st["batches"] <= 6, st      # the burst shares launches across budgets
+    assert st["requests"] == 37
+    assert st["batches"] <= 8, st      # the burst shares launches across budgets
     for r, b, lo, n in reqs:
         assert r.error is None, r.error
         qq = torch.from_numpy(np.ascontiguousarray(q[lo:lo + n])).cuda()
         # BF16: the batch's shortlist is pruned against its largest k, which keeps
         # a superset of what the request's own k keeps (certified pruning)
-        ids, dist = P.search_ivf(idx[b.d_c], qq, b.d_c, b.d_s, b.nprobe, b.k, storage=b.storage,
-                                 rerank_k=b.rerank_k)
+        if b.method == 1:
+            ids, dist = P.search_ivfopq(idx[b.d_c], qq, b.d_c, b.nprobe, b.k)
+        else:
+            ids, dist = P.search_ivf(idx[b.d_c], qq, b.d_c, b.d_s, b.nprobe, b.k,
+                                     storage=b.storage, rerank_k=b.rerank_k)
         assert np.array_equal(r.ids, ids.cpu().numpy())
         assert np.array_equal(r.dist.view(np.int32),
                               np.ascontiguousarray(dist.cpu().numpy()).view(np.int32))
