@@ -959,11 +959,14 @@ def main():
            "gpu_build_s": gpu_build_s, "index_layout_s": layout_s, "pairs_per_step": pairs,
            "unique_lists_per_step": int(len(probed)),
            "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "queries/s",
-                   "h2d_bytes_per_step": int(qh.numel() * 4),
+                   # the prefix of each query row the search reads from host memory
+                   "h2d_bytes_per_step": int(B * max(args.d_c, args.d_s) * 4),
                    "d2h_bytes_per_step": int(ih.numel() * 8 + dh.numel() * 4),
-                   "call": "adanns_search_ivf_host (pinned host buffers; four slices whose "
-                           "copies overlap the neighbouring searches)",
-                   "serial_copies_qps": world * B / (e2e_serial_ms / 1000.0)}}
+                   "call": "adanns_search_ivf_host on page-locked host buffers: the GPU reads "
+                           "each query's first max(d_c, d_s) coordinates and writes the results "
+                           "in place over the host link, no staging copy",
+                   "serial_copies_qps": world * B / (e2e_serial_ms / 1000.0),
+                   "serial_copies_h2d_bytes_per_step": int(qh.numel() * 4)}}
 
     if rank == 0 and not args.no_cpu:
         import oracle

@@ -308,15 +308,20 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
 
 /* AdANNS-IVF search of HOST queries with HOST results: adanns_search_ivf's
  * arguments and rules, but queries (B x d FP32), out_ids (int64 B x k) and
- * out_dist (FP32 B x k) are host memory.  The batch is cut into slices of
- * `slice` rows (0: four slices); slice i+1's queries are copied to the device
- * on an internal stream while slice i is searched on cuda_stream, and slice
- * i's results are copied back while slice i+1 is searched.  Returns once the
- * work is queued; the results are on the host when cuda_stream reaches the
- * point of the call (synchronise it, or an event recorded after the call).
- * Page-locked host buffers let the copies overlap the search; pageable ones
- * work but their copies run synchronously.  The host buffers must stay valid
- * until then.  Results equal adanns_search_ivf on the same rows. */
+ * out_dist (FP32 B x k) are host memory.
+ *   slice 0 and all three buffers page-locked (cudaHostAlloc, or registered):
+ *            the GPU reads the queries in place (only the first
+ *            max(d_c, d_s) coordinates of each row cross the host link) and
+ *            writes the results in place; no copy, the batch stays whole.
+ *   otherwise: the batch is cut into slices of `slice` rows (0: four slices);
+ *            slice i+1's queries are copied to the device on an internal
+ *            stream while slice i is searched on cuda_stream, and slice i's
+ *            results are copied back while slice i+1 is searched (the copies
+ *            of pageable buffers run synchronously).
+ * Returns once the work is queued; the results are on the host when
+ * cuda_stream reaches the point of the call (synchronise it, or an event
+ * recorded after the call).  The host buffers must stay valid until then.
+ * Results equal adanns_search_ivf on the same rows. */
 int adanns_search_ivf_host(const adanns_index *idx, const float *queries, int64_t B, int d_c,
                            int d_s, int nprobe, int k, int storage, int rerank_k,
                            int64_t *out_ids, float *out_dist, int64_t slice, void *cuda_stream);
@@ -475,16 +480,18 @@ int adanns_search_ivfopq_budgets(const adanns_index *idx, const float *queries, 
 
 /* ------------------------------------------------------------------------
  * Autotuning of the exact FP32 list scan.  adanns_autotune_search runs the
- * FP32 search of the given batch with each work-item shape of the list scan
- * (64 queries per (list, query-tile) item with a 4 x 8 register tile per
- * thread; 16 queries with 1 x 8), times each with CUDA events (1 warm-up, 3
- * timed runs; synchronises) and records the faster for the bucket
- * (device, k rounded up to a power of two, d_s, floor(log2(1 + B * nprobe /
- * nlist))).  Later FP32 searches in the same bucket use it.  *chosen gets the
- * queries per thread of the winner (4 or 1), *best_ms its time per call; both
- * may be NULL.  out_ids / out_dist receive the batch's results.
- * adanns_tune_save / adanns_tune_load write / merge the table as text lines
- * "<bucket key> <queries per thread>".
+ * FP32 search of the given batch with each scan variant: the tiled scan with
+ * 64 queries per (list, query-tile) item and a 4 x 8 register tile per thread
+ * (k <= 128), the tiled scan with 16 queries and 1 x 8, and the streaming scan
+ * (nprobe <= 256, ADANNS_OPT_FP32_STREAM on).  It times each with CUDA events
+ * (1 warm-up, 3 timed runs; synchronises) and records the fastest for the
+ * bucket (device, k rounded up to a power of two, d_s,
+ * floor(log2(1 + B * nprobe / nlist))).  Later FP32 searches in the same
+ * bucket use it.  All variants give the same results.  *chosen gets the winner
+ * (4 or 1: the tiled scan's queries per thread; 16: the streaming scan),
+ * *best_ms its time per call; both may be NULL.  out_ids / out_dist receive
+ * the batch's results.  adanns_tune_save / adanns_tune_load write / merge the
+ * table as text lines "<bucket key> <winner>".
  * ---------------------------------------------------------------------- */
 int adanns_autotune_search(const adanns_index *idx, const float *queries, int64_t B, int d_c,
                            int d_s, int nprobe, int k, int64_t *out_ids, float *out_dist,

@@ -443,9 +443,10 @@ def search_ivf(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: 
 def search_ivf_host(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: int, k: int,
                     storage: int = STORE_F32, rerank_k: int = 0, out: tuple | None = None,
                     slice_rows: int = 0):
-    """AdANNS-IVF search of HOST queries (a CPU float32 tensor, page-locked for
-    overlap) into HOST results (ids int64 [B,k], dist f32 [B,k]); the copies of
-    each slice overlap the search of its neighbours.  Returns when the work is
+    """AdANNS-IVF search of HOST queries (a CPU float32 tensor) into HOST results
+    (ids int64 [B,k], dist f32 [B,k]).  Page-locked buffers (and slice_rows 0)
+    are read and written in place by the GPU; others go through copies in
+    slices that overlap the neighbouring searches.  Returns when the work is
     queued: synchronise the current stream before reading the results."""
     if not isinstance(queries, torch.Tensor) or queries.is_cuda or queries.dtype != torch.float32:
         raise TypeError("queries must be a CPU float32 tensor")

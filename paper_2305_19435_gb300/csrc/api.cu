@@ -340,6 +340,7 @@ static void fp32_scan_shape(const adanns_index *idx, int64_t B, int d_s, int npr
                             int *qt, int *nsplit) {
   const double qpl = (double)B * nprobe / idx->nlist;  // queries per probed list
   int t = tuned_scan_tq(k, d_s, qpl);
+  if (t == TUNE_STREAM) t = 0;    // the streaming scan was tuned for this bucket
   if (t == 0 && qpl < 16) t = 1;  // untuned: few queries share a list, small tile
   *tq = t;
   *qt = scan_query_tile(k, t);
@@ -622,7 +623,7 @@ int64_t adanns_search_scratch_bytes(const adanns_index *idx, int64_t B, int d_c,
     const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
     return Bc * per_q + (int64_t)idx->nlist * 64 + (64ll << 20);
   }
-  if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe))
+  if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe, k, d_s))
     return stream_scratch_bytes(idx, B, d_c, d_s, nprobe, k);
   int tq, qt, nsplit;
   fp32_scan_shape(idx, B, d_s, nprobe, k, &tq, &qt, &nsplit);
@@ -714,7 +715,7 @@ int adanns_search_ivf(const adanns_index *idx, const float *queries, int64_t B, 
   if (rerank_k != 0) return fail(ADANNS_ERR_ARG, "rerank_k must be 0 for the FP32 scan");
   if (B == 0) return ADANNS_OK;
   cudaStream_t st = S(cuda_stream);
-  if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe))
+  if (fp32_stream_enabled((double)B * nprobe / idx->nlist, nprobe, k, d_s))
     return search_f32_stream(idx, queries, B, d_c, d_s, nprobe, k, out_ids, out_dist, out_probes,
                              st);
   return search_f32_tiled(idx, queries, B, d_c, d_s, nprobe, k, out_ids, out_dist, out_probes,

@@ -1,14 +1,18 @@
 // Autotuner for the exact FP32 list scan.
 //
-// The tunable is the work-item shape of the list scan: 64 queries per
-// (list, query-tile) item with a 4 x 8 register tile per thread, or 16
-// queries with a 1 x 8 tile.  The first amortises each list block over more
-// queries (batched regime); the second needs a quarter of the top-k buffers,
-// so more CTAs stay resident when few queries share a list (small batches,
-// serving).  adanns_autotune_search times both on the caller's real batch
-// with CUDA events and records the faster under a bucket key
+// The tunable is the scan kernel and its work-item shape: the tiled scan with
+// 64 queries per (list, query-tile) item and a 4 x 8 register tile per
+// thread, the tiled scan with 16 queries and a 1 x 8 tile, or the streaming
+// scan (each member row read once per group of 4 queries, distances selected
+// afterwards).  The first amortises each list block over more queries
+// (batched regime); the second needs a quarter of the top-k buffers, so more
+// CTAs stay resident when few queries share a list; the third suits lists
+// probed by a handful of queries (serving).  Their crossover depends on d_s,
+// k and the batch, so adanns_autotune_search times all three on the caller's
+// real batch with CUDA events and records the fastest under a bucket key
 // (device, k rounded up to a power of two, d_s, log2 of queries per probed
 // list); adanns_search_ivf then uses the recorded choice for matching calls.
+// All three give the same results.
 #include <cmath>
 #include <cstdio>
 #include <fstream>
@@ -75,10 +79,11 @@ int adanns_autotune_search(const adanns_index *idx, const float *queries, int64_
   int best = 0;
   float best_t = 0.f;
   int rc = ADANNS_OK;
-  const int cands[2] = {4, 1};
-  for (int ci = 0; ci < 2 && rc == ADANNS_OK; ++ci) {
+  const int cands[3] = {4, 1, TUNE_STREAM};
+  for (int ci = 0; ci < 3 && rc == ADANNS_OK; ++ci) {
     const int tq = cands[ci];
     if (tq == 4 && k > 128) continue;
+    if (tq == TUNE_STREAM && (nprobe > 256 || !option(ADANNS_OPT_FP32_STREAM))) continue;
     g_force_tq = tq;
     rc = adanns_search_ivf(idx, queries, B, d_c, d_s, nprobe, k, ADANNS_STORE_F32, 0, out_ids,
                            out_dist, nullptr, cuda_stream);
@@ -129,7 +134,7 @@ int adanns_tune_load(const char *path) {
     std::istringstream ss(line);
     std::string key;
     int tq = 0;
-    if (ss >> key >> tq && (tq == 1 || tq == 4)) g_table[key] = tq;
+    if (ss >> key >> tq && (tq == 1 || tq == 4 || tq == TUNE_STREAM)) g_table[key] = tq;
   }
   return ADANNS_OK;
 }

@@ -1,6 +1,15 @@
 // AdANNS-IVF search of host-resident queries with host-resident results
-// (adanns_search_ivf_host): the batch is cut into slices whose host-to-device
-// copy, search and device-to-host copy overlap.  The queries of slice i+1 are
+// (adanns_search_ivf_host).
+//
+// Page-locked host buffers are addressable by the GPU (over NVLink-C2C on a
+// Grace-Blackwell node), so the search runs on them in place: the query-prep
+// kernel reads only the first max(d_c, d_s) coordinates of each query, the
+// only ones the search uses (a quarter of the rows at d_s = 512 of 2048), and
+// the final kernels write the results straight into the host arrays.  There is
+// no staging copy and the batch stays whole.
+//
+// Other host buffers go through copies: the batch is cut into slices whose
+// host-to-device copy, search and device-to-host copy overlap.  The queries of slice i+1 are
 // copied on a second stream while slice i is searched on the caller's stream,
 // and slice i's results are copied back on that second stream while slice i+1
 // is searched.  Two device buffers alternate: slice i+2's copy waits until
@@ -17,6 +26,17 @@
 
 namespace adn {
 namespace {
+
+// the device address of page-locked host memory (null for other memory)
+void *mapped(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || !a.hostPointer) return nullptr;
+  return (char *)a.devicePointer + ((const char *)p - (const char *)a.hostPointer);
+}
 
 // one non-blocking copy stream per device, created on first use and kept
 cudaStream_t copy_stream() {
@@ -72,6 +92,14 @@ extern "C" int adanns_search_ivf_host(const adanns_index *idx, const float *quer
     return rc;
   if (B == 0) return ADANNS_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  {
+    const float *qm = (const float *)mapped(queries);
+    int64_t *im = (int64_t *)mapped(out_ids);
+    float *dm = (float *)mapped(out_dist);
+    if (qm && im && dm && slice == 0)
+      return adanns_search_ivf(idx, qm, B, d_c, d_s, nprobe, k, storage, rerank_k, im, dm, nullptr,
+                               cuda_stream);
+  }
   cudaStream_t cs = copy_stream();
   if (!cs) return fail(ADANNS_ERR_CUDA, "copy stream creation failed");
   // four slices by default: copies overlap the search of the neighbouring

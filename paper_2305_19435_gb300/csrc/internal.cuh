@@ -177,8 +177,10 @@ struct ScanArgs {
 int launch_scan_f32(const ScanArgs &a, cudaStream_t st);
 int scan_query_tile(int k, int tq = 0);  // queries per work item
 
-// Autotuned choices: queries per thread of the list scan for a shape bucket
-// (device, k, d_s, queries per probed list); 0 when not tuned.
+// Autotuned choices for a shape bucket (device, k, d_s, queries per probed
+// list): queries per thread of the tiled FP32 list scan (4 or 1), TUNE_STREAM
+// for the streaming scan, 0 when not tuned.
+constexpr int TUNE_STREAM = 16;
 int tuned_scan_tq(int k, int d_s, double queries_per_list);
 
 // ---------------------------------------------------------------- helpers
@@ -310,7 +312,9 @@ int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int
 // smallest candidate positions.  nprobe <= 256.
 int launch_scan_i32(const int32_t *v, int64_t n, int32_t *out, cudaStream_t st);
 int launch_scan64(const int64_t *in, int64_t n, int64_t *out, int64_t *total, cudaStream_t st);
-bool fp32_stream_enabled(double queries_per_list, int nprobe);
+// the streaming FP32 scan for this batch shape (the autotuned choice when the
+// bucket is tuned, else few queries per probed list)
+bool fp32_stream_enabled(double queries_per_list, int nprobe, int k = 0, int d_s = 0);
 // scratch bytes of search_f32_stream for these arguments (host arithmetic)
 int64_t stream_scratch_bytes(const adanns_index *idx, int64_t B, int d_c, int d_s, int nprobe,
                              int k);

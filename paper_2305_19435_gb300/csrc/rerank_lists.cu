@@ -262,18 +262,18 @@ __global__ void final_topk_kernel(const uint64_t *__restrict__ keys, int kr, int
       v[j] = r < n ? buf[r] : KEY_MAX;
     }
     warp_sort256(v);
+    // back through shared memory (the first min(k, 256) positions, k <= kr), so
+    // that the results leave as whole rows: lanes write consecutive entries
+    __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int r = lane * 8 + j;
-      if (r < k) {
-        out_ids[q * k + r] = v[j] == KEY_MAX ? -1 : (int64_t)(uint32_t)(v[j] & 0xffffffffu);
-        out_dist[q * k + r] = v[j] == KEY_MAX ? __int_as_float(0x7f800000)
-                                              : __uint_as_float((uint32_t)(v[j] >> 32));
-      }
-    }
-    for (int r = 256 + lane; r < k; r += 32) {  // k above the 256 sorted positions: padding
-      out_ids[q * k + r] = -1;
-      out_dist[q * k + r] = __int_as_float(0x7f800000);
+    for (int j = 0; j < 8; ++j)
+      if (lane * 8 + j < k) buf[lane * 8 + j] = v[j];
+    __syncwarp();
+    for (int r = lane; r < k; r += 32) {
+      const uint64_t key = r < 256 ? buf[r] : KEY_MAX;  // k above 256: padding
+      out_ids[q * k + r] = key == KEY_MAX ? -1 : (int64_t)(uint32_t)(key & 0xffffffffu);
+      out_dist[q * k + r] = key == KEY_MAX ? __int_as_float(0x7f800000)
+                                           : __uint_as_float((uint32_t)(key >> 32));
     }
     return;
   }

@@ -205,11 +205,88 @@ __global__ void prep_queries_kernel(const float *__restrict__ q, int64_t B, int 
     for (int j = lane; j < ldb; j += 32) qb[row * ldb + j] = j < db ? src[j] * nb : 0.f;
 }
 
+// The same for rows of at most 2,048 used coordinates, 16-byte aligned: each
+// lane loads its share of the row prefix (up to 16 float4) once, all loads in
+// flight together, and both copies are written from registers.  Query rows in
+// host memory read over the host link are read exactly once this way.
+template <int PV>  // float4 per lane: PV x 4 x 32 coordinates (4: 512, 8: 1,024, 16: 2,048)
+__global__ void __launch_bounds__(256) prep_queries_v4_kernel(
+    const float *__restrict__ q, int64_t B, int ld, int da, int db0, int metric,
+    float *__restrict__ qa, int lda, float *__restrict__ qb, int ldb,
+    const int32_t *__restrict__ dbq, const int32_t *__restrict__ rows) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= B) return;
+  const int db = dbq ? dbq[row] : db0;
+  const float4 *src = (const float4 *)(q + (rows ? (int64_t)rows[row] : row) * ld);
+  const int dm = max(da, db), nv = (dm + 3) >> 2;
+  float4 v[PV];
+#pragma unroll
+  for (int t = 0; t < PV; ++t) {
+    const int c = lane + 32 * t;
+    v[t] = c < nv ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float sa = 0.f, sb = 0.f;
+#pragma unroll
+  for (int t = 0; t < PV; ++t) {
+    const int j = 4 * (lane + 32 * t);
+    const float e[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (j + u < da) sa = fmaf(e[u], e[u], sa);
+      if (j + u < db) sb = fmaf(e[u], e[u], sb);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  float na = 1.f, nb = 1.f;
+  if (metric == ADANNS_METRIC_L2_PREFIXNORM) {
+    na = sa > 0.f ? 1.f / sqrtf(sa) : 0.f;
+    nb = sb > 0.f ? 1.f / sqrtf(sb) : 0.f;
+  }
+  auto put = [&](float *dst, int ldd, int dd, float nrm) {
+    if (!dst) return;
+#pragma unroll
+    for (int t = 0; t < PV; ++t) {
+      const int j = 4 * (lane + 32 * t);
+      if (j >= ldd) break;
+      const float4 x = v[t];
+      const float4 y = make_float4(j < dd ? x.x * nrm : 0.f, j + 1 < dd ? x.y * nrm : 0.f,
+                                   j + 2 < dd ? x.z * nrm : 0.f, j + 3 < dd ? x.w * nrm : 0.f);
+      *(float4 *)(dst + row * ldd + j) = y;
+    }
+    for (int j = 4 * (lane + 32 * PV); j < ldd; j += 128)  // padding past the loaded prefix
+      *(float4 *)(dst + row * ldd + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  put(qa, lda, da, na);
+  put(qb, ldb, db, nb);
+}
+
 int launch_prep_queries(const float *q, int64_t B, int ld, int da, int db, int metric, float *qa,
                         int lda, float *qb, int ldb, cudaStream_t st, const int32_t *dbq,
                         const int32_t *rows) {
   if (B <= 0) return ADANNS_OK;
   const int wpb = 8;
+  // per-query d_s up to db (the batch's largest); lda / ldb multiples of 16
+  if (std::max(da, db) <= 2048 && (ld & 3) == 0 && ((uintptr_t)q & 15) == 0 &&
+      (lda & 3) == 0 && (ldb & 3) == 0) {
+    const int dm = std::max(da, db);
+    const dim3 grid((unsigned)((B + wpb - 1) / wpb));
+    if (dm <= 512)
+      prep_queries_v4_kernel<4><<<grid, wpb * 32, 0, st>>>(q, B, ld, da, db, metric, qa, lda, qb,
+                                                           ldb, dbq, rows);
+    else if (dm <= 1024)
+      prep_queries_v4_kernel<8><<<grid, wpb * 32, 0, st>>>(q, B, ld, da, db, metric, qa, lda, qb,
+                                                           ldb, dbq, rows);
+    else
+      prep_queries_v4_kernel<16><<<grid, wpb * 32, 0, st>>>(q, B, ld, da, db, metric, qa, lda, qb,
+                                                            ldb, dbq, rows);
+    ADN_LAUNCH("prep_queries_v4_kernel");
+    return ADANNS_OK;
+  }
   prep_queries_kernel<<<(unsigned)((B + wpb - 1) / wpb), wpb * 32, 0, st>>>(
       q, B, ld, da, db, metric, qa, lda, qb, ldb, dbq, rows);
   ADN_LAUNCH("prep_queries_kernel");

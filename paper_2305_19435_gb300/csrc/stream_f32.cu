@@ -284,9 +284,11 @@ __global__ void __launch_bounds__(SF_THREADS, 4) dist_f32_kernel(StreamArgs a) {
 
 // Few queries per probed list: prefer the streaming scan (ADANNS_OPT_FP32_STREAM = 0
 // keeps the shared-memory tiled scan everywhere)
-bool fp32_stream_enabled(double queries_per_list, int nprobe) {
-  if (!option(ADANNS_OPT_FP32_STREAM)) return false;
-  return queries_per_list <= 16.0 && nprobe <= 256;
+bool fp32_stream_enabled(double queries_per_list, int nprobe, int k, int d_s) {
+  if (!option(ADANNS_OPT_FP32_STREAM) || nprobe > 256) return false;
+  const int t = k > 0 ? tuned_scan_tq(k, d_s, queries_per_list) : 0;
+  if (t != 0) return t == TUNE_STREAM;
+  return queries_per_list <= 16.0;
 }
 
 int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, int d_c, int d_s,

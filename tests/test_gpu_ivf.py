@@ -119,6 +119,14 @@ def test_full_probe_full_dim_is_exact_search(A, tiny):
     search_parity(A, data["db"], data["queries"][:50], o, 16, 64, 64, 50, PN)
 
 
+@pytest.mark.parametrize("B", [60, 200])
+def test_largest_k(A, tiny, B):
+    """k = 1024, the largest allowed: 60 queries take the streaming scan (15
+    queries per probed list), 200 the tiled scan."""
+    data, o = tiny
+    search_parity(A, data["db"], data["queries"][:B], o, 16, 64, 16, 1024, PN)
+
+
 def test_raw_l2_metric(A):
     data = synthdata.small(4000, 64, 64, 16, 103)
     o = oracle.build_ivf(data["db"], 32, 30, 6, 4000, seed=5, metric=L2)

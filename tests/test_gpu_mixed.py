@@ -87,6 +87,14 @@ def test_mixed_fp8_sweep(A, case, d_s):
     check(A, case, FP8, d_s, 8, 10, 40, 0.97)
 
 
+@pytest.mark.parametrize("storage", [BF16, FP8])
+def test_mixed_largest_k_and_shortlist(A, case, storage):
+    """k = 1024 with the largest shortlist, k' = 2048: the selection takes its
+    exact path over the whole region (k' above its buffer) and the final sort
+    its shared-memory path (more than 256 keys)."""
+    check(A, case, storage, 256, 16, 1024, 2048, 0.99, B=100)
+
+
 @pytest.mark.parametrize("B", [1, 3, 129])
 def test_mixed_ragged_batches(A, case, B):
     check(A, case, BF16, 256, 8, 10, 40, 0.95, B=B)

@@ -77,13 +77,13 @@ def test_autotune_choice_is_correct_and_used(A, case, tmp_path):
     data, o, g = case
     q = cu(data["queries"])
     tq, ms = A.autotune(g, q, 32, 128, 6, 20)
-    assert tq in (1, 4) and ms > 0
+    assert tq in (1, 4, 16) and ms > 0     # tiled 64- or 16-query items, or the streaming scan
     # the tuned search still matches the oracle
     gi, gd = A.search_ivf(g, q, 32, 128, 6, 20)
     oracle_check(data, o, data["queries"], gi.cpu().numpy(), gd.cpu().numpy(), 128, 6, 20)
-    # k above 128 only has the 16-query shape
+    # k above 128: the 16-query tile or the streaming scan
     tq2, _ = A.autotune(g, q[:64], 32, 64, 4, 200)
-    assert tq2 == 1
+    assert tq2 in (1, 16)
     path = os.path.join(tmp_path, "tune.txt")
     A.tune_save(path)
     lines = open(path).read().split("\n")
@@ -91,8 +91,8 @@ def test_autotune_choice_is_correct_and_used(A, case, tmp_path):
     A.tune_load(path)
 
 
-def test_small_tile_variant_matches_oracle(A, case):
-    """The 16-query shape is what autotune runs last; its output is checked."""
+def test_last_autotune_variant_matches_oracle(A, case):
+    """The streaming scan is what autotune runs last; its output is checked."""
     data, o, g = case
     q = cu(data["queries"][:300])
     B = 300
