@@ -381,6 +381,69 @@ __global__ void probe_fill_kernel(const uint64_t *__restrict__ ckeys, int64_t n,
   pair_out[pos] = (int32_t)e;
 }
 
+// Block-aggregated variants for lists of at most PB_MAXL (the common case):
+// a block takes PB_ITEMS consecutive pairs, counts them per list in shared
+// memory and touches each list's global counter once, so the global atomics
+// (which contend when many queries probe one list) drop by about the number of
+// the block's pairs per list.  Fill reserves one range per (block, list) and
+// places the block's pairs in it in item order.
+constexpr int PB_THREADS = 256;
+constexpr int PB_ITEMS = 4096;
+constexpr int PB_MAXL = 8192;
+
+__global__ void __launch_bounds__(PB_THREADS) probe_count_block_kernel(
+    const uint64_t *__restrict__ ckeys, int64_t n, int nprobe, int s0, int ns, int nlist,
+    int32_t *__restrict__ lcnt, int32_t *__restrict__ probes_out) {
+  extern __shared__ int s_hist[];  // [nlist]
+  for (int b = threadIdx.x; b < nlist; b += PB_THREADS) s_hist[b] = 0;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * PB_ITEMS;
+  for (int j = threadIdx.x; j < PB_ITEMS; j += PB_THREADS) {
+    const int64_t i = i0 + j;
+    if (i >= n) break;
+    const int64_t e = slot_pair(i, nprobe, s0, ns);
+    const int l = probe_list(ckeys[e]);
+    if (probes_out) probes_out[e] = l;
+    if (l >= 0) atomicAdd(&s_hist[l], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nlist; b += PB_THREADS)
+    if (s_hist[b]) atomicAdd(&lcnt[b], s_hist[b]);
+}
+
+__global__ void __launch_bounds__(PB_THREADS) probe_fill_block_kernel(
+    const uint64_t *__restrict__ ckeys, int64_t n, int nprobe, int s0, int ns, int nlist,
+    const int32_t *__restrict__ lbeg, int32_t *__restrict__ lfill, int32_t *__restrict__ pair_q,
+    int32_t *__restrict__ pair_out) {
+  extern __shared__ int s_hist[];  // [nlist] counts, then [nlist] positions
+  int *s_pos = s_hist + nlist;
+  for (int b = threadIdx.x; b < nlist; b += PB_THREADS) s_hist[b] = 0;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * PB_ITEMS;
+  for (int j = threadIdx.x; j < PB_ITEMS; j += PB_THREADS) {
+    const int64_t i = i0 + j;
+    if (i >= n) break;
+    const int l = probe_list(ckeys[slot_pair(i, nprobe, s0, ns)]);
+    if (l >= 0) atomicAdd(&s_hist[l], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nlist; b += PB_THREADS) {
+    const int c = s_hist[b];
+    s_pos[b] = c ? lbeg[b] + atomicAdd(&lfill[b], c) : 0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < PB_ITEMS; j += PB_THREADS) {
+    const int64_t i = i0 + j;
+    if (i >= n) break;
+    const int64_t e = slot_pair(i, nprobe, s0, ns);
+    const int l = probe_list(ckeys[e]);
+    if (l < 0) continue;  // a masked slot has no pair
+    const int pos = atomicAdd(&s_pos[l], 1);
+    pair_q[pos] = (int32_t)(e / nprobe);
+    pair_out[pos] = (int32_t)e;
+  }
+}
+
 __global__ void probe_tiles_kernel(const int32_t *__restrict__ lcnt,
                                    const int32_t *__restrict__ lbeg,
                                    const int32_t *__restrict__ tbeg, int nlist, int qt,
@@ -417,12 +480,31 @@ int launch_invert_probe_slots(const uint64_t *ckeys, int64_t B, int nprobe, int 
   ADN_CUDA(cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * nlist, st));
   ADN_CUDA(cudaMemsetAsync(lfill, 0, sizeof(int32_t) * nlist, st));
   const unsigned g = (unsigned)((std::max<int64_t>(n, 1) + 255) / 256);
-  probe_count_kernel<<<g, 256, 0, st>>>(ckeys, n, nprobe, s0, ns, lcnt, probes_out);
-  ADN_LAUNCH("probe_count_kernel");
+  // block-aggregated counting when many pairs share each list
+  const bool blocked = nlist <= PB_MAXL && n >= (int64_t)4 * nlist;
+  const unsigned gb = (unsigned)((std::max<int64_t>(n, 1) + PB_ITEMS - 1) / PB_ITEMS);
+  if (blocked) {
+    const size_t sm = sizeof(int) * nlist;
+    ADN_CUDA(ensure_smem((const void *)probe_count_block_kernel, sm));
+    probe_count_block_kernel<<<gb, PB_THREADS, sm, st>>>(ckeys, n, nprobe, s0, ns, nlist, lcnt,
+                                                         probes_out);
+    ADN_LAUNCH("probe_count_block_kernel");
+  } else {
+    probe_count_kernel<<<g, 256, 0, st>>>(ckeys, n, nprobe, s0, ns, lcnt, probes_out);
+    ADN_LAUNCH("probe_count_kernel");
+  }
   probe_scan_kernel<<<1, 1024, 0, st>>>(lcnt, nlist, qt, lbeg, tbeg, ntiles);
   ADN_LAUNCH("probe_scan_kernel");
-  probe_fill_kernel<<<g, 256, 0, st>>>(ckeys, n, nprobe, s0, ns, lbeg, lfill, pair_q, pair_out);
-  ADN_LAUNCH("probe_fill_kernel");
+  if (blocked) {
+    const size_t sm = sizeof(int) * 2 * nlist;
+    ADN_CUDA(ensure_smem((const void *)probe_fill_block_kernel, sm));
+    probe_fill_block_kernel<<<gb, PB_THREADS, sm, st>>>(ckeys, n, nprobe, s0, ns, nlist, lbeg,
+                                                        lfill, pair_q, pair_out);
+    ADN_LAUNCH("probe_fill_block_kernel");
+  } else {
+    probe_fill_kernel<<<g, 256, 0, st>>>(ckeys, n, nprobe, s0, ns, lbeg, lfill, pair_q, pair_out);
+    ADN_LAUNCH("probe_fill_kernel");
+  }
   probe_tiles_kernel<<<(nlist + 255) / 256, 256, 0, st>>>(lcnt, lbeg, tbeg, nlist, qt, tile_list,
                                                           tile_beg, tile_cnt);
   ADN_LAUNCH("probe_tiles_kernel");
