@@ -340,14 +340,15 @@ __global__ void coarse_tiles_kernel(int64_t B, int ntiles, int64_t npad, int32_t
   }
 }
 
-// One warp per query (k <= 32): the k-th smallest key (two-digit warp radix
-// select over the key row) gives the threshold; the centroids under it (at
-// most CP_CAND, collected in list order) are scored exactly, one per lane,
-// with the same arithmetic as the FP32 kernels, and the k nearest by
+// One warp per query (k <= 32): the top byte of the k-th smallest key (one
+// radix pass over the key row) gives an upper bound of that key, the end of
+// its 256-key bucket, and the threshold above it; the centroids under the
+// threshold (at most CP_CAND, collected in list order) are scored exactly, one
+// per lane, with the same arithmetic as the FP32 kernels, and the k nearest by
 // (distance, list id) are written.  More candidates than CP_CAND (a loose
 // bound) take a second pass that scores them while streaming the row.
 constexpr int CP_WARPS = 8;
-constexpr int CP_CAND = 64;
+constexpr int CP_CAND = 96;
 
 __global__ void __launch_bounds__(CP_WARPS * 32) coarse_pick_kernel(
     const uint16_t *__restrict__ keys, int64_t npad, int nlist, const float *__restrict__ qc,
@@ -363,9 +364,10 @@ __global__ void __launch_bounds__(CP_WARPS * 32) coarse_pick_kernel(
   for (int j = lane; j < d_c; j += 32) s_q[warp][j] = qc[q * ldq + j];
   const uint16_t *kq = keys + q * npad;
   int below, neq;
-  const uint32_t kth = warp_radix_kth<2>(
-      nlist, k, [&](int i) -> uint32_t { return __ldg(kq + i); }, s_hist[warp], s_sh[warp],
-      below, neq);
+  const uint32_t kth = (warp_radix_kth<1>(
+                            nlist, k, [&](int i) -> uint32_t { return __ldg(kq + i) >> 8; },
+                            s_hist[warp], s_sh[warp], below, neq)
+                        << 8) | 0xFFu;
   const double rq = (double)qrho[q];
   const double E = 2.0 * (rmax + rq * cmax + rmax * rq) * (1.0 + 1e-3) + e_rest;
   const uint32_t thr = kth + (uint32_t)ceil(2.0 * 16384.0 * (ldexp(1.0, -15) + E)) + 1u;

@@ -197,7 +197,8 @@ __global__ void prep_lowp_kernel(const float *__restrict__ qs, int ldq, int64_t 
 }
 
 // Qt[t][kb][r][0:128 B] = row pair_q[tile_beg[t] + r] of the low-precision
-// queries at block kb (zero rows past the tile's count); grid (max_tiles, nkb).
+// queries at block kb; rows past the tile's count are left as they are (the
+// scan computes them but never reads their results); grid (max_tiles, nkb).
 __global__ void gather_qtiles_kernel(const unsigned char *__restrict__ qlow, int nkb,
                                      const int32_t *__restrict__ tile_beg,
                                      const int32_t *__restrict__ tile_cnt,
@@ -208,14 +209,10 @@ __global__ void gather_qtiles_kernel(const unsigned char *__restrict__ qlow, int
   if (t >= *ntiles) return;
   const int beg = tile_beg[t], cnt = tile_cnt[t];
   uint4 *dst = (uint4 *)(qt + (((int64_t)t * nkb + kb) * 128) * 128);
-  for (int e = threadIdx.x; e < 128 * 8; e += blockDim.x) {
+  for (int e = threadIdx.x; e < cnt * 8; e += blockDim.x) {
     const int r = e >> 3, c = e & 7;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (r < cnt) {
-      const int q = pair_q[beg + r];
-      v = ((const uint4 *)(qlow + ((int64_t)q * nkb + kb) * 128))[c];
-    }
-    dst[e] = v;
+    const int q = pair_q[beg + r];
+    dst[e] = ((const uint4 *)(qlow + ((int64_t)q * nkb + kb) * 128))[c];
   }
 }
 
@@ -234,15 +231,20 @@ __global__ void cand_count_kernel(const uint64_t *__restrict__ ckeys, int64_t B,
   qtot[q] = t;
 }
 
-// single CTA exclusive scan (int64): rounds of 1024 threads x 8 consecutive
-// values (serial per thread, shuffle scan per warp, one scan of the warp sums)
-__global__ void __launch_bounds__(1024) scan64_kernel(const int64_t *__restrict__ in, int64_t n,
-                                                      int64_t *__restrict__ out,
-                                                      int64_t *__restrict__ total) {
+// Exclusive scan (int64) of rounds of 8,192 values: 1024 threads x 8
+// consecutive values (serial per thread, shuffle scan per warp, one scan of the
+// warp sums).  One CTA walks [first, last) from `carry0` (the sum before
+// first); with part != NULL a CTA per round only writes its round's sum there.
+__device__ __forceinline__ void scan64_rounds(const int64_t *__restrict__ in, int64_t first,
+                                              int64_t last, int64_t carry0,
+                                              int64_t *__restrict__ out,
+                                              int64_t *__restrict__ total,
+                                              int64_t *__restrict__ part) {
   __shared__ int64_t wsum[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int64_t carry = 0;
-  for (int64_t base = 0; base < n; base += 8192) {
+  const int64_t n = last;
+  int64_t carry = carry0;
+  for (int64_t base = first; base < n; base += 8192) {
     const int64_t i0 = base + (int64_t)tid * 8;
     int64_t v[8], sum = 0;
 #pragma unroll
@@ -269,15 +271,40 @@ __global__ void __launch_bounds__(1024) scan64_kernel(const int64_t *__restrict_
     }
     __syncthreads();
     int64_t ex = carry + (warp > 0 ? wsum[warp - 1] : 0) + inc - sum;
+    if (!part) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (i0 + j < n) out[i0 + j] = ex;
-      ex += v[j];
+      for (int j = 0; j < 8; ++j) {
+        if (i0 + j < n) out[i0 + j] = ex;
+        ex += v[j];
+      }
     }
     carry += wsum[31];
     __syncthreads();  // wsum is rewritten by the next round
   }
+  if (tid == 0 && part) *part = carry;
   if (tid == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(1024) scan64_kernel(const int64_t *__restrict__ in, int64_t n,
+                                                      int64_t *__restrict__ out,
+                                                      int64_t *__restrict__ total) {
+  scan64_rounds(in, 0, n, 0, out, total, nullptr);
+}
+
+// multi-CTA form: CTA b sums round b (part[b]), then rescans it from the
+// exclusive prefix of the round sums (partx[b])
+__global__ void __launch_bounds__(1024) scan64_part_kernel(const int64_t *__restrict__ in,
+                                                           int64_t n, int64_t *__restrict__ part) {
+  const int64_t b0 = (int64_t)blockIdx.x * 8192;
+  scan64_rounds(in, b0, min(n, b0 + 8192), 0, nullptr, nullptr, part + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) scan64_apply_kernel(const int64_t *__restrict__ in,
+                                                            int64_t n,
+                                                            const int64_t *__restrict__ partx,
+                                                            int64_t *__restrict__ out) {
+  const int64_t b0 = (int64_t)blockIdx.x * 8192;
+  scan64_rounds(in, b0, min(n, b0 + 8192), partx[blockIdx.x], out, nullptr, nullptr);
 }
 
 __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, int nprobe,
@@ -296,8 +323,23 @@ __global__ void cand_base_kernel(const uint64_t *__restrict__ ckeys, int64_t B, 
 // exclusive scan of n int64 values (one CTA); *total = their sum when non-null
 int launch_scan64(const int64_t *in, int64_t n, int64_t *out, int64_t *total, cudaStream_t st) {
   if (n <= 0) return ADANNS_OK;
-  scan64_kernel<<<1, 1024, 0, st>>>(in, n, out, total);
+  const int64_t nb = (n + 8191) / 8192;
+  if (nb <= 2 || nb > 8192) {  // one or two rounds (or very many): one CTA
+    scan64_kernel<<<1, 1024, 0, st>>>(in, n, out, total);
+    ADN_LAUNCH("scan64_kernel");
+    return ADANNS_OK;
+  }
+  // a CTA per round: round sums, their scan (one CTA, at most one round), the rounds
+  Scratch s(st);
+  int64_t *part, *partx;
+  int rc;
+  if ((rc = s.get(&part, (size_t)nb)) || (rc = s.get(&partx, (size_t)nb))) return rc;
+  scan64_part_kernel<<<(unsigned)nb, 1024, 0, st>>>(in, n, part);
+  ADN_LAUNCH("scan64_part_kernel");
+  scan64_kernel<<<1, 1024, 0, st>>>(part, nb, partx, total);
   ADN_LAUNCH("scan64_kernel");
+  scan64_apply_kernel<<<(unsigned)nb, 1024, 0, st>>>(in, n, partx, out);
+  ADN_LAUNCH("scan64_apply_kernel");
   return ADANNS_OK;
 }
 
@@ -308,8 +350,8 @@ int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int
   const unsigned g = (unsigned)((B + 255) / 256);
   cand_count_kernel<<<g, 256, 0, st>>>(ckeys, B, nprobe, list_off, qtot);
   ADN_LAUNCH("cand_count_kernel");
-  scan64_kernel<<<1, 1024, 0, st>>>(qtot, B, qbase, nullptr);
-  ADN_LAUNCH("scan64_kernel");
+  int rc;
+  if ((rc = launch_scan64(qtot, B, qbase, nullptr, st))) return rc;
   cand_base_kernel<<<g, 256, 0, st>>>(ckeys, B, nprobe, list_off, qbase, pbase);
   ADN_LAUNCH("cand_base_kernel");
   return ADANNS_OK;
