@@ -307,18 +307,27 @@ __global__ void __launch_bounds__(GS_WARPS * 32) graph_search_kernel(GsArgs a) {
     __syncwarp();
     if (lane == 0) done[sel] = 1;
     ++nexp;
-    // neighbours not in the list, scored by one lane each
+    // neighbours not in the list, scored by one lane each.  A neighbour's key
+    // (distance bits, id) is the same every time it is scored and keys are
+    // unique, so it is in the (sorted) list exactly when its key is: a binary
+    // search instead of a scan of the list
     int nn = 0;
     for (int r0 = 0; r0 < a.R; r0 += 32) {
       const int r = r0 + lane;
       const int32_t u = r < a.R ? a.nbr[(int64_t)v * a.R + r] : -1;
       bool in = u < 0;
-      for (int i = 0; i < n && !in; ++i) in = (int32_t)(uint32_t)(lst[i] & 0xffffffffu) == u;
-      const unsigned m = __ballot_sync(0xffffffffu, !in);
+      uint64_t key = KEY_MAX;
       if (!in) {
-        const uint64_t key = gkey(sqdist(qv, a.xg + (int64_t)u * a.ldg, a.d_g), u);
-        mrg[nn + __popc(m & lanemask_lt())] = key;
+        key = gkey(sqdist(qv, a.xg + (int64_t)u * a.ldg, a.d_g), u);
+        int lo = 0, hi = n;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (lst[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        in = lo < n && lst[lo] == key;
       }
+      const unsigned m = __ballot_sync(0xffffffffu, !in);
+      if (!in) mrg[nn + __popc(m & lanemask_lt())] = key;
       nn += __popc(m);
     }
     __syncwarp();
