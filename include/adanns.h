@@ -142,10 +142,12 @@ int adanns_profile_read_host(double *us, int nstage);
  *   values[0]  (query, candidate) pairs re-scored by the exact rerank of the
  *              low-precision tiers, after the certified pruning
  *   values[1]  shortlist slots (queries x rerank_k) of those calls
- *   values[2]  candidates kept by the filtered tensor-core scan
- *              (ADANNS_OPT_SCAN_FILTER) for the shortlist selection
- *   values[3]  queries whose kept candidates exceeded the selection's
- *              on-chip buffer (selected from global memory instead)
+ *   values[2]  candidates kept for the exact shortlist selection: by the
+ *              filtered tensor-core scan (ADANNS_OPT_SCAN_FILTER), else by
+ *              the selection's own threshold pass over the scan's keys
+ *   values[3]  queries whose kept candidates missed the selection's
+ *              on-chip buffer (too many, or fewer than the shortlist), so
+ *              that they were selected from global memory instead
  * Entries beyond the known counters are 0.
  */
 int adanns_profile_read_counters(int64_t *values, int ncounter);

@@ -332,7 +332,8 @@ int search_f32_stream(const adanns_index *idx, const float *queries, int64_t B, 
                       cudaStream_t st, const QueryBudgets *qb = nullptr);
 int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, int kk, int k, const float *qrho, float rmax,
-                    float e_rest, int prune, int64_t B, int64_t *out, cudaStream_t st);
+                    float e_rest, int prune, int64_t B, int64_t *out, unsigned long long *stats,
+                    cudaStream_t st);
 // Filtered tensor-core scan: from the keys of each query's nearest list
 // (cand0 + q * stride0, the list of probe slot 0), tau = their kk-th smallest
 // (0xFFFF with fewer than kk members) and slot 0's records with key <= tau;

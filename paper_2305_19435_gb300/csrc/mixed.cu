@@ -448,7 +448,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   }
   // survivors and slow-path queries of the selection, for adanns_profile_read_counters
   unsigned long long *stats = nullptr;
-  if (filt && profiling() && (rc = s.get(&stats, 2))) return rc;
+  if (profiling() && (rc = s.get(&stats, 2))) return rc;
   const int gi = gran_index(d_s);
   const float *mscale = idx->invn + (int64_t)gi * idx->N;
   const float *cx = idx->lowp_cx[which] + (int64_t)gi * idx->N;
@@ -549,7 +549,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
       rc = filt ? launch_select_surv(rec, rcnt, pbase, ckeys, nprobe, idx->list_off, kk, k, qrho,
                                      rmax, e_rest, prune ? 1 : 0, nb, cids, stats, st)
                 : launch_select16(cand, ckeys, nprobe, qbase, idx->list_off, kk, k, qrho, rmax,
-                                  e_rest, prune ? 1 : 0, nb, cids, st);
+                                  e_rest, prune ? 1 : 0, nb, cids, stats, st);
       if (rc) return rc;
       if (stats) {
         profile_count(PC_SURVIVORS, (const int64_t *)stats, st);

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
     const uint16_t *__restrict__ cand, const uint64_t *__restrict__ ckeys, int nprobe,
     const int64_t *__restrict__ qbase, const int64_t *__restrict__ list_off, int kk, int k,
     const float *__restrict__ qrho, float rmax, float e_rest, int prune, int64_t B,
-    int64_t *__restrict__ out) {
+    int64_t *__restrict__ out, unsigned long long *__restrict__ stats) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   SwState &s = ((SwState *)smem)[warp];
@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
       }
       __syncwarp();
       const int n = s.n;
+      if (stats && lane == 0) atomicAdd(stats, (unsigned long long)n);
       // 3. exact select on the buffer
       if (n >= kk && n <= SW_BUF &&
           warp_select16<false>(n, kk, kq, prune_delta,
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
                                [&](int i) -> int { return (int)s.u.b.idx[i]; }, o, s))
         return;
     }
+    if (stats && lane == 0) atomicAdd(stats + 1, 1ull);  // the buffer path failed
   }
   // exact select over the whole region (index = candidate position)
   warp_select16<true>(ptotal, kk, kq, prune_delta, [&](int i) -> uint32_t { return src[i]; }, id_at,
@@ -496,13 +498,14 @@ int launch_select_surv(const uint32_t *rec, const int *rcnt, const int64_t *pbas
 
 int launch_select16(const uint16_t *cand, const uint64_t *ckeys, int nprobe, const int64_t *qbase,
                     const int64_t *list_off, int kk, int k, const float *qrho, float rmax,
-                    float e_rest, int prune, int64_t B, int64_t *out, cudaStream_t st) {
+                    float e_rest, int prune, int64_t B, int64_t *out, unsigned long long *stats,
+                    cudaStream_t st) {
   if (nprobe > SW_MAXP) return fail(ADANNS_ERR_ARG, "select16: nprobe above 128");
   if (B <= 0) return ADANNS_OK;
   const size_t sm = sizeof(SwState) * SW_WARPS;
   ADN_CUDA(ensure_smem((const void *)select16_kernel, sm));
   select16_kernel<<<(unsigned)((B + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, sm, st>>>(
-      cand, ckeys, nprobe, qbase, list_off, kk, k, qrho, rmax, e_rest, prune, B, out);
+      cand, ckeys, nprobe, qbase, list_off, kk, k, qrho, rmax, e_rest, prune, B, out, stats);
   ADN_LAUNCH("select16_kernel");
   return ADANNS_OK;
 }
