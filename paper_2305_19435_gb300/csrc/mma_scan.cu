@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   // balance) and hands their ids to the MMA issuer and the epilogue in order
   __shared__ uint64_t qfull[TQD], qempty[TQD];
   __shared__ int qids[TQD];
-  __shared__ float s_cb[2][BN], s_ca[2][BN];  // per member of the tile: -2 s_x nu_x, |x|^2
+  __shared__ __align__(16) float s_cb[2][BN];
+  __shared__ __align__(16) float s_ca[2][BN];  // per member of the tile: -2 s_x nu_x, 2^14 |x|^2
   // filtered mode: survivors per tile row of the current and the previous work item
   __shared__ int s_rc[2][BM];
   __shared__ uint32_t tmem_base_s;
@@ -394,6 +395,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       const int cbuf = ib & 1;
       bool stop = false;
+      // the row's terms in key units: key = round(clamp(d) * 2^14) with
+      // d * 2^14 = (2^14 s_q) (-2 s_x nu_x) (q~ . x~) + 2^14 (|q|^2 + |x|^2);
+      // scaling by 2^14 is exact, so the keys are those of the unscaled form
+      const float qsk = 16384.f * qs, q2k = 16384.f * q2;
       // per-member terms of member tile mt (thread et < BN holds member et of
       // the tile), loaded one tile ahead so the loads overlap the drain
       auto load_terms = [&](int mt) -> float2 {
@@ -402,7 +407,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int m = mt * BN + et;
           const float c = m < nl ? __ldg(a.cx + off + m) : 0.f;
           v.x = -2.f * c;
-          v.y = m < nl ? (a.x2 ? __ldg(a.x2 + off + m) : (c > 0.f ? 1.f : 0.f)) : 3.0e38f;
+          // |x|^2 in key units (x 2^14, exact); members past the list end: huge
+          v.y = m < nl ? 16384.f * (a.x2 ? __ldg(a.x2 + off + m) : (c > 0.f ? 1.f : 0.f)) : 3.0e38f;
         }
         return v;
       };
@@ -459,19 +465,24 @@ __global__ void __launch_bounds__(THREADS, 1)
             tmem_ld32(tbase + c_lo + c0, r);
             uint32_t packed[16];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              uint32_t kk[2];
+            for (int j = 0; j < 32; j += 4) {
+              // the four columns' member terms in one 16-byte read each
+              const float4 cb = *(const float4 *)&s_cb[acc][c_lo + c0 + j];
+              const float4 ca = *(const float4 *)&s_ca[acc][c_lo + c0 + j];
+              const float cbv[4] = {cb.x, cb.y, cb.z, cb.w}, cav[4] = {ca.x, ca.y, ca.z, ca.w};
+              uint32_t kk[4];
 #pragma unroll
-              for (int u = 0; u < 2; ++u) {
+              for (int u = 0; u < 4; ++u) {
                 // approximate squared distance as a 16-bit fixed-point key:
-                // round(d * 2^14), d clamped to [0, 4); members past the list
-                // end get the largest key
-                const int c = c_lo + c0 + j + u;
-                float d = fmaf(qs * s_cb[acc][c], __uint_as_float(r[j + u]), q2 + s_ca[acc][c]);
-                d = fminf(fmaxf(d, 0.f), 3.9999f);
-                kk[u] = (uint32_t)__float2uint_rn(d * 16384.f);
+                // round(d * 2^14), d clamped to [0, 3.9999]; members past the
+                // list end get the largest key.  The lower clamp is the
+                // conversion's saturation.
+                const float dk = fminf(fmaf(qsk * cbv[u], __uint_as_float(r[j + u]), q2k + cav[u]),
+                                       3.9999f * 16384.f);
+                asm("cvt.rni.sat.u32.f32 %0, %1;" : "=r"(kk[u]) : "f"(dk));
               }
               packed[j >> 1] = kk[0] | (kk[1] << 16);
+              packed[(j >> 1) + 1] = kk[2] | (kk[3] << 16);
             }
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
