@@ -68,8 +68,7 @@ void free_index(adanns_index *x) {
     cudaFree(x->lowp_sx[i]);
     cudaFree(x->lowp_cx[i]);
   }
-  cudaFree(x->rr_order);
-  for (int i = 0; i < 4; ++i) cudaFree(x->rr_cstart[i]);
+  for (int i = 0; i < 4; ++i) cudaFree(x->rr_cmap[i]);
   delete[] x->h_list_off;
   delete x;
 }
@@ -307,24 +306,20 @@ int build_rerank_order(adanns_index *x, cudaStream_t st) {
     }
   }
   int rc;
-  if ((rc = dmalloc(&x->rr_order, (size_t)nl))) return rc;
-  ADN_CUDA(cudaMemcpyAsync(x->rr_order, ord.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice,
-                           st));
-  std::vector<int32_t> cs[4];
+  std::vector<int4> cm[4];
   for (int ci = 0; ci < 4; ++ci) {
     const int mc = 64 >> ci;
-    cs[ci].resize((size_t)nl + 1);
-    int64_t t = 0;
     for (int i = 0; i < nl; ++i) {
-      cs[ci][(size_t)i] = (int32_t)t;
       const int l = ord[(size_t)i];
-      t += (x->h_list_off[l + 1] - x->h_list_off[l] + mc - 1) / mc;
+      const int64_t n_l = x->h_list_off[l + 1] - x->h_list_off[l];
+      for (int64_t m0 = 0; m0 < n_l; m0 += mc)
+        cm[ci].push_back(make_int4(l, (int)m0, (int)x->h_list_off[l], (int)n_l));
     }
-    cs[ci][(size_t)nl] = (int32_t)t;
-    x->rr_chunks[ci] = (int)t;
-    if ((rc = dmalloc(&x->rr_cstart[ci], (size_t)nl + 1))) return rc;
-    ADN_CUDA(cudaMemcpyAsync(x->rr_cstart[ci], cs[ci].data(), sizeof(int32_t) * (nl + 1),
-                             cudaMemcpyHostToDevice, st));
+    x->rr_chunks[ci] = (int)cm[ci].size();
+    if ((rc = dmalloc(&x->rr_cmap[ci], std::max<size_t>(cm[ci].size(), 1)))) return rc;
+    if (!cm[ci].empty())
+      ADN_CUDA(cudaMemcpyAsync(x->rr_cmap[ci], cm[ci].data(), sizeof(int4) * cm[ci].size(),
+                               cudaMemcpyHostToDevice, st));
   }
   ADN_CUDA(cudaStreamSynchronize(st));  // the host tables go out of scope
   return ADANNS_OK;

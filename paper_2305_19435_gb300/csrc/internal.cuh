@@ -435,12 +435,12 @@ struct adanns_index {
   // per granularity g: max over members of nu_g(x) * |(x - s_x x~)[0:g]|, the
   // largest relative quantisation residual of a normalised prefix (host copy)
   float lowp_rmax[2][adn::NGRAN] = {};
-  // rerank work order: lists in a nearest-neighbour chain of the centroids
-  // (rr_order[i] = list at position i), and for the member-chunk sizes
-  // 64 / 32 / 16 / 8 the first chunk of each ordered list (nlist + 1 entries)
-  // and the chunk total
-  int32_t *rr_order = nullptr;
-  int32_t *rr_cstart[4] = {nullptr, nullptr, nullptr, nullptr};
+  // rerank work order: lists in a nearest-neighbour chain of the centroids,
+  // cut into member chunks of 64 / 32 / 16 / 8; rr_cmap[ci][c] = (list, first
+  // member, list offset, list size) of chunk c in that order, so that a
+  // rerank CTA finds its chunk and list with one load, and rr_chunks[ci] the
+  // chunk count
+  int4 *rr_cmap[4] = {nullptr, nullptr, nullptr, nullptr};
   int rr_chunks[4] = {0, 0, 0, 0};
   int64_t *h_list_off = nullptr;  // host copy of list offsets
   int *dev_err = nullptr;         // sticky device status word (tensor-core pipeline timeouts)

@@ -22,7 +22,7 @@ namespace adn {
 // both the sorted order's layout and each member's first pair (mstart).
 __global__ void pair_pos_kernel(const int64_t *__restrict__ cand, int64_t n,
                                 const int64_t *__restrict__ list_off, int32_t *__restrict__ ppos,
-                                int32_t *__restrict__ pmem, int32_t *__restrict__ cnt) {
+                                int32_t *__restrict__ cnt) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int64_t v = cand[e];
@@ -30,15 +30,15 @@ __global__ void pair_pos_kernel(const int64_t *__restrict__ cand, int64_t n,
     ppos[e] = -1;
     return;
   }
-  const int m = (int)(v & 0xffffffffll);
-  const int32_t p = (int32_t)(list_off[v >> 32] + m);
+  const int32_t p = (int32_t)(list_off[v >> 32] + (v & 0xffffffffll));
   ppos[e] = p;
-  pmem[e] = m;
   atomicAdd(&cnt[p], 1);
 }
 
 // order[cursor[p]++] = e for every kept pair (the order among one member's
-// pairs does not matter: each pair writes its own slot); npairs = the count
+// pairs does not matter: each pair writes its own slot); npairs = the count.
+// A pair's member follows from its place in the order: member p owns
+// [mstart[p], mstart[p + 1]).
 __global__ void pair_scatter_kernel(const int32_t *__restrict__ ppos, int64_t n,
                                     int32_t *__restrict__ cursor, int32_t *__restrict__ order,
                                     const int32_t *__restrict__ mstart, int64_t N,
@@ -81,28 +81,21 @@ static_assert(RC_MAX_MC == 64, "chunk sizes 64, 32, 16, 8 have precomputed chunk
 template <bool FULL, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
     const int32_t *__restrict__ order, const int32_t *__restrict__ mstart,
-    const int32_t *__restrict__ pmem, const int32_t *__restrict__ list_ids, int kr,
+    const int32_t *__restrict__ list_ids, int kr,
     const float *__restrict__ qs, int ldq, int d_s, const float *__restrict__ xpm, int d_pad,
-    const int64_t *__restrict__ list_off, const float *__restrict__ mscale, int mc,
-    const int32_t *__restrict__ lorder, const int32_t *__restrict__ cstart, int nlist,
-    uint64_t *__restrict__ keys, int *__restrict__ err) {
+    const float *__restrict__ mscale, int mc, const int4 *__restrict__ cmap, uint64_t *__restrict__ keys, int *__restrict__ err) {
   extern __shared__ __align__(16) float rows[];  // [mc][d_s + 4]
   constexpr int HW = NT / 16;  // half-warps per CTA
   __shared__ int s_e[NT], s_m[NT], s_q[NT];
   __shared__ float s_nu[RC_MAX_MC];
   __shared__ uint32_t s_id[RC_MAX_MC];
-  // chunk -> (list, first member): the last order position whose first chunk
-  // is <= blockIdx.x (empty lists own no chunk and are passed over)
-  const int item = (int)blockIdx.x;
-  int lo = 0, hi = nlist - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (cstart[mid] <= item) lo = mid; else hi = mid - 1;
-  }
-  const int l = lorder[lo];
-  const int64_t off = list_off[l];
-  const int nl = (int)(list_off[l + 1] - off);
-  const int m_first = (item - cstart[lo]) * mc;
+  __shared__ int s_ms[RC_MAX_MC + 1];  // the chunk members' first pairs, and the end
+  // chunk -> (list, first member, list offset, list size): one load from the
+  // index's chunk map
+  const int4 cl = cmap[blockIdx.x];
+  const int64_t off = cl.z;
+  const int nl = cl.w;
+  const int m_first = cl.y;
   const int rs = d_s + 4, nseg = d_s >> 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = lane >> 4, hl = lane & 15, hw = warp * 2 + half;
@@ -113,9 +106,8 @@ __global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
     const int m0 = m_first;
     if (m0 >= nl) return;
     const int m1 = min(nl, m0 + mc), nm = m1 - m0;
-    const int p0 = mstart[off + m0], p1 = mstart[off + m1];
-    if (p0 >= p1) return;
-    // member rows: block b of the chunk is nm x 16 contiguous floats
+    // member rows (they need the chunk map only, so they load while the pair
+    // range is read): block b of the chunk is nm x 16 contiguous floats
     const int per_b = nm * 4;  // float4 per block
     for (int t = threadIdx.x; t < per_b * ((d_s + 15) >> 4); t += NT) {
       const int b = t / per_b, w = t - b * per_b, mm = w >> 2, part = w & 3;
@@ -125,23 +117,37 @@ __global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
                       stream);
     }
     cp_async_commit();  // the copies land while the first metadata batch loads
+    for (int t = threadIdx.x; t <= nm; t += NT) s_ms[t] = mstart[off + m0 + t];
     for (int t = threadIdx.x; t < nm; t += NT) {
       s_nu[t] = mscale ? mscale[off + m0 + t] : 1.f;
       s_id[t] = (uint32_t)list_ids[off + m0 + t];
+    }
+    __syncthreads();
+    const int p0 = s_ms[0], p1 = s_ms[nm];
+    if (p0 >= p1) {  // no pair re-scores a member of this chunk
+      cp_async_wait<0>();
+      return;
     }
     for (int base = p0; base < p1; base += NT) {
       const int nb = min(NT, p1 - base);
       if (base != p0) __syncthreads();  // previous metadata consumed
       if ((int)threadIdx.x < nb) {
-        const int e = order[base + threadIdx.x];
-        int mm = pmem[e] - m0;
-        if ((unsigned)mm >= (unsigned)nm) {  // inconsistent sort: report, skip the pair
+        const int i = base + threadIdx.x;
+        const int e = order[i];
+        // the pair's member: the last one whose first pair is at or before i
+        int lo = 0, hi = nm - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_ms[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        int mm = lo;
+        if (e < 0 || i >= s_ms[mm + 1]) {  // inconsistent sort: report, skip the pair
           atomicOr(err, ADANNS_DEVERR_RERANK);
           mm = -1;
         }
-        s_e[threadIdx.x] = e;
+        s_e[threadIdx.x] = max(e, 0);
         s_m[threadIdx.x] = mm;
-        s_q[threadIdx.x] = e / kr;
+        s_q[threadIdx.x] = max(e, 0) / kr;
       }
       cp_async_wait<0>();
       __syncthreads();  // rows and metadata visible
@@ -303,21 +309,20 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
   if (B <= 0) return ADANNS_OK;
   const int64_t n = B * kr;
   if (n > INT32_MAX) return fail(ADANNS_ERR_ARG, "rerank slice too large");
-  const int nlist = idx->nlist;
   const int64_t N = idx->N;
   Scratch s(st);
-  int32_t *ppos, *pmem, *order, *mstart, *cursor;
+  int32_t *ppos, *order, *mstart, *cursor;
   int64_t *npairs;
   uint64_t *keys;
   int rc;
-  if ((rc = s.get(&ppos, n)) || (rc = s.get(&pmem, n)) || (rc = s.get(&order, n)) ||
+  if ((rc = s.get(&ppos, n)) || (rc = s.get(&order, n)) ||
       (rc = s.get(&keys, n)) || (rc = s.get(&mstart, (size_t)N + 1)) ||
       (rc = s.get(&cursor, (size_t)N + 1)) || (rc = s.get(&npairs, 1)))
     return rc;
   {
     StageTimer t(ST_RR_SORT, st);
     ADN_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (N + 1), st));
-    pair_pos_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, n, idx->list_off, ppos, pmem,
+    pair_pos_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, n, idx->list_off, ppos,
                                                                   cursor);
     ADN_LAUNCH("pair_pos_kernel");
     if ((rc = launch_scan_i32(cursor, N + 1, mstart, st))) return rc;
@@ -344,10 +349,9 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
       auto go = [&](auto kern, int nt) -> cudaError_t {
         cudaError_t e = ensure_smem((const void *)kern, rs);
         if (e != cudaSuccess) return e;
-        kern<<<(unsigned)chunks, nt, rs, st>>>(order, mstart, pmem, idx->list_ids, kr, qs, ldq,
-                                               d_s, idx->xpm, idx->d_pad, idx->list_off, mscale,
-                                               mc, idx->rr_order, idx->rr_cstart[ci], nlist, keys,
-                                               idx->dev_err);
+        kern<<<(unsigned)chunks, nt, rs, st>>>(order, mstart, idx->list_ids, kr, qs, ldq,
+                                               d_s, idx->xpm, idx->d_pad, mscale, mc,
+                                               idx->rr_cmap[ci], keys, idx->dev_err);
         return cudaSuccess;
       };
       const bool wide = d_s >= 1024;
