@@ -50,6 +50,18 @@ __global__ void pair_scatter_kernel(const int32_t *__restrict__ ppos, int64_t n,
   if (p >= 0) order[atomicAdd(&cursor[p], 1)] = (int32_t)e;
 }
 
+// The pair range [first, end) of every member chunk, for this search's sort:
+// a rerank CTA reads it with its chunk map entry, so that its first batch of
+// pairs is requested together with the member rows
+__global__ void chunk_pairs_kernel(const int4 *__restrict__ cmap, int nchunk, int mc,
+                                   const int32_t *__restrict__ mstart, int2 *__restrict__ cpair) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchunk) return;
+  const int4 cl = cmap[c];  // (list, first member, list offset, list size)
+  const int m1 = min(cl.w, cl.y + mc);
+  cpair[c] = make_int2(mstart[cl.z + cl.y], mstart[cl.z + m1]);
+}
+
 // One CTA per (list, chunk of mc members): the chunk's member rows are read
 // once, coalesced from the prefix-major storage, into shared memory (rows
 // padded by 4 floats against bank conflicts); the chunk's pairs (consecutive
@@ -83,7 +95,8 @@ __global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
     const int32_t *__restrict__ order, const int32_t *__restrict__ mstart,
     const int32_t *__restrict__ list_ids, int kr,
     const float *__restrict__ qs, int ldq, int d_s, const float *__restrict__ xpm, int d_pad,
-    const float *__restrict__ mscale, int mc, const int4 *__restrict__ cmap, uint64_t *__restrict__ keys, int *__restrict__ err) {
+    const float *__restrict__ mscale, int mc, const int4 *__restrict__ cmap,
+    const int2 *__restrict__ cpair, uint64_t *__restrict__ keys, int *__restrict__ err) {
   extern __shared__ __align__(16) float rows[];  // [mc][d_s + 4]
   constexpr int HW = NT / 16;  // half-warps per CTA
   __shared__ int s_e[NT], s_m[NT], s_q[NT];
@@ -93,6 +106,7 @@ __global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
   // chunk -> (list, first member, list offset, list size): one load from the
   // index's chunk map
   const int4 cl = cmap[blockIdx.x];
+  const int2 pr = cpair[blockIdx.x];
   const int64_t off = cl.z;
   const int nl = cl.w;
   const int m_first = cl.y;
@@ -104,10 +118,11 @@ __global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
   const uint64_t keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
   {
     const int m0 = m_first;
-    if (m0 >= nl) return;
+    const int p0 = pr.x, p1 = pr.y;
+    if (m0 >= nl || p0 >= p1) return;  // no pair re-scores a member of this chunk
     const int m1 = min(nl, m0 + mc), nm = m1 - m0;
-    // member rows (they need the chunk map only, so they load while the pair
-    // range is read): block b of the chunk is nm x 16 contiguous floats
+    // member rows, the members' first pairs and the first batch of pairs, all
+    // requested at once: block b of the chunk is nm x 16 contiguous floats
     const int per_b = nm * 4;  // float4 per block
     for (int t = threadIdx.x; t < per_b * ((d_s + 15) >> 4); t += NT) {
       const int b = t / per_b, w = t - b * per_b, mm = w >> 2, part = w & 3;
@@ -117,23 +132,19 @@ __global__ void __launch_bounds__(NT, MINB) rerank_chunks_kernel(
                       stream);
     }
     cp_async_commit();  // the copies land while the first metadata batch loads
+    const int e_first = (int)threadIdx.x < p1 - p0 ? order[p0 + threadIdx.x] : 0;
     for (int t = threadIdx.x; t <= nm; t += NT) s_ms[t] = mstart[off + m0 + t];
     for (int t = threadIdx.x; t < nm; t += NT) {
       s_nu[t] = mscale ? mscale[off + m0 + t] : 1.f;
       s_id[t] = (uint32_t)list_ids[off + m0 + t];
     }
-    __syncthreads();
-    const int p0 = s_ms[0], p1 = s_ms[nm];
-    if (p0 >= p1) {  // no pair re-scores a member of this chunk
-      cp_async_wait<0>();
-      return;
-    }
+    __syncthreads();  // s_ms visible
     for (int base = p0; base < p1; base += NT) {
       const int nb = min(NT, p1 - base);
       if (base != p0) __syncthreads();  // previous metadata consumed
       if ((int)threadIdx.x < nb) {
         const int i = base + threadIdx.x;
-        const int e = order[i];
+        const int e = base == p0 ? e_first : order[i];
         // the pair's member: the last one whose first pair is at or before i
         int lo = 0, hi = nm - 1;
         while (lo < hi) {
@@ -312,6 +323,7 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
   const int64_t N = idx->N;
   Scratch s(st);
   int32_t *ppos, *order, *mstart, *cursor;
+  int2 *cpair;
   int64_t *npairs;
   uint64_t *keys;
   int rc;
@@ -319,6 +331,10 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
       (rc = s.get(&keys, n)) || (rc = s.get(&mstart, (size_t)N + 1)) ||
       (rc = s.get(&cursor, (size_t)N + 1)) || (rc = s.get(&npairs, 1)))
     return rc;
+  const int mc = rerank_chunk_members(d_s);
+  const int ci = rerank_chunk_index(mc);
+  const int chunks = idx->rr_chunks[ci];
+  if ((rc = s.get(&cpair, (size_t)std::max(chunks, 1)))) return rc;
   {
     StageTimer t(ST_RR_SORT, st);
     ADN_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (N + 1), st));
@@ -331,18 +347,20 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
     pair_scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ppos, n, cursor, order, mstart,
                                                                       N, npairs);
     ADN_LAUNCH("pair_scatter_kernel");
+    if (chunks > 0) {
+      chunk_pairs_kernel<<<(unsigned)((chunks + 255) / 256), 256, 0, st>>>(
+          idx->rr_cmap[ci], chunks, mc, mstart, cpair);
+      ADN_LAUNCH("chunk_pairs_kernel");
+    }
   }
   profile_count(PC_RERANK_PAIRS, npairs, st);  // pairs left after pruning
   profile_count_host(PC_SHORTLIST_SLOTS, n);
   {
     StageTimer t(ST_RR_PAIRS, st);
-    const int mc = rerank_chunk_members(d_s);
     const size_t rs = (size_t)mc * (d_s + 4) * 4;
     const bool full = d_s % 512 == 0;
     // slots of padding or pruned candidates keep the empty key
     ADN_CUDA(cudaMemsetAsync(keys, 0xFF, sizeof(uint64_t) * n, st));
-    const int ci = rerank_chunk_index(mc);
-    const int chunks = idx->rr_chunks[ci];
     if (chunks > 0) {
       // long prefixes (eight-member chunks of up to 64 KB of rows): 256 threads
       // share a chunk; shorter ones: 128 threads, eight CTAs per SM
@@ -351,7 +369,7 @@ int launch_rerank_lists(const int64_t *cand, int kr, int64_t B, const float *qs,
         if (e != cudaSuccess) return e;
         kern<<<(unsigned)chunks, nt, rs, st>>>(order, mstart, idx->list_ids, kr, qs, ldq,
                                                d_s, idx->xpm, idx->d_pad, mscale, mc,
-                                               idx->rr_cmap[ci], keys, idx->dev_err);
+                                               idx->rr_cmap[ci], cpair, keys, idx->dev_err);
         return cudaSuccess;
       };
       const bool wide = d_s >= 1024;
