@@ -100,6 +100,17 @@ int64_t adanns_launch_count(void);
  *                             SM (as 4-byte records).  Both give the same
  *                             result.  Lists of more than 65,536 members always
  *                             take the first.
+ *   ADANNS_OPT_NARROW_SCAN    1 (default): when few queries share a probed
+ *                             list (at most 24 on average) and the prefix spans
+ *                             16 or more K-blocks (d_s >= 1024 for BF16, 2048
+ *                             for FP8), the BF16 / FP8 tensor-core scan takes
+ *                             tiles of 128 members x 32 queries instead of 128
+ *                             queries x 256 members; 2: those tiles at any d_s
+ *                             when few queries share a list; 0: the wide tiles
+ *                             always.  The approximate keys agree (the tensor
+ *                             cores may round the dot products of the two tile
+ *                             shapes differently in the last FP32 place); the
+ *                             exact rerank follows.
  *   ADANNS_OPT_TEST_SKIP_LOAD test hook, -1 (default).  n >= 0 makes the next
  *                             tensor-core scan launch (one launch; the option
  *                             then returns to -1) leave out stage load n (in
@@ -120,7 +131,8 @@ int64_t adanns_launch_count(void);
 #define ADANNS_OPT_WAIT_LIMIT_NS 5
 #define ADANNS_OPT_TEST_SKIP_LOAD 6
 #define ADANNS_OPT_SCAN_FILTER 7
-#define ADANNS_OPT_COUNT 8
+#define ADANNS_OPT_NARROW_SCAN 8
+#define ADANNS_OPT_COUNT 9
 int adanns_set_option(int option, int64_t value);
 int adanns_get_option(int option, int64_t *value);
 

@@ -116,6 +116,7 @@ OPT_SCRATCH_BYTES = 4
 OPT_WAIT_LIMIT_NS = 5
 OPT_TEST_SKIP_LOAD = 6
 OPT_SCAN_FILTER = 7
+OPT_NARROW_SCAN = 8
 
 
 def set_option(opt: int, value: int):

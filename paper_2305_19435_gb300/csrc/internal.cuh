@@ -240,6 +240,8 @@ enum Stage {
 };
 
 // Tensor-core list scan of the mixed-precision path (mma_scan.cu).
+// queries per tile of the narrow tensor-core scan (tiles of 128 members x this)
+constexpr int MMA_NARROW_QT = 32;
 struct MmaScanArgs {
   const int32_t *tile_list, *tile_beg, *tile_cnt;
   const int *ntiles_dev;

@@ -197,18 +197,19 @@ __global__ void prep_lowp_kernel(const float *__restrict__ qs, int ldq, int64_t 
 }
 
 // Qt[t][kb][r][0:128 B] = row pair_q[tile_beg[t] + r] of the low-precision
-// queries at block kb; rows past the tile's count are left as they are (the
-// scan computes them but never reads their results); grid (max_tiles, nkb).
+// queries at block kb (rpt rows per tile and block); rows past the tile's
+// count are left as they are (the scan computes them but never reads their
+// results); grid (max_tiles, nkb).
 __global__ void gather_qtiles_kernel(const unsigned char *__restrict__ qlow, int nkb,
                                      const int32_t *__restrict__ tile_beg,
                                      const int32_t *__restrict__ tile_cnt,
                                      const int *__restrict__ ntiles,
-                                     const int32_t *__restrict__ pair_q,
+                                     const int32_t *__restrict__ pair_q, int rpt,
                                      unsigned char *__restrict__ qt) {
   const int t = blockIdx.x, kb = blockIdx.y;
   if (t >= *ntiles) return;
   const int beg = tile_beg[t], cnt = tile_cnt[t];
-  uint4 *dst = (uint4 *)(qt + (((int64_t)t * nkb + kb) * 128) * 128);
+  uint4 *dst = (uint4 *)(qt + (((int64_t)t * nkb + kb) * rpt) * 128);
   for (int e = threadIdx.x; e < cnt * 8; e += blockDim.x) {
     const int r = e >> 3, c = e & 7;
     const int q = pair_q[beg + r];
@@ -360,6 +361,9 @@ int launch_cand_segments(const uint64_t *ckeys, int64_t B, int nprobe, const int
 // ---------------------------------------------------------------- tensor-core scan launcher
 int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
                     const MmaScanArgs &a, cudaStream_t st);
+// tiles of 128 members x MMA_NARROW_QT queries (few queries per probed list)
+int launch_mma_narrow(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
+                      const MmaScanArgs &a, cudaStream_t st);
 
 // Certified shortlist pruning (exact: the result equals the unpruned rerank).
 // A shortlisted candidate c is dropped before the exact rerank when its key
@@ -399,13 +403,19 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   const int nkb = (d_s + epb - 1) / epb;
   const int nlist = idx->nlist;
   const int dcp = pad16(d_c), dsp = pad16(d_s);
-  const int qt = 128;
   const bool filt = scan_filter_enabled(idx);
+  // few queries per probed list: tiles of 128 members x 32 queries, where they
+  // were measured faster than the wide tiles (16 K-blocks or more: d_s >= 1024
+  // for BF16, 2048 for FP8), or at any d_s when the option asks for them
+  const int64_t nopt = option(ADANNS_OPT_NARROW_SCAN);
+  const bool narrow = !filt && nopt != 0 && (double)B * nprobe <= 24.0 * nlist &&
+                      (nopt == 2 || nkb >= 16);
+  const int qt = narrow ? MMA_NARROW_QT : 128;
   const int64_t seg_q = (int64_t)nprobe * (((int64_t)idx->max_list + 7) & ~7ll);
   // filtered: the keys of each query's nearest list, one segment per query
   const int64_t stride0 = ((int64_t)idx->max_list + 7) & ~7ll;
   const int64_t per_q = (filt ? seg_q * 4 + stride0 * 2 : seg_q * 2) +
-                        (int64_t)nprobe * ((int64_t)nkb * 128 * 128 / qt + 36) +
+                        (int64_t)nprobe * ((int64_t)nkb * 128 + 36) +
                         (int64_t)(dcp + dsp) * 4 + (int64_t)nkb * 128 + (int64_t)kk * 8 + 64;
   // slices bounded by a scratch budget (the candidate keys dominate it)
   const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B, scratch_budget() / per_q));
@@ -437,7 +447,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
       (rc = s.get(&counter, 3)) || (rc = s.get(&qtot, Bc)) ||
       (rc = s.get(&qbase, Bc)) || (rc = s.get(&pbase, (size_t)Bc * nprobe)) ||
       (rc = s.get(&cids, (size_t)Bc * kk)) || (rc = s.get(&qlow, (size_t)Bc * nkb * 128)) ||
-      (rc = s.get(&qtile, (size_t)max_tiles * nkb * 128 * 128)))
+      (rc = s.get(&qtile, (size_t)max_tiles * nkb * qt * 128)))
     return rc;
   if (filt) {
     if ((rc = s.get(&rec, (size_t)Bc * seg_q)) || (rc = s.get(&rcnt, (size_t)Bc * nprobe)) ||
@@ -481,8 +491,10 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     m.err = err;
     m.tile_counter = counter + 1 + set;  // zeroed with the cluster-mapping counter
     m.fp8 = fp8;
-    return launch_mma_scan(qtile + t0 * nkb * 128 * 128, ntile_cap * nkb * 128, idx->lowp[which],
-                           xrows, m, st);
+    return narrow ? launch_mma_narrow(qtile + t0 * nkb * qt * 128, ntile_cap * nkb * qt,
+                                      idx->lowp[which], xrows, m, st)
+                  : launch_mma_scan(qtile + t0 * nkb * 128 * 128, ntile_cap * nkb * 128,
+                                    idx->lowp[which], xrows, m, st);
   };
   for (int64_t b0 = 0; b0 < B; b0 += Bc) {
     const int64_t nb = std::min(Bc, B - b0);
@@ -511,7 +523,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
                                           tbeg, pair_q, pair_out, tl, tb, tc, ntiles, probes, st)))
         return rc;
       gather_qtiles_kernel<<<dim3((unsigned)tiles_a, nkb), 256, 0, st>>>(qlow, nkb, tb, tc, ntiles,
-                                                                         pair_q, qtile);
+                                                                         pair_q, qt, qtile);
       ADN_LAUNCH("gather_qtiles_kernel");
       if (tiles_b > 0) {
         const int64_t o1 = nb;  // pairs of set 0
@@ -521,8 +533,8 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
                                             probes, st)))
           return rc;
         gather_qtiles_kernel<<<dim3((unsigned)tiles_b, nkb), 256, 0, st>>>(
-            qlow, nkb, tb + tiles_a, tc + tiles_a, ntiles + 1, pair_q + o1,
-            qtile + tiles_a * nkb * 128 * 128);
+            qlow, nkb, tb + tiles_a, tc + tiles_a, ntiles + 1, pair_q + o1, qt,
+            qtile + tiles_a * nkb * qt * 128);
         ADN_LAUNCH("gather_qtiles_kernel");
       }
       if ((rc = launch_cand_segments(ckeys, nb, nprobe, idx->list_off, qtot, qbase, pbase, st)))

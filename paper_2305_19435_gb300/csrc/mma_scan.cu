@@ -556,6 +556,238 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- narrow tiles
+// The same scan for the memory-bound regime, where only a few queries probe
+// each list.  The roles of the operands are swapped: a tile is 128 members
+// (the MMA's M, TMEM lanes) by up to NQ = 32 queries (N, TMEM columns), so a
+// pipeline stage holds 16 KB of member rows and 4 KB of query rows instead of
+// 16 KB of mostly empty query rows and 32 KB of member rows: the stages in
+// flight are nearly all database bytes, and the MMA no longer computes 128
+// query rows for two or three live ones.  An epilogue thread holds one member
+// and writes its keys for the tile's queries (a warp stores 32 consecutive
+// members' keys per query).  The key arithmetic is the wide kernel's.
+constexpr int NQ = 32;                      // queries per narrow tile (N)
+constexpr int NMT = 128;                    // members per narrow tile (M)
+constexpr int NA_BYTES = NMT * ROWB;        // 16 KB of member rows
+constexpr int NB_BYTES = NQ * ROWB;         // 4 KB of query rows
+constexpr int NACC = 4;                     // accumulators of NQ columns
+constexpr int N_THREADS = 64 + 128;         // producer, MMA, four epilogue warps
+
+template <int NS>
+__global__ void __launch_bounds__(N_THREADS, 1)
+    mma_narrow_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
+                      MmaScanArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *sX = smem;                    // NS x 16 KB member rows
+  unsigned char *sQ = smem + NS * NA_BYTES;    // NS x 4 KB query rows
+  __shared__ uint64_t full[NS], empty[NS], tfull[NACC], tempty[NACC];
+  __shared__ uint64_t qfull[TQD], qempty[TQD];
+  __shared__ int qids[TQD];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < NACC; ++s) {
+      mbar_init(&tfull[s], 1);
+      mbar_init(&tempty[s], 128);
+    }
+    for (int s = 0; s < TQD; ++s) {
+      mbar_init(&qfull[s], 1);
+      mbar_init(&qempty[s], 1 + 128);
+    }
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(NACC * NQ));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+  const int ntiles = *a.ntiles_dev;
+  const uint32_t idesc = a.fp8 ? ((1u << 4) | ((uint32_t)(NQ >> 3) << 17) | ((uint32_t)(NMT >> 4) << 24))
+                               : ((1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NQ >> 3) << 17) |
+                                  ((uint32_t)(NMT >> 4) << 24));
+  auto give_up = [&](int code) {
+    atomicExch(&abort_s, 1);
+    atomicCAS(a.err, 0, code);
+  };
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmX) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmQ) : "memory");
+      int stage = 0, qs = 0;
+      uint32_t phase = 0, qph = 0;
+      for (;;) {
+        int t = atomicAdd(a.tile_counter, 1);
+        if (t >= ntiles || ld_abort(&abort_s)) t = -1;
+        if (!mbar_wait(&qempty[qs], qph ^ 1, a.wait_ns)) {
+          give_up(9);
+          break;
+        }
+        qids[qs] = t;
+        mbar_arrive(&qfull[qs]);
+        if (++qs == TQD) { qs = 0; qph ^= 1; }
+        if (t < 0) break;
+        const int list = a.tile_list[t];
+        const int64_t off = a.list_off[list];
+        const int nl = (int)(a.list_off[list + 1] - off);
+        const int nmt = (nl + NMT - 1) / NMT;
+        bool ok = true;
+        for (int mt = 0; mt < nmt && ok && !ld_abort(&abort_s); ++mt)
+          for (int kb = 0; kb < a.nkb; ++kb) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, a.wait_ns)) {
+              give_up(10);
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&full[stage], NA_BYTES + NB_BYTES);
+            tma_load_2d(sX + stage * NA_BYTES, &tmX, &full[stage], 0,
+                        (int)(off * a.d_blocks) + kb * nl + mt * NMT);
+            tma_load_2d(sQ + stage * NB_BYTES, &tmQ, &full[stage], 0, (t * a.nkb + kb) * NQ);
+            if (++stage == NS) { stage = 0; phase ^= 1; }
+          }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: D[member][query] = X . Q^T
+    if (lane == 0) {
+      int stage = 0, acc = 0, qs = 0;
+      uint32_t phase = 0, aphase = 0, qph = 0;
+      while (!ld_abort(&abort_s)) {
+        if (!mbar_wait(&qfull[qs], qph, a.wait_ns)) {
+          give_up(11);
+          break;
+        }
+        const int t = qids[qs];
+        mbar_arrive(&qempty[qs]);
+        if (++qs == TQD) { qs = 0; qph ^= 1; }
+        if (t < 0) break;
+        const int list = a.tile_list[t];
+        const int nl = (int)(a.list_off[list + 1] - a.list_off[list]);
+        const int nmt = (nl + NMT - 1) / NMT;
+        bool ok = true;
+        for (int mt = 0; mt < nmt && ok && !ld_abort(&abort_s); ++mt) {
+          if (!mbar_wait(&tempty[acc], aphase ^ 1, a.wait_ns)) {
+            give_up(12);
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem + (uint32_t)(acc * NQ);
+          for (int kb = 0; kb < a.nkb; ++kb) {
+            if (!mbar_wait(&full[stage], phase, a.wait_ns)) {
+              give_up(13);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t xbase = smem_u32(sX + stage * NA_BYTES);
+            const uint32_t qbase = smem_u32(sQ + stage * NB_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_issue(d_tmem, sw128_desc(xbase + ks * 32), sw128_desc(qbase + ks * 32), idesc,
+                        (kb > 0 || ks > 0) ? 1u : 0u, a.fp8 != 0);
+            mma_commit(&empty[stage]);
+            if (++stage == NS) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(&tfull[acc]);
+          if (++acc == NACC) { acc = 0; aphase ^= 1; }
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, one member per thread (TMEM lane
+    // quadrant warp % 4), the tile's queries as columns
+    const int quarter = warp & 3;
+    int acc = 0, qs = 0;
+    uint32_t aphase = 0, qph = 0;
+    for (;;) {
+      if (!mbar_wait(&qfull[qs], qph, a.wait_ns)) {
+        give_up(14);
+        break;
+      }
+      const int t = qids[qs];
+      mbar_arrive(&qempty[qs]);
+      if (++qs == TQD) { qs = 0; qph ^= 1; }
+      if (t < 0) break;
+      const int list = a.tile_list[t];
+      const int64_t off = a.list_off[list];
+      const int nl = (int)(a.list_off[list + 1] - off);
+      const int npad = (nl + 7) & ~7;
+      const int nmt = (nl + NMT - 1) / NMT;
+      const int cnt = a.tile_cnt[t];
+      // lane j holds query column j's segment start and terms in key units
+      long long base = 0;
+      float qsk = 0.f, q2k = 0.f;
+      if (lane < cnt) {
+        const int p = a.pair_out[a.tile_beg[t] + lane];
+        const int q = p / a.nprobe;
+        base = a.pbase[p];
+        qsk = 16384.f * a.qsc[q];
+        q2k = 16384.f * a.qn2[q];
+      }
+      bool stop = false;
+      for (int mt = 0; mt < nmt; ++mt) {
+        const int m = mt * NMT + quarter * 32 + lane;
+        float cb = 0.f, cak = 3.0e38f;  // members past the list end: the largest key
+        if (m < nl) {
+          const float c = __ldg(a.cx + off + m);
+          cb = -2.f * c;
+          cak = 16384.f * (a.x2 ? __ldg(a.x2 + off + m) : (c > 0.f ? 1.f : 0.f));
+        }
+        if (!mbar_wait(&tfull[acc], aphase, a.wait_ns)) {
+          give_up(15);
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * NQ), r);
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+          if (j >= cnt) break;  // uniform in the warp
+          const float qj = __shfl_sync(0xffffffffu, qsk, j);
+          const float q2j = __shfl_sync(0xffffffffu, q2k, j);
+          const long long bj = __shfl_sync(0xffffffffu, base, j);
+          if (m < npad) {
+            const float dk =
+                fminf(fmaf(qj * cb, __uint_as_float(r[j]), q2j + cak), 3.9999f * 16384.f);
+            uint32_t key;
+            asm("cvt.rni.sat.u32.f32 %0, %1;" : "=r"(key) : "f"(dk));
+            a.cand[bj + m] = (uint16_t)key;
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[acc]);
+        if (++acc == NACC) { acc = 0; aphase ^= 1; }
+      }
+      if (stop || ld_abort(&abort_s)) break;
+    }
+  }
+  __syncthreads();
+  if (ld_abort(&abort_s)) {
+    // let any copy still in flight land before the shared memory is released
+    for (int i = 0; i < 1 << 14; ++i) __nanosleep(1000);
+  }
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(NACC * NQ));
+  }
+}
+
 // ---------------------------------------------------------------- host side
 namespace {
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -597,6 +829,26 @@ int make_map(CUtensorMap *m, const void *base, int64_t rows, int box_rows, bool 
   return ADANNS_OK;
 }
 }  // namespace
+
+static_assert(NQ == MMA_NARROW_QT, "narrow tile width shared with the host");
+constexpr int NS_NARROW = 8;  // 8 x 20 KB stages
+
+int launch_mma_narrow(const void *qtiles, int64_t qrows, const void *xlow, int64_t xrows,
+                      const MmaScanArgs &a, cudaStream_t st) {
+  if (a.rec || a.tau || a.pstride) return fail(ADANNS_ERR_ARG, "narrow scan: unfiltered keys only");
+  CUtensorMap tX, tQ;
+  int rc;
+  if ((rc = make_map(&tX, xlow, xrows, NMT, a.fp8 != 0))) return rc;
+  if ((rc = make_map(&tQ, qtiles, qrows, NQ, a.fp8 != 0))) return rc;
+  MmaScanArgs b = a;
+  b.wait_ns = (uint64_t)option(ADANNS_OPT_WAIT_LIMIT_NS);
+  b.skip_fill = -1;
+  const size_t smem = (size_t)NS_NARROW * (NA_BYTES + NB_BYTES) + 1024;
+  ADN_CUDA(ensure_smem((const void *)mma_narrow_kernel<NS_NARROW>, smem));
+  mma_narrow_kernel<NS_NARROW><<<num_sms(), N_THREADS, smem, st>>>(tX, tQ, b);
+  ADN_LAUNCH("mma_narrow_kernel");
+  return ADANNS_OK;
+}
 
 // stage count and staging width per element type (see the kernel's notes)
 constexpr int NS_BF16 = 4, SC_BF16 = 16, NS_FP8 = 3, SC_FP8 = 64;

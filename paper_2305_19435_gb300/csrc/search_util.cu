@@ -99,6 +99,7 @@ void init_options() {
     g_opt[ADANNS_OPT_WAIT_LIMIT_NS] = 2000000000ll;
     g_opt[ADANNS_OPT_TEST_SKIP_LOAD] = -1;
     g_opt[ADANNS_OPT_SCAN_FILTER] = 0;
+    g_opt[ADANNS_OPT_NARROW_SCAN] = 1;
   });
 }
 }  // namespace
@@ -123,6 +124,9 @@ int set_option(int o, int64_t v) {
     case ADANNS_OPT_RERANK_PRUNE:
     case ADANNS_OPT_SCAN_FILTER:
       if (v != 0 && v != 1) return fail(ADANNS_ERR_ARG, "this option takes 0 or 1");
+      break;
+    case ADANNS_OPT_NARROW_SCAN:
+      if (v < 0 || v > 2) return fail(ADANNS_ERR_ARG, "this option takes 0, 1 or 2");
       break;
     case ADANNS_OPT_SCRATCH_BYTES:
       if (v < (1ll << 20)) return fail(ADANNS_ERR_ARG, "scratch budget below 1 MiB");

@@ -88,6 +88,9 @@ def test_runtime_options_without_device(lib):
     assert lib.adanns_get_option(4, ctypes.byref(v)) == 0 and v.value == 1 << 30
     assert lib.adanns_set_option(4, 12 << 30) == 0
     assert lib.adanns_get_option(6, ctypes.byref(v)) == 0 and v.value == -1
+    assert lib.adanns_get_option(8, ctypes.byref(v)) == 0 and v.value == 1  # narrow tiles: auto
+    assert lib.adanns_set_option(8, 3) == -1            # 0, 1 or 2
+    assert lib.adanns_set_option(8, 2) == 0 and lib.adanns_set_option(8, 1) == 0
 
 
 def test_index_import_rejects_bad_files_without_device(lib, tmp_path):

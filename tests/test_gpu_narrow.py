@@ -1,0 +1,74 @@
+"""The narrow-tile tensor-core scan: when few queries share a probed list, the
+BF16 / FP8 scan takes tiles of 128 members x 32 queries (members on the MMA's
+M side) instead of 128 queries x 256 members.  It only chooses the shortlist,
+so every returned distance must still be the exact FP32 distance of its id,
+the ids must reach the oracle's recall, and a shortlist that holds every
+candidate must give exactly the wide tiles' result."""
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+from test_gpu_mixed import BF16, FP8, check, cu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    import paper_2305_19435_gb300 as P
+    P.build()
+    assert torch.cuda.is_available()
+    return P
+
+
+@pytest.fixture(scope="module")
+def case(A):
+    # 48 lists of ~830 members: seven 128-member tiles per list
+    data = synthdata.small(40_000, 400, 256, 64, 431)
+    o = oracle.build_ivf(data["db"], 32, 48, 8, 20_000, seed=33)
+    g = A.index_create(cu(data["db"]), cu(o["centroids"]), cu(o["assign"].astype(np.int32)),
+                       storage=1 | BF16 | FP8)
+    yield data, o, g
+    g.free()
+
+
+@pytest.mark.parametrize("storage,d_s,nprobe,k,kr,B", [
+    (BF16, 256, 4, 10, 40, 64), (BF16, 64, 8, 100, 400, 33), (BF16, 128, 2, 10, 40, 1),
+    (BF16, 256, 4, 50, 200, 250), (FP8, 256, 4, 10, 40, 64), (FP8, 128, 8, 10, 40, 100)])
+def test_narrow_scan_matches_oracle(A, case, storage, d_s, nprobe, k, kr, B):
+    """Batches with at most 24 queries per probed list on average (B = 250 with
+    4 probes over 48 lists gives lists with more than 32 queries, so several
+    query tiles per list), narrow tiles forced at these short prefixes: exact
+    distances of the returned ids, recall@10."""
+    data, o, g = case
+    assert B * nprobe <= 24 * 48
+    with A.option(A.OPT_NARROW_SCAN, 2):
+        check(A, case, storage, d_s, nprobe, k, kr, 0.97 if storage == FP8 else 0.99, B=B)
+    g.status()
+
+
+@pytest.mark.parametrize("storage", [BF16, FP8])
+def test_narrow_and_wide_tiles_agree(A, case, storage):
+    """The two tile shapes give the same shortlists up to the rounding of the
+    tensor cores' dot products: the same ids almost everywhere, the same
+    distance bits wherever the ids agree, and, with a shortlist that holds
+    every candidate, exactly the same result."""
+    data, o, g = case
+    q = cu(data["queries"][:96])
+    args = (32, 256, 4, 20)
+    full = (32, 256, 2, 20)  # two lists of ~830 members: a 2,048 shortlist holds them all
+    with A.option(A.OPT_NARROW_SCAN, 0):
+        iw, dw = A.search_ivf(g, q, *args, storage=storage, rerank_k=80)
+        iwf, dwf = A.search_ivf(g, q, *full, storage=storage, rerank_k=2048)
+    with A.option(A.OPT_NARROW_SCAN, 2):
+        i_n, d_n = A.search_ivf(g, q, *args, storage=storage, rerank_k=80)
+        inf, dnf = A.search_ivf(g, q, *full, storage=storage, rerank_k=2048)
+    g.status()
+    iw, dw, i_n, d_n = (x.cpu().numpy() for x in (iw, dw, i_n, d_n))
+    same = iw == i_n
+    assert same.mean() >= 0.99, same.mean()
+    assert np.array_equal(dw.view(np.int32)[same], d_n.view(np.int32)[same])
+    assert torch.equal(iwf, inf)
+    assert torch.equal(dwf.view(torch.int32), dnf.view(torch.int32))
