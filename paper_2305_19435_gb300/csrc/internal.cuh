@@ -262,6 +262,8 @@ struct MmaScanArgs {
   int *err;
   int *tile_counter;         // zeroed before the launch: next tile to take
   int fp8;
+  int few;                   // few queries per probed list (memory-bound): FP8 takes the
+                             // four-stage ring with narrow key staging, as BF16 does
   // filtered mode (rec != NULL, tau != NULL): instead of every key, each
   // (query, probe slot) pair p keeps only its members with key <= tau[query],
   // as 32-bit records (key << 16 | member index, lists below 65,537 members)

@@ -491,6 +491,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
     m.err = err;
     m.tile_counter = counter + 1 + set;  // zeroed with the cluster-mapping counter
     m.fp8 = fp8;
+    m.few = (double)B * nprobe <= 24.0 * nlist ? 1 : 0;
     return narrow ? launch_mma_narrow(qtile + t0 * nkb * qt * 128, ntile_cap * nkb * qt,
                                       idx->lowp[which], xrows, m, st)
                   : launch_mma_scan(qtile + t0 * nkb * 128 * 128, ntile_cap * nkb * 128,

@@ -21,7 +21,8 @@
 // BF16 (a third of a microsecond of MMA work per stage) takes four stages, so
 // that more loads are in flight, and 16-column staging to make room for them;
 // FP8 (twice the MMA rate, the drain is the limit) keeps three stages and
-// 64-column staging, whose stores are fewer and wider.  Every mbarrier wait is
+// 64-column staging, whose stores are fewer and wider, except where few
+// queries share a list (the loads are the limit there: four stages).  Every mbarrier wait is
 // bounded: on timeout the kernel records an error, stops issuing work, lets
 // in-flight copies land and frees TMEM.
 #include <cuda.h>
@@ -865,7 +866,7 @@ int launch_mma_scan(const void *qtiles, int64_t qrows, const void *xlow, int64_t
   MmaScanArgs b = a;
   b.wait_ns = (uint64_t)option(ADANNS_OPT_WAIT_LIMIT_NS);
   b.skip_fill = (int)take_option(ADANNS_OPT_TEST_SKIP_LOAD, -1);
-  if (a.fp8) {
+  if (a.fp8 && !a.few) {
     const size_t smem = mma_scan_smem(NS_FP8, SC_FP8);
     ADN_CUDA(ensure_smem((const void *)mma_scan_kernel<NS_FP8, SC_FP8>, smem));
     mma_scan_kernel<NS_FP8, SC_FP8><<<num_sms(), THREADS, smem, st>>>(tA, tB, b);
