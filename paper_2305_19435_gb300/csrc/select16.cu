@@ -68,17 +68,43 @@ __device__ __forceinline__ uint32_t warp_kth16(int n, int kth, KeyF key, St &s, 
 // smallest key + prune_delta become -1.  Keys equal to the cut are taken by
 // ascending position: a warp sort of up to SW_TIE of them, else a prefix count
 // (keys in position order) or a radix select on their positions.
+// key_limit: every candidate key below it is among the n (the set may lack
+// larger ones).  When the keys up to the pruning bound are all present and
+// number at most kk, they are the winners that survive the pruning (they all
+// rank within the kk smallest), so they are written directly, -1 after them,
+// without the kk-th key or its ties.
 template <bool ORDERED, class KeyF, class IdF, class PosF, class St>
 __device__ __forceinline__ bool warp_select16(int n, int kk, int kq, int prune_delta, KeyF key, IdF id, PosF pos,
-                              int64_t *o, St &s) {
+                              int64_t *o, St &s, uint32_t key_limit = 0) {
   const int lane = threadIdx.x & 31;
-  int below, neq;
-  const uint32_t T = warp_kth16(n, kk, key, s, below, neq);
   uint32_t keep_max = 0xFFFFFFFFu;
   if (kq > 0) {
     int b2, n2;
     keep_max = warp_kth16(n, kq, key, s, b2, n2) + (uint32_t)prune_delta;
+    // (a wide bound, as at FP8 precision, rarely leaves kk or fewer keys under
+    // it: the count is not tried there)
+    if (keep_max < key_limit && prune_delta <= 1024) {
+      int c = 0;
+      for (int i = lane; i < n; i += 32) c += key(i) <= keep_max ? 1 : 0;
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o2);
+      if (c <= kk) {
+        int base = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+          const int i = i0 + lane;
+          const bool in = i < n && key(i) <= keep_max;
+          const unsigned b = __ballot_sync(0xffffffffu, in);
+          if (in) o[base + __popc(b & lanemask_lt())] = id(i);
+          base += __popc(b);
+        }
+        for (int r = c + lane; r < kk; r += 32) o[r] = -1;
+        __syncwarp();
+        return true;
+      }
+    }
   }
+  int below, neq;
+  const uint32_t T = warp_kth16(n, kk, key, s, below, neq);
   if (lane == 0) s.cnt = s.ecnt = 0;
   __syncwarp();
   const int need_eq = kk - below;
@@ -273,14 +299,14 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
           warp_select16<false>(n, kk, kq, prune_delta,
                                [&](int i) -> uint32_t { return s.u.b.key[i]; },
                                [&](int i) -> int64_t { return id_at((int)s.u.b.idx[i]); },
-                               [&](int i) -> int { return (int)s.u.b.idx[i]; }, o, s))
+                               [&](int i) -> int { return (int)s.u.b.idx[i]; }, o, s, T))
         return;
     }
     if (stats && lane == 0) atomicAdd(stats + 1, 1ull);  // the buffer path failed
   }
   // exact select over the whole region (index = candidate position)
   warp_select16<true>(ptotal, kk, kq, prune_delta, [&](int i) -> uint32_t { return src[i]; }, id_at,
-                      [&](int i) -> int { return i; }, o, s);
+                      [&](int i) -> int { return i; }, o, s, 0x10000u);
 }
 
 // ---------------------------------------------------------------- filtered scan
