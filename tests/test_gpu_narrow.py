@@ -72,3 +72,36 @@ def test_narrow_and_wide_tiles_agree(A, case, storage):
     assert np.array_equal(dw.view(np.int32)[same], d_n.view(np.int32)[same])
     assert torch.equal(iwf, inf)
     assert torch.equal(dwf.view(torch.int32), dnf.view(torch.int32))
+
+
+@pytest.fixture(scope="module")
+def long_case(A):
+    # a 1024-coordinate prefix: 16 BF16 K-blocks, where the narrow tiles are
+    # taken by default
+    data = synthdata.small(16_000, 200, 1024, 32, 437)
+    o = oracle.build_ivf(data["db"], 32, 32, 6, 16_000, seed=35)
+    g = A.index_create(cu(data["db"]), cu(o["centroids"]), cu(o["assign"].astype(np.int32)),
+                       storage=1 | BF16 | FP8)
+    yield data, o, g
+    g.free()
+
+
+@pytest.mark.parametrize("storage,opt", [(BF16, 1), (FP8, 2)])
+def test_narrow_scan_long_prefix(A, long_case, storage, opt):
+    """d_s = 1024 with a few queries per list: BF16 on the default rule (16
+    K-blocks), FP8 forced (8 K-blocks); exact distances of the returned ids and
+    recall@10 against the oracle, and the same result as the wide tiles when
+    the shortlist holds every candidate."""
+    data, o, g = long_case
+    with A.option(A.OPT_NARROW_SCAN, opt):
+        check(A, long_case, storage, 1024, 3, 10, 40, 0.97 if storage == FP8 else 0.99, B=120)
+        i_n, d_n = A.search_ivf(g, cu(data["queries"][:40]), 32, 1024, 1, 10, storage=storage,
+                                rerank_k=2048)
+    with A.option(A.OPT_NARROW_SCAN, 0):
+        iw, dw = A.search_ivf(g, cu(data["queries"][:40]), 32, 1024, 1, 10, storage=storage,
+                              rerank_k=2048)
+    g.status()
+    sizes = np.diff(o["list_off"])
+    assert sizes.max() <= 2048  # one list per query: the shortlist holds every candidate
+    assert torch.equal(i_n, iw)
+    assert torch.equal(d_n.view(torch.int32), dw.view(torch.int32))
