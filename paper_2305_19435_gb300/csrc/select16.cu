@@ -257,16 +257,20 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
       //    16-byte group; a lane with survivors claims its slots with one
       //    shared-memory atomic
       const uint32_t TT = T | (T << 16), TL = TT & 0x7FFF7FFFu;
-      for (int c0 = 0; c0 < nvec; c0 += 32 * SW_PF) {
-        uint4 v[SW_PF];
+      // two halves of SW_PF / 2 groups per lane: one half loads while the
+      // other is compared
+      constexpr int HB = SW_PF / 2;
+      auto load = [&](uint4(&v)[HB], int cb) {
 #pragma unroll
-        for (int f = 0; f < SW_PF; ++f) {
-          const int c = c0 + f * 32 + lane;
+        for (int f = 0; f < HB; ++f) {
+          const int c = cb + f * 32 + lane;
           v[f] = c < nvec ? g[c] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
         }
+      };
+      auto compact = [&](const uint4(&v)[HB], int cb) {
 #pragma unroll
-        for (int f = 0; f < SW_PF; ++f) {
-          const int c = c0 + f * 32 + lane;
+        for (int f = 0; f < HB; ++f) {
+          const int c = cb + f * 32 + lane;
           const uint32_t w[4] = {v[f].x, v[f].y, v[f].z, v[f].w};
           uint32_t lt[4];
 #pragma unroll
@@ -290,6 +294,14 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 6) select16_kernel(
             }
           }
         }
+      };
+      uint4 va[HB], vb[HB];
+      load(va, 0);
+      for (int c0 = 0; c0 < nvec; c0 += 2 * 32 * HB) {
+        load(vb, c0 + 32 * HB);
+        compact(va, c0);
+        load(va, c0 + 2 * 32 * HB);
+        compact(vb, c0 + 32 * HB);
       }
       __syncwarp();
       const int n = s.n;
