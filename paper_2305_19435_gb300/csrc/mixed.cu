@@ -199,21 +199,31 @@ __global__ void prep_lowp_kernel(const float *__restrict__ qs, int ldq, int64_t 
 // Qt[t][kb][r][0:128 B] = row pair_q[tile_beg[t] + r] of the low-precision
 // queries at block kb (rpt rows per tile and block); rows past the tile's
 // count are left as they are (the scan computes them but never reads their
-// results); grid (max_tiles, nkb).
+// results).  One CTA per tile: a thread takes a (row, 16-byte chunk) and
+// copies it for every K-block, up to eight loads in flight, with the row's
+// query index read once; grid (max_tiles).
 __global__ void gather_qtiles_kernel(const unsigned char *__restrict__ qlow, int nkb,
                                      const int32_t *__restrict__ tile_beg,
                                      const int32_t *__restrict__ tile_cnt,
                                      const int *__restrict__ ntiles,
                                      const int32_t *__restrict__ pair_q, int rpt,
                                      unsigned char *__restrict__ qt) {
-  const int t = blockIdx.x, kb = blockIdx.y;
+  const int t = blockIdx.x;
   if (t >= *ntiles) return;
   const int beg = tile_beg[t], cnt = tile_cnt[t];
-  uint4 *dst = (uint4 *)(qt + (((int64_t)t * nkb + kb) * rpt) * 128);
   for (int e = threadIdx.x; e < cnt * 8; e += blockDim.x) {
     const int r = e >> 3, c = e & 7;
-    const int q = pair_q[beg + r];
-    dst[e] = ((const uint4 *)(qlow + ((int64_t)q * nkb + kb) * 128))[c];
+    const uint4 *src = (const uint4 *)(qlow + (int64_t)pair_q[beg + r] * nkb * 128) + c;
+    uint4 *dst = (uint4 *)(qt + ((int64_t)t * nkb * rpt + r) * 128) + c;
+    for (int k0 = 0; k0 < nkb; k0 += 8) {
+      uint4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < nkb) v[u] = src[(k0 + u) * 8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < nkb) dst[(int64_t)(k0 + u) * rpt * 8] = v[u];
+    }
   }
 }
 
@@ -523,8 +533,8 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
       if ((rc = launch_invert_probe_slots(ckeys, nb, nprobe, 0, ns0, nlist, qt, lcnt, lbeg, lfill,
                                           tbeg, pair_q, pair_out, tl, tb, tc, ntiles, probes, st)))
         return rc;
-      gather_qtiles_kernel<<<dim3((unsigned)tiles_a, nkb), 256, 0, st>>>(qlow, nkb, tb, tc, ntiles,
-                                                                         pair_q, qt, qtile);
+      gather_qtiles_kernel<<<(unsigned)tiles_a, 256, 0, st>>>(qlow, nkb, tb, tc, ntiles, pair_q, qt,
+                                                              qtile);
       ADN_LAUNCH("gather_qtiles_kernel");
       if (tiles_b > 0) {
         const int64_t o1 = nb;  // pairs of set 0
@@ -533,7 +543,7 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
                                             tl + tiles_a, tb + tiles_a, tc + tiles_a, ntiles + 1,
                                             probes, st)))
           return rc;
-        gather_qtiles_kernel<<<dim3((unsigned)tiles_b, nkb), 256, 0, st>>>(
+        gather_qtiles_kernel<<<(unsigned)tiles_b, 256, 0, st>>>(
             qlow, nkb, tb + tiles_a, tc + tiles_a, ntiles + 1, pair_q + o1, qt,
             qtile + tiles_a * nkb * qt * 128);
         ADN_LAUNCH("gather_qtiles_kernel");
