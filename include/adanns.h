@@ -510,8 +510,33 @@ int adanns_search_ivfopq_budgets(const adanns_index *idx, const float *queries, 
 int adanns_autotune_search(const adanns_index *idx, const float *queries, int64_t B, int d_c,
                            int d_s, int nprobe, int k, int64_t *out_ids, float *out_dist,
                            void *cuda_stream, int *chosen, float *best_ms);
+/*
+ * Autotuning of the BF16 / FP8 tensor-core list scan's tile shape (the scan of
+ * Algorithm 1 on the low-precision tier).  adanns_autotune_search_lowp runs
+ * adanns_search_ivf of the given batch (storage ADANNS_STORE_BF16 or
+ * ADANNS_STORE_FP8E4M3, rerank_k as there) once with tiles of 128 queries x
+ * 256 members and once with tiles of 128 members x 32 queries, times each
+ * with CUDA events (1 warm-up, 3 timed runs; synchronises) and records the
+ * faster for the bucket (device, tier, d_s, floor(log2(1 + B * nprobe /
+ * nlist))).  Later searches of that tier in the same bucket take the recorded
+ * shape in place of the ADANNS_OPT_NARROW_SCAN = 1 rule.  The two shapes'
+ * approximate keys agree up to the tensor cores' rounding of their dot
+ * products; the exact rerank makes the returned distances exact either way.
+ * *chosen gets 128 or 32 (queries per tile), *best_ms the time per call; both
+ * may be NULL.  out_ids / out_dist receive the batch's results (last shape
+ * run).  ADANNS_ERR_ARG for another storage or when ADANNS_OPT_NARROW_SCAN is
+ * not 1 (a forced shape leaves nothing to tune).  The table is shared with
+ * adanns_autotune_search (adanns_tune_save / adanns_tune_load).
+ */
+int adanns_autotune_search_lowp(const adanns_index *idx, const float *queries, int64_t B,
+                                int d_c, int d_s, int nprobe, int k, int storage, int rerank_k,
+                                int64_t *out_ids, float *out_dist, void *cuda_stream,
+                                int *chosen, float *best_ms);
 int adanns_tune_save(const char *path);
 int adanns_tune_load(const char *path);
+/* Forget every recorded choice (FP32 scan and tile shapes): later searches
+ * take the built-in rules again. */
+int adanns_tune_clear(void);
 
 /* ------------------------------------------------------------------------
  * Search plans (batched search replayed from a captured CUDA graph).

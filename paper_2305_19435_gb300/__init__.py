@@ -75,8 +75,11 @@ def lib():
         L.adanns_search_scratch_bytes.argtypes = [P, i64, i32, i32, i32, i32, i32, i32]
         L.adanns_search_scratch_bytes.restype = i64
         L.adanns_autotune_search.argtypes = [P, P, i64, i32, i32, i32, i32, P, P, P, P, P]
+        L.adanns_autotune_search_lowp.argtypes = [P, P, i64, i32, i32, i32, i32, i32, i32, P, P,
+                                                  P, P, P]
         L.adanns_tune_save.argtypes = [ctypes.c_char_p]
         L.adanns_tune_load.argtypes = [ctypes.c_char_p]
+        L.adanns_tune_clear.argtypes = []
         L.adanns_plan_create.argtypes = [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, P, P]
         L.adanns_plan_launch.argtypes = [P, P]
         L.adanns_plan_free.argtypes = [P]
@@ -692,12 +695,32 @@ def autotune(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: in
     return ch.value, ms.value
 
 
+def autotune_lowp(index: Index, queries: torch.Tensor, d_c: int, d_s: int, nprobe: int, k: int,
+                  storage: int, rerank_k: int):
+    """Time the BF16 / FP8 tensor-core scan's two tile shapes on this batch
+    and record the faster for its bucket; returns (queries per tile: 128 or
+    32, ms per call)."""
+    _need(queries, torch.float32, "queries", 2)
+    B = queries.shape[0]
+    ids = torch.empty(B, k, dtype=torch.int64, device=queries.device)
+    dist = torch.empty(B, k, dtype=torch.float32, device=queries.device)
+    ch, ms = ctypes.c_int(), ctypes.c_float()
+    _check(lib().adanns_autotune_search_lowp(index.handle, _ptr(queries), B, d_c, d_s, nprobe, k,
+                                             storage, rerank_k, _ptr(ids), _ptr(dist), _stream(),
+                                             ctypes.byref(ch), ctypes.byref(ms)))
+    return ch.value, ms.value
+
+
 def tune_save(path: str):
     _check(lib().adanns_tune_save(path.encode()))
 
 
 def tune_load(path: str):
     _check(lib().adanns_tune_load(path.encode()))
+
+
+def tune_clear():
+    _check(lib().adanns_tune_clear())
 
 
 # ---------------------------------------------------------------- lists on several GPUs

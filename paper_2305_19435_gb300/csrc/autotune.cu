@@ -13,6 +13,14 @@
 // (device, k rounded up to a power of two, d_s, log2 of queries per probed
 // list); adanns_search_ivf then uses the recorded choice for matching calls.
 // All three give the same results.
+//
+// The BF16 / FP8 tensor-core list scan has two tile shapes: 128 queries x 256
+// members (each member tile feeds a whole query tile: the batched regime) and
+// 128 members x 32 queries (a tile's stage is nearly all database bytes when a
+// list is probed by a handful of queries).  adanns_autotune_search_lowp times
+// both on the caller's batch and records the faster under (device, tier, d_s,
+// log2 of queries per probed list); the low-precision search uses it in place
+// of its built-in rule.
 #include <cmath>
 #include <cstdio>
 #include <fstream>
@@ -29,6 +37,7 @@ namespace {
 std::mutex g_tmu;
 std::map<std::string, int> g_table;
 thread_local int g_force_tq = 0;
+thread_local int g_force_qt = 0;
 
 std::string device_tag() {
   int dev = 0;
@@ -51,7 +60,25 @@ std::string bucket_key(int k, int d_s, double qpl) {
   return device_tag() + "|k" + std::to_string(kp) + "|ds" + std::to_string(d_s) + "|q" +
          std::to_string(qb);
 }
+std::string lowp_key(int which, int d_s, double qpl) {
+  const int qb = (int)std::floor(std::log2(qpl + 1.0));
+  return device_tag() + "|lp" + (which == 1 ? "fp8" : "bf16") + "|ds" + std::to_string(d_s) +
+         "|q" + std::to_string(qb);
+}
+
+bool valid_entry(const std::string &key, int v) {
+  if (key.find("|lp") != std::string::npos) return v == 128 || v == MMA_NARROW_QT;
+  return v == 1 || v == 4 || v == TUNE_STREAM;
+}
 }  // namespace
+
+int tuned_lowp_qt(int which, int d_s, double queries_per_list) {
+  if (g_force_qt) return g_force_qt;
+  std::lock_guard<std::mutex> g(g_tmu);
+  if (g_table.empty()) return 0;
+  auto it = g_table.find(lowp_key(which, d_s, queries_per_list));
+  return it == g_table.end() ? 0 : it->second;
+}
 
 int tuned_scan_tq(int k, int d_s, double queries_per_list) {
   if (g_force_tq) return g_force_tq;
@@ -115,12 +142,70 @@ int adanns_autotune_search(const adanns_index *idx, const float *queries, int64_
   return ADANNS_OK;
 }
 
+int adanns_autotune_search_lowp(const adanns_index *idx, const float *queries, int64_t B,
+                                int d_c, int d_s, int nprobe, int k, int storage, int rerank_k,
+                                int64_t *out_ids, float *out_dist, void *cuda_stream,
+                                int *chosen, float *best_ms) {
+  if (!idx) return fail(ADANNS_ERR_ARG, "index is NULL");
+  if (B < 1) return fail(ADANNS_ERR_ARG, "need a non-empty batch");
+  if (storage != ADANNS_STORE_BF16 && storage != ADANNS_STORE_FP8E4M3)
+    return fail(ADANNS_ERR_ARG, "autotune_search_lowp: storage must be BF16 or FP8-E4M3");
+  if (option(ADANNS_OPT_NARROW_SCAN) != 1)
+    return fail(ADANNS_ERR_ARG,
+                "autotune_search_lowp: ADANNS_OPT_NARROW_SCAN fixes the tile shape (set it to 1)");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0, e1;
+  ADN_CUDA(cudaEventCreate(&e0));
+  ADN_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_t = 0.f;
+  int rc = ADANNS_OK;
+  const int cands[2] = {128, MMA_NARROW_QT};
+  for (int ci = 0; ci < 2 && rc == ADANNS_OK; ++ci) {
+    g_force_qt = cands[ci];
+    rc = adanns_search_ivf(idx, queries, B, d_c, d_s, nprobe, k, storage, rerank_k, out_ids,
+                           out_dist, nullptr, cuda_stream);
+    if (rc) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && rc == ADANNS_OK; ++r)
+      rc = adanns_search_ivf(idx, queries, B, d_c, d_s, nprobe, k, storage, rerank_k, out_ids,
+                             out_dist, nullptr, cuda_stream);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.f;
+    if (best == 0 || ms < best_t) {
+      best = cands[ci];
+      best_t = ms;
+    }
+  }
+  g_force_qt = 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  const int which = storage == ADANNS_STORE_FP8E4M3 ? 1 : 0;
+  {
+    std::lock_guard<std::mutex> g(g_tmu);
+    g_table[lowp_key(which, d_s, (double)B * nprobe / idx->nlist)] = best;
+  }
+  if (chosen) *chosen = best;
+  if (best_ms) *best_ms = best_t;
+  return ADANNS_OK;
+}
+
 int adanns_tune_save(const char *path) {
   if (!path) return fail(ADANNS_ERR_ARG, "path is NULL");
   std::lock_guard<std::mutex> g(g_tmu);
   std::ofstream f(path);
   if (!f) return fail(ADANNS_ERR_ARG, std::string("cannot write ") + path);
   for (auto &kv : g_table) f << kv.first << " " << kv.second << "\n";
+  return ADANNS_OK;
+}
+
+int adanns_tune_clear(void) {
+  std::lock_guard<std::mutex> g(g_tmu);
+  g_table.clear();
   return ADANNS_OK;
 }
 
@@ -134,7 +219,7 @@ int adanns_tune_load(const char *path) {
     std::istringstream ss(line);
     std::string key;
     int tq = 0;
-    if (ss >> key >> tq && (tq == 1 || tq == 4 || tq == TUNE_STREAM)) g_table[key] = tq;
+    if (ss >> key >> tq && valid_entry(key, tq)) g_table[key] = tq;
   }
   return ADANNS_OK;
 }

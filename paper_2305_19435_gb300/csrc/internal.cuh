@@ -182,6 +182,11 @@ int scan_query_tile(int k, int tq = 0);  // queries per work item
 // for the streaming scan, 0 when not tuned.
 constexpr int TUNE_STREAM = 16;
 int tuned_scan_tq(int k, int d_s, double queries_per_list);
+// Autotuned tile of the BF16 / FP8 tensor-core list scan for a bucket (device,
+// tier, d_s, queries per probed list): 128 (128 queries x 256 members) or
+// MMA_NARROW_QT (128 members x 32 queries); 0 when not tuned.  which: 0 BF16,
+// 1 FP8.
+int tuned_lowp_qt(int which, int d_s, double queries_per_list);
 
 // ---------------------------------------------------------------- helpers
 // dims_b_q (or null): a per-query dims_b for the second copy; rows (or null):

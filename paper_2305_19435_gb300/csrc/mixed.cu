@@ -417,9 +417,14 @@ int search_mixed(const adanns_index *idx, const float *queries, int64_t B, int d
   // few queries per probed list: tiles of 128 members x 32 queries, where they
   // were measured faster than the wide tiles (16 K-blocks or more: d_s >= 1024
   // for BF16, 2048 for FP8), or at any d_s when the option asks for them
+  // (with the default rule, a tile shape the autotuner recorded for this
+  // bucket takes precedence)
   const int64_t nopt = option(ADANNS_OPT_NARROW_SCAN);
-  const bool narrow = !filt && nopt != 0 && (double)B * nprobe <= 24.0 * nlist &&
-                      (nopt == 2 || nkb >= 16);
+  const double qpl = (double)B * nprobe / nlist;
+  const int tuned = nopt == 1 ? tuned_lowp_qt(which, d_s, qpl) : 0;
+  const bool narrow = !filt && nopt != 0 &&
+                      (tuned ? tuned == MMA_NARROW_QT
+                             : qpl <= 24.0 && (nopt == 2 || nkb >= 16));
   const int qt = narrow ? MMA_NARROW_QT : 128;
   const int64_t seg_q = (int64_t)nprobe * (((int64_t)idx->max_list + 7) & ~7ll);
   // filtered: the keys of each query's nearest list, one segment per query

@@ -105,3 +105,48 @@ def test_narrow_scan_long_prefix(A, long_case, storage, opt):
     assert sizes.max() <= 2048  # one list per query: the shortlist holds every candidate
     assert torch.equal(i_n, iw)
     assert torch.equal(d_n.view(torch.int32), dw.view(torch.int32))
+
+
+def test_autotune_lowp_records_and_uses_a_tile_shape(A, case, tmp_path):
+    """The tile-shape autotuner times both shapes on a batch with few queries
+    per probed list and records the faster; later searches in that bucket take
+    it, giving exactly the result of the same shape forced by the option, with
+    exact distances and the oracle's recall; the table survives a save, clear
+    and load."""
+    data, o, g = case
+    q = cu(data["queries"][:64])
+    args = (32, 256, 4, 10)
+    chosen = {}
+    try:
+        for storage in (BF16, FP8):
+            qt, ms = A.autotune_lowp(g, q, *args, storage, 40)
+            assert qt in (128, 32) and ms > 0
+            chosen[storage] = qt
+            ti, td = A.search_ivf(g, q, *args, storage=storage, rerank_k=40)
+            with A.option(A.OPT_NARROW_SCAN, 2 if qt == 32 else 0):
+                fi, fd = A.search_ivf(g, q, *args, storage=storage, rerank_k=40)
+            assert torch.equal(ti, fi)
+            assert torch.equal(td.view(torch.int32), fd.view(torch.int32))
+        # the tuned search against the oracle (exact distances, recall@10)
+        check(A, case, BF16, 256, 4, 10, 40, 0.99, B=64)
+        path = str(tmp_path / "tune.txt")
+        A.tune_save(path)
+        lines = open(path).read().split("\n")
+        assert any("|lpbf16|ds256|" in l and l.endswith(f" {chosen[BF16]}") for l in lines)
+        assert any("|lpfp8|ds256|" in l and l.endswith(f" {chosen[FP8]}") for l in lines)
+        A.tune_clear()
+        A.tune_load(path)
+        ti2, td2 = A.search_ivf(g, q, *args, storage=BF16, rerank_k=40)
+        with A.option(A.OPT_NARROW_SCAN, 2 if chosen[BF16] == 32 else 0):
+            fi2, fd2 = A.search_ivf(g, q, *args, storage=BF16, rerank_k=40)
+        assert torch.equal(ti2, fi2)
+        assert torch.equal(td2.view(torch.int32), fd2.view(torch.int32))
+        # nothing to tune: a forced shape, or the exact FP32 scan
+        with A.option(A.OPT_NARROW_SCAN, 0):
+            with pytest.raises(A.AdannsError):
+                A.autotune_lowp(g, q, *args, BF16, 40)
+        with pytest.raises(A.AdannsError):
+            A.autotune_lowp(g, q, *args, 1, 0)
+    finally:
+        A.tune_clear()  # later modules take the built-in rule
+    g.status()
