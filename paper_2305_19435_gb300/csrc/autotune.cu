@@ -1,4 +1,5 @@
-// Autotuner for the exact FP32 list scan.
+// Autotuners for the exact FP32 list scan and for the tile shape of the
+// BF16 / FP8 tensor-core list scan.
 //
 // The tunable is the scan kernel and its work-item shape: the tiled scan with
 // 64 queries per (list, query-tile) item and a 4 x 8 register tile per
